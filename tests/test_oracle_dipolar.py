@@ -1,0 +1,91 @@
+"""Pins of the oracle's dipolar mean field Phi = IDFT[Ut(k) DFT(n)], Ut = 3 kz^2/k^2 - 1.
+
+The paper evaluates the dipolar term "by a Fourier transformation to momentum space using a
+convolution theorem" (Solution method).  Pins:
+  * brute force: the FFT path equals the direct circular convolution with the real-space
+    kernel K = naive IDFT(Ut) on tiny grids;
+  * closed form: for a cylindrical Gaussian density the dipolar energy 1/2 int Phi n equals
+    -f(kappa) / (2 (2 pi)^{3/2} s_rho^2 s_z) (Lahaye et al., Rep. Prog. Phys. 72, 126401
+    (2009)), f the anisotropy function, for both kappa < 1 and kappa > 1; the closed form is
+    itself checked against an independent 1D quadrature of the k-space integral;
+  * symmetry: an isotropic density has zero dipolar energy on a cubic grid.
+"""
+import numpy as np
+import pytest
+from scipy import integrate
+
+
+def f_kappa(k):
+    """Anisotropy function of the dipolar energy of a Gaussian (kappa = s_rho / s_z)."""
+    if k < 1:
+        s = np.sqrt(1 - k * k)
+        return (1 + 2 * k * k) / (1 - k * k) - 3 * k * k * np.arctanh(s) / (1 - k * k) ** 1.5
+    s = np.sqrt(k * k - 1)
+    return (1 + 2 * k * k) / (1 - k * k) + 3 * k * k * np.arctan(s) / (k * k - 1) ** 1.5
+
+
+def e_dd_closed(sr, sz):
+    return -f_kappa(sr / sz) / (2 * (2 * np.pi) ** 1.5 * sr * sr * sz)
+
+
+def e_dd_quadrature(sr, sz):
+    # 1/2 int d^3k/(2 pi)^3 (3 cos^2 a - 1) exp(-(k_rho^2 sr^2 + k_z^2 sz^2)/2); the radial
+    # integral int k^2 exp(-k^2 A/2) dk = sqrt(pi/2) A^{-3/2} is done analytically.
+    def integrand(u):
+        a = (1 - u * u) * sr * sr + u * u * sz * sz
+        return (3 * u * u - 1) * np.sqrt(np.pi / 2) * a ** -1.5
+    val, _ = integrate.quad(integrand, -1, 1, epsabs=1e-15, epsrel=1e-13, limit=200)
+    return 0.5 * 2 * np.pi * val / (2 * np.pi) ** 3
+
+
+def gaussian_density(n, h, sr, sz):
+    x = (np.arange(n) - n // 2) * h
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    return np.exp(-(X ** 2 + Y ** 2) / sr ** 2 - Z ** 2 / sz ** 2) / (np.pi ** 1.5 * sr * sr * sz)
+
+
+def grid_e_dd(orc, n, h, sr, sz):
+    p = orc.make_params((n, n, n), h, 1e-3, orc.REAL_TIME, (1, 1, 1), 0.0, 1.0)
+    dens = gaussian_density(n, h, sr, sz)
+    return 0.5 * np.sum(orc.dipolar_phi(p, dens) * dens) * h ** 3
+
+
+def test_kernel_geometry(orc):
+    # Ut = 3 cos^2(angle to z) - 1: +2 along the dipole axis, -1 perpendicular, 0 at k = 0.
+    p = orc.make_params((8, 8, 8), 0.5, 1e-3, orc.REAL_TIME, (1, 1, 1), 0, 1)
+    ut = orc.dipolar_kernel(p)
+    assert ut[0, 0, 0] == 0.0
+    assert ut[0, 0, 1] == pytest.approx(2.0) and ut[0, 0, 7] == pytest.approx(2.0)
+    assert ut[1, 0, 0] == pytest.approx(-1.0) and ut[0, 3, 0] == pytest.approx(-1.0)
+    assert ut[1, 0, 1] == pytest.approx(0.5)          # 45 degrees: 3/2 - 1
+    assert np.array_equal(ut, ut[::-1, ::-1, ::-1][np.ix_(*[np.roll(np.arange(8), 1)] * 3)])  # even
+
+
+@pytest.mark.parametrize("shape,h", [((4, 6, 8), (0.5, 0.4, 0.3)), ((6, 6, 6), 0.7), ((8, 4, 6), (0.3, 0.9, 0.5))])
+def test_fft_convolution_equals_direct(orc, shape, h):
+    from paper_1610_05329_gb300 import inputs
+    p = orc.make_params(shape, h, 1e-3, orc.REAL_TIME, (1, 1, 1), 0, 1)
+    n = inputs.uniform(5, int(np.prod(shape)), 0, 1).reshape(shape)
+    phi_fft = orc.dipolar_phi(p, n)
+    phi_dir = orc.dipolar_phi_direct(p, n)
+    assert np.max(np.abs(phi_fft - phi_dir)) < 1e-13 * np.max(np.abs(phi_dir))
+
+
+@pytest.mark.parametrize("sr,sz", [(1.0, 0.6), (0.6, 1.0)])
+def test_closed_form_is_the_integral(sr, sz):
+    assert e_dd_closed(sr, sz) == pytest.approx(e_dd_quadrature(sr, sz), rel=1e-12)
+
+
+@pytest.mark.parametrize("sr,sz", [(1.0, 0.6), (0.6, 1.0)])
+def test_gaussian_dipolar_energy(orc, sr, sz):
+    exact = e_dd_closed(sr, sz)
+    small = grid_e_dd(orc, 32, 0.3, sr, sz)   # box 9.6
+    large = grid_e_dd(orc, 64, 0.3, sr, sz)   # box 19.2
+    assert np.sign(large) == np.sign(exact)
+    assert abs(large - exact) < 2e-4 * abs(exact)
+    # the remaining error is the periodic-box error: it shrinks as the box grows
+    assert abs(large - exact) < 0.2 * abs(small - exact)
+
+
+def test_isotropic_density_has_no_dipolar_energy(orc):
+    assert abs(grid_e_dd(orc, 32, 0.3, 1.0, 1.0)) < 1e-15
