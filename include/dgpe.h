@@ -1,0 +1,170 @@
+/*
+ * dgpe.h -- C ABI of the GB300 split-step Crank-Nicolson (SSCN) solver for the 3D dipolar
+ * Gross-Pitaevskii equation (arXiv 1610.05329).
+ *
+ * What is computed.  The paper ("Nature of problem", "Solution method") solves the
+ * time-dependent GP equation with contact and dipolar interaction in an anisotropic
+ * harmonic trap by the split-step Crank-Nicolson method, in imaginary or real time, with
+ * the dipolar term evaluated in momentum space through the convolution theorem, using a
+ * real-to-complex FFT ("Summary of revisions", DBEC-GP-OMP).  The dimensionless model this
+ * library implements is
+ *
+ *     i dpsi/dt = [ -1/2 lap + V + g |psi|^2 + gdd Phi ] psi
+ *     V   = 1/2 (nu_x^2 x^2 + nu_y^2 y^2 + nu_z^2 z^2)
+ *     Phi = IDFT[ Ut(k) DFT(|psi|^2) ],  Ut(k) = 3 k_z^2 / |k|^2 - 1,  Ut(0) = 0
+ *
+ * on the grid x_i = (i - nx/2) hx (same for y, z), k_m = 2 pi m / (n h) with m signed.
+ * One step is: the potential step psi <- psi exp(-i theta) (real time) or
+ * psi exp(-theta) (imaginary time), theta = dt (V + g n + gdd Phi) with n, Phi of the
+ * incoming state; then Crank-Nicolson along x, y and z,
+ * (1 - c D) psi' = (1 + c D) psi on the interior of every grid line, D the 3-point second
+ * difference, psi = 0 on the two wall points of the line, c = i dt/(4 h^2) (real time) or
+ * dt/(4 h^2) (imaginary time); in imaginary time psi is then divided by sqrt(norm),
+ * norm = hx hy hz sum |psi|^2.  The three sweeps commute exactly, so the library may run
+ * them in any order.
+ *
+ * Memory and layout.  psi is row-major [nx][ny][nz] (z fastest), complex values stored as
+ * interleaved (re, im) pairs: complex128 for DGPE_FP64, complex64 for DGPE_MIXED.  All
+ * device memory the solver uses is one workspace of dgpe_workspace_bytes() bytes: the
+ * caller may own it (params.workspace, e.g. a PyTorch tensor) or let dgpe_create allocate
+ * it with cudaMalloc.  Nothing is kept in global variables: one context per stream.
+ *
+ * Errors.  Every int-returning call returns DGPE_OK (0) or a negative DGPE_E* code; no C++
+ * exception crosses the ABI.  Parameter checks happen before any CUDA call, so invalid
+ * parameters are reported even on a machine without a GPU.  Errors found on the device
+ * (non-finite norm) are latched and returned by the next synchronising call
+ * (dgpe_sync, dgpe_observables, dgpe_get_psi with a host buffer, dgpe_get_phi).
+ * A context is not thread-safe: calls on one context must not overlap.
+ */
+#ifndef DGPE_H
+#define DGPE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGPE_OK 0
+#define DGPE_EINVAL (-1)        /* bad argument or parameter */
+#define DGPE_ENOMEM (-2)        /* device allocation failed or workspace too small */
+#define DGPE_ECUDA (-3)         /* a CUDA runtime call or kernel launch failed */
+#define DGPE_ENONFINITE (-4)    /* NaN/Inf met in a reduction (norm) on the device */
+#define DGPE_ETIMEOUT (-5)      /* a bounded device-side wait gave up */
+#define DGPE_EUNSUPPORTED (-6)  /* valid request this build does not support */
+
+#define DGPE_REAL_TIME 0
+#define DGPE_IMAG_TIME 1
+
+#define DGPE_FP64 0   /* complex128 psi; FFT, phase and CN in FP64 */
+#define DGPE_MIXED 1  /* complex64 psi; FFT, phase and CN in FP32; norm/mu/E sums in FP64 */
+
+#define DGPE_HOST 0
+#define DGPE_DEVICE 1
+
+/* Sub-steps for dgpe_substep (each is one factor of the split step). */
+#define DGPE_SUB_POTENTIAL 0  /* psi <- psi e^{-i theta} (or e^{-theta}); no renormalisation */
+#define DGPE_SUB_CN_X 1
+#define DGPE_SUB_CN_Y 2
+#define DGPE_SUB_CN_Z 3
+
+/*
+ * Problem description.  Sizes: 4 <= n <= 512, n even, n = 2^a 3^b (every size of the
+ * paper's "FFT-friendly" advice that this build's radix-2/3/4/8 transforms cover).
+ * h, dt > 0 and finite; nu, g, gdd finite.  workspace: NULL, or device memory of at least
+ * workspace_bytes >= dgpe_workspace_bytes(p) bytes, 256-byte aligned, owned by the caller
+ * and kept alive until dgpe_destroy.
+ */
+typedef struct dgpe_params {
+  int nx, ny, nz;
+  double hx, hy, hz;
+  double dt;
+  int mode;           /* DGPE_REAL_TIME or DGPE_IMAG_TIME */
+  int precision;      /* DGPE_FP64 or DGPE_MIXED */
+  double nu[3];       /* trap frequencies nu_x, nu_y, nu_z */
+  double g;           /* contact strength */
+  double gdd;         /* dipolar strength (dipoles along z) */
+  void *workspace;    /* optional caller-owned device memory */
+  size_t workspace_bytes;
+} dgpe_params;
+
+/* Observables of the current state, FP64.  norm = h^3 sum |psi|^2; the energy terms use the
+ * 3-point Laplacian with zero values outside the grid:
+ *   e_kin = h^3 sum 1/2 Re conj(psi) (-lap psi),  e_trap = h^3 sum V n,
+ *   e_contact = h^3 sum g n^2 / 2,  e_dipolar = h^3 sum gdd Phi n / 2,
+ *   energy = e_kin + e_trap + e_contact + e_dipolar,
+ *   mu = (e_kin + e_trap + 2 e_contact + 2 e_dipolar) / norm,
+ *   rms[d] = sqrt(sum d^2 n / sum n). */
+typedef struct dgpe_obs {
+  double norm, mu, energy;
+  double rms[3];
+  double e_kin, e_trap, e_contact, e_dipolar;
+} dgpe_obs;
+
+/* Per-kernel timing record (see dgpe_set_timing). bytes_per_launch is the kernel's
+ * algorithmic HBM traffic (each input read once, each output written once). */
+typedef struct dgpe_kernel_time {
+  char name[32];
+  double total_ms;
+  long long launches;
+  double bytes_per_launch;
+} dgpe_kernel_time;
+
+typedef struct dgpe_ctx dgpe_ctx;
+
+/* Device bytes the solver needs for p (only shape and precision matter).  Host-only. */
+int dgpe_workspace_bytes(const dgpe_params *p, size_t *bytes);
+
+/* Validate p, set up the workspace, FFT twiddles and Crank-Nicolson factor tables on
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream).  psi starts at zero.
+ * On success *out owns the context; free it with dgpe_destroy. */
+int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out);
+
+/* Change dt, mode, nu, g, gdd or h (e.g. the quench or a trap schedule) without
+ * reallocation; shape and precision must stay the same (else DGPE_EINVAL).
+ * Stream-ordered: takes effect for work enqueued afterwards. */
+int dgpe_set_params(dgpe_ctx *ctx, const dgpe_params *p);
+
+/* Copy psi in from `where` = DGPE_HOST or DGPE_DEVICE memory (layout above; complex128 for
+ * FP64, complex64 for MIXED).  The caller keeps ownership.  Clears latched device errors. */
+int dgpe_set_psi(dgpe_ctx *ctx, const void *psi, int where);
+
+/* Copy the current psi (pending renormalisation applied) to `out` in host or device memory.
+ * Host copies synchronise the stream; device copies are stream-ordered. */
+int dgpe_get_psi(dgpe_ctx *ctx, void *out, int where);
+
+/* Enqueue nsteps >= 0 SSCN steps (stream-ordered, asynchronous; replayed from a CUDA graph).
+ * In imaginary time every step renormalises (applied lazily: see dgpe_get_psi). */
+int dgpe_step(dgpe_ctx *ctx, int nsteps);
+
+/* Apply one factor of the split step (DGPE_SUB_*) once, without renormalisation. */
+int dgpe_substep(dgpe_ctx *ctx, int which);
+
+/* Compute the observables of the current state; synchronises the stream.
+ * Returns DGPE_ENONFINITE if a sum is NaN/Inf. */
+int dgpe_observables(dgpe_ctx *ctx, dgpe_obs *o);
+
+/* Dipolar potential Phi = IDFT[Ut DFT(|psi|^2)] of the current state (real, [nx][ny][nz],
+ * double for FP64, float for MIXED) into host or device memory.  Synchronises for host. */
+int dgpe_get_phi(dgpe_ctx *ctx, void *out, int where);
+
+/* Wait for the stream; returns a latched device error if any. */
+int dgpe_sync(dgpe_ctx *ctx);
+
+/* Per-kernel timing: when enabled, dgpe_step launches kernels one by one with CUDA events
+ * around each (instead of replaying the graph) and accumulates their durations. */
+int dgpe_set_timing(dgpe_ctx *ctx, int enable);
+/* Synchronises, then copies up to `max` records into out and sets *n to the number of
+ * kernels timed. */
+int dgpe_kernel_times(dgpe_ctx *ctx, dgpe_kernel_time *out, int max, int *n);
+
+/* Static text for an error code. */
+const char *dgpe_strerror(int code);
+
+/* Free the context and whatever it allocated (not a caller-owned workspace). NULL is ok. */
+void dgpe_destroy(dgpe_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGPE_H */

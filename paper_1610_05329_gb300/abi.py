@@ -1,0 +1,303 @@
+"""Thin ctypes binding of the C ABI in include/dgpe.h (libdgpe.so).
+
+Functions keep the C names and only marshal arguments; every step of the solver runs in
+the CUDA kernels of the library.  ``Condensate`` is a convenience wrapper whose device
+memory (the solver workspace) is a PyTorch tensor and whose stream is PyTorch's current
+stream.  There is no fallback: if libdgpe.so is missing or fails to load, ``load()`` raises.
+"""
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdgpe.so")
+
+DGPE_OK = 0
+DGPE_EINVAL = -1
+DGPE_ENOMEM = -2
+DGPE_ECUDA = -3
+DGPE_ENONFINITE = -4
+DGPE_ETIMEOUT = -5
+DGPE_EUNSUPPORTED = -6
+
+DGPE_REAL_TIME = 0
+DGPE_IMAG_TIME = 1
+DGPE_FP64 = 0
+DGPE_MIXED = 1
+DGPE_HOST = 0
+DGPE_DEVICE = 1
+DGPE_SUB_POTENTIAL = 0
+DGPE_SUB_CN_X = 1
+DGPE_SUB_CN_Y = 2
+DGPE_SUB_CN_Z = 3
+
+
+class dgpe_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
+                ("dt", ctypes.c_double), ("mode", ctypes.c_int), ("precision", ctypes.c_int),
+                ("nu", ctypes.c_double * 3), ("g", ctypes.c_double), ("gdd", ctypes.c_double),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class dgpe_obs(ctypes.Structure):
+    _fields_ = [("norm", ctypes.c_double), ("mu", ctypes.c_double), ("energy", ctypes.c_double),
+                ("rms", ctypes.c_double * 3), ("e_kin", ctypes.c_double), ("e_trap", ctypes.c_double),
+                ("e_contact", ctypes.c_double), ("e_dipolar", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"norm": self.norm, "mu": self.mu, "energy": self.energy, "rms": tuple(self.rms),
+                "e_kin": self.e_kin, "e_trap": self.e_trap, "e_contact": self.e_contact,
+                "e_dipolar": self.e_dipolar}
+
+
+class dgpe_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("total_ms", ctypes.c_double),
+                ("launches", ctypes.c_longlong), ("bytes_per_launch", ctypes.c_double)]
+
+
+class DgpeError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (%d)" % (what, strerror(code), code))
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every function declared in include/dgpe.h
+_P = ctypes.POINTER
+_SIGNATURES = [
+    ("dgpe_workspace_bytes", ctypes.c_int, [_P(dgpe_params), _P(ctypes.c_size_t)]),
+    ("dgpe_create", ctypes.c_int, [_P(dgpe_params), ctypes.c_void_p, _P(ctypes.c_void_p)]),
+    ("dgpe_set_params", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_params)]),
+    ("dgpe_set_psi", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("dgpe_get_psi", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("dgpe_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("dgpe_substep", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("dgpe_observables", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_obs)]),
+    ("dgpe_get_phi", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("dgpe_sync", ctypes.c_int, [ctypes.c_void_p]),
+    ("dgpe_set_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("dgpe_kernel_times", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_kernel_time), ctypes.c_int, _P(ctypes.c_int)]),
+    ("dgpe_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("dgpe_destroy", None, [ctypes.c_void_p]),
+]
+
+
+def load():
+    """Load libdgpe.so (built by paper_1610_05329_gb300.build); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libdgpe.so not found at %s: run paper_1610_05329_gb300/build.py "
+                                   "(there is no CPU fallback)" % LIB_PATH)
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, res, args in _SIGNATURES:
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+        return _lib
+
+
+def _check(rc, what):
+    if rc != DGPE_OK:
+        raise DgpeError(rc, what)
+
+
+def strerror(code):
+    return load().dgpe_strerror(int(code)).decode()
+
+
+def make_params(shape, h, dt, mode=DGPE_IMAG_TIME, precision=DGPE_FP64, nu=(1.0, 1.0, 1.0), g=0.0, gdd=0.0,
+                workspace=None, workspace_bytes=0):
+    hx, hy, hz = (h, h, h) if np.isscalar(h) else tuple(h)
+    p = dgpe_params()
+    p.nx, p.ny, p.nz = (int(v) for v in shape)
+    p.hx, p.hy, p.hz = float(hx), float(hy), float(hz)
+    p.dt = float(dt)
+    p.mode = int(mode)
+    p.precision = int(precision)
+    p.nu[0], p.nu[1], p.nu[2] = (float(v) for v in nu)
+    p.g, p.gdd = float(g), float(gdd)
+    p.workspace = workspace
+    p.workspace_bytes = int(workspace_bytes)
+    return p
+
+
+# ---- raw C calls (return codes checked, names as in dgpe.h) ----------------------------
+def dgpe_workspace_bytes(params):
+    n = ctypes.c_size_t(0)
+    _check(load().dgpe_workspace_bytes(ctypes.byref(params), ctypes.byref(n)), "dgpe_workspace_bytes")
+    return n.value
+
+
+def dgpe_create(params, stream=0):
+    ctx = ctypes.c_void_p()
+    _check(load().dgpe_create(ctypes.byref(params), ctypes.c_void_p(stream or None), ctypes.byref(ctx)),
+           "dgpe_create")
+    return ctx
+
+
+def dgpe_set_params(ctx, params):
+    _check(load().dgpe_set_params(ctx, ctypes.byref(params)), "dgpe_set_params")
+
+
+def dgpe_set_psi(ctx, ptr, where):
+    _check(load().dgpe_set_psi(ctx, ctypes.c_void_p(ptr), int(where)), "dgpe_set_psi")
+
+
+def dgpe_get_psi(ctx, ptr, where):
+    _check(load().dgpe_get_psi(ctx, ctypes.c_void_p(ptr), int(where)), "dgpe_get_psi")
+
+
+def dgpe_step(ctx, nsteps):
+    _check(load().dgpe_step(ctx, int(nsteps)), "dgpe_step")
+
+
+def dgpe_substep(ctx, which):
+    _check(load().dgpe_substep(ctx, int(which)), "dgpe_substep")
+
+
+def dgpe_observables(ctx):
+    o = dgpe_obs()
+    _check(load().dgpe_observables(ctx, ctypes.byref(o)), "dgpe_observables")
+    return o.as_dict()
+
+
+def dgpe_get_phi(ctx, ptr, where):
+    _check(load().dgpe_get_phi(ctx, ctypes.c_void_p(ptr), int(where)), "dgpe_get_phi")
+
+
+def dgpe_sync(ctx):
+    _check(load().dgpe_sync(ctx), "dgpe_sync")
+
+
+def dgpe_set_timing(ctx, enable):
+    _check(load().dgpe_set_timing(ctx, 1 if enable else 0), "dgpe_set_timing")
+
+
+def dgpe_kernel_times(ctx, max_kernels=16):
+    arr = (dgpe_kernel_time * max_kernels)()
+    n = ctypes.c_int(0)
+    _check(load().dgpe_kernel_times(ctx, arr, max_kernels, ctypes.byref(n)), "dgpe_kernel_times")
+    return [{"name": arr[i].name.decode(), "total_ms": arr[i].total_ms, "launches": arr[i].launches,
+             "bytes_per_launch": arr[i].bytes_per_launch} for i in range(min(n.value, max_kernels))]
+
+
+def dgpe_destroy(ctx):
+    if ctx:
+        load().dgpe_destroy(ctx)
+
+
+# ---- convenience wrapper: PyTorch owns the device memory and the stream ----------------
+class Condensate:
+    """One solver context on the current CUDA device and PyTorch's current stream.
+
+    psi arrays are [nx][ny][nz] complex128 (FP64) or complex64 (MIXED); numpy arrays are
+    host memory, torch CUDA tensors device memory.
+    """
+
+    def __init__(self, shape, h, dt, mode=DGPE_IMAG_TIME, precision=DGPE_FP64, nu=(1.0, 1.0, 1.0),
+                 g=0.0, gdd=0.0, device=None):
+        import torch
+        self._torch = torch
+        self.shape = tuple(int(v) for v in shape)
+        self.precision = precision
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.cdtype = torch.complex128 if precision == DGPE_FP64 else torch.complex64
+        self.rdtype = torch.float64 if precision == DGPE_FP64 else torch.float32
+        self.np_cdtype = np.complex128 if precision == DGPE_FP64 else np.complex64
+        self._params = make_params(shape, h, dt, mode, precision, nu, g, gdd)
+        nbytes = dgpe_workspace_bytes(self._params)
+        self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self._params.workspace = self._ws.data_ptr()
+        self._params.workspace_bytes = nbytes
+        self.stream = torch.cuda.current_stream(self.device)
+        self.ctx = dgpe_create(self._params, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            dgpe_destroy(self.ctx)
+            self.ctx = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_params(self, **kw):
+        p = self._params
+        for k, v in kw.items():
+            if k == "h":
+                hx, hy, hz = (v, v, v) if np.isscalar(v) else tuple(v)
+                p.hx, p.hy, p.hz = hx, hy, hz
+            elif k == "nu":
+                p.nu[0], p.nu[1], p.nu[2] = (float(x) for x in v)
+            elif k in ("dt", "g", "gdd"):
+                setattr(p, k, float(v))
+            elif k == "mode":
+                p.mode = int(v)
+            else:
+                raise KeyError(k)
+        dgpe_set_params(self.ctx, p)
+
+    def set_psi(self, psi):
+        torch = self._torch
+        if isinstance(psi, torch.Tensor):
+            t = psi.to(device=self.device, dtype=self.cdtype).contiguous()
+            assert tuple(t.shape) == self.shape
+            dgpe_set_psi(self.ctx, t.data_ptr(), DGPE_DEVICE)
+            self._keep = t   # the copy is stream-ordered: keep the source alive
+        else:
+            a = np.ascontiguousarray(psi, dtype=self.np_cdtype)
+            assert a.shape == self.shape
+            dgpe_set_psi(self.ctx, a.ctypes.data, DGPE_HOST)
+
+    def get_psi(self, host=True):
+        if host:
+            out = np.empty(self.shape, dtype=self.np_cdtype)
+            dgpe_get_psi(self.ctx, out.ctypes.data, DGPE_HOST)
+            return out
+        out = self._torch.empty(self.shape, dtype=self.cdtype, device=self.device)
+        dgpe_get_psi(self.ctx, out.data_ptr(), DGPE_DEVICE)
+        return out
+
+    def phi(self, host=True):
+        if host:
+            out = np.empty(self.shape, dtype=np.float64 if self.precision == DGPE_FP64 else np.float32)
+            dgpe_get_phi(self.ctx, out.ctypes.data, DGPE_HOST)
+            return out
+        out = self._torch.empty(self.shape, dtype=self.rdtype, device=self.device)
+        dgpe_get_phi(self.ctx, out.data_ptr(), DGPE_DEVICE)
+        return out
+
+    def step(self, nsteps=1):
+        dgpe_step(self.ctx, nsteps)
+
+    def substep(self, which):
+        dgpe_substep(self.ctx, which)
+
+    def observables(self):
+        return dgpe_observables(self.ctx)
+
+    def sync(self):
+        dgpe_sync(self.ctx)
+
+    def set_timing(self, enable):
+        dgpe_set_timing(self.ctx, enable)
+
+    def kernel_times(self):
+        return dgpe_kernel_times(self.ctx)

@@ -1,0 +1,583 @@
+// C-ABI of the GB300 SSCN solver (declared in include/dgpe.h): parameter checks, the
+// workspace layout, the step sequence K1..K7 (replayed from a CUDA graph) and the
+// synchronising calls.  All arithmetic of the step runs in the kernels of
+// dgpe_device.cuh; this file only orders them on the caller's stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "dgpe.h"
+#include "dgpe_internal.h"
+
+using namespace dgpe;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool is_2a3b(int n) {
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+bool finite(double v) { return isfinite(v) != 0; }
+
+// Radix plan: as many radix-8 stages as possible, then one radix-4 or radix-2 stage for
+// the rest of the power of two, then the radix-3 stages.
+FftPlan make_plan(int n) {
+  FftPlan p{};
+  p.n = n;
+  int m = n, k = 0;
+  while (m % 8 == 0) {
+    p.radix[k++] = 8;
+    m /= 8;
+  }
+  if (m % 4 == 0) {
+    p.radix[k++] = 4;
+    m /= 4;
+  }
+  if (m % 2 == 0) {
+    p.radix[k++] = 2;
+    m /= 2;
+  }
+  while (m % 3 == 0) {
+    p.radix[k++] = 3;
+    m /= 3;
+  }
+  p.nstages = k;
+  return p;
+}
+
+// Interior points per lane of the chunked Thomas solve: ceil(m / 32) rounded up to even
+// (an odd slot stride keeps the 32 lanes on distinct shared-memory banks).
+int cn_chunk(int n) {
+  const int m = n - 2;
+  int c = (m + kWarp - 1) / kWarp;
+  if (c < 2) c = 2;
+  if (c % 2) ++c;
+  return c;
+}
+
+int check_shape(const dgpe_params *p) {
+  const int dims[3] = {p->nx, p->ny, p->nz};
+  for (int d = 0; d < 3; ++d) {
+    const int n = dims[d];
+    if (n < 4 || n > 512 || n % 2 != 0 || !is_2a3b(n)) return DGPE_EINVAL;
+    if (cn_chunk(n) > kCnMaxChunk) return DGPE_EUNSUPPORTED;
+  }
+  if (p->precision != DGPE_FP64 && p->precision != DGPE_MIXED) return DGPE_EINVAL;
+  return DGPE_OK;
+}
+
+int check_physics(const dgpe_params *p) {
+  if (!(p->hx > 0 && p->hy > 0 && p->hz > 0) || !finite(p->hx) || !finite(p->hy) || !finite(p->hz))
+    return DGPE_EINVAL;
+  if (p->mode != DGPE_REAL_TIME && p->mode != DGPE_IMAG_TIME) return DGPE_EINVAL;
+  if (!finite(p->dt) || p->dt == 0.0) return DGPE_EINVAL;
+  if (p->mode == DGPE_IMAG_TIME && !(p->dt > 0)) return DGPE_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (!finite(p->nu[d])) return DGPE_EINVAL;
+  if (!finite(p->g) || !finite(p->gdd)) return DGPE_EINVAL;
+  return DGPE_OK;
+}
+
+struct Layout {
+  size_t state, partials, tw[3], cn[3], psi, spec, total;
+};
+
+Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
+  const size_t e = (size_t)(p->precision == DGPE_FP64 ? 16 : 8);
+  const int n[3] = {p->nx, p->ny, p->nz};
+  Layout L{};
+  size_t off = 0;
+  L.state = off;
+  off += align_up(sizeof(DevState));
+  L.partials = off;
+  off += align_up((size_t)max_blocks * 8 * sizeof(double));
+  for (int d = 0; d < 3; ++d) {
+    L.tw[d] = off;
+    off += align_up((size_t)n[d] * e);
+  }
+  for (int d = 0; d < 3; ++d) {
+    L.cn[d] = off;
+    off += align_up((size_t)5 * (n[d] - 2) * e);
+  }
+  L.psi = off;
+  off += align_up((size_t)p->nx * p->ny * p->nz * e);
+  L.spec = off;
+  off += align_up((size_t)(p->nz / 2 + 1) * p->nx * p->ny * e);
+  L.total = off;
+  (void)ks;
+  return L;
+}
+
+const KernelSet *kernel_set(int precision) { return precision == DGPE_FP64 ? kernels_f64() : kernels_f32(); }
+
+KArgs base_args(const dgpe_params *p) {
+  KArgs a{};
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.nzh = p->nz / 2 + 1;
+  for (int d = 0; d < 3; ++d) {
+    const int n = d == 0 ? p->nx : d == 1 ? p->ny : p->nz;
+    a.plan[d] = make_plan(n);
+    a.cn[d].m = n - 2;
+    a.cn[d].chunk = cn_chunk(n);
+  }
+  return a;
+}
+
+void set_physics(KArgs &a, const dgpe_params *p) {
+  a.hx = p->hx;
+  a.hy = p->hy;
+  a.hz = p->hz;
+  a.dt = p->dt;
+  a.g = p->g;
+  a.gdd = p->gdd;
+  a.vx = 0.5 * p->nu[0] * p->nu[0];
+  a.vy = 0.5 * p->nu[1] * p->nu[1];
+  a.vz = 0.5 * p->nu[2] * p->nu[2];
+  a.inv_ntot = 1.0 / ((double)p->nx * p->ny * p->nz);
+  a.imag = p->mode == DGPE_IMAG_TIME;
+}
+
+int map_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return DGPE_OK;
+  if (e == cudaErrorMemoryAllocation) return DGPE_ENOMEM;
+  return DGPE_ECUDA;
+}
+
+const char *kKernelNames[kNumKernels] = {"k1_density_r2c_z",      "k2_fft_y",   "k3_fft_x_dipolar_ifft_x",
+                                         "k4_ifft_y",             "k5_c2r_z_phase_cn_z", "k6_cn_y",
+                                         "k7_cn_x_reduce",        "materialize", "observables"};
+
+}  // namespace
+
+struct dgpe_ctx {
+  dgpe_params p;
+  const KernelSet *ks;
+  cudaStream_t stream;
+  cudaStream_t cap_stream;
+  void *ws;
+  bool owns_ws;
+  Layout L;
+  KArgs args;
+  cudaGraphExec_t graph;
+  bool graph_valid;
+  bool timing;
+  std::vector<cudaEvent_t> ev_free;
+  struct Pending {
+    int kernel;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  double total_ms[kNumKernels];
+  long long launches[kNumKernels];
+  int latched;
+};
+
+namespace {
+
+void *at(dgpe_ctx *c, size_t off) { return static_cast<char *>(c->ws) + off; }
+
+double kernel_bytes(const dgpe_ctx *c, int k) {
+  const double e = c->ks->elem_bytes;
+  const double ntot = (double)c->p.nx * c->p.ny * c->p.nz;
+  const double nspec = (double)(c->p.nz / 2 + 1) * c->p.nx * c->p.ny;
+  switch (k) {
+    case kK1DensityR2Cz: return e * (ntot + nspec);
+    case kK2FftY:
+    case kK3FftXDipolar:
+    case kK4IfftY: return 2 * e * nspec;
+    case kK5C2RzPhaseCnz: return e * (nspec + 2 * ntot);
+    case kK6CnY:
+    case kK7CnXReduce:
+    case kKMaterialize: return 2 * e * ntot;
+    case kKObs: return e * (nspec + 5 * ntot);
+    default: return 0;
+  }
+}
+
+cudaEvent_t get_event(dgpe_ctx *c) {
+  if (!c->ev_free.empty()) {
+    cudaEvent_t e = c->ev_free.back();
+    c->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Launch one kernel of the step on stream st, timed with events when timing is on.
+template <typename F>
+int launch(dgpe_ctx *c, cudaStream_t st, int kernel, F &&f) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c->timing) {
+    a = get_event(c);
+    b = get_event(c);
+    if (!a || !b) return DGPE_ECUDA;
+    if (cudaEventRecord(a, st) != cudaSuccess) return DGPE_ECUDA;
+  }
+  const int rc = map_cuda(f());
+  if (rc != DGPE_OK) return rc;
+  if (c->timing) {
+    if (cudaEventRecord(b, st) != cudaSuccess) return DGPE_ECUDA;
+    c->pending.push_back({kernel, a, b});
+  }
+  return DGPE_OK;
+}
+
+int enqueue_potential_transforms(dgpe_ctx *c, cudaStream_t st) {
+  const KArgs &a = c->args;
+  const KernelSet *ks = c->ks;
+  int rc;
+  if ((rc = launch(c, st, kK1DensityR2Cz, [&] { return ks->k1(a, st); }))) return rc;
+  if ((rc = launch(c, st, kK2FftY, [&] { return ks->k2(a, st); }))) return rc;
+  if ((rc = launch(c, st, kK3FftXDipolar, [&] { return ks->k3(a, st); }))) return rc;
+  if ((rc = launch(c, st, kK4IfftY, [&] { return ks->k4(a, st); }))) return rc;
+  return DGPE_OK;
+}
+
+int enqueue_step(dgpe_ctx *c, cudaStream_t st) {
+  const KArgs &a = c->args;
+  const KernelSet *ks = c->ks;
+  int rc;
+  if ((rc = enqueue_potential_transforms(c, st))) return rc;
+  if ((rc = launch(c, st, kK5C2RzPhaseCnz, [&] { return ks->k5(a, kZStep, st); }))) return rc;
+  if ((rc = launch(c, st, kK6CnY, [&] { return ks->k6(a, st); }))) return rc;
+  if ((rc = launch(c, st, kK7CnXReduce, [&] { return ks->k7(a, 1, a.imag, st); }))) return rc;
+  return DGPE_OK;
+}
+
+int build_graph(dgpe_ctx *c) {
+  if (c->graph_valid) return DGPE_OK;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  const bool timing = c->timing;
+  c->timing = false;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    c->timing = timing;
+    return map_cuda(e);
+  }
+  const int rc = enqueue_step(c, c->cap_stream);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(c->cap_stream, &g);
+  c->timing = timing;
+  if (rc != DGPE_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return map_cuda(e);
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return map_cuda(e);
+  }
+  c->graph_valid = true;
+  return DGPE_OK;
+}
+
+int setup_tables(dgpe_ctx *c) {
+  const dgpe_params *p = &c->p;
+  const double h[3] = {p->hx, p->hy, p->hz};
+  for (int d = 0; d < 3; ++d) {
+    const double r = p->dt / (4.0 * h[d] * h[d]);
+    const int rc = map_cuda(c->ks->cn_tables(at(c, c->L.cn[d]), c->args.cn[d].m, c->args.cn[d].chunk, r,
+                                             p->mode == DGPE_IMAG_TIME, c->stream));
+    if (rc) return rc;
+  }
+  return DGPE_OK;
+}
+
+// Read the device flags after a synchronisation; latch a device error.
+int check_device_flags(dgpe_ctx *c) {
+  unsigned int flags = 0;
+  cudaError_t e = cudaMemcpy(&flags, &static_cast<DevState *>(at(c, c->L.state))->flags, sizeof(flags),
+                             cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return map_cuda(e);
+  if (flags & kFlagNonFinite) c->latched = DGPE_ENONFINITE;
+  return c->latched;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dgpe_strerror(int code) {
+  switch (code) {
+    case DGPE_OK: return "ok";
+    case DGPE_EINVAL: return "invalid argument or parameter";
+    case DGPE_ENOMEM: return "out of device memory or workspace too small";
+    case DGPE_ECUDA: return "CUDA runtime error";
+    case DGPE_ENONFINITE: return "non-finite value in a device reduction";
+    case DGPE_ETIMEOUT: return "device-side wait timed out";
+    case DGPE_EUNSUPPORTED: return "unsupported by this build";
+    default: return "unknown error code";
+  }
+}
+
+int dgpe_workspace_bytes(const dgpe_params *p, size_t *bytes) {
+  if (!p || !bytes) return DGPE_EINVAL;
+  int rc = check_shape(p);
+  if (rc) return rc;
+  // the block count of the reducing kernels depends only on shape and precision
+  const KernelSet *ks = kernel_set(p->precision);
+  *bytes = layout_of(p, ks, ks->max_blocks(base_args(p))).total;
+  return DGPE_OK;
+}
+
+int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out) {
+  if (!p || !out) return DGPE_EINVAL;
+  *out = nullptr;
+  int rc = check_shape(p);
+  if (rc) return rc;
+  if ((rc = check_physics(p))) return rc;
+  size_t need = 0;
+  dgpe_workspace_bytes(p, &need);
+  if (p->workspace) {
+    if (p->workspace_bytes < need) return DGPE_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(p->workspace) % kAlign) return DGPE_EINVAL;
+  }
+  dgpe_ctx *c = new (std::nothrow) dgpe_ctx();
+  if (!c) return DGPE_ENOMEM;
+  c->p = *p;
+  c->ks = kernel_set(p->precision);
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->args = base_args(p);
+  set_physics(c->args, p);
+  c->L = layout_of(p, c->ks, c->ks->max_blocks(c->args));
+  rc = map_cuda(c->ks->init());
+  if (!rc) rc = map_cuda(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  if (!rc) {
+    if (p->workspace) {
+      c->ws = p->workspace;
+      c->owns_ws = false;
+    } else {
+      rc = map_cuda(cudaMalloc(&c->ws, c->L.total));
+      c->owns_ws = rc == DGPE_OK;
+    }
+  }
+  if (rc) {
+    dgpe_destroy(c);
+    return rc;
+  }
+  KArgs &a = c->args;
+  a.state = static_cast<DevState *>(at(c, c->L.state));
+  a.partials = static_cast<double *>(at(c, c->L.partials));
+  a.psi = at(c, c->L.psi);
+  a.spec = at(c, c->L.spec);
+  for (int d = 0; d < 3; ++d) {
+    a.tw[d] = at(c, c->L.tw[d]);
+    a.cn[d].tab = at(c, c->L.cn[d]);
+  }
+  const int n[3] = {p->nx, p->ny, p->nz};
+  rc = map_cuda(cudaMemsetAsync(a.psi, 0, (size_t)p->nx * p->ny * p->nz * c->ks->elem_bytes, c->stream));
+  if (!rc) rc = map_cuda(c->ks->reset_state(a.state, c->stream));
+  for (int d = 0; d < 3 && !rc; ++d) rc = map_cuda(c->ks->twiddles(const_cast<void *>(a.tw[d]), n[d], c->stream));
+  if (!rc) rc = setup_tables(c);
+  if (rc) {
+    dgpe_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return DGPE_OK;
+}
+
+int dgpe_set_params(dgpe_ctx *c, const dgpe_params *p) {
+  if (!c || !p) return DGPE_EINVAL;
+  if (p->nx != c->p.nx || p->ny != c->p.ny || p->nz != c->p.nz || p->precision != c->p.precision)
+    return DGPE_EINVAL;
+  int rc = check_physics(p);
+  if (rc) return rc;
+  void *ws = c->p.workspace;
+  const size_t wsb = c->p.workspace_bytes;
+  c->p = *p;
+  c->p.workspace = ws;
+  c->p.workspace_bytes = wsb;
+  set_physics(c->args, p);
+  c->graph_valid = false;
+  return setup_tables(c);
+}
+
+int dgpe_set_psi(dgpe_ctx *c, const void *psi, int where) {
+  if (!c || !psi || (where != DGPE_HOST && where != DGPE_DEVICE)) return DGPE_EINVAL;
+  const size_t bytes = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;
+  int rc = map_cuda(cudaMemcpyAsync(c->args.psi, psi, bytes,
+                                    where == DGPE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+  if (!rc) rc = map_cuda(c->ks->reset_state(c->args.state, c->stream));
+  if (!rc && where == DGPE_HOST) rc = map_cuda(cudaStreamSynchronize(c->stream));
+  if (!rc) c->latched = DGPE_OK;
+  return rc;
+}
+
+int dgpe_get_psi(dgpe_ctx *c, void *out, int where) {
+  if (!c || !out || (where != DGPE_HOST && where != DGPE_DEVICE)) return DGPE_EINVAL;
+  const size_t bytes = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;
+  int rc = launch(c, c->stream, kKMaterialize, [&] { return c->ks->materialize(c->args, c->stream); });
+  if (rc) return rc;
+  rc = map_cuda(cudaMemcpyAsync(out, c->args.psi, bytes,
+                                where == DGPE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+  if (rc) return rc;
+  if (where == DGPE_HOST) {
+    rc = map_cuda(cudaStreamSynchronize(c->stream));
+    if (rc) return rc;
+    return check_device_flags(c);
+  }
+  return DGPE_OK;
+}
+
+int dgpe_step(dgpe_ctx *c, int nsteps) {
+  if (!c || nsteps < 0) return DGPE_EINVAL;
+  if (nsteps == 0) return DGPE_OK;
+  if (c->timing) {
+    for (int s = 0; s < nsteps; ++s) {
+      const int rc = enqueue_step(c, c->stream);
+      if (rc) return rc;
+    }
+    return DGPE_OK;
+  }
+  int rc = build_graph(c);
+  if (rc) return rc;
+  for (int s = 0; s < nsteps; ++s) {
+    rc = map_cuda(cudaGraphLaunch(c->graph, c->stream));
+    if (rc) return rc;
+  }
+  return DGPE_OK;
+}
+
+int dgpe_substep(dgpe_ctx *c, int which) {
+  if (!c) return DGPE_EINVAL;
+  const KArgs &a = c->args;
+  const KernelSet *ks = c->ks;
+  cudaStream_t st = c->stream;
+  switch (which) {
+    case DGPE_SUB_POTENTIAL: {
+      // absorb the pending renormalisation first: the phase step then runs with s = 1
+      int rc = launch(c, st, kKMaterialize, [&] { return ks->materialize(a, st); });
+      if (!rc) rc = enqueue_potential_transforms(c, st);
+      if (!rc) rc = launch(c, st, kK5C2RzPhaseCnz, [&] { return ks->k5(a, kZPhaseOnly, st); });
+      return rc;
+    }
+    case DGPE_SUB_CN_X: return launch(c, st, kK7CnXReduce, [&] { return ks->k7(a, 0, 0, st); });
+    case DGPE_SUB_CN_Y: return launch(c, st, kK6CnY, [&] { return ks->k6(a, st); });
+    case DGPE_SUB_CN_Z: return launch(c, st, kK5C2RzPhaseCnz, [&] { return ks->k5(a, kZCnOnly, st); });
+    default: return DGPE_EINVAL;
+  }
+}
+
+int dgpe_observables(dgpe_ctx *c, dgpe_obs *o) {
+  if (!c || !o) return DGPE_EINVAL;
+  int rc = enqueue_potential_transforms(c, c->stream);
+  if (!rc) rc = launch(c, c->stream, kKObs, [&] { return c->ks->k5(c->args, kZObs, c->stream); });
+  if (rc) return rc;
+  double v[10];
+  rc = map_cuda(cudaMemcpyAsync(v, c->args.state->obs, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+  if (!rc) rc = map_cuda(cudaStreamSynchronize(c->stream));
+  if (rc) return rc;
+  o->norm = v[0];
+  o->mu = v[1];
+  o->energy = v[2];
+  o->rms[0] = v[3];
+  o->rms[1] = v[4];
+  o->rms[2] = v[5];
+  o->e_kin = v[6];
+  o->e_trap = v[7];
+  o->e_contact = v[8];
+  o->e_dipolar = v[9];
+  return check_device_flags(c);
+}
+
+int dgpe_get_phi(dgpe_ctx *c, void *out, int where) {
+  if (!c || !out || (where != DGPE_HOST && where != DGPE_DEVICE)) return DGPE_EINVAL;
+  const size_t bytes = (size_t)c->p.nx * c->p.ny * c->p.nz * (c->ks->elem_bytes / 2);
+  void *dst = out;
+  int rc = DGPE_OK;
+  if (where == DGPE_HOST) {
+    rc = map_cuda(cudaMallocAsync(&dst, bytes, c->stream));
+    if (rc) return rc;
+  }
+  KArgs a = c->args;
+  a.out = dst;
+  rc = enqueue_potential_transforms(c, c->stream);
+  if (!rc) rc = map_cuda(c->ks->k5(a, kZPhi, c->stream));
+  if (where == DGPE_HOST) {
+    if (!rc) rc = map_cuda(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+    cudaFreeAsync(dst, c->stream);
+    if (!rc) rc = map_cuda(cudaStreamSynchronize(c->stream));
+    if (!rc) rc = check_device_flags(c);
+  }
+  return rc;
+}
+
+int dgpe_sync(dgpe_ctx *c) {
+  if (!c) return DGPE_EINVAL;
+  const int rc = map_cuda(cudaStreamSynchronize(c->stream));
+  if (rc) return rc;
+  return check_device_flags(c);
+}
+
+int dgpe_set_timing(dgpe_ctx *c, int enable) {
+  if (!c) return DGPE_EINVAL;
+  c->timing = enable != 0;
+  return DGPE_OK;
+}
+
+int dgpe_kernel_times(dgpe_ctx *c, dgpe_kernel_time *out, int max, int *n) {
+  if (!c || (!out && max > 0) || !n) return DGPE_EINVAL;
+  int rc = map_cuda(cudaStreamSynchronize(c->stream));
+  if (rc) return rc;
+  for (const auto &pd : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pd.a, pd.b) == cudaSuccess) {
+      c->total_ms[pd.kernel] += ms;
+      c->launches[pd.kernel] += 1;
+    }
+    c->ev_free.push_back(pd.a);
+    c->ev_free.push_back(pd.b);
+  }
+  c->pending.clear();
+  int k = 0;
+  for (int q = 0; q < kNumKernels; ++q) {
+    if (c->launches[q] == 0) continue;
+    if (k < max) {
+      memset(&out[k], 0, sizeof(out[k]));
+      strncpy(out[k].name, kKernelNames[q], sizeof(out[k].name) - 1);
+      out[k].total_ms = c->total_ms[q];
+      out[k].launches = c->launches[q];
+      out[k].bytes_per_launch = kernel_bytes(c, q);
+    }
+    ++k;
+    c->total_ms[q] = 0;
+    c->launches[q] = 0;
+  }
+  *n = k;
+  return DGPE_OK;
+}
+
+void dgpe_destroy(dgpe_ctx *c) {
+  if (!c) return;
+  if (c->ws) cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (const auto &pd : c->pending) {
+    cudaEventDestroy(pd.a);
+    cudaEventDestroy(pd.b);
+  }
+  for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+  if (c->owns_ws && c->ws) cudaFree(c->ws);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,984 @@
+// Device code of the SSCN step: complex arithmetic, shared-memory Stockham FFT stages,
+// the chunked Thomas solver of the Crank-Nicolson sweeps, and the kernel templates.
+// Instantiated once per precision by kernels_f64.cu and kernels_f32.cu.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "dgpe_internal.h"
+
+namespace dgpe {
+
+// ---------------------------------------------------------------------------------------
+// Complex arithmetic
+// ---------------------------------------------------------------------------------------
+template <typename R>
+struct alignas(2 * sizeof(R)) cplx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cplx<R> operator+(cplx<R> a, cplx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cplx<R> operator-(cplx<R> a, cplx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ cplx<R> operator*(cplx<R> a, cplx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// a * conj(b)
+template <typename R>
+__device__ __forceinline__ cplx<R> mul_conj(cplx<R> a, cplx<R> b) {
+  return {a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im};
+}
+template <typename R>
+__device__ __forceinline__ cplx<R> scale(cplx<R> a, R s) { return {a.re * s, a.im * s}; }
+template <typename R>
+__device__ __forceinline__ cplx<R> mul_i(cplx<R> a) { return {-a.im, a.re}; }
+template <typename R>
+__device__ __forceinline__ cplx<R> mul_mi(cplx<R> a) { return {a.im, -a.re}; }
+template <typename R>
+__device__ __forceinline__ cplx<R> czero() { return {R(0), R(0)}; }
+
+// Coefficients of the Crank-Nicolson solve: complex (real time) or real (imaginary time).
+template <typename R>
+__device__ __forceinline__ cplx<R> mul(R a, cplx<R> v) { return {a * v.re, a * v.im}; }
+template <typename R>
+__device__ __forceinline__ cplx<R> mul(cplx<R> a, cplx<R> v) { return a * v; }
+template <typename T>
+__device__ __forceinline__ T coef_one();
+template <>
+__device__ __forceinline__ double coef_one<double>() { return 1.0; }
+template <>
+__device__ __forceinline__ float coef_one<float>() { return 1.0f; }
+template <>
+__device__ __forceinline__ cplx<double> coef_one<cplx<double>>() { return {1.0, 0.0}; }
+template <>
+__device__ __forceinline__ cplx<float> coef_one<cplx<float>>() { return {1.0f, 0.0f}; }
+
+__device__ __forceinline__ double shfl_up(double v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ float shfl_up(float v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ double shfl_down(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ float shfl_down(float v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+template <typename R>
+__device__ __forceinline__ cplx<R> shfl_up(cplx<R> v, int d) { return {shfl_up(v.re, d), shfl_up(v.im, d)}; }
+template <typename R>
+__device__ __forceinline__ cplx<R> shfl_down(cplx<R> v, int d) { return {shfl_down(v.re, d), shfl_down(v.im, d)}; }
+
+__device__ __forceinline__ void sin_cos(double x, double *s, double *c) { sincos(x, s, c); }
+__device__ __forceinline__ void sin_cos(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ double exp_r(double x) { return exp(x); }
+__device__ __forceinline__ float exp_r(float x) { return expf(x); }
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ cplx<double> ldg(const cplx<double> *p) {
+  double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+  return {v.x, v.y};
+}
+template <>
+__device__ __forceinline__ cplx<float> ldg(const cplx<float> *p) {
+  float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+  return {v.x, v.y};
+}
+
+// ---------------------------------------------------------------------------------------
+// Tile shapes per precision.  Rows of strided tiles are 128 B (8 complex128 or 16
+// complex64) so every global access of a tile row is one full cache line.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+struct Tiles;
+template <>
+struct Tiles<double> {
+  static constexpr int kZLines = 8;       // z-lines per CTA in K1/K5 (4 pairs)
+  static constexpr int kZThreads = 256;   // one warp per z-line for the CN-z solve
+  static constexpr int kXCols = 4;        // consecutive y columns per K3 tile
+  static constexpr int kCnCols = 8;       // consecutive z columns per K6/K7 tile
+  static constexpr int kCnThreads = 256;  // one warp per line
+  static constexpr int kYBudget = 2048;   // K2/K4: lines per CTA = budget / ny
+};
+template <>
+struct Tiles<float> {
+  static constexpr int kZLines = 16;
+  static constexpr int kZThreads = 512;
+  static constexpr int kXCols = 8;
+  static constexpr int kCnCols = 16;
+  static constexpr int kCnThreads = 512;
+  static constexpr int kYBudget = 4096;
+};
+constexpr int kFftThreads = 256;
+
+template <typename R>
+__host__ __device__ inline int y_lines_per_cta(int ny) {
+  int l = Tiles<R>::kYBudget / ny;
+  return l < 2 ? 2 : (l > 32 ? 32 : l);
+}
+
+// Slot of grid point n of a line in a Crank-Nicolson tile: one padding slot after every
+// `chunk` interior points, so that the 32 lanes solving one line hit distinct banks.
+__host__ __device__ inline int cn_slot(int n, int chunk) { return n + (n > 0 ? (n - 1) / chunk : 0); }
+__host__ __device__ inline int cn_slots(int n, int chunk) { return n + (n - 2) / chunk; }
+
+// ---------------------------------------------------------------------------------------
+// FFT: radix-2/3/4/8 butterflies (DIR = -1 forward e^{-i..}, +1 inverse, unnormalised)
+// ---------------------------------------------------------------------------------------
+template <typename R, int DIR>
+__device__ __forceinline__ void bf2(cplx<R> *v) {
+  const cplx<R> a = v[0], b = v[1];
+  v[0] = a + b;
+  v[1] = a - b;
+}
+
+template <typename R, int DIR>
+__device__ __forceinline__ void bf4(cplx<R> &a0, cplx<R> &a1, cplx<R> &a2, cplx<R> &a3) {
+  const cplx<R> t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3;
+  const cplx<R> d = a1 - a3;
+  const cplx<R> t3 = DIR < 0 ? mul_mi(d) : mul_i(d);
+  a0 = t0 + t2;
+  a2 = t0 - t2;
+  a1 = t1 + t3;
+  a3 = t1 - t3;
+}
+
+template <typename R, int DIR>
+__device__ __forceinline__ void bf8(cplx<R> *v) {
+  cplx<R> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  cplx<R> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  bf4<R, DIR>(e0, e1, e2, e3);
+  bf4<R, DIR>(o0, o1, o2, o3);
+  const R h = R(0.70710678118654752440084436210485);
+  // o_k *= w8^k, w8 = e^{DIR 2 pi i / 8}
+  cplx<R> p1, p2, p3;
+  if (DIR < 0) {
+    p1 = {(o1.re + o1.im) * h, (o1.im - o1.re) * h};
+    p2 = mul_mi(o2);
+    p3 = {(o3.im - o3.re) * h, -(o3.re + o3.im) * h};
+  } else {
+    p1 = {(o1.re - o1.im) * h, (o1.re + o1.im) * h};
+    p2 = mul_i(o2);
+    p3 = {-(o3.re + o3.im) * h, (o3.re - o3.im) * h};
+  }
+  v[0] = e0 + o0;
+  v[4] = e0 - o0;
+  v[1] = e1 + p1;
+  v[5] = e1 - p1;
+  v[2] = e2 + p2;
+  v[6] = e2 - p2;
+  v[3] = e3 + p3;
+  v[7] = e3 - p3;
+}
+
+template <typename R, int DIR>
+__device__ __forceinline__ void bf3(cplx<R> *v) {
+  const R s3 = R(0.86602540378443864676372317075294);
+  const cplx<R> t = v[1] + v[2];
+  const cplx<R> u = scale(v[1] - v[2], s3);
+  const cplx<R> m = {v[0].re - R(0.5) * t.re, v[0].im - R(0.5) * t.im};
+  v[0] = v[0] + t;
+  if (DIR < 0) {
+    v[1] = m + mul_mi(u);
+    v[2] = m + mul_i(u);
+  } else {
+    v[1] = m + mul_i(u);
+    v[2] = m + mul_mi(u);
+  }
+}
+
+template <typename R, int DIR, int P>
+__device__ __forceinline__ void butterfly(cplx<R> *v) {
+  if (P == 2) bf2<R, DIR>(v);
+  else if (P == 3) bf3<R, DIR>(v);
+  else if (P == 4) bf4<R, DIR>(v[0], v[1], v[2], v[3]);
+  else bf8<R, DIR>(v);
+}
+
+// One Stockham autosort stage of radix P over `nlines` lines held in shared memory,
+// element e of line l at [e * sb + l].  ns = product of the radices of earlier stages.
+// Butterfly j reads x[j + r n/P], twiddles by w_n^{r (j mod ns) n/(ns P)}, and writes the
+// P outputs to (j div ns) ns P + (j mod ns) + s ns.
+template <typename R, int DIR, int P>
+__device__ __forceinline__ void fft_stage(const cplx<R> *__restrict__ src, cplx<R> *__restrict__ dst, int n,
+                                          int ns, int nlines, int sb, const cplx<R> *__restrict__ tw) {
+  const int nbf = n / P;
+  const int total = nbf * nlines;
+  const int twstep = n / (ns * P);
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int line = idx % nlines;
+    const int j = idx / nlines;
+    const int k = j % ns;
+    cplx<R> v[P];
+#pragma unroll
+    for (int r = 0; r < P; ++r) v[r] = src[(j + r * nbf) * sb + line];
+    if (ns > 1) {
+#pragma unroll
+      for (int r = 1; r < P; ++r) {
+        const cplx<R> w = ldg(tw + r * k * twstep);
+        v[r] = DIR < 0 ? v[r] * w : mul_conj(v[r], w);
+      }
+    }
+    butterfly<R, DIR, P>(v);
+    const int base = (j - k) * P + k;
+#pragma unroll
+    for (int s = 0; s < P; ++s) dst[(base + s * ns) * sb + line] = v[s];
+  }
+}
+
+// Full transform of `nlines` lines (ping-pong between a and b); returns the buffer that
+// holds the result.  The caller synchronises before the call (input written).
+template <typename R, int DIR>
+__device__ cplx<R> *fft_lines(cplx<R> *a, cplx<R> *b, const FftPlan &pl, int nlines, int sb,
+                              const cplx<R> *tw) {
+  int ns = 1;
+  for (int st = 0; st < pl.nstages; ++st) {
+    const int p = pl.radix[st];
+    if (p == 8) fft_stage<R, DIR, 8>(a, b, pl.n, ns, nlines, sb, tw);
+    else if (p == 4) fft_stage<R, DIR, 4>(a, b, pl.n, ns, nlines, sb, tw);
+    else if (p == 3) fft_stage<R, DIR, 3>(a, b, pl.n, ns, nlines, sb, tw);
+    else fft_stage<R, DIR, 2>(a, b, pl.n, ns, nlines, sb, tw);
+    __syncthreads();
+    cplx<R> *t = a;
+    a = b;
+    b = t;
+    ns *= p;
+  }
+  return a;
+}
+
+// ---------------------------------------------------------------------------------------
+// Crank-Nicolson along one line: solve (1 - cD) chi = psi on the m interior points
+// (Dirichlet walls), then psi' = 2 chi - psi = (1 - cD)^{-1} (1 + cD) psi.
+//
+// Chunked Thomas algorithm, one warp per line, lane t owns interior points
+// [t C, t C + C).  With the LU factors alpha_i = c / e_{i-1}, beta_i = 1 / e_i,
+//   forward  y_i = psi_i + alpha_i y_{i-1},   backward chi_i = beta_i (y_i + c chi_{i+1}),
+// each lane runs both recurrences on its chunk from zero boundary values, and the exact
+// solution follows by linearity:
+//   y_i   = y0_i + P_i Y_t,                   Y_t = y at the point before the chunk,
+//   chi_i = chi0_i + Y_t H_i + X_{t+1} G_i,   X_{t+1} = chi at the point after the chunk,
+// with P, H, G precomputed per position (see k_cn_tables).  The carries Y_t and X_t are
+// affine recurrences across lanes, resolved by warp-shuffle scans of (A, B) pairs.
+// Element n of the line is at buf[cn_slot(n, C) * es].
+// ---------------------------------------------------------------------------------------
+template <typename R, typename Coef>
+__device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m, int chunk,
+                                        const Coef *__restrict__ tab, Coef c) {
+  const int t = threadIdx.x & (kWarp - 1);
+  const int s0 = t * chunk;
+  const int len = max(0, min(chunk, m - s0));
+  const Coef *alpha = tab;
+  const Coef *beta = tab + m;
+  const Coef *P = tab + 2 * m;
+  const Coef *H = tab + 3 * m;
+  const Coef *G = tab + 4 * m;
+
+  cplx<R> y[kCnMaxChunk];
+  cplx<R> acc = czero<R>();
+#pragma unroll
+  for (int e = 0; e < kCnMaxChunk; ++e) {
+    if (e < len) {
+      const int i = s0 + e;
+      acc = buf[(i + 1 + t) * es] + mul(ldg(alpha + i), acc);
+      y[e] = acc;
+    }
+  }
+  // forward carries: Y_{t+1} = A_t Y_t + B_t, Y_0 = 0
+  Coef A = len > 0 ? ldg(P + s0 + len - 1) : coef_one<Coef>();
+  cplx<R> B = acc;
+#pragma unroll
+  for (int d = 1; d < kWarp; d <<= 1) {
+    const Coef Ap = shfl_up(A, d);
+    const cplx<R> Bp = shfl_up(B, d);
+    if (t >= d) {
+      B = mul(A, Bp) + B;
+      A = A * Ap;
+    }
+  }
+  cplx<R> Y = shfl_up(B, 1);
+  if (t == 0) Y = czero<R>();
+
+  acc = czero<R>();
+#pragma unroll
+  for (int e = kCnMaxChunk - 1; e >= 0; --e) {
+    if (e < len) {
+      const int i = s0 + e;
+      acc = mul(ldg(beta + i), y[e] + mul(c, acc));
+      y[e] = acc;
+    }
+  }
+  // backward carries: X_t = G_{s0} X_{t+1} + (chi0_{s0} + H_{s0} Y_t), X_32 = 0
+  Coef A2 = len > 0 ? ldg(G + s0) : coef_one<Coef>();
+  cplx<R> B2 = len > 0 ? acc + mul(ldg(H + s0), Y) : czero<R>();
+#pragma unroll
+  for (int d = 1; d < kWarp; d <<= 1) {
+    const Coef An = shfl_down(A2, d);
+    const cplx<R> Bn = shfl_down(B2, d);
+    if (t + d < kWarp) {
+      B2 = mul(A2, Bn) + B2;
+      A2 = A2 * An;
+    }
+  }
+  cplx<R> X = shfl_down(B2, 1);
+  if (t == kWarp - 1) X = czero<R>();
+
+#pragma unroll
+  for (int e = 0; e < kCnMaxChunk; ++e) {
+    if (e < len) {
+      const int i = s0 + e;
+      const cplx<R> chi = y[e] + mul(ldg(H + i), Y) + mul(ldg(G + i), X);
+      const int q = (i + 1 + t) * es;
+      const cplx<R> v = buf[q];
+      buf[q] = {R(2) * chi.re - v.re, R(2) * chi.im - v.im};
+    }
+  }
+  if (t == 0) {
+    buf[0] = czero<R>();
+    buf[cn_slot(m + 1, chunk) * es] = czero<R>();
+  }
+}
+
+template <typename R, typename Coef>
+struct CnCoef;
+template <typename R>
+struct CnCoef<R, R> {
+  __device__ static R make(double r) { return R(r); }
+};
+template <typename R>
+struct CnCoef<R, cplx<R>> {
+  __device__ static cplx<R> make(double r) { return {R(0), R(r)}; }
+};
+
+// ---------------------------------------------------------------------------------------
+// Reductions (FP64): warp shuffle, then across warps; deterministic order.
+// ---------------------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*red)[NV]) {
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x / kWarp;
+  const int nwarps = (blockDim.x + kWarp - 1) / kWarp;
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+    for (int d = kWarp / 2; d > 0; d >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], d);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[warp][q] = v[q];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      v[q] = lane < nwarps ? red[lane][q] : 0.0;
+      for (int d = kWarp / 2; d > 0; d >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], d);
+    }
+  }
+}
+
+// Store this block's partial sums; the last block to finish adds all partials in block
+// order and returns true (in every thread of that block) with the totals in thread 0.
+template <int NV>
+__device__ bool reduce_across_blocks(double (&v)[NV], double *partials, unsigned int *ticket) {
+  __shared__ double red[32][NV];
+  __shared__ bool last;
+  const int nblocks = gridDim.x * gridDim.y;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  block_sum<NV>(v, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) partials[(size_t)bid * NV + q] = v[q];
+    __threadfence();
+    const unsigned int prev = atomicAdd(ticket, 1u);
+    last = (prev == (unsigned int)nblocks - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] += __ldcg(partials + (size_t)b * NV + q);
+  block_sum<NV>(v, red);
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+__device__ __forceinline__ double coordinate(int i, int n, double h) { return (double)(i - n / 2) * h; }
+
+// ---------------------------------------------------------------------------------------
+// Set-up kernels
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__global__ void k_twiddles(cplx<R> *tw, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    double s, c;
+    sincospi(2.0 * (double)t / (double)n, &s, &c);
+    tw[t] = {R(c), R(-s)};
+  }
+}
+
+// LU factors of tridiag(-c, 1 + 2c, -c) (order m) and the chunk response tables P, H, G
+// of the chunked Thomas solve (see cn_line), computed in FP64 by one thread in one pass:
+//   e_0 = 1 + 2c, e_i = 1 + 2c - c alpha_i, alpha_i = c / e_{i-1}, beta_i = 1 / e_i;
+//   per chunk [s0, end]: P_s0 = alpha_s0, P_i = alpha_i P_{i-1};
+//   H_end = beta_end P_end, H_i = beta_i (P_i + c H_{i+1});
+//   G_end = beta_end c,     G_i = beta_i c G_{i+1}.
+struct Z64 {
+  double re, im;
+};
+__device__ __forceinline__ Z64 zmul(Z64 a, Z64 b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ Z64 zadd(Z64 a, Z64 b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ Z64 zdiv(Z64 a, Z64 b) {
+  const double d = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+
+template <typename R, typename Coef>
+__device__ __forceinline__ void store_coef(Coef *tab, int k, Z64 v) {
+  if constexpr (sizeof(Coef) == sizeof(R)) tab[k] = Coef(v.re);
+  else tab[k] = Coef{R(v.re), R(v.im)};
+}
+
+template <typename R, typename Coef>
+__global__ void k_cn_tables(Coef *tab, int m, int chunk, double r, int imag) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const Z64 c = imag ? Z64{r, 0.0} : Z64{0.0, r};
+  const Z64 diag = {1.0 + 2.0 * c.re, 2.0 * c.im};
+  const Z64 one = {1.0, 0.0};
+  Z64 al[kCnMaxChunk], be[kCnMaxChunk], pv[kCnMaxChunk];
+  Z64 e_prev = diag;
+  for (int s0 = 0; s0 < m; s0 += chunk) {
+    const int end = min(s0 + chunk, m) - 1;
+    for (int i = s0; i <= end; ++i) {
+      Z64 a = {0.0, 0.0}, e = diag;
+      if (i > 0) {
+        a = zdiv(c, e_prev);
+        const Z64 ca = zmul(c, a);
+        e = Z64{diag.re - ca.re, diag.im - ca.im};
+      }
+      al[i - s0] = a;
+      be[i - s0] = zdiv(one, e);
+      e_prev = e;
+      store_coef<R>(tab, i, a);
+      store_coef<R>(tab, m + i, be[i - s0]);
+    }
+    Z64 p = al[0];
+    pv[0] = p;
+    for (int i = s0 + 1; i <= end; ++i) {
+      p = zmul(p, al[i - s0]);
+      pv[i - s0] = p;
+    }
+    for (int i = s0; i <= end; ++i) store_coef<R>(tab, 2 * m + i, pv[i - s0]);
+    Z64 h = zmul(be[end - s0], pv[end - s0]);
+    Z64 gg = zmul(be[end - s0], c);
+    store_coef<R>(tab, 3 * m + end, h);
+    store_coef<R>(tab, 4 * m + end, gg);
+    for (int i = end - 1; i >= s0; --i) {
+      h = zmul(be[i - s0], zadd(pv[i - s0], zmul(c, h)));
+      gg = zmul(be[i - s0], zmul(c, gg));
+      store_coef<R>(tab, 3 * m + i, h);
+      store_coef<R>(tab, 4 * m + i, gg);
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_reset_state(DevState *st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    st->s = 1.0;
+    st->norm = 0.0;
+    st->flags = 0u;
+    st->ticket = 0u;
+    st->steps = 0ull;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K1: n = s^2 |psi|^2 of kZLines consecutive z-lines (i, j0..), packed in pairs as the
+// real and imaginary parts of one complex line, forward FFT along z, then the two real
+// spectra are separated (X1 = (Z_m + conj Z_{N-m})/2, X2 = (Z_m - conj Z_{N-m})/2i) and
+// the half spectrum m = 0..nz/2 is stored to spec[m][i][j].
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int BZ = Tiles<R>::kZLines;
+  constexpr int SB = BZ / 2 + 1;
+  const int nz = a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
+  const int nl = min(BZ, a.ny - j0), np = nl >> 1;
+  C *za = reinterpret_cast<C *>(smem_raw);
+  C *zb = za + nz * SB;
+  const double s = a.state->s;
+  const R s2 = R(s * s);
+  const C *psi = reinterpret_cast<const C *>(a.psi) + ((size_t)i * a.ny + j0) * nz;
+  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
+    const int b = e / nz, n = e - b * nz;
+    const C v = psi[e];
+    R *z = reinterpret_cast<R *>(za + n * SB + (b >> 1));
+    z[b & 1] = s2 * (v.re * v.re + v.im * v.im);
+  }
+  __syncthreads();
+  const C *res = fft_lines<R, -1>(za, zb, a.plan[2], np, SB, reinterpret_cast<const C *>(a.tw[2]));
+  C *spec = reinterpret_cast<C *>(a.spec) + (size_t)i * a.ny + j0;
+  const size_t plane = (size_t)a.nx * a.ny;
+  for (int e = threadIdx.x; e < a.nzh * np; e += blockDim.x) {
+    const int p = e % np, m = e / np;
+    const C zm = res[m * SB + p];
+    const C zc = res[((nz - m) % nz) * SB + p];
+    const C x1 = {R(0.5) * (zm.re + zc.re), R(0.5) * (zm.im - zc.im)};
+    const C x2 = {R(0.5) * (zm.im + zc.im), R(0.5) * (zc.re - zm.re)};
+    C *dst = spec + m * plane + 2 * p;
+    dst[0] = x1;
+    dst[1] = x2;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K2 / K4: FFT along y of the contiguous lines spec[m][i][:].
+// ---------------------------------------------------------------------------------------
+template <typename R, int DIR>
+__global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = a.ny;
+  const int L = y_lines_per_cta<R>(n);
+  const int SB = L + 1;
+  const size_t total = (size_t)a.nzh * a.nx;
+  const size_t l0 = (size_t)blockIdx.x * L;
+  const int nl = (int)min((size_t)L, total - l0);
+  C *za = reinterpret_cast<C *>(smem_raw);
+  C *zb = za + n * SB;
+  C *spec = reinterpret_cast<C *>(a.spec) + l0 * n;
+  for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
+    const int l = e / n, k = e - l * n;
+    za[k * SB + l] = spec[e];
+  }
+  __syncthreads();
+  const C *res = fft_lines<R, DIR>(za, zb, a.plan[1], nl, SB, reinterpret_cast<const C *>(a.tw[1]));
+  for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
+    const int l = e / n, k = e - l * n;
+    spec[e] = res[k * SB + l];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K3: for the plane kz = m, lines along x (stride ny), kXCols consecutive ky per CTA:
+// forward FFT along x, multiply by Ut(kx, ky, kz) = 3 kz^2 / |k|^2 - 1 (Ut(0) = 0),
+// inverse FFT along x.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R dipolar_kernel(int ix, int iy, int iz, const KArgs &a) {
+  const double two_pi = 6.283185307179586476925286766559;
+  const int mx = ix <= a.nx / 2 ? ix : ix - a.nx;
+  const int my = iy <= a.ny / 2 ? iy : iy - a.ny;
+  const double kx = two_pi * (double)mx / ((double)a.nx * a.hx);
+  const double ky = two_pi * (double)my / ((double)a.ny * a.hy);
+  const double kz = two_pi * (double)iz / ((double)a.nz * a.hz);
+  if constexpr (sizeof(R) == 8) {
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    return k2 > 0.0 ? 3.0 * kz * kz / k2 - 1.0 : 0.0;
+  } else {
+    const float fx = (float)kx, fy = (float)ky, fz = (float)kz;
+    const float k2 = fx * fx + fy * fy + fz * fz;
+    return k2 > 0.0f ? 3.0f * fz * fz / k2 - 1.0f : 0.0f;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int BX = Tiles<R>::kXCols;
+  constexpr int SB = BX;
+  const int n = a.nx, m = blockIdx.y, j0 = blockIdx.x * BX;
+  const int nb = min(BX, a.ny - j0);
+  C *za = reinterpret_cast<C *>(smem_raw);
+  C *zb = za + n * SB;
+  C *spec = reinterpret_cast<C *>(a.spec) + (size_t)m * a.nx * a.ny + j0;
+  for (int e = threadIdx.x; e < n * nb; e += blockDim.x) {
+    const int b = e % nb, k = e / nb;
+    za[k * SB + b] = spec[(size_t)k * a.ny + b];
+  }
+  __syncthreads();
+  const C *tw = reinterpret_cast<const C *>(a.tw[0]);
+  C *res = fft_lines<R, -1>(za, zb, a.plan[0], nb, SB, tw);
+  for (int e = threadIdx.x; e < n * nb; e += blockDim.x) {
+    const int b = e % nb, k = e / nb;
+    res[k * SB + b] = scale(res[k * SB + b], dipolar_kernel<R>(k, j0 + b, m, a));
+  }
+  __syncthreads();
+  C *other = (res == za) ? zb : za;
+  const C *out = fft_lines<R, +1>(res, other, a.plan[0], nb, SB, tw);
+  for (int e = threadIdx.x; e < n * nb; e += blockDim.x) {
+    const int b = e % nb, k = e / nb;
+    spec[(size_t)k * a.ny + b] = out[k * SB + b];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K5: the z-line kernel.  For kZLines lines (i, j0..): inverse half-spectrum transform
+// along z (C2R, two real lines per complex FFT; the imaginary parts of the kz = 0 and
+// kz = nz/2 bins are dropped), Phi = result / (nx ny nz); then, per zmode, the potential
+// step psi <- s psi e^{-i theta} (real time) or s psi e^{-theta} (imaginary time) with
+// theta = dt (V + g s^2 |psi|^2 + gdd Phi), and the Crank-Nicolson solve along z.
+// ---------------------------------------------------------------------------------------
+template <typename R, typename Coef>
+__global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmode) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int BZ = Tiles<R>::kZLines;
+  constexpr int SB = BZ / 2 + 1;
+  const int nz = a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
+  const int nl = min(BZ, a.ny - j0), np = nl >> 1;
+  const int chunk = a.cn[2].chunk;
+  const int LS = cn_slots(nz, chunk);
+  C *za = reinterpret_cast<C *>(smem_raw);
+  C *zb = za + nz * SB;
+  C *tile = zb + nz * SB;
+  const double s = a.state->s;
+  const R inv_ntot = R(a.inv_ntot);
+  const size_t line0 = (size_t)i * a.ny + j0;
+  const C *res = nullptr;
+
+  if (zmode != kZCnOnly) {
+    const C *spec = reinterpret_cast<const C *>(a.spec) + line0;
+    const size_t plane = (size_t)a.nx * a.ny;
+    const int half = nz / 2;
+    for (int e = threadIdx.x; e < a.nzh * np; e += blockDim.x) {
+      const int p = e % np, m = e / np;
+      C x1 = spec[m * plane + 2 * p];
+      C x2 = spec[m * plane + 2 * p + 1];
+      if (m == 0 || m == half) {
+        x1.im = R(0);
+        x2.im = R(0);
+      }
+      za[m * SB + p] = {x1.re - x2.im, x1.im + x2.re};
+      if (m > 0 && m < half) za[(nz - m) * SB + p] = {x1.re + x2.im, x2.re - x1.im};
+    }
+    __syncthreads();
+    res = fft_lines<R, +1>(za, zb, a.plan[2], np, SB, reinterpret_cast<const C *>(a.tw[2]));
+  }
+
+  if (zmode == kZPhi) {
+    R *out = reinterpret_cast<R *>(a.out) + line0 * nz;
+    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
+      const int b = e / nz, n = e - b * nz;
+      const C z = res[n * SB + (b >> 1)];
+      out[e] = ((b & 1) ? z.im : z.re) * inv_ntot;
+    }
+    return;
+  }
+
+  C *psi = reinterpret_cast<C *>(a.psi) + line0 * nz;
+  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
+    const int b = e / nz, n = e - b * nz;
+    tile[b * LS + cn_slot(n, chunk)] = psi[e];
+  }
+  __syncthreads();
+
+  if (zmode == kZObs) {
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const R sr = R(s);
+    const double x = coordinate(i, a.nx, a.hx);
+    const R ihx2 = R(1.0 / (a.hx * a.hx)), ihy2 = R(1.0 / (a.hy * a.hy)), ihz2 = R(1.0 / (a.hz * a.hz));
+    const C *gpsi = reinterpret_cast<const C *>(a.psi);
+    const size_t sx = (size_t)a.ny * nz;
+    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
+      const int b = e / nz, n = e - b * nz;
+      const int j = j0 + b;
+      const C *row = tile + b * LS;
+      const C c = scale(row[cn_slot(n, chunk)], sr);
+      const C zm = n > 0 ? scale(row[cn_slot(n - 1, chunk)], sr) : czero<R>();
+      const C zp = n < nz - 1 ? scale(row[cn_slot(n + 1, chunk)], sr) : czero<R>();
+      const size_t q = (line0 + b) * nz + n;
+      const C ym = j > 0 ? scale(gpsi[q - nz], sr) : czero<R>();
+      const C yp = j < a.ny - 1 ? scale(gpsi[q + nz], sr) : czero<R>();
+      const C xm = i > 0 ? scale(gpsi[q - sx], sr) : czero<R>();
+      const C xp = i < a.nx - 1 ? scale(gpsi[q + sx], sr) : czero<R>();
+      const C lap = {(xm.re - R(2) * c.re + xp.re) * ihx2 + (ym.re - R(2) * c.re + yp.re) * ihy2 +
+                         (zm.re - R(2) * c.re + zp.re) * ihz2,
+                     (xm.im - R(2) * c.im + xp.im) * ihx2 + (ym.im - R(2) * c.im + yp.im) * ihy2 +
+                         (zm.im - R(2) * c.im + zp.im) * ihz2};
+      const C z = res[n * SB + (b >> 1)];
+      const double phi = (double)(((b & 1) ? z.im : z.re) * inv_ntot);
+      const double dens = (double)c.re * c.re + (double)c.im * c.im;
+      const double y = coordinate(j, a.ny, a.hy), zc = coordinate(n, nz, a.hz);
+      v[0] += dens;
+      v[1] += -0.5 * ((double)c.re * lap.re + (double)c.im * lap.im);
+      v[2] += (a.vx * x * x + a.vy * y * y + a.vz * zc * zc) * dens;
+      v[3] += a.g * dens * dens;
+      v[4] += a.gdd * phi * dens;
+      v[5] += x * x * dens;
+      v[6] += y * y * dens;
+      v[7] += zc * zc * dens;
+    }
+    if (reduce_across_blocks<8>(v, a.partials, &a.state->ticket) && threadIdx.x == 0) {
+      const double dv = a.hx * a.hy * a.hz;
+      DevState *st = a.state;
+      for (int q = 0; q < 8; ++q) st->sums[q] = v[q];
+      const double norm = dv * v[0];
+      const double ekin = dv * v[1], etrap = dv * v[2], econ = 0.5 * dv * v[3], edd = 0.5 * dv * v[4];
+      st->obs[0] = norm;
+      st->obs[1] = dv * (v[1] + v[2] + v[3] + v[4]) / norm;
+      st->obs[2] = ekin + etrap + econ + edd;
+      st->obs[3] = sqrt(v[5] / v[0]);
+      st->obs[4] = sqrt(v[6] / v[0]);
+      st->obs[5] = sqrt(v[7] / v[0]);
+      st->obs[6] = ekin;
+      st->obs[7] = etrap;
+      st->obs[8] = econ;
+      st->obs[9] = edd;
+      bool finite = true;
+      for (int q = 0; q < 10; ++q) finite = finite && isfinite(st->obs[q]);
+      if (!finite) st->flags |= kFlagNonFinite;
+    }
+    return;
+  }
+
+  if (zmode == kZStep || zmode == kZPhaseOnly) {
+    const R sr = R(s);
+    const double x = coordinate(i, a.nx, a.hx);
+    const R vxx = R(a.vx * x * x);
+    const R dt = R(a.dt), g = R(a.g), gdd = R(a.gdd), vy = R(a.vy), vz = R(a.vz);
+    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
+      const int b = e / nz, n = e - b * nz;
+      const int q = b * LS + cn_slot(n, chunk);
+      const C v = scale(tile[q], sr);
+      const C z = res[n * SB + (b >> 1)];
+      const R phi = ((b & 1) ? z.im : z.re) * inv_ntot;
+      const R y = R(coordinate(j0 + b, a.ny, a.hy)), zc = R(coordinate(n, nz, a.hz));
+      const R dens = v.re * v.re + v.im * v.im;
+      const R theta = dt * (vxx + vy * y * y + vz * zc * zc + g * dens + gdd * phi);
+      if (a.imag) {
+        tile[q] = scale(v, exp_r(-theta));
+      } else {
+        R sn, cs;
+        sin_cos(theta, &sn, &cs);
+        tile[q] = {v.re * cs + v.im * sn, v.im * cs - v.re * sn};
+      }
+    }
+    __syncthreads();
+  }
+
+  if (zmode == kZStep || zmode == kZCnOnly) {
+    const Coef c = CnCoef<R, Coef>::make(a.dt / (4.0 * a.hz * a.hz));
+    const Coef *tab = reinterpret_cast<const Coef *>(a.cn[2].tab);
+    for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp)
+      cn_line<R, Coef>(tile + b * LS, 1, a.cn[2].m, chunk, tab, c);
+    __syncthreads();
+  }
+
+  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
+    const int b = e / nz, n = e - b * nz;
+    psi[e] = tile[b * LS + cn_slot(n, chunk)];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K6 / K7: Crank-Nicolson along y (AXIS = 1, lines psi[i][:][k]) or x (AXIS = 0, lines
+// psi[:][j][k]) for kCnCols consecutive k per CTA.  K7 (x) also reduces sum n, x^2 n,
+// y^2 n, z^2 n in FP64 and, in the last block, sets the norm and the pending
+// renormalisation factor s = 1/sqrt(norm) (imaginary time) or 1 (real time).
+// ---------------------------------------------------------------------------------------
+template <typename R, typename Coef, int AXIS>
+__global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce, int renorm) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int B = Tiles<R>::kCnCols;
+  constexpr int SB = B + 1;
+  const int N = AXIS == 0 ? a.nx : a.ny;
+  const double h = AXIS == 0 ? a.hx : a.hy;
+  const int chunk = a.cn[AXIS].chunk;
+  const int k0 = blockIdx.x * B;
+  const int nb = min(B, a.nz - k0);
+  const int fixed = blockIdx.y;
+  size_t base, stride;
+  if (AXIS == 1) {
+    base = (size_t)fixed * a.ny * a.nz + k0;
+    stride = (size_t)a.nz;
+  } else {
+    base = (size_t)fixed * a.nz + k0;
+    stride = (size_t)a.ny * a.nz;
+  }
+  C *tile = reinterpret_cast<C *>(smem_raw);
+  C *psi = reinterpret_cast<C *>(a.psi) + base;
+  for (int e = threadIdx.x; e < N * nb; e += blockDim.x) {
+    const int b = e % nb, n = e / nb;
+    tile[cn_slot(n, chunk) * SB + b] = psi[(size_t)n * stride + b];
+  }
+  __syncthreads();
+  const Coef c = CnCoef<R, Coef>::make(a.dt / (4.0 * h * h));
+  const Coef *tab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
+  for (int b = threadIdx.x / kWarp; b < nb; b += blockDim.x / kWarp)
+    cn_line<R, Coef>(tile + b, SB, a.cn[AXIS].m, chunk, tab, c);
+  __syncthreads();
+  double v[4] = {0, 0, 0, 0};
+  for (int e = threadIdx.x; e < N * nb; e += blockDim.x) {
+    const int b = e % nb, n = e / nb;
+    const C w = tile[cn_slot(n, chunk) * SB + b];
+    psi[(size_t)n * stride + b] = w;
+    if (AXIS == 0 && reduce) {
+      const double d = (double)w.re * w.re + (double)w.im * w.im;
+      const double x = coordinate(n, a.nx, a.hx), y = coordinate(fixed, a.ny, a.hy),
+                   z = coordinate(k0 + b, a.nz, a.hz);
+      v[0] += d;
+      v[1] += x * x * d;
+      v[2] += y * y * d;
+      v[3] += z * z * d;
+    }
+  }
+  if (AXIS == 0 && reduce) {
+    if (reduce_across_blocks<4>(v, a.partials, &a.state->ticket) && threadIdx.x == 0) {
+      DevState *st = a.state;
+      const double norm = a.hx * a.hy * a.hz * v[0];
+      for (int q = 0; q < 4; ++q) st->sums[q] = v[q];
+      st->norm = norm;
+      const bool ok = isfinite(norm) && norm > 0.0;
+      if (!ok) st->flags |= kFlagNonFinite;
+      st->s = (renorm && ok) ? 1.0 / sqrt(norm) : 1.0;
+      st->steps += 1ull;
+    }
+  }
+}
+
+// psi <- s psi, then s <- 1 (set by the last block).
+template <typename R>
+__global__ void k_materialize(KArgs a, size_t count) {
+  using C = cplx<R>;
+  const R s = R(a.state->s);
+  C *psi = reinterpret_cast<C *>(a.psi);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < count; q += (size_t)gridDim.x * blockDim.x)
+    psi[q] = scale(psi[q], s);
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&a.state->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    a.state->s = 1.0;
+    a.state->ticket = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host launchers of one precision.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+struct Impl {
+  using C = cplx<R>;
+  using T = Tiles<R>;
+  static constexpr size_t E = sizeof(C);
+
+  static size_t smem_z_fft(const KArgs &a) { return 2 * (size_t)a.nz * (T::kZLines / 2 + 1) * E; }
+  static size_t smem_k5(const KArgs &a) {
+    return smem_z_fft(a) + (size_t)T::kZLines * cn_slots(a.nz, a.cn[2].chunk) * E;
+  }
+  static size_t smem_y(const KArgs &a) { return 2 * (size_t)a.ny * (y_lines_per_cta<R>(a.ny) + 1) * E; }
+  static size_t smem_x(const KArgs &a) { return 2 * (size_t)a.nx * T::kXCols * E; }
+  static size_t smem_cn(int n, int chunk) { return (size_t)cn_slots(n, chunk) * (T::kCnCols + 1) * E; }
+
+  static dim3 grid_z(const KArgs &a) { return dim3((a.ny + T::kZLines - 1) / T::kZLines, a.nx); }
+  static dim3 grid_cn(const KArgs &a, int axis) {
+    return dim3((a.nz + T::kCnCols - 1) / T::kCnCols, axis == 0 ? a.ny : a.nx);
+  }
+
+  template <typename K>
+  static cudaError_t allow_smem(K kernel) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  }
+
+  static cudaError_t init() {
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) {
+      if (e == cudaSuccess) e = r;
+    };
+    chk(allow_smem(k1_density_r2cz<R>));
+    chk(allow_smem(k_ffty<R, -1>));
+    chk(allow_smem(k_ffty<R, +1>));
+    chk(allow_smem(k3_fftx_dipolar<R>));
+    chk(allow_smem(k5_zline<R, R>));
+    chk(allow_smem(k5_zline<R, C>));
+    chk(allow_smem(k_cn<R, R, 0>));
+    chk(allow_smem(k_cn<R, R, 1>));
+    chk(allow_smem(k_cn<R, C, 0>));
+    chk(allow_smem(k_cn<R, C, 1>));
+    return e;
+  }
+
+  static cudaError_t twiddles(void *tw, int n, cudaStream_t st) {
+    k_twiddles<R><<<(n + 127) / 128, 128, 0, st>>>(reinterpret_cast<C *>(tw), n);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t cn_tables(void *tab, int m, int chunk, double r, int imag, cudaStream_t st) {
+    if (imag) k_cn_tables<R, R><<<1, 1, 0, st>>>(reinterpret_cast<R *>(tab), m, chunk, r, imag);
+    else k_cn_tables<R, C><<<1, 1, 0, st>>>(reinterpret_cast<C *>(tab), m, chunk, r, imag);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t reset_state(DevState *s, cudaStream_t st) {
+    k_reset_state<R><<<1, 32, 0, st>>>(s);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t k1(const KArgs &a, cudaStream_t st) {
+    k1_density_r2cz<R><<<grid_z(a), T::kZThreads, smem_z_fft(a), st>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t k2(const KArgs &a, cudaStream_t st) {
+    const size_t lines = (size_t)a.nzh * a.nx;
+    const int L = y_lines_per_cta<R>(a.ny);
+    k_ffty<R, -1><<<(unsigned)((lines + L - 1) / L), kFftThreads, smem_y(a), st>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t k3(const KArgs &a, cudaStream_t st) {
+    dim3 grid((a.ny + T::kXCols - 1) / T::kXCols, a.nzh);
+    k3_fftx_dipolar<R><<<grid, kFftThreads, smem_x(a), st>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t k4(const KArgs &a, cudaStream_t st) {
+    const size_t lines = (size_t)a.nzh * a.nx;
+    const int L = y_lines_per_cta<R>(a.ny);
+    k_ffty<R, +1><<<(unsigned)((lines + L - 1) / L), kFftThreads, smem_y(a), st>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t k5(const KArgs &a, int zmode, cudaStream_t st) {
+    if (a.imag) k5_zline<R, R><<<grid_z(a), T::kZThreads, smem_k5(a), st>>>(a, zmode);
+    else k5_zline<R, C><<<grid_z(a), T::kZThreads, smem_k5(a), st>>>(a, zmode);
+    return cudaGetLastError();
+  }
+  static cudaError_t k6(const KArgs &a, cudaStream_t st) {
+    const size_t sm = smem_cn(a.ny, a.cn[1].chunk);
+    if (a.imag) k_cn<R, R, 1><<<grid_cn(a, 1), T::kCnThreads, sm, st>>>(a, 0, 0);
+    else k_cn<R, C, 1><<<grid_cn(a, 1), T::kCnThreads, sm, st>>>(a, 0, 0);
+    return cudaGetLastError();
+  }
+  static cudaError_t k7(const KArgs &a, int reduce, int renorm, cudaStream_t st) {
+    const size_t sm = smem_cn(a.nx, a.cn[0].chunk);
+    if (a.imag) k_cn<R, R, 0><<<grid_cn(a, 0), T::kCnThreads, sm, st>>>(a, reduce, renorm);
+    else k_cn<R, C, 0><<<grid_cn(a, 0), T::kCnThreads, sm, st>>>(a, reduce, renorm);
+    return cudaGetLastError();
+  }
+  static cudaError_t materialize(const KArgs &a, cudaStream_t st) {
+    const size_t count = (size_t)a.nx * a.ny * a.nz;
+    size_t blocks = (count + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_materialize<R><<<(unsigned)blocks, 256, 0, st>>>(a, count);
+    return cudaGetLastError();
+  }
+  static int max_blocks(const KArgs &a) {
+    const dim3 z = grid_z(a), x = grid_cn(a, 0);
+    const int bz = (int)(z.x * z.y), bx = (int)(x.x * x.y);
+    return bz > bx ? bz : bx;
+  }
+
+  static const KernelSet *set() {
+    static const KernelSet ks = {(int)E, &init, &twiddles, &cn_tables, &reset_state, &k1, &k2, &k3, &k4, &k5, &k6, &k7,
+                                 &materialize, &max_blocks};
+    return &ks;
+  }
+};
+
+}  // namespace dgpe

@@ -1,0 +1,103 @@
+// Internal interface between the C-ABI host code (dgpe_api.cu) and the kernel translation
+// units (kernels_f64.cu, kernels_f32.cu).  Plain structs only; no CUDA device code here.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace dgpe {
+
+constexpr int kMaxStages = 12;
+constexpr int kWarp = 32;
+constexpr int kCnMaxChunk = 16;   // interior points per lane of the chunked Thomas solve
+
+// Mixed-radix plan of one transform length: n = radix[0] * radix[1] * ...
+struct FftPlan {
+  int n;
+  int nstages;
+  int radix[kMaxStages];
+};
+
+// Crank-Nicolson factor tables of one direction (interior size m = n - 2, chunk length c):
+// five arrays of m coefficients [alpha | beta | P | H | G] (complex in real time, real in
+// imaginary time), element type matching the kernel precision.
+struct CnTab {
+  const void *tab;
+  int m;
+  int chunk;
+};
+
+// Device-resident solver state (lives in the workspace).
+struct DevState {
+  double s;          // pending renormalisation factor: the state is s * psi_buf
+  double norm;       // hx hy hz sum |psi_buf|^2 after the last full step
+  double sums[8];    // last reduction (step: n, x^2 n, y^2 n, z^2 n; obs: 8 terms)
+  double obs[12];    // observables of the last dgpe_observables call
+  unsigned int flags;   // bit 0: non-finite norm
+  unsigned int ticket;  // last-block-done counter of the fused reductions
+  unsigned long long steps;
+};
+constexpr unsigned kFlagNonFinite = 1u;
+
+// Everything a kernel needs, passed by value.
+struct KArgs {
+  int nx, ny, nz, nzh;         // nzh = nz/2 + 1 (half-spectrum length along z)
+  double hx, hy, hz;
+  double dt, g, gdd;
+  double vx, vy, vz;           // 0.5 * nu_d^2
+  double inv_ntot;             // 1 / (nx ny nz)
+  int imag;                    // 1 = imaginary time
+  void *psi;                   // [nx][ny][nz] complex
+  void *spec;                  // [nzh][nx][ny] complex, the z-half-spectrum-major layout
+  DevState *state;
+  double *partials;            // per-block reduction partials
+  const void *tw[3];           // twiddles e^{-2 pi i t / n_d}, t < n_d, for d = x, y, z
+  FftPlan plan[3];
+  CnTab cn[3];
+  void *out;                   // optional output (Phi for get_phi)
+};
+
+// Modes of the z-line kernel (C2R along z + potential step + CN along z).
+enum ZMode : int {
+  kZStep = 0,        // phase, then CN-z
+  kZPhaseOnly = 1,   // phase only
+  kZCnOnly = 2,      // CN-z only (no transform)
+  kZPhi = 3,         // write Phi to args.out
+  kZObs = 4,         // observables reduction
+};
+
+// Kernel identifiers (timing records, launch table).
+enum KernelId : int {
+  kK1DensityR2Cz = 0,
+  kK2FftY,
+  kK3FftXDipolar,
+  kK4IfftY,
+  kK5C2RzPhaseCnz,
+  kK6CnY,
+  kK7CnXReduce,
+  kKMaterialize,
+  kKObs,
+  kNumKernels
+};
+
+// Host-side launchers of one precision (implemented in kernels_f64.cu / kernels_f32.cu).
+struct KernelSet {
+  int elem_bytes;  // sizeof complex element
+  cudaError_t (*init)();
+  cudaError_t (*twiddles)(void *tw, int n, cudaStream_t st);
+  cudaError_t (*cn_tables)(void *tab, int m, int chunk, double r, int imag, cudaStream_t st);
+  cudaError_t (*reset_state)(DevState *st_ptr, cudaStream_t st);
+  cudaError_t (*k1)(const KArgs &a, cudaStream_t st);
+  cudaError_t (*k2)(const KArgs &a, cudaStream_t st);   // forward FFT along y
+  cudaError_t (*k3)(const KArgs &a, cudaStream_t st);   // FFT-x, x Ut, IFFT-x
+  cudaError_t (*k4)(const KArgs &a, cudaStream_t st);   // inverse FFT along y
+  cudaError_t (*k5)(const KArgs &a, int zmode, cudaStream_t st);
+  cudaError_t (*k6)(const KArgs &a, cudaStream_t st);   // CN-y
+  cudaError_t (*k7)(const KArgs &a, int reduce, int renorm, cudaStream_t st);  // CN-x
+  cudaError_t (*materialize)(const KArgs &a, cudaStream_t st);
+  int (*max_blocks)(const KArgs &a);   // upper bound on blocks of any reducing kernel
+};
+
+const KernelSet *kernels_f64();
+const KernelSet *kernels_f32();
+
+}  // namespace dgpe

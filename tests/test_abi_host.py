@@ -1,0 +1,89 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every
+function include/dgpe.h declares, and rejects invalid parameters before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1610_05329_gb300 import abi, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return abi.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "dgpe.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dgpe_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_api():
+    names = declared_functions()
+    for n in ["dgpe_create", "dgpe_set_params", "dgpe_set_psi", "dgpe_get_psi", "dgpe_step",
+              "dgpe_observables", "dgpe_sync", "dgpe_strerror", "dgpe_destroy", "dgpe_workspace_bytes"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert {s[0] for s in abi._SIGNATURES} == set(declared_functions())
+
+
+def test_strerror(lib):
+    assert abi.strerror(0) == "ok"
+    assert "invalid" in abi.strerror(abi.DGPE_EINVAL)
+    assert abi.strerror(-999) == "unknown error code"
+
+
+def params(**kw):
+    base = dict(shape=(16, 16, 16), h=0.2, dt=0.004, mode=abi.DGPE_IMAG_TIME, precision=abi.DGPE_FP64,
+                nu=(1, 1, 1), g=20, gdd=10)
+    base.update(kw)
+    return abi.make_params(**base)
+
+
+def test_workspace_bytes(lib):
+    n64 = abi.dgpe_workspace_bytes(params(shape=(64, 64, 64)))
+    n32 = abi.dgpe_workspace_bytes(params(shape=(64, 64, 64), precision=abi.DGPE_MIXED))
+    psi64 = 64 ** 3 * 16
+    spec64 = 33 * 64 * 64 * 16
+    assert psi64 + spec64 <= n64 < psi64 + spec64 + (1 << 20)
+    assert n32 < n64 * 0.55
+
+
+@pytest.mark.parametrize("bad", [
+    dict(shape=(5, 16, 16)), dict(shape=(16, 14, 16)), dict(shape=(16, 16, 2)), dict(shape=(1024, 16, 16)),
+    dict(shape=(16, 16, 10)), dict(h=0.0), dict(h=(0.2, -0.1, 0.2)), dict(h=float("nan")), dict(dt=0.0),
+    dict(dt=-0.01), dict(dt=float("inf")), dict(mode=2), dict(precision=7), dict(g=float("nan")),
+    dict(nu=(1, float("inf"), 1)),
+])
+def test_create_rejects_invalid_parameters_without_touching_the_gpu(lib, bad):
+    p = params(**bad)
+    ctx = ctypes.c_void_p()
+    rc = lib.dgpe_create(ctypes.byref(p), None, ctypes.byref(ctx))
+    assert rc == abi.DGPE_EINVAL
+    assert not ctx.value
+
+
+def test_null_arguments(lib):
+    assert lib.dgpe_create(None, None, None) == abi.DGPE_EINVAL
+    assert lib.dgpe_step(None, 1) == abi.DGPE_EINVAL
+    assert lib.dgpe_sync(None) == abi.DGPE_EINVAL
+    lib.dgpe_destroy(None)
+    n = ctypes.c_size_t()
+    assert lib.dgpe_workspace_bytes(ctypes.byref(params(shape=(7, 8, 8))), ctypes.byref(n)) == abi.DGPE_EINVAL
+
+
+def test_too_small_workspace_is_rejected(lib):
+    p = params()
+    p.workspace = 1 << 20
+    p.workspace_bytes = 16
+    ctx = ctypes.c_void_p()
+    assert lib.dgpe_create(ctypes.byref(p), None, ctypes.byref(ctx)) == abi.DGPE_ENOMEM

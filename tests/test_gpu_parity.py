@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on the same
+seeded inputs.  FP64 bar: relative L2 error of psi <= 1e-10 (the stated tolerance of the
+FP64 path); sub-steps are held to 1e-12.  Shapes cover several tiles, ragged tails
+(sizes that are not multiples of the 8/16-wide tiles), the smallest size 4 and the largest
+line length 512 along each axis."""
+import numpy as np
+import pytest
+
+from paper_1610_05329_gb300 import abi, inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_STEP_TOL = 1e-10
+FP64_SUB_TOL = 1e-12
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1610_05329_gb300 import build
+    build.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    abi.load()
+
+
+def make(orc, shape, h, dt, mode, nu=(1.0, 1.1, 0.9), g=25.0, gdd=15.0, precision=abi.DGPE_FP64):
+    gpu = abi.Condensate(shape, h, dt, mode=mode, precision=precision, nu=nu, g=g, gdd=gdd)
+    p = orc.make_params(shape, h, dt, orc.IMAG_TIME if mode == abi.DGPE_IMAG_TIME else orc.REAL_TIME, nu, g, gdd)
+    return gpu, p
+
+
+def state(shape, h, seed=3):
+    # a trapped-cloud shape plus seeded noise on both parts (every sub-step sees a complex field)
+    psi = inputs.gaussian_psi(shape, h, width=1.0, noise=1e-3, seed=seed)
+    psi = psi + 1e-3j * inputs.random_psi(shape, seed=seed + 1).real
+    return np.ascontiguousarray(psi)
+
+
+SHAPES = [((4, 6, 8), 0.9), ((8, 12, 16), 0.6), ((16, 16, 16), 0.5), ((24, 18, 36), 0.35),
+          ((32, 48, 24), 0.3)]
+
+
+@pytest.mark.parametrize("shape,h", SHAPES)
+@pytest.mark.parametrize("mode", [abi.DGPE_REAL_TIME, abi.DGPE_IMAG_TIME])
+def test_cn_sweeps_match_oracle(orc, shape, h, mode):
+    psi = state(shape, h)
+    gpu, p = make(orc, shape, h, 0.01, mode)
+    for which, axis in [(abi.DGPE_SUB_CN_X, 0), (abi.DGPE_SUB_CN_Y, 1), (abi.DGPE_SUB_CN_Z, 2)]:
+        gpu.set_psi(psi)
+        gpu.substep(which)
+        got = gpu.get_psi()
+        want = orc.cn_sweep(p, psi, axis)
+        assert rel(got, want) < FP64_SUB_TOL, (which, rel(got, want))
+    gpu.close()
+
+
+@pytest.mark.parametrize("shape,h", SHAPES)
+def test_dipolar_potential_matches_oracle(orc, shape, h):
+    psi = state(shape, h)
+    gpu, p = make(orc, shape, h, 0.01, abi.DGPE_REAL_TIME)
+    gpu.set_psi(psi)
+    got = gpu.phi()
+    want = orc.dipolar_phi(p, np.abs(psi) ** 2)
+    assert rel(got, want) < FP64_SUB_TOL
+    gpu.close()
+
+
+@pytest.mark.parametrize("shape,h", SHAPES)
+@pytest.mark.parametrize("mode", [abi.DGPE_REAL_TIME, abi.DGPE_IMAG_TIME])
+def test_potential_step_matches_oracle(orc, shape, h, mode):
+    psi = state(shape, h)
+    gpu, p = make(orc, shape, h, 0.02, mode)
+    gpu.set_psi(psi)
+    gpu.substep(abi.DGPE_SUB_POTENTIAL)
+    assert rel(gpu.get_psi(), orc.potential_step(p, psi)) < FP64_SUB_TOL
+    gpu.close()
+
+
+@pytest.mark.parametrize("shape,h", SHAPES)
+def test_observables_match_oracle(orc, shape, h):
+    psi = state(shape, h)
+    gpu, p = make(orc, shape, h, 0.01, abi.DGPE_IMAG_TIME)
+    gpu.set_psi(psi)
+    got, want = gpu.observables(), orc.observables(p, psi)
+    for k in ("norm", "mu", "energy", "e_kin", "e_trap", "e_contact", "e_dipolar"):
+        assert got[k] == pytest.approx(want[k], rel=1e-11, abs=1e-13), k
+    for d in range(3):
+        assert got["rms"][d] == pytest.approx(want["rms"][d], rel=1e-11)
+    gpu.close()
+
+
+@pytest.mark.parametrize("shape,h", SHAPES)
+@pytest.mark.parametrize("mode", [abi.DGPE_REAL_TIME, abi.DGPE_IMAG_TIME])
+def test_full_steps_match_oracle(orc, shape, h, mode):
+    psi = state(shape, h)
+    gpu, p = make(orc, shape, h, 0.005, mode)
+    gpu.set_psi(psi)
+    gpu.step(12)
+    got = gpu.get_psi()
+    want = orc.step(p, psi, 12)
+    assert rel(got, want) < FP64_STEP_TOL
+    gpu.close()
+
+
+@pytest.mark.parametrize("shape", [(512, 6, 8), (6, 512, 8), (8, 6, 512)])
+def test_longest_lines(orc, shape):
+    psi = state(shape, 0.05)
+    gpu, p = make(orc, shape, 0.05, 0.001, abi.DGPE_REAL_TIME)
+    gpu.set_psi(psi)
+    gpu.step(2)
+    assert rel(gpu.get_psi(), orc.step(p, psi, 2)) < FP64_STEP_TOL
+    gpu.close()
+
+
+def test_imaginary_time_64cubed_200_steps(orc):
+    """The 64^3 imaginary-time workload (h = 0.2, dt = 0.004, nu = 1, g = 20, gdd = 10,
+    Gaussian + 1e-3 noise with seed 1, 200 steps) against the oracle: psi, mu, E, rms."""
+    shape, h = (64, 64, 64), 0.2
+    psi0 = inputs.gaussian_psi(shape, h, noise=1e-3, seed=1)
+    gpu, p = make(orc, shape, h, 0.004, abi.DGPE_IMAG_TIME, nu=(1, 1, 1), g=20, gdd=10)
+    gpu.set_psi(psi0)
+    gpu.step(200)
+    got = gpu.get_psi()
+    want = orc.step(p, psi0, 200)
+    assert rel(got, want) < FP64_STEP_TOL
+    og, ow = gpu.observables(), orc.observables(p, want)
+    for k in ("norm", "mu", "energy"):
+        assert og[k] == pytest.approx(ow[k], rel=1e-11)
+    gpu.close()
+
+
+def test_set_params_quench_matches_oracle(orc):
+    shape, h = (16, 24, 20), 0.45
+    psi = state(shape, h)
+    gpu, p_im = make(orc, shape, h, 0.01, abi.DGPE_IMAG_TIME)
+    gpu.set_psi(psi)
+    gpu.step(5)
+    gpu.set_params(mode=abi.DGPE_REAL_TIME, dt=0.003, g=12.0)
+    gpu.step(5)
+    want = orc.step(p_im, psi, 5)
+    p_re = orc.make_params(shape, h, 0.003, orc.REAL_TIME, (1.0, 1.1, 0.9), 12.0, 15.0)
+    want = orc.step(p_re, want, 5)
+    assert rel(gpu.get_psi(), want) < FP64_STEP_TOL
+    gpu.close()
+
+
+def test_device_psi_roundtrip_and_real_time_norm():
+    import torch
+    shape, h = (32, 32, 32), 0.3
+    gpu = abi.Condensate(shape, h, 0.002, mode=abi.DGPE_REAL_TIME, nu=(1, 1, 1), g=30, gdd=10)
+    psi = torch.from_numpy(inputs.gaussian_psi(shape, h, seed=5)).cuda()
+    gpu.set_psi(psi)
+    n0 = gpu.observables()["norm"]
+    out = gpu.get_psi(host=False)
+    # the first sweeps zero the walls; compare the norm after one step onwards
+    gpu.step(1)
+    n1 = gpu.observables()["norm"]
+    gpu.step(100)
+    n2 = gpu.observables()["norm"]
+    assert abs(n2 - n1) < 1e-12 * n1
+    assert torch.equal(out, psi)
+    assert n0 > 0
+    gpu.close()
+
+
+def test_nonfinite_state_is_reported():
+    shape, h = (16, 16, 16), 0.4
+    gpu = abi.Condensate(shape, h, 0.01, mode=abi.DGPE_IMAG_TIME, g=10, gdd=5)
+    psi = inputs.gaussian_psi(shape, h)
+    psi[8, 8, 8] = np.nan
+    gpu.set_psi(psi)
+    gpu.step(1)
+    with pytest.raises(abi.DgpeError) as e:
+        gpu.sync()
+    assert e.value.code == abi.DGPE_ENONFINITE
+    # set_psi clears the latched error; the context stays usable
+    gpu.set_psi(inputs.gaussian_psi(shape, h))
+    gpu.step(1)
+    gpu.sync()
+    gpu.close()
+
+
+@pytest.mark.parametrize("mode", [abi.DGPE_REAL_TIME, abi.DGPE_IMAG_TIME])
+def test_mixed_precision_error_vs_oracle(orc, mode):
+    """FP32 path (complex64 psi, FP32 FFT/phase/CN, FP64 reductions): errors against the
+    FP64 oracle after 20 steps.  Bounds: FP32 round-off (6e-8) times the step count and
+    the transform depth, with margin."""
+    shape, h = (32, 24, 40), 0.3
+    psi = state(shape, h)
+    gpu, p = make(orc, shape, h, 0.005, mode, precision=abi.DGPE_MIXED)
+    gpu.set_psi(psi.astype(np.complex64))
+    gpu.step(20)
+    got = gpu.get_psi().astype(np.complex128)
+    want = orc.step(p, psi.astype(np.complex64).astype(np.complex128), 20)
+    err = rel(got, want)
+    assert err < 2e-5, err
+    og, ow = gpu.observables(), orc.observables(p, want)
+    assert og["mu"] == pytest.approx(ow["mu"], rel=2e-5)
+    assert og["energy"] == pytest.approx(ow["energy"], rel=2e-5)
+    gpu.close()
