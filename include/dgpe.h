@@ -161,6 +161,10 @@ int dgpe_kernel_times(dgpe_ctx *ctx, dgpe_kernel_time *out, int max, int *n);
 /* Static text for an error code. */
 const char *dgpe_strerror(int code);
 
+/* Name and text of the last CUDA runtime error this thread's calls met (empty if none);
+ * valid until the next call on the same thread. */
+const char *dgpe_last_cuda_error(void);
+
 /* Free the context and whatever it allocated (not a caller-owned workspace). NULL is ok. */
 void dgpe_destroy(dgpe_ctx *ctx);
 

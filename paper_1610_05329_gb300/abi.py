@@ -60,7 +60,10 @@ class dgpe_kernel_time(ctypes.Structure):
 
 class DgpeError(RuntimeError):
     def __init__(self, code, what):
-        super().__init__("%s: %s (%d)" % (what, strerror(code), code))
+        msg = "%s: %s (%d)" % (what, strerror(code), code)
+        if code == DGPE_ECUDA:
+            msg += " [%s]" % dgpe_last_cuda_error()
+        super().__init__(msg)
         self.code = code
 
 
@@ -83,6 +86,7 @@ _SIGNATURES = [
     ("dgpe_set_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("dgpe_kernel_times", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_kernel_time), ctypes.c_int, _P(ctypes.c_int)]),
     ("dgpe_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("dgpe_last_cuda_error", ctypes.c_char_p, []),
     ("dgpe_destroy", None, [ctypes.c_void_p]),
 ]
 
@@ -111,6 +115,10 @@ def _check(rc, what):
 
 def strerror(code):
     return load().dgpe_strerror(int(code)).decode()
+
+
+def dgpe_last_cuda_error():
+    return load().dgpe_last_cuda_error().decode()
 
 
 def make_params(shape, h, dt, mode=DGPE_IMAG_TIME, precision=DGPE_FP64, nu=(1.0, 1.0, 1.0), g=0.0, gdd=0.0,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <new>
@@ -148,8 +149,11 @@ void set_physics(KArgs &a, const dgpe_params *p) {
   a.imag = p->mode == DGPE_IMAG_TIME;
 }
 
+thread_local char g_last_cuda_error[128] = "";
+
 int map_cuda(cudaError_t e) {
   if (e == cudaSuccess) return DGPE_OK;
+  snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return DGPE_ENOMEM;
   return DGPE_ECUDA;
 }
@@ -327,6 +331,8 @@ const char *dgpe_strerror(int code) {
     default: return "unknown error code";
   }
 }
+
+const char *dgpe_last_cuda_error(void) { return g_last_cuda_error; }
 
 int dgpe_workspace_bytes(const dgpe_params *p, size_t *bytes) {
   if (!p || !bytes) return DGPE_EINVAL;

@@ -884,9 +884,17 @@ struct Impl {
     return dim3((a.nz + T::kCnCols - 1) / T::kCnCols, axis == 0 ? a.ny : a.nx);
   }
 
+  // Allow each kernel the device's opt-in shared memory minus its static shared memory.
   template <typename K>
   static cudaError_t allow_smem(K kernel) {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
   }
 
   static cudaError_t init() {
