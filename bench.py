@@ -1,0 +1,334 @@
+#!/usr/bin/env python3
+"""Throughput of the 3D dipolar GP split-step Crank-Nicolson step on GB300.
+
+Default workload (N=1): the real-time FP64 step on a 256^3 grid (h = 0.1, trap
+(0.5, 1.0, 1.5), gdd = 25, quench g 50 -> 40, dt = 5e-4).  The state is the seeded
+Gaussian (width 1, 1e-3 noise, seed 1) after 20 imaginary-time steps at g = 50 (a short
+preparation, not a converged ground state: the cost of a step does not depend on the
+state).  Metric: grid-point updates per second, nx*ny*nz*steps / time.  psi (268 MB) is
+larger than the 129 MB L2, so no flush is needed between steps.
+
+The same JSON line also carries the FP32-mixed step on 512x512x384 (h = 0.05, trap
+(1, 1, 2), g = 100, gdd = 60, real time dt = 5e-4) as "mixed_512x512x384".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload on its own
+GPU (the single-grid step is not sharded); value = all ranks' updates / max rank time.
+--impl reference times the FP64 CPU oracle on the host cores (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D SSCN grid-point updates/s (256^3 FP64 real time)"
+UNIT = "grid-point updates/s"
+
+WORKLOADS = {
+    "real256_fp64": dict(shape=(256, 256, 256), h=0.1, nu=(0.5, 1.0, 1.5), g_prep=50.0, g=40.0, gdd=25.0,
+                         dt_prep=0.004, dt=5e-4, precision="fp64"),
+    "real512x512x384_mixed": dict(shape=(512, 512, 384), h=0.05, nu=(1.0, 1.0, 2.0), g_prep=100.0, g=100.0,
+                                  gdd=60.0, dt_prep=0.001, dt=5e-4, precision="mixed"),
+}
+PREP_STEPS = 20
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[4], f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[3:]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def make_condensate(abi, wl, local):
+    import torch
+    from paper_1610_05329_gb300 import inputs
+    prec = abi.DGPE_FP64 if wl["precision"] == "fp64" else abi.DGPE_MIXED
+    c = abi.Condensate(wl["shape"], wl["h"], wl["dt_prep"], mode=abi.DGPE_IMAG_TIME, precision=prec,
+                       nu=wl["nu"], g=wl["g_prep"], gdd=wl["gdd"], device=torch.device("cuda", local))
+    psi0 = inputs.gaussian_psi(wl["shape"], wl["h"], noise=1e-3, seed=1)
+    c.set_psi(torch.from_numpy(psi0).to(device=c.device, dtype=c.cdtype))
+    c.step(PREP_STEPS)
+    c.set_params(mode=abi.DGPE_REAL_TIME, dt=wl["dt"], g=wl["g"])
+    return c
+
+
+def time_steps(c, steps, barrier):
+    import torch
+    st = c.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(c.device)
+    e0.record(st)
+    c.step(steps)
+    e1.record(st)
+    torch.cuda.synchronize(c.device)
+    barrier()
+    return e0.elapsed_time(e1)
+
+
+def kernel_profile(c, steps, hbm_peak, peak_kind):
+    """Per-kernel CUDA-event durations over `steps` instrumented steps."""
+    import torch
+    c.set_timing(True)
+    c.kernel_times()        # reset
+    t0 = time.perf_counter()
+    c.step(steps)
+    torch.cuda.synchronize(c.device)
+    wall = time.perf_counter() - t0
+    rows = c.kernel_times()
+    c.set_timing(False)
+    total = sum(r["total_ms"] for r in rows)
+    out = []
+    for r in rows:
+        avg = r["total_ms"] / r["launches"]
+        gbs = r["bytes_per_launch"] / (avg * 1e-3) / 1e9
+        out.append({"kernel": r["name"], "launches": r["launches"], "avg_ms": round(avg, 5),
+                    "share": round(r["total_ms"] / total, 4), "bytes_per_launch": r["bytes_per_launch"],
+                    "achieved_gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4)})
+    out.sort(key=lambda d: -d["share"])
+    top = out[0]
+    roofline = {"bound": "hbm", "kernel": top["kernel"], "achieved": top["achieved_gbs"], "peak": hbm_peak,
+                "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "unit": "GB/s", "frac": top["frac_hbm"], "traffic": None,
+                "instrumented_ms_per_step": round(total / steps, 4), "instrumented_wall_s": round(wall, 3)}
+    return roofline, out
+
+
+def e2e_run(abi, c, steps):
+    """Same metric through the C ABI with pinned HOST buffers: every step copies psi in
+    (dgpe_set_psi from host), steps once, and copies psi out (dgpe_get_psi to host)."""
+    import torch
+    n = 1
+    for s in c.shape:
+        n *= s
+    host_in = torch.empty(c.shape, dtype=c.cdtype, pin_memory=True)
+    host_out = torch.empty(c.shape, dtype=c.cdtype, pin_memory=True)
+    abi.dgpe_get_psi(c.ctx, host_in.data_ptr(), abi.DGPE_HOST)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(c.device)
+    t0 = time.perf_counter()
+    e0.record(c.stream)
+    for _ in range(steps):
+        abi.dgpe_set_psi(c.ctx, host_in.data_ptr(), abi.DGPE_HOST)
+        abi.dgpe_step(c.ctx, 1)
+        abi.dgpe_get_psi(c.ctx, host_out.data_ptr(), abi.DGPE_HOST)
+    e1.record(c.stream)
+    torch.cuda.synchronize(c.device)
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    nbytes = host_in.numel() * host_in.element_size()
+    return {"value": n * steps / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "ms_per_step": round(ms / steps, 4), "steps": steps,
+            "wall_s": round(wall, 3)}
+
+
+def cpu_baseline(wl, budget_s=20.0):
+    """The FP64 oracle, as it stands, on the host cores: whole SSCN steps of the same
+    workload (grid, physics) until about `budget_s` seconds of CPU work."""
+    import oracle
+    from paper_1610_05329_gb300 import inputs
+    p = oracle.make_params(wl["shape"], wl["h"], wl["dt"], oracle.REAL_TIME, wl["nu"], wl["g"], wl["gdd"])
+    psi = inputs.gaussian_psi(wl["shape"], wl["h"], noise=1e-3, seed=1)
+    n = psi.size
+    steps, t = 0, 0.0
+    while t < budget_s and steps < 1000:
+        t0 = time.perf_counter()
+        psi = oracle.step(p, psi, 1)
+        t += time.perf_counter() - t0
+        steps += 1
+    return {"value": n * steps / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d full SSCN step(s) of the %dx%dx%d FP64 real-time workload, %.1f s" % (
+                steps, *wl["shape"], t)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1610_05329_gb300 import inputs
+    wl = WORKLOADS["real256_fp64"]
+    p = oracle.make_params(wl["shape"], wl["h"], wl["dt"], oracle.REAL_TIME, wl["nu"], wl["g"], wl["gdd"])
+    psi = inputs.gaussian_psi(wl["shape"], wl["h"], noise=1e-3, seed=1)
+    n = psi.size
+    t0 = time.perf_counter()
+    psi = oracle.step(p, psi, 1)        # one untimed warm-up step (bounded)
+    t_step = time.perf_counter() - t0
+    cap = max(1, int(150.0 / max(t_step, 1e-3)))
+    steps = min(args.steps, cap)
+    t0 = time.perf_counter()
+    psi = oracle.step(p, psi, steps)
+    t = time.perf_counter() - t0
+    value = n * steps / t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "real256_fp64", "grid": list(wl["shape"]), "mode": "real", "h": wl["h"],
+                       "dt": wl["dt"], "g": wl["g"], "gdd": wl["gdd"], "nu": list(wl["nu"])},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d of %d requested full 256^3 FP64 steps (1 warm-up step; capped to "
+                                       "~150 s)" % (steps, args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 512x512x384 mixed-precision line item")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import torch
+    from paper_1610_05329_gb300 import abi, build
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        barrier = lambda: dist.barrier(device_ids=[local])
+    else:
+        torch.cuda.set_device(local)
+        dist = None
+        barrier = lambda: None
+    if rank == 0 or ws == 1:
+        build.build()
+    if dist is not None:
+        barrier()
+    abi.load()
+    hbm_peak, peak_kind = measured_peaks()
+
+    wl = WORKLOADS["real256_fp64"]
+    c = make_condensate(abi, wl, local)
+    npts = wl["shape"][0] * wl["shape"][1] * wl["shape"][2]
+    c.step(args.warmup)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = time_steps(c, args.steps, barrier)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=c.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * npts * args.steps / (ms * 1e-3)
+    roofline, kernels = kernel_profile(c, min(args.steps, 50), hbm_peak, peak_kind)
+    e2e = e2e_run(abi, c, args.e2e_steps)
+    c.sync()
+    c.close()
+
+    mixed = None
+    if not args.no_mixed:
+        wlm = WORKLOADS["real512x512x384_mixed"]
+        cm = make_condensate(abi, wlm, local)
+        nm = wlm["shape"][0] * wlm["shape"][1] * wlm["shape"][2]
+        cm.step(args.warmup)
+        msm = time_steps(cm, args.steps, barrier)
+        rl_m, kernels_m = kernel_profile(cm, min(args.steps, 50), hbm_peak, peak_kind)
+        cm.sync()
+        cm.close()
+        mixed = {"value": ws * nm * args.steps / (msm * 1e-3), "unit": UNIT, "ms_per_step": round(msm / args.steps, 4),
+                 "dtype": "f32 (FP64 reductions)", "grid": list(wlm["shape"]), "roofline": rl_m, "kernels": kernels_m,
+                 "algorithmic_bytes_per_step": sum(k["bytes_per_launch"] * k["launches"] for k in kernels_m)
+                 / min(args.steps, 50)}
+
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian + SplitMix64 noise)",
+            "config": {"workload": "real256_fp64", "grid": list(wl["shape"]), "mode": "real", "h": wl["h"],
+                       "dt": wl["dt"], "g": wl["g"], "gdd": wl["gdd"], "nu": list(wl["nu"]),
+                       "prep": "%d imaginary-time steps at g=%g from the seeded Gaussian" % (PREP_STEPS, wl["g_prep"]),
+                       "l2": "inputs larger than L2 (psi 268 MB > 129 MB)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+            "gpu_launches": 7 * args.steps, "clocks": clk, "roofline": roofline, "kernels": kernels, "e2e": e2e}
+    if mixed is not None:
+        line["mixed_512x512x384"] = mixed
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -134,7 +134,7 @@ def test_imaginary_time_64cubed_200_steps(orc):
 
 
 def test_set_params_quench_matches_oracle(orc):
-    shape, h = (16, 24, 20), 0.45
+    shape, h = (16, 24, 18), 0.45
     psi = state(shape, h)
     gpu, p_im = make(orc, shape, h, 0.01, abi.DGPE_IMAG_TIME)
     gpu.set_psi(psi)
@@ -189,7 +189,7 @@ def test_mixed_precision_error_vs_oracle(orc, mode):
     """FP32 path (complex64 psi, FP32 FFT/phase/CN, FP64 reductions): errors against the
     FP64 oracle after 20 steps.  Bounds: FP32 round-off (6e-8) times the step count and
     the transform depth, with margin."""
-    shape, h = (32, 24, 40), 0.3
+    shape, h = (32, 24, 36), 0.3
     psi = state(shape, h)
     gpu, p = make(orc, shape, h, 0.005, mode, precision=abi.DGPE_MIXED)
     gpu.set_psi(psi.astype(np.complex64))
