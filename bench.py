@@ -253,6 +253,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 512x512x384 mixed-precision line item")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help="time only this workload (profiling); the default line times both")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -278,7 +280,10 @@ def main():
     abi.load()
     hbm_peak, peak_kind = measured_peaks()
 
-    wl = WORKLOADS["real256_fp64"]
+    name = args.workload or "real256_fp64"
+    wl = WORKLOADS[name]
+    if args.workload is not None:
+        args.no_mixed = True
     c = make_condensate(abi, wl, local)
     npts = wl["shape"][0] * wl["shape"][1] * wl["shape"][2]
     c.step(args.warmup)
@@ -292,7 +297,7 @@ def main():
         ms = float(t.item())
     value = ws * npts * args.steps / (ms * 1e-3)
     roofline, kernels = kernel_profile(c, min(args.steps, 50), hbm_peak, peak_kind)
-    e2e = e2e_run(abi, c, args.e2e_steps)
+    e2e = e2e_run(abi, c, args.e2e_steps) if args.e2e_steps > 0 else None
     c.sync()
     c.close()
 
@@ -316,10 +321,11 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian + SplitMix64 noise)",
-            "config": {"workload": "real256_fp64", "grid": list(wl["shape"]), "mode": "real", "h": wl["h"],
+            "config": {"workload": name, "grid": list(wl["shape"]), "mode": "real", "h": wl["h"],
                        "dt": wl["dt"], "g": wl["g"], "gdd": wl["gdd"], "nu": list(wl["nu"]),
                        "prep": "%d imaginary-time steps at g=%g from the seeded Gaussian" % (PREP_STEPS, wl["g_prep"]),
-                       "l2": "inputs larger than L2 (psi 268 MB > 129 MB)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+                       "l2": "inputs larger than L2 (psi %d MB > 129 MB)" % (npts * (16 if wl["precision"] == "fp64" else 8) >> 20),
+                       "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "gpu_launches": 7 * args.steps, "clocks": clk, "roofline": roofline, "kernels": kernels, "e2e": e2e}
     if mixed is not None:
         line["mixed_512x512x384"] = mixed

@@ -92,28 +92,60 @@ struct Tiles;
 template <>
 struct Tiles<double> {
   static constexpr int kZLines = 8;       // z-lines per CTA in K1/K5 (4 pairs)
-  static constexpr int kZThreads = 256;   // one warp per z-line for the CN-z solve
+  static constexpr int kZThreads = 256;   // 8 warps: one z-line per warp in the CN-z solve
   static constexpr int kXCols = 4;        // consecutive y columns per K3 tile
-  static constexpr int kCnCols = 8;       // consecutive z columns per K6/K7 tile
-  static constexpr int kCnThreads = 256;  // one warp per line
-  static constexpr int kYBudget = 2048;   // K2/K4: lines per CTA = budget / ny
+  static constexpr int kCnCols = 8;       // consecutive z columns per K6/K7 tile (128 B rows)
+  static constexpr int kCnThreads = 128;  // 4 warps, two lines per warp
+  static constexpr int kYBudget = 2048;   // K2/K4: lines per CTA ~ budget / ny
 };
 template <>
 struct Tiles<float> {
   static constexpr int kZLines = 16;
-  static constexpr int kZThreads = 512;
+  static constexpr int kZThreads = 256;
   static constexpr int kXCols = 8;
   static constexpr int kCnCols = 16;
-  static constexpr int kCnThreads = 512;
+  static constexpr int kCnThreads = 256;
   static constexpr int kYBudget = 4096;
 };
 constexpr int kFftThreads = 256;
+constexpr int kUnroll = 8;  // loads in flight per thread in the register-staged load loops
 
+// K2/K4 lines per CTA: a power of two in [2, 32] (it must divide the block size).
 template <typename R>
 __host__ __device__ inline int y_lines_per_cta(int ny) {
-  int l = Tiles<R>::kYBudget / ny;
-  return l < 2 ? 2 : (l > 32 ? 32 : l);
+  int l = 2;
+  while (l * 2 <= 32 && l * 2 * ny <= Tiles<R>::kYBudget) l *= 2;
+  return l;
 }
+
+// ---------------------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async): every copy of a tile is in flight at
+// once instead of one dependent load per loop iteration.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <typename C>
+__device__ __forceinline__ void cp_async(C *dst, const C *src) {
+  static_assert(sizeof(C) == 8 || sizeof(C) == 16, "8- or 16-byte elements");
+  if constexpr (sizeof(C) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Double-float accumulator (Knuth's TwoSum): FP64-quality running sums from FP32 terms
+// without FP64 instructions per term.
+struct DFAcc {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = __fadd_rn(hi, v);
+    const float bp = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    hi = t;
+    lo = __fadd_rn(lo, err);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 // Slot of grid point n of a line in a Crank-Nicolson tile: one padding slot after every
 // `chunk` interior points, so that the 32 lanes solving one line hit distinct banks.
@@ -196,17 +228,19 @@ __device__ __forceinline__ void butterfly(cplx<R> *v) {
 // One Stockham autosort stage of radix P over `nlines` lines held in shared memory,
 // element e of line l at [e * sb + l].  ns = product of the radices of earlier stages.
 // Butterfly j reads x[j + r n/P], twiddles by w_n^{r (j mod ns) n/(ns P)}, and writes the
-// P outputs to (j div ns) ns P + (j mod ns) + s ns.
+// P outputs to (j div ns) ns P + (j mod ns) + s ns.  Thread t works on line t mod lw
+// (lw divides the block size) and on every (blockDim/lw)-th butterfly of it.
 template <typename R, int DIR, int P>
 __device__ __forceinline__ void fft_stage(const cplx<R> *__restrict__ src, cplx<R> *__restrict__ dst, int n,
-                                          int ns, int nlines, int sb, const cplx<R> *__restrict__ tw) {
+                                          int ns, int lw, int nlines, int sb, const cplx<R> *__restrict__ tw) {
   const int nbf = n / P;
-  const int total = nbf * nlines;
+  const int line = threadIdx.x % lw;
+  if (line >= nlines) return;
+  const int jstep = blockDim.x / lw;
   const int twstep = n / (ns * P);
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int line = idx % nlines;
-    const int j = idx / nlines;
-    const int k = j % ns;
+  const bool pow2 = (ns & (ns - 1)) == 0;
+  for (int j = threadIdx.x / lw; j < nbf; j += jstep) {
+    const int k = pow2 ? (j & (ns - 1)) : (j % ns);
     cplx<R> v[P];
 #pragma unroll
     for (int r = 0; r < P; ++r) v[r] = src[(j + r * nbf) * sb + line];
@@ -224,18 +258,18 @@ __device__ __forceinline__ void fft_stage(const cplx<R> *__restrict__ src, cplx<
   }
 }
 
-// Full transform of `nlines` lines (ping-pong between a and b); returns the buffer that
-// holds the result.  The caller synchronises before the call (input written).
+// Full transform of `nlines` (<= lw) lines (ping-pong between a and b); returns the
+// buffer holding the result.  The caller synchronises before the call (input written).
 template <typename R, int DIR>
-__device__ cplx<R> *fft_lines(cplx<R> *a, cplx<R> *b, const FftPlan &pl, int nlines, int sb,
+__device__ cplx<R> *fft_lines(cplx<R> *a, cplx<R> *b, const FftPlan &pl, int lw, int nlines, int sb,
                               const cplx<R> *tw) {
   int ns = 1;
   for (int st = 0; st < pl.nstages; ++st) {
     const int p = pl.radix[st];
-    if (p == 8) fft_stage<R, DIR, 8>(a, b, pl.n, ns, nlines, sb, tw);
-    else if (p == 4) fft_stage<R, DIR, 4>(a, b, pl.n, ns, nlines, sb, tw);
-    else if (p == 3) fft_stage<R, DIR, 3>(a, b, pl.n, ns, nlines, sb, tw);
-    else fft_stage<R, DIR, 2>(a, b, pl.n, ns, nlines, sb, tw);
+    if (p == 8) fft_stage<R, DIR, 8>(a, b, pl.n, ns, lw, nlines, sb, tw);
+    else if (p == 4) fft_stage<R, DIR, 4>(a, b, pl.n, ns, lw, nlines, sb, tw);
+    else if (p == 3) fft_stage<R, DIR, 3>(a, b, pl.n, ns, lw, nlines, sb, tw);
+    else fft_stage<R, DIR, 2>(a, b, pl.n, ns, lw, nlines, sb, tw);
     __syncthreads();
     cplx<R> *t = a;
     a = b;
@@ -503,7 +537,8 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) 
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int BZ = Tiles<R>::kZLines;
-  constexpr int SB = BZ / 2 + 1;
+  constexpr int PZ = BZ / 2;
+  constexpr int SB = PZ + 1;
   const int nz = a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
   const int nl = min(BZ, a.ny - j0), np = nl >> 1;
   C *za = reinterpret_cast<C *>(smem_raw);
@@ -511,25 +546,39 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) 
   const double s = a.state->s;
   const R s2 = R(s * s);
   const C *psi = reinterpret_cast<const C *>(a.psi) + ((size_t)i * a.ny + j0) * nz;
-  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
-    const int b = e / nz, n = e - b * nz;
-    const C v = psi[e];
-    R *z = reinterpret_cast<R *>(za + n * SB + (b >> 1));
-    z[b & 1] = s2 * (v.re * v.re + v.im * v.im);
+  const int total = nl * nz;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kUnroll * blockDim.x) {
+    C v[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < total) v[u] = psi[e];
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < total) {
+        const int b = e / nz, n = e - b * nz;
+        R *z = reinterpret_cast<R *>(za + n * SB + (b >> 1));
+        z[b & 1] = s2 * (v[u].re * v[u].re + v[u].im * v[u].im);
+      }
+    }
   }
   __syncthreads();
-  const C *res = fft_lines<R, -1>(za, zb, a.plan[2], np, SB, reinterpret_cast<const C *>(a.tw[2]));
+  const C *res = fft_lines<R, -1>(za, zb, a.plan[2], PZ, np, SB, reinterpret_cast<const C *>(a.tw[2]));
   C *spec = reinterpret_cast<C *>(a.spec) + (size_t)i * a.ny + j0;
   const size_t plane = (size_t)a.nx * a.ny;
-  for (int e = threadIdx.x; e < a.nzh * np; e += blockDim.x) {
-    const int p = e % np, m = e / np;
-    const C zm = res[m * SB + p];
-    const C zc = res[((nz - m) % nz) * SB + p];
-    const C x1 = {R(0.5) * (zm.re + zc.re), R(0.5) * (zm.im - zc.im)};
-    const C x2 = {R(0.5) * (zm.im + zc.im), R(0.5) * (zc.re - zm.re)};
-    C *dst = spec + m * plane + 2 * p;
-    dst[0] = x1;
-    dst[1] = x2;
+  const int p = threadIdx.x % PZ;
+  if (p < np) {
+    for (int m = threadIdx.x / PZ; m < a.nzh; m += blockDim.x / PZ) {
+      const C zm = res[m * SB + p];
+      const C zc = res[((nz - m) % nz) * SB + p];
+      const C x1 = {R(0.5) * (zm.re + zc.re), R(0.5) * (zm.im - zc.im)};
+      const C x2 = {R(0.5) * (zm.im + zc.im), R(0.5) * (zc.re - zm.re)};
+      C *dst = spec + m * plane + 2 * p;
+      dst[0] = x1;
+      dst[1] = x2;
+    }
   }
 }
 
@@ -551,10 +600,12 @@ __global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a) {
   C *spec = reinterpret_cast<C *>(a.spec) + l0 * n;
   for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
     const int l = e / n, k = e - l * n;
-    za[k * SB + l] = spec[e];
+    cp_async(za + k * SB + l, spec + e);
   }
+  cp_async_wait_all();
   __syncthreads();
-  const C *res = fft_lines<R, DIR>(za, zb, a.plan[1], nl, SB, reinterpret_cast<const C *>(a.tw[1]));
+  const C *res = fft_lines<R, DIR>(za, zb, a.plan[1], L, nl, SB, reinterpret_cast<const C *>(a.tw[1]));
+#pragma unroll 4
   for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
     const int l = e / n, k = e - l * n;
     spec[e] = res[k * SB + l];
@@ -571,16 +622,19 @@ __device__ __forceinline__ R dipolar_kernel(int ix, int iy, int iz, const KArgs 
   const double two_pi = 6.283185307179586476925286766559;
   const int mx = ix <= a.nx / 2 ? ix : ix - a.nx;
   const int my = iy <= a.ny / 2 ? iy : iy - a.ny;
-  const double kx = two_pi * (double)mx / ((double)a.nx * a.hx);
-  const double ky = two_pi * (double)my / ((double)a.ny * a.hy);
-  const double kz = two_pi * (double)iz / ((double)a.nz * a.hz);
   if constexpr (sizeof(R) == 8) {
+    const double kx = two_pi * (double)mx / ((double)a.nx * a.hx);
+    const double ky = two_pi * (double)my / ((double)a.ny * a.hy);
+    const double kz = two_pi * (double)iz / ((double)a.nz * a.hz);
     const double k2 = kx * kx + ky * ky + kz * kz;
     return k2 > 0.0 ? 3.0 * kz * kz / k2 - 1.0 : 0.0;
   } else {
-    const float fx = (float)kx, fy = (float)ky, fz = (float)kz;
-    const float k2 = fx * fx + fy * fy + fz * fz;
-    return k2 > 0.0f ? 3.0f * fz * fz / k2 - 1.0f : 0.0f;
+    const float tp = 6.283185307f;
+    const float kx = tp * (float)mx / ((float)a.nx * (float)a.hx);
+    const float ky = tp * (float)my / ((float)a.ny * (float)a.hy);
+    const float kz = tp * (float)iz / ((float)a.nz * (float)a.hz);
+    const float k2 = kx * kx + ky * ky + kz * kz;
+    return k2 > 0.0f ? 3.0f * kz * kz / k2 - 1.0f : 0.0f;
   }
 }
 
@@ -595,23 +649,25 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
   C *za = reinterpret_cast<C *>(smem_raw);
   C *zb = za + n * SB;
   C *spec = reinterpret_cast<C *>(a.spec) + (size_t)m * a.nx * a.ny + j0;
-  for (int e = threadIdx.x; e < n * nb; e += blockDim.x) {
-    const int b = e % nb, k = e / nb;
-    za[k * SB + b] = spec[(size_t)k * a.ny + b];
+  for (int e = threadIdx.x; e < n * BX; e += blockDim.x) {
+    const int b = e % BX, k = e / BX;
+    if (b < nb) cp_async(za + k * SB + b, spec + (size_t)k * a.ny + b);
   }
+  cp_async_wait_all();
   __syncthreads();
   const C *tw = reinterpret_cast<const C *>(a.tw[0]);
-  C *res = fft_lines<R, -1>(za, zb, a.plan[0], nb, SB, tw);
-  for (int e = threadIdx.x; e < n * nb; e += blockDim.x) {
-    const int b = e % nb, k = e / nb;
-    res[k * SB + b] = scale(res[k * SB + b], dipolar_kernel<R>(k, j0 + b, m, a));
+  C *res = fft_lines<R, -1>(za, zb, a.plan[0], BX, nb, SB, tw);
+  for (int e = threadIdx.x; e < n * BX; e += blockDim.x) {
+    const int b = e % BX, k = e / BX;
+    if (b < nb) res[k * SB + b] = scale(res[k * SB + b], dipolar_kernel<R>(k, j0 + b, m, a));
   }
   __syncthreads();
   C *other = (res == za) ? zb : za;
-  const C *out = fft_lines<R, +1>(res, other, a.plan[0], nb, SB, tw);
-  for (int e = threadIdx.x; e < n * nb; e += blockDim.x) {
-    const int b = e % nb, k = e / nb;
-    spec[(size_t)k * a.ny + b] = out[k * SB + b];
+  const C *out = fft_lines<R, +1>(res, other, a.plan[0], BX, nb, SB, tw);
+#pragma unroll 4
+  for (int e = threadIdx.x; e < n * BX; e += blockDim.x) {
+    const int b = e % BX, k = e / BX;
+    if (b < nb) spec[(size_t)k * a.ny + b] = out[k * SB + b];
   }
 }
 
@@ -627,7 +683,8 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int BZ = Tiles<R>::kZLines;
-  constexpr int SB = BZ / 2 + 1;
+  constexpr int PZ = BZ / 2;
+  constexpr int SB = PZ + 1;
   const int nz = a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
   const int nl = min(BZ, a.ny - j0), np = nl >> 1;
   const int chunk = a.cn[2].chunk;
@@ -638,25 +695,50 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
   const double s = a.state->s;
   const R inv_ntot = R(a.inv_ntot);
   const size_t line0 = (size_t)i * a.ny + j0;
+  C *psi = reinterpret_cast<C *>(a.psi) + line0 * nz;
   const C *res = nullptr;
+
+  // psi tile: asynchronous copies, overlapped with the spectrum load and the C2R transform
+  if (zmode != kZPhi) {
+    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
+      const int b = e / nz, n = e - b * nz;
+      cp_async(tile + b * LS + cn_slot(n, chunk), psi + e);
+    }
+  }
 
   if (zmode != kZCnOnly) {
     const C *spec = reinterpret_cast<const C *>(a.spec) + line0;
     const size_t plane = (size_t)a.nx * a.ny;
     const int half = nz / 2;
-    for (int e = threadIdx.x; e < a.nzh * np; e += blockDim.x) {
-      const int p = e % np, m = e / np;
-      C x1 = spec[m * plane + 2 * p];
-      C x2 = spec[m * plane + 2 * p + 1];
-      if (m == 0 || m == half) {
-        x1.im = R(0);
-        x2.im = R(0);
+    const int p = threadIdx.x % PZ;
+    const int mstep = blockDim.x / PZ;
+    if (p < np) {
+      for (int m0 = threadIdx.x / PZ; m0 < a.nzh; m0 += kUnroll * mstep) {
+        C x1[kUnroll], x2[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int m = m0 + u * mstep;
+          if (m < a.nzh) {
+            x1[u] = spec[m * plane + 2 * p];
+            x2[u] = spec[m * plane + 2 * p + 1];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int m = m0 + u * mstep;
+          if (m < a.nzh) {
+            if (m == 0 || m == half) {
+              x1[u].im = R(0);
+              x2[u].im = R(0);
+            }
+            za[m * SB + p] = {x1[u].re - x2[u].im, x1[u].im + x2[u].re};
+            if (m > 0 && m < half) za[(nz - m) * SB + p] = {x1[u].re + x2[u].im, x2[u].re - x1[u].im};
+          }
+        }
       }
-      za[m * SB + p] = {x1.re - x2.im, x1.im + x2.re};
-      if (m > 0 && m < half) za[(nz - m) * SB + p] = {x1.re + x2.im, x2.re - x1.im};
     }
     __syncthreads();
-    res = fft_lines<R, +1>(za, zb, a.plan[2], np, SB, reinterpret_cast<const C *>(a.tw[2]));
+    res = fft_lines<R, +1>(za, zb, a.plan[2], PZ, np, SB, reinterpret_cast<const C *>(a.tw[2]));
   }
 
   if (zmode == kZPhi) {
@@ -668,12 +750,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
     }
     return;
   }
-
-  C *psi = reinterpret_cast<C *>(a.psi) + line0 * nz;
-  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
-    const int b = e / nz, n = e - b * nz;
-    tile[b * LS + cn_slot(n, chunk)] = psi[e];
-  }
+  cp_async_wait_all();
   __syncthreads();
 
   if (zmode == kZObs) {
@@ -768,6 +845,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
     __syncthreads();
   }
 
+#pragma unroll 4
   for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
     const int b = e / nz, n = e - b * nz;
     psi[e] = tile[b * LS + cn_slot(n, chunk)];
@@ -776,10 +854,34 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
 
 // ---------------------------------------------------------------------------------------
 // K6 / K7: Crank-Nicolson along y (AXIS = 1, lines psi[i][:][k]) or x (AXIS = 0, lines
-// psi[:][j][k]) for kCnCols consecutive k per CTA.  K7 (x) also reduces sum n, x^2 n,
-// y^2 n, z^2 n in FP64 and, in the last block, sets the norm and the pending
+// psi[:][j][k]) for kCnCols consecutive k per CTA (one warp per line).  K7 (x) also sums
+// n, x^2 n, y^2 n, z^2 n (FP64 totals; per-thread partial sums in FP64 for FP64 data and
+// in double-float for FP32 data) and, in the last block, sets the norm and the pending
 // renormalisation factor s = 1/sqrt(norm) (imaginary time) or 1 (real time).
 // ---------------------------------------------------------------------------------------
+template <typename R>
+struct RowSums;
+template <>
+struct RowSums<double> {
+  double s0 = 0.0, sx = 0.0;
+  __device__ __forceinline__ void add(double d, double x2) {
+    s0 += d;
+    sx = fma(x2, d, sx);
+  }
+  __device__ __forceinline__ double total() const { return s0; }
+  __device__ __forceinline__ double xmoment() const { return sx; }
+};
+template <>
+struct RowSums<float> {
+  DFAcc s0, sx;
+  __device__ __forceinline__ void add(float d, float x2) {
+    s0.add(d);
+    sx.add(__fmul_rn(x2, d));
+  }
+  __device__ __forceinline__ double total() const { return s0.value(); }
+  __device__ __forceinline__ double xmoment() const { return sx.value(); }
+};
+
 template <typename R, typename Coef, int AXIS>
 __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce, int renorm) {
   using C = cplx<R>;
@@ -801,33 +903,38 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
     stride = (size_t)a.ny * a.nz;
   }
   C *tile = reinterpret_cast<C *>(smem_raw);
+  R *x2tab = reinterpret_cast<R *>(tile + cn_slots(N, chunk) * SB);
   C *psi = reinterpret_cast<C *>(a.psi) + base;
-  for (int e = threadIdx.x; e < N * nb; e += blockDim.x) {
-    const int b = e % nb, n = e / nb;
-    tile[cn_slot(n, chunk) * SB + b] = psi[(size_t)n * stride + b];
+  for (int e = threadIdx.x; e < N * B; e += blockDim.x) {
+    const int b = e % B, n = e / B;
+    if (b < nb) cp_async(tile + cn_slot(n, chunk) * SB + b, psi + (size_t)n * stride + b);
   }
+  if (AXIS == 0 && reduce)
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+      const double x = coordinate(n, a.nx, a.hx);
+      x2tab[n] = R(x * x);
+    }
+  cp_async_wait_all();
   __syncthreads();
   const Coef c = CnCoef<R, Coef>::make(a.dt / (4.0 * h * h));
   const Coef *tab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
   for (int b = threadIdx.x / kWarp; b < nb; b += blockDim.x / kWarp)
     cn_line<R, Coef>(tile + b, SB, a.cn[AXIS].m, chunk, tab, c);
   __syncthreads();
-  double v[4] = {0, 0, 0, 0};
-  for (int e = threadIdx.x; e < N * nb; e += blockDim.x) {
-    const int b = e % nb, n = e / nb;
-    const C w = tile[cn_slot(n, chunk) * SB + b];
-    psi[(size_t)n * stride + b] = w;
-    if (AXIS == 0 && reduce) {
-      const double d = (double)w.re * w.re + (double)w.im * w.im;
-      const double x = coordinate(n, a.nx, a.hx), y = coordinate(fixed, a.ny, a.hy),
-                   z = coordinate(k0 + b, a.nz, a.hz);
-      v[0] += d;
-      v[1] += x * x * d;
-      v[2] += y * y * d;
-      v[3] += z * z * d;
+  const int b = threadIdx.x % B;   // B divides the block size: the column is fixed per thread
+  RowSums<R> acc;
+  if (b < nb) {
+#pragma unroll 4
+    for (int n = threadIdx.x / B; n < N; n += blockDim.x / B) {
+      const C w = tile[cn_slot(n, chunk) * SB + b];
+      psi[(size_t)n * stride + b] = w;
+      if (AXIS == 0 && reduce) acc.add(w.re * w.re + w.im * w.im, x2tab[n]);
     }
   }
   if (AXIS == 0 && reduce) {
+    const double z = coordinate(k0 + b, a.nz, a.hz), y = coordinate(fixed, a.ny, a.hy);
+    const double t = b < nb ? acc.total() : 0.0;
+    double v[4] = {t, b < nb ? acc.xmoment() : 0.0, y * y * t, z * z * t};
     if (reduce_across_blocks<4>(v, a.partials, &a.state->ticket) && threadIdx.x == 0) {
       DevState *st = a.state;
       const double norm = a.hx * a.hy * a.hz * v[0];
@@ -877,7 +984,9 @@ struct Impl {
   }
   static size_t smem_y(const KArgs &a) { return 2 * (size_t)a.ny * (y_lines_per_cta<R>(a.ny) + 1) * E; }
   static size_t smem_x(const KArgs &a) { return 2 * (size_t)a.nx * T::kXCols * E; }
-  static size_t smem_cn(int n, int chunk) { return (size_t)cn_slots(n, chunk) * (T::kCnCols + 1) * E; }
+  static size_t smem_cn(int n, int chunk) {
+    return (size_t)cn_slots(n, chunk) * (T::kCnCols + 1) * E + (size_t)n * sizeof(R);
+  }
 
   static dim3 grid_z(const KArgs &a) { return dim3((a.ny + T::kZLines - 1) / T::kZLines, a.nx); }
   static dim3 grid_cn(const KArgs &a, int axis) {
