@@ -158,6 +158,31 @@ int dgpe_set_timing(dgpe_ctx *ctx, int enable);
  * kernels timed. */
 int dgpe_kernel_times(dgpe_ctx *ctx, dgpe_kernel_time *out, int max, int *n);
 
+/* Norm and rms sizes of a caller's psi without allocating any device memory.
+ *
+ * The paper has no counterpart of this call; it exists for callers that cannot allocate:
+ * a framework that owns all device memory through its own pool and treats any outside
+ * cudaMalloc as a bug, a monitoring hook run every step of a time-critical loop where
+ * cudaMalloc/cudaFree would synchronise the device and stall other streams, or a process
+ * running so close to its memory limit that a new allocation may fail.  It needs no
+ * context and no workspace: the scratch of its reduction (per-block partial sums and a
+ * counter, 256 KiB) is one fixed array inside the library, of which every GPU that loads
+ * the library keeps one copy until the process exits.
+ *
+ * psi: device memory, [nx][ny][nz] complex128 (p->precision = DGPE_FP64) or complex64
+ * (DGPE_MIXED), owned by the caller.  Only p->nx, ny, nz, hx, hy, hz and precision are
+ * read; the grid is x_i = (i - nx/2) hx as everywhere in this library.
+ * out: device memory for 4 doubles, owned by the caller: norm = hx hy hz sum |psi|^2,
+ * rms_x, rms_y, rms_z (sqrt(sum d^2 |psi|^2 / sum |psi|^2)), written in stream order.
+ * Sizes: at most 2^27 = 512^3 points (the fixed scratch holds the partial sums of that
+ * many); larger grids return DGPE_EUNSUPPORTED.  Bad pointers or sizes: DGPE_EINVAL.
+ * The first call on each GPU looks up that GPU's copy of the scratch array; make that
+ * first call before any stream capture.  Every call on a GPU shares the same scratch, so
+ * calls whose GPU work may overlap (e.g. on unordered streams) race and give wrong
+ * results: order them on one stream or with events.  Asynchronous: returns after
+ * enqueueing a memset and one kernel on cuda_stream (NULL = legacy default stream). */
+int dgpe_moments_noalloc(const void *psi, const dgpe_params *p, double *out, void *cuda_stream);
+
 /* Static text for an error code. */
 const char *dgpe_strerror(int code);
 

@@ -85,6 +85,7 @@ _SIGNATURES = [
     ("dgpe_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("dgpe_set_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("dgpe_kernel_times", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_kernel_time), ctypes.c_int, _P(ctypes.c_int)]),
+    ("dgpe_moments_noalloc", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_params), ctypes.c_void_p, ctypes.c_void_p]),
     ("dgpe_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("dgpe_last_cuda_error", ctypes.c_char_p, []),
     ("dgpe_destroy", None, [ctypes.c_void_p]),
@@ -195,6 +196,13 @@ def dgpe_kernel_times(ctx, max_kernels=16):
     _check(load().dgpe_kernel_times(ctx, arr, max_kernels, ctypes.byref(n)), "dgpe_kernel_times")
     return [{"name": arr[i].name.decode(), "total_ms": arr[i].total_ms, "launches": arr[i].launches,
              "bytes_per_launch": arr[i].bytes_per_launch} for i in range(min(n.value, max_kernels))]
+
+
+def dgpe_moments_noalloc(psi_ptr, params, out_ptr, stream=0):
+    """Norm and rms sizes of a device psi into 4 device doubles, allocating nothing (for
+    callers whose device memory is owned elsewhere or who must not allocate mid-run)."""
+    _check(load().dgpe_moments_noalloc(ctypes.c_void_p(psi_ptr), ctypes.byref(params), ctypes.c_void_p(out_ptr),
+                                       ctypes.c_void_p(stream or None)), "dgpe_moments_noalloc")
 
 
 def dgpe_destroy(ctx):

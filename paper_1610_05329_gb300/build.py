@@ -1,7 +1,7 @@
 """Build the CUDA library libdgpe.so in-tree (nvcc, sm_103a only).
 
-Three translation units (the C-ABI host code and one kernel set per precision) compile in
-parallel, then link into paper_1610_05329_gb300/_build/libdgpe.so with the CUDA runtime
+The translation units (the C-ABI host code, one kernel set per precision, and the
+allocation-free moments call) compile in parallel, then link into paper_1610_05329_gb300/_build/libdgpe.so with the CUDA runtime
 linked statically.  nvcc cross-compiles, so this also runs on a machine without a GPU.
 """
 import os
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdgpe.so")
-SOURCES = ["dgpe_api.cu", "kernels_f64.cu", "kernels_f32.cu"]
+SOURCES = ["dgpe_api.cu", "kernels_f64.cu", "kernels_f32.cu", "dgpe_noalloc.cu"]
 HEADERS = ["dgpe_device.cuh", "dgpe_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

@@ -1,0 +1,109 @@
+// dgpe_moments_noalloc: the norm and rms sizes of a caller's psi, computed without any
+// device allocation.  The scratch memory of its reduction (per-block partial sums and the
+// last-block counter) is a file-scope __device__ array of fixed size, so the call needs
+// neither a context nor a workspace.  The paper has no counterpart of this entry point.
+//
+// Scratch: kNoAllocMaxBlocks x 4 doubles of partial sums + one counter, 256 KiB in all.
+// Every GPU that loads libdgpe.so holds one copy of it until the process exits, and every
+// call on that GPU shares it: calls whose work overlaps on the GPU (different streams
+// without ordering between them) race on it and give wrong results.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <mutex>
+
+#include "dgpe.h"
+#include "dgpe_device.cuh"
+
+using namespace dgpe;
+
+namespace {
+
+constexpr int kNoAllocThreads = 256;
+constexpr int kNoAllocPointsPerThread = 64;
+constexpr int kNoAllocMaxBlocks = 8192;
+constexpr long long kNoAllocPointsPerBlock = (long long)kNoAllocThreads * kNoAllocPointsPerThread;
+constexpr long long kNoAllocMaxPoints = kNoAllocMaxBlocks * kNoAllocPointsPerBlock;  // 2^27 = 512^3
+
+struct NoAllocScratch {
+  unsigned int ticket;            // last-block counter: must be 0 when a reduction starts
+  unsigned int pad[63];
+  double partials[kNoAllocMaxBlocks * 4];
+};
+
+__device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of this GPU's copy of the scratch array, looked up once per device with
+// that device current (in host code the symbol itself is only a host-side stand-in).
+int scratch_address(NoAllocScratch **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DGPE_ECUDA;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DGPE_ECUDA;
+    g_scratch_addr[dev] = p;
+  }
+  *out = static_cast<NoAllocScratch *>(g_scratch_addr[dev]);
+  return DGPE_OK;
+}
+
+// Sums n, x^2 n, y^2 n, z^2 n over a contiguous range of points per block (FP64), then the
+// last block turns them into norm = hx hy hz sum n and rms_d = sqrt(sum d^2 n / sum n).
+template <typename R>
+__global__ void __launch_bounds__(kNoAllocThreads)
+    k_moments_noalloc(const cplx<R> *__restrict__ psi, int nx, int ny, int nz, double hx, double hy, double hz,
+                      long long npts, NoAllocScratch *scr, double *out) {
+  const long long begin = (long long)blockIdx.x * kNoAllocPointsPerBlock;
+  const long long end = min(begin + kNoAllocPointsPerBlock, npts);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const long long plane = (long long)ny * nz;
+  for (long long q = begin + threadIdx.x; q < end; q += blockDim.x) {
+    const cplx<R> w = psi[q];
+    const double d = (double)w.re * w.re + (double)w.im * w.im;
+    const int i = (int)(q / plane);
+    const long long rem = q - (long long)i * plane;
+    const int j = (int)(rem / nz), k = (int)(rem - (long long)j * nz);
+    const double x = coordinate(i, nx, hx), y = coordinate(j, ny, hy), z = coordinate(k, nz, hz);
+    v[0] += d;
+    v[1] += x * x * d;
+    v[2] += y * y * d;
+    v[3] += z * z * d;
+  }
+  if (reduce_across_blocks<4>(v, scr->partials, &scr->ticket) && threadIdx.x == 0) {
+    out[0] = hx * hy * hz * v[0];
+    out[1] = sqrt(v[1] / v[0]);
+    out[2] = sqrt(v[2] / v[0]);
+    out[3] = sqrt(v[3] / v[0]);
+  }
+}
+
+}  // namespace
+
+extern "C" int dgpe_moments_noalloc(const void *psi, const dgpe_params *p, double *out, void *cuda_stream) {
+  if (!psi || !p || !out) return DGPE_EINVAL;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return DGPE_EINVAL;
+  if (!(p->hx > 0 && p->hy > 0 && p->hz > 0) || !isfinite(p->hx) || !isfinite(p->hy) || !isfinite(p->hz))
+    return DGPE_EINVAL;
+  if (p->precision != DGPE_FP64 && p->precision != DGPE_MIXED) return DGPE_EINVAL;
+  const long long npts = (long long)p->nx * p->ny * p->nz;
+  if (npts > kNoAllocMaxPoints) return DGPE_EUNSUPPORTED;   // beyond the fixed scratch
+  NoAllocScratch *scr = nullptr;
+  int rc = scratch_address(&scr);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // the counter must start at zero (a reduction that was cut short may have left it set)
+  if (cudaMemsetAsync(&scr->ticket, 0, sizeof(unsigned int), st) != cudaSuccess) return DGPE_ECUDA;
+  const unsigned blocks = (unsigned)((npts + kNoAllocPointsPerBlock - 1) / kNoAllocPointsPerBlock);
+  if (p->precision == DGPE_FP64)
+    k_moments_noalloc<double><<<blocks, kNoAllocThreads, 0, st>>>(static_cast<const cplx<double> *>(psi), p->nx,
+                                                                  p->ny, p->nz, p->hx, p->hy, p->hz, npts, scr, out);
+  else
+    k_moments_noalloc<float><<<blocks, kNoAllocThreads, 0, st>>>(static_cast<const cplx<float> *>(psi), p->nx,
+                                                                 p->ny, p->nz, p->hx, p->hy, p->hz, npts, scr, out);
+  return cudaGetLastError() == cudaSuccess ? DGPE_OK : DGPE_ECUDA;
+}
