@@ -55,14 +55,20 @@ FftPlan make_plan(int n) {
   return p;
 }
 
-// Interior points per lane of the chunked Thomas solve: ceil(m / 32) rounded up to even
-// (an odd slot stride keeps the 32 lanes on distinct shared-memory banks).
+// Interior points per lane of the chunked Thomas solve: the smallest power of two >= 2
+// with 32 lanes covering the m = n - 2 unknowns (a power of two keeps the slot arithmetic
+// to shifts; an even chunk gives an odd slot stride, so the lanes hit distinct banks).
 int cn_chunk(int n) {
   const int m = n - 2;
-  int c = (m + kWarp - 1) / kWarp;
-  if (c < 2) c = 2;
-  if (c % 2) ++c;
+  int c = 2;
+  while (c * kWarp < m) c *= 2;
   return c;
+}
+
+int log2_int(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
 }
 
 int check_shape(const dgpe_params *p) {
@@ -131,6 +137,7 @@ KArgs base_args(const dgpe_params *p) {
     a.plan[d] = make_plan(n);
     a.cn[d].m = n - 2;
     a.cn[d].chunk = cn_chunk(n);
+    a.cn[d].lchunk = log2_int(a.cn[d].chunk);
   }
   return a;
 }

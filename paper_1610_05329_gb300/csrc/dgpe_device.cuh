@@ -132,6 +132,9 @@ __device__ __forceinline__ void cp_async(C *dst, const C *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Double-float accumulator (Knuth's TwoSum): FP64-quality running sums from FP32 terms
 // without FP64 instructions per term.
@@ -148,9 +151,10 @@ struct DFAcc {
 };
 
 // Slot of grid point n of a line in a Crank-Nicolson tile: one padding slot after every
-// `chunk` interior points, so that the 32 lanes solving one line hit distinct banks.
-__host__ __device__ inline int cn_slot(int n, int chunk) { return n + (n > 0 ? (n - 1) / chunk : 0); }
-__host__ __device__ inline int cn_slots(int n, int chunk) { return n + (n - 2) / chunk; }
+// chunk = 2^lchunk interior points, so that the 32 lanes solving one line hit distinct
+// banks.  cn_slots = slots of a line of n points.
+__host__ __device__ inline int cn_slot(int n, int lchunk) { return n + (max(n - 1, 0) >> lchunk); }
+__host__ __device__ inline int cn_slots(int n, int lchunk) { return n + ((n - 2) >> lchunk); }
 
 // ---------------------------------------------------------------------------------------
 // FFT: radix-2/3/4/8 butterflies (DIR = -1 forward e^{-i..}, +1 inverse, unnormalised)
@@ -292,12 +296,13 @@ __device__ cplx<R> *fft_lines(cplx<R> *a, cplx<R> *b, const FftPlan &pl, int lw,
 //   chi_i = chi0_i + Y_t H_i + X_{t+1} G_i,   X_{t+1} = chi at the point after the chunk,
 // with P, H, G precomputed per position (see k_cn_tables).  The carries Y_t and X_t are
 // affine recurrences across lanes, resolved by warp-shuffle scans of (A, B) pairs.
-// Element n of the line is at buf[cn_slot(n, C) * es].
+// Element n of the line is at buf[cn_slot(n, lchunk) * es].
 // ---------------------------------------------------------------------------------------
 template <typename R, typename Coef>
-__device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m, int chunk,
+__device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m, int lchunk,
                                         const Coef *__restrict__ tab, Coef c) {
   const int t = threadIdx.x & (kWarp - 1);
+  const int chunk = 1 << lchunk;
   const int s0 = t * chunk;
   const int len = max(0, min(chunk, m - s0));
   const Coef *alpha = tab;
@@ -367,7 +372,7 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   }
   if (t == 0) {
     buf[0] = czero<R>();
-    buf[cn_slot(m + 1, chunk) * es] = czero<R>();
+    buf[(m + 1 + (m >> lchunk)) * es] = czero<R>();
   }
 }
 
@@ -687,8 +692,8 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
   constexpr int SB = PZ + 1;
   const int nz = a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
   const int nl = min(BZ, a.ny - j0), np = nl >> 1;
-  const int chunk = a.cn[2].chunk;
-  const int LS = cn_slots(nz, chunk);
+  const int lc = a.cn[2].lchunk;
+  const int LS = cn_slots(nz, lc);
   C *za = reinterpret_cast<C *>(smem_raw);
   C *zb = za + nz * SB;
   C *tile = zb + nz * SB;
@@ -702,7 +707,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
   if (zmode != kZPhi) {
     for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
       const int b = e / nz, n = e - b * nz;
-      cp_async(tile + b * LS + cn_slot(n, chunk), psi + e);
+      cp_async(tile + b * LS + cn_slot(n, lc), psi + e);
     }
   }
 
@@ -764,9 +769,9 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
       const int b = e / nz, n = e - b * nz;
       const int j = j0 + b;
       const C *row = tile + b * LS;
-      const C c = scale(row[cn_slot(n, chunk)], sr);
-      const C zm = n > 0 ? scale(row[cn_slot(n - 1, chunk)], sr) : czero<R>();
-      const C zp = n < nz - 1 ? scale(row[cn_slot(n + 1, chunk)], sr) : czero<R>();
+      const C c = scale(row[cn_slot(n, lc)], sr);
+      const C zm = n > 0 ? scale(row[cn_slot(n - 1, lc)], sr) : czero<R>();
+      const C zp = n < nz - 1 ? scale(row[cn_slot(n + 1, lc)], sr) : czero<R>();
       const size_t q = (line0 + b) * nz + n;
       const C ym = j > 0 ? scale(gpsi[q - nz], sr) : czero<R>();
       const C yp = j < a.ny - 1 ? scale(gpsi[q + nz], sr) : czero<R>();
@@ -819,7 +824,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
     const R dt = R(a.dt), g = R(a.g), gdd = R(a.gdd), vy = R(a.vy), vz = R(a.vz);
     for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
       const int b = e / nz, n = e - b * nz;
-      const int q = b * LS + cn_slot(n, chunk);
+      const int q = b * LS + cn_slot(n, lc);
       const C v = scale(tile[q], sr);
       const C z = res[n * SB + (b >> 1)];
       const R phi = ((b & 1) ? z.im : z.re) * inv_ntot;
@@ -841,14 +846,14 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
     const Coef c = CnCoef<R, Coef>::make(a.dt / (4.0 * a.hz * a.hz));
     const Coef *tab = reinterpret_cast<const Coef *>(a.cn[2].tab);
     for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp)
-      cn_line<R, Coef>(tile + b * LS, 1, a.cn[2].m, chunk, tab, c);
+      cn_line<R, Coef>(tile + b * LS, 1, a.cn[2].m, lc, tab, c);
     __syncthreads();
   }
 
 #pragma unroll 4
   for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
     const int b = e / nz, n = e - b * nz;
-    psi[e] = tile[b * LS + cn_slot(n, chunk)];
+    psi[e] = tile[b * LS + cn_slot(n, lc)];
   }
 }
 
@@ -882,6 +887,9 @@ struct RowSums<float> {
   __device__ __forceinline__ double xmoment() const { return sx.value(); }
 };
 
+// Persistent, double-buffered: each CTA walks the tiles (fixed index, k-tile)
+// blockIdx.x, blockIdx.x + gridDim.x, ...; the cp.async copies of the next tile are in
+// flight while the current tile is solved and stored.
 template <typename R, typename Coef, int AXIS>
 __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce, int renorm) {
   using C = cplx<R>;
@@ -889,52 +897,85 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
   constexpr int B = Tiles<R>::kCnCols;
   constexpr int SB = B + 1;
   const int N = AXIS == 0 ? a.nx : a.ny;
-  const double h = AXIS == 0 ? a.hx : a.hy;
-  const int chunk = a.cn[AXIS].chunk;
-  const int k0 = blockIdx.x * B;
-  const int nb = min(B, a.nz - k0);
-  const int fixed = blockIdx.y;
-  size_t base, stride;
-  if (AXIS == 1) {
-    base = (size_t)fixed * a.ny * a.nz + k0;
-    stride = (size_t)a.nz;
-  } else {
-    base = (size_t)fixed * a.nz + k0;
-    stride = (size_t)a.ny * a.nz;
-  }
-  C *tile = reinterpret_cast<C *>(smem_raw);
-  R *x2tab = reinterpret_cast<R *>(tile + cn_slots(N, chunk) * SB);
-  C *psi = reinterpret_cast<C *>(a.psi) + base;
-  for (int e = threadIdx.x; e < N * B; e += blockDim.x) {
-    const int b = e % B, n = e / B;
-    if (b < nb) cp_async(tile + cn_slot(n, chunk) * SB + b, psi + (size_t)n * stride + b);
-  }
-  if (AXIS == 0 && reduce)
+  const int nfixed = AXIS == 0 ? a.ny : a.nx;
+  const int nkt = (a.nz + B - 1) / B;
+  const int ntiles = nfixed * nkt;
+  const int lc = a.cn[AXIS].lchunk;
+  const int slots = cn_slots(N, lc);
+  C *cur = reinterpret_cast<C *>(smem_raw);
+  C *nxt = cur + slots * SB;
+  R *x2tab = reinterpret_cast<R *>(nxt + slots * SB);
+  const size_t stride = AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
+  C *gpsi = reinterpret_cast<C *>(a.psi);
+  const int b = threadIdx.x % B;   // B divides the block size: the column is fixed per thread
+  const int n0 = threadIdx.x / B, nstep = blockDim.x / B;
+  const bool do_reduce = AXIS == 0 && reduce;
+
+  auto tile_origin = [&](int tile, int &fixed, int &k0) -> size_t {
+    fixed = tile / nkt;
+    k0 = (tile - fixed * nkt) * B;
+    return AXIS == 1 ? (size_t)fixed * a.ny * a.nz + k0 : (size_t)fixed * a.nz + k0;
+  };
+  auto issue = [&](int tile, C *buf) {
+    int fixed, k0;
+    const size_t base = tile_origin(tile, fixed, k0);
+    if (b < min(B, a.nz - k0)) {
+      const C *src = gpsi + base + b + (size_t)n0 * stride;
+      for (int n = n0; n < N; n += nstep, src += nstep * stride) cp_async(buf + cn_slot(n, lc) * SB + b, src);
+    }
+    cp_async_commit();
+  };
+
+  if (do_reduce)
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
       const double x = coordinate(n, a.nx, a.hx);
       x2tab[n] = R(x * x);
     }
-  cp_async_wait_all();
-  __syncthreads();
-  const Coef c = CnCoef<R, Coef>::make(a.dt / (4.0 * h * h));
+  const Coef c = CnCoef<R, Coef>::make(a.dt / (4.0 * (AXIS == 0 ? a.hx * a.hx : a.hy * a.hy)));
   const Coef *tab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
-  for (int b = threadIdx.x / kWarp; b < nb; b += blockDim.x / kWarp)
-    cn_line<R, Coef>(tile + b, SB, a.cn[AXIS].m, chunk, tab, c);
-  __syncthreads();
-  const int b = threadIdx.x % B;   // B divides the block size: the column is fixed per thread
-  RowSums<R> acc;
-  if (b < nb) {
-#pragma unroll 4
-    for (int n = threadIdx.x / B; n < N; n += blockDim.x / B) {
-      const C w = tile[cn_slot(n, chunk) * SB + b];
-      psi[(size_t)n * stride + b] = w;
-      if (AXIS == 0 && reduce) acc.add(w.re * w.re + w.im * w.im, x2tab[n]);
+  double v[4] = {0, 0, 0, 0};
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) issue(tile, cur);
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int next = tile + gridDim.x;
+    if (next < ntiles) {
+      issue(next, nxt);
+      cp_async_wait_group<1>();
+    } else {
+      cp_async_wait_group<0>();
     }
+    __syncthreads();
+    int fixed, k0;
+    const size_t base = tile_origin(tile, fixed, k0);
+    const int nb = min(B, a.nz - k0);
+    for (int l = threadIdx.x / kWarp; l < nb; l += blockDim.x / kWarp)
+      cn_line<R, Coef>(cur + l, SB, a.cn[AXIS].m, lc, tab, c);
+    __syncthreads();
+    if (b < nb) {
+      RowSums<R> rs;
+      C *dst = gpsi + base + b + (size_t)n0 * stride;
+#pragma unroll 4
+      for (int n = n0; n < N; n += nstep, dst += nstep * stride) {
+        const C w = cur[cn_slot(n, lc) * SB + b];
+        *dst = w;
+        if (do_reduce) rs.add(w.re * w.re + w.im * w.im, x2tab[n]);
+      }
+      if (do_reduce) {
+        const double t = rs.total();
+        const double z = coordinate(k0 + b, a.nz, a.hz), y = coordinate(fixed, a.ny, a.hy);
+        v[0] += t;
+        v[1] += rs.xmoment();
+        v[2] += y * y * t;
+        v[3] += z * z * t;
+      }
+    }
+    __syncthreads();   // `cur` is refilled by the prefetch two tiles ahead
+    C *t = cur;
+    cur = nxt;
+    nxt = t;
   }
-  if (AXIS == 0 && reduce) {
-    const double z = coordinate(k0 + b, a.nz, a.hz), y = coordinate(fixed, a.ny, a.hy);
-    const double t = b < nb ? acc.total() : 0.0;
-    double v[4] = {t, b < nb ? acc.xmoment() : 0.0, y * y * t, z * z * t};
+  if (do_reduce) {
     if (reduce_across_blocks<4>(v, a.partials, &a.state->ticket) && threadIdx.x == 0) {
       DevState *st = a.state;
       const double norm = a.hx * a.hy * a.hz * v[0];
@@ -980,17 +1021,33 @@ struct Impl {
 
   static size_t smem_z_fft(const KArgs &a) { return 2 * (size_t)a.nz * (T::kZLines / 2 + 1) * E; }
   static size_t smem_k5(const KArgs &a) {
-    return smem_z_fft(a) + (size_t)T::kZLines * cn_slots(a.nz, a.cn[2].chunk) * E;
+    return smem_z_fft(a) + (size_t)T::kZLines * cn_slots(a.nz, a.cn[2].lchunk) * E;
   }
   static size_t smem_y(const KArgs &a) { return 2 * (size_t)a.ny * (y_lines_per_cta<R>(a.ny) + 1) * E; }
   static size_t smem_x(const KArgs &a) { return 2 * (size_t)a.nx * T::kXCols * E; }
-  static size_t smem_cn(int n, int chunk) {
-    return (size_t)cn_slots(n, chunk) * (T::kCnCols + 1) * E + (size_t)n * sizeof(R);
+  static size_t smem_cn(int n, int lchunk) {
+    return 2 * (size_t)cn_slots(n, lchunk) * (T::kCnCols + 1) * E + (size_t)n * sizeof(R);
   }
 
   static dim3 grid_z(const KArgs &a) { return dim3((a.ny + T::kZLines - 1) / T::kZLines, a.nx); }
+  // persistent grid of the CN kernels: all tiles, capped at the number of co-resident CTAs
+  static int sm_count() {
+    static int n = 0;
+    if (!n) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+      if (n <= 0) n = 1;
+    }
+    return n;
+  }
   static dim3 grid_cn(const KArgs &a, int axis) {
-    return dim3((a.nz + T::kCnCols - 1) / T::kCnCols, axis == 0 ? a.ny : a.nx);
+    const int tiles = ((a.nz + T::kCnCols - 1) / T::kCnCols) * (axis == 0 ? a.ny : a.nx);
+    const int n = a.cn[axis].m + 2;
+    const size_t sm = smem_cn(n, a.cn[axis].lchunk);
+    const int per_sm = sm * 2 + 4096 <= 227 * 1024 ? 2 : 1;
+    const int cap = sm_count() * per_sm;
+    return dim3(tiles < cap ? tiles : cap);
   }
 
   // Allow each kernel the device's opt-in shared memory minus its static shared memory.
@@ -1067,13 +1124,13 @@ struct Impl {
     return cudaGetLastError();
   }
   static cudaError_t k6(const KArgs &a, cudaStream_t st) {
-    const size_t sm = smem_cn(a.ny, a.cn[1].chunk);
+    const size_t sm = smem_cn(a.ny, a.cn[1].lchunk);
     if (a.imag) k_cn<R, R, 1><<<grid_cn(a, 1), T::kCnThreads, sm, st>>>(a, 0, 0);
     else k_cn<R, C, 1><<<grid_cn(a, 1), T::kCnThreads, sm, st>>>(a, 0, 0);
     return cudaGetLastError();
   }
   static cudaError_t k7(const KArgs &a, int reduce, int renorm, cudaStream_t st) {
-    const size_t sm = smem_cn(a.nx, a.cn[0].chunk);
+    const size_t sm = smem_cn(a.nx, a.cn[0].lchunk);
     if (a.imag) k_cn<R, R, 0><<<grid_cn(a, 0), T::kCnThreads, sm, st>>>(a, reduce, renorm);
     else k_cn<R, C, 0><<<grid_cn(a, 0), T::kCnThreads, sm, st>>>(a, reduce, renorm);
     return cudaGetLastError();
@@ -1085,9 +1142,11 @@ struct Impl {
     k_materialize<R><<<(unsigned)blocks, 256, 0, st>>>(a, count);
     return cudaGetLastError();
   }
+  // Host-only bound (no device query): the CN grid never exceeds its tile count.
   static int max_blocks(const KArgs &a) {
-    const dim3 z = grid_z(a), x = grid_cn(a, 0);
-    const int bz = (int)(z.x * z.y), bx = (int)(x.x * x.y);
+    const dim3 z = grid_z(a);
+    const int bz = (int)(z.x * z.y);
+    const int bx = ((a.nz + T::kCnCols - 1) / T::kCnCols) * a.ny;
     return bz > bx ? bz : bx;
   }
 

@@ -23,7 +23,8 @@ struct FftPlan {
 struct CnTab {
   const void *tab;
   int m;
-  int chunk;
+  int chunk;    // interior points per lane, a power of two
+  int lchunk;   // log2(chunk)
 };
 
 // Device-resident solver state (lives in the workspace).
