@@ -113,7 +113,7 @@ Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
   }
   for (int d = 0; d < 3; ++d) {
     L.cn[d] = off;
-    off += align_up((size_t)5 * (n[d] - 2) * e);
+    off += align_up((size_t)5 * kWarp * cn_chunk(n[d]) * e);   // lane-interleaved tables
   }
   L.psi = off;
   off += align_up((size_t)p->nx * p->ny * p->nz * e);

@@ -305,11 +305,13 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   const int chunk = 1 << lchunk;
   const int s0 = t * chunk;
   const int len = max(0, min(chunk, m - s0));
-  const Coef *alpha = tab;
-  const Coef *beta = tab + m;
-  const Coef *P = tab + 2 * m;
-  const Coef *H = tab + 3 * m;
-  const Coef *G = tab + 4 * m;
+  // tables are lane-interleaved: entry of interior point t*chunk + e at [e * 32 + t]
+  const int mp = kWarp << lchunk;
+  const Coef *alpha = tab + t;
+  const Coef *beta = tab + mp + t;
+  const Coef *P = tab + 2 * mp + t;
+  const Coef *H = tab + 3 * mp + t;
+  const Coef *G = tab + 4 * mp + t;
 
   cplx<R> y[kCnMaxChunk];
   cplx<R> acc = czero<R>();
@@ -317,12 +319,12 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   for (int e = 0; e < kCnMaxChunk; ++e) {
     if (e < len) {
       const int i = s0 + e;
-      acc = buf[(i + 1 + t) * es] + mul(ldg(alpha + i), acc);
+      acc = buf[(i + 1 + t) * es] + mul(ldg(alpha + e * kWarp), acc);
       y[e] = acc;
     }
   }
   // forward carries: Y_{t+1} = A_t Y_t + B_t, Y_0 = 0
-  Coef A = len > 0 ? ldg(P + s0 + len - 1) : coef_one<Coef>();
+  Coef A = len > 0 ? ldg(P + (len - 1) * kWarp) : coef_one<Coef>();
   cplx<R> B = acc;
 #pragma unroll
   for (int d = 1; d < kWarp; d <<= 1) {
@@ -341,13 +343,13 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   for (int e = kCnMaxChunk - 1; e >= 0; --e) {
     if (e < len) {
       const int i = s0 + e;
-      acc = mul(ldg(beta + i), y[e] + mul(c, acc));
+      acc = mul(ldg(beta + e * kWarp), y[e] + mul(c, acc));
       y[e] = acc;
     }
   }
   // backward carries: X_t = G_{s0} X_{t+1} + (chi0_{s0} + H_{s0} Y_t), X_32 = 0
-  Coef A2 = len > 0 ? ldg(G + s0) : coef_one<Coef>();
-  cplx<R> B2 = len > 0 ? acc + mul(ldg(H + s0), Y) : czero<R>();
+  Coef A2 = len > 0 ? ldg(G) : coef_one<Coef>();
+  cplx<R> B2 = len > 0 ? acc + mul(ldg(H), Y) : czero<R>();
 #pragma unroll
   for (int d = 1; d < kWarp; d <<= 1) {
     const Coef An = shfl_down(A2, d);
@@ -364,7 +366,7 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   for (int e = 0; e < kCnMaxChunk; ++e) {
     if (e < len) {
       const int i = s0 + e;
-      const cplx<R> chi = y[e] + mul(ldg(H + i), Y) + mul(ldg(G + i), X);
+      const cplx<R> chi = y[e] + mul(ldg(H + e * kWarp), Y) + mul(ldg(G + e * kWarp), X);
       const int q = (i + 1 + t) * es;
       const cplx<R> v = buf[q];
       buf[q] = {R(2) * chi.re - v.re, R(2) * chi.im - v.im};
@@ -480,6 +482,9 @@ __device__ __forceinline__ void store_coef(Coef *tab, int k, Z64 v) {
 template <typename R, typename Coef>
 __global__ void k_cn_tables(Coef *tab, int m, int chunk, double r, int imag) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  // lane-interleaved layout: interior point i = t*chunk + e of table q at q*mp + e*32 + t
+  const int mp = kWarp * chunk;
+  auto at = [&](int q, int i) { return q * mp + (i % chunk) * kWarp + i / chunk; };
   const Z64 c = imag ? Z64{r, 0.0} : Z64{0.0, r};
   const Z64 diag = {1.0 + 2.0 * c.re, 2.0 * c.im};
   const Z64 one = {1.0, 0.0};
@@ -497,8 +502,8 @@ __global__ void k_cn_tables(Coef *tab, int m, int chunk, double r, int imag) {
       al[i - s0] = a;
       be[i - s0] = zdiv(one, e);
       e_prev = e;
-      store_coef<R>(tab, i, a);
-      store_coef<R>(tab, m + i, be[i - s0]);
+      store_coef<R>(tab, at(0, i), a);
+      store_coef<R>(tab, at(1, i), be[i - s0]);
     }
     Z64 p = al[0];
     pv[0] = p;
@@ -506,16 +511,16 @@ __global__ void k_cn_tables(Coef *tab, int m, int chunk, double r, int imag) {
       p = zmul(p, al[i - s0]);
       pv[i - s0] = p;
     }
-    for (int i = s0; i <= end; ++i) store_coef<R>(tab, 2 * m + i, pv[i - s0]);
+    for (int i = s0; i <= end; ++i) store_coef<R>(tab, at(2, i), pv[i - s0]);
     Z64 h = zmul(be[end - s0], pv[end - s0]);
     Z64 gg = zmul(be[end - s0], c);
-    store_coef<R>(tab, 3 * m + end, h);
-    store_coef<R>(tab, 4 * m + end, gg);
+    store_coef<R>(tab, at(3, end), h);
+    store_coef<R>(tab, at(4, end), gg);
     for (int i = end - 1; i >= s0; --i) {
       h = zmul(be[i - s0], zadd(pv[i - s0], zmul(c, h)));
       gg = zmul(be[i - s0], zmul(c, gg));
-      store_coef<R>(tab, 3 * m + i, h);
-      store_coef<R>(tab, 4 * m + i, gg);
+      store_coef<R>(tab, at(3, i), h);
+      store_coef<R>(tab, at(4, i), gg);
     }
   }
 }

@@ -18,8 +18,9 @@ struct FftPlan {
 };
 
 // Crank-Nicolson factor tables of one direction (interior size m = n - 2, chunk length c):
-// five arrays of m coefficients [alpha | beta | P | H | G] (complex in real time, real in
-// imaginary time), element type matching the kernel precision.
+// five arrays [alpha | beta | P | H | G] of 32*c coefficients each (complex in real time,
+// real in imaginary time, in the kernel precision), lane-interleaved: the entry of interior
+// point t*c + e sits at e*32 + t, so the 32 lanes of a warp read one contiguous segment.
 struct CnTab {
   const void *tab;
   int m;
