@@ -65,7 +65,53 @@ __device__ __forceinline__ cplx<R> shfl_up(cplx<R> v, int d) { return {shfl_up(v
 template <typename R>
 __device__ __forceinline__ cplx<R> shfl_down(cplx<R> v, int d) { return {shfl_down(v.re, d), shfl_down(v.im, d)}; }
 
-__device__ __forceinline__ void sin_cos(double x, double *s, double *c) { sincos(x, s, c); }
+// FP64 sine and cosine: Taylor series (coefficients (-1)^k/(2k+1)! and (-1)^k/(2k)!) on
+// |r| <= pi/4 after Cody & Waite (1980) reduction r = x - k pi/2, with pi/2 split into
+// three doubles (two of 32 significant bits, so k * part is exact for |k| < 2^21).  The
+// first omitted terms, r^19/19! and r^20/20!, are below 1e-19.  The phase step's angles
+// are usually inside pi/4, where no reduction runs: about 20 FP64 instructions instead of
+// the general library routine (GB300 issues 2 FP64 instructions per clock per SM).
+__device__ __forceinline__ void sin_cos(double x, double *s, double *c) {
+  double r = x;
+  int q = 0;
+  if (fabs(x) > 0.7853981633974483) {
+    if (!(fabs(x) < 1.0e6)) {   // huge or non-finite: the general routine
+      sincos(x, s, c);
+      return;
+    }
+    const double k = rint(x * 0.6366197723675814);
+    r = fma(-k, 1.5707963267341256, x);
+    r = fma(-k, 6.077100506303966e-11, r);
+    r = fma(-k, 2.0222662487959506e-21, r);
+    q = ((int)k) & 3;
+  }
+  const double u = r * r;
+  double ps = 2.8114572543455206e-15;
+  ps = fma(ps, u, -7.647163731819816e-13);
+  ps = fma(ps, u, 1.6059043836821613e-10);
+  ps = fma(ps, u, -2.505210838544172e-08);
+  ps = fma(ps, u, 2.7557319223985893e-06);
+  ps = fma(ps, u, -0.0001984126984126984);
+  ps = fma(ps, u, 0.008333333333333333);
+  ps = fma(ps, u, -0.16666666666666666);
+  const double sr = fma(r * u, ps, r);
+  double pc = -1.5619206968586225e-16;
+  pc = fma(pc, u, 4.779477332387385e-14);
+  pc = fma(pc, u, -1.1470745597729725e-11);
+  pc = fma(pc, u, 2.08767569878681e-09);
+  pc = fma(pc, u, -2.755731922398589e-07);
+  pc = fma(pc, u, 2.48015873015873e-05);
+  pc = fma(pc, u, -0.001388888888888889);
+  pc = fma(pc, u, 0.041666666666666664);
+  pc = fma(pc, u, -0.5);
+  const double cr = fma(u, pc, 1.0);
+  switch (q) {
+    case 0: *s = sr; *c = cr; break;
+    case 1: *s = cr; *c = -sr; break;
+    case 2: *s = -sr; *c = -cr; break;
+    default: *s = -cr; *c = sr; break;
+  }
+}
 __device__ __forceinline__ void sin_cos(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 __device__ __forceinline__ float exp_r(float x) { return expf(x); }
@@ -823,19 +869,32 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
   }
 
   if (zmode == kZStep || zmode == kZPhaseOnly) {
-    const R sr = R(s);
+    // theta = dt (V + g n + gdd Phi): dt V_z per n and dt (V_x + V_y) per line come from
+    // small per-CTA tables; the 1/(nx ny nz) of the inverse transform is folded into gdd.
+    R *tz = reinterpret_cast<R *>(tile + BZ * LS);
+    R *txy = tz + nz;
     const double x = coordinate(i, a.nx, a.hx);
-    const R vxx = R(a.vx * x * x);
-    const R dt = R(a.dt), g = R(a.g), gdd = R(a.gdd), vy = R(a.vy), vz = R(a.vz);
+    for (int n = threadIdx.x; n < nz; n += blockDim.x) {
+      const double zc = coordinate(n, nz, a.hz);
+      tz[n] = R(a.dt * a.vz * zc * zc);
+    }
+    if (threadIdx.x < BZ) {
+      const double y = coordinate(j0 + threadIdx.x, a.ny, a.hy);
+      txy[threadIdx.x] = R(a.dt * (a.vx * x * x + a.vy * y * y));
+    }
+    __syncthreads();
+    const R sr = R(s);
+    const bool scaled = s != 1.0;
+    const R dtg = R(a.dt * a.g), dtgdd = R(a.dt * a.gdd * a.inv_ntot);
     for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
       const int b = e / nz, n = e - b * nz;
       const int q = b * LS + cn_slot(n, lc);
-      const C v = scale(tile[q], sr);
+      C v = tile[q];
+      if (scaled) v = scale(v, sr);
       const C z = res[n * SB + (b >> 1)];
-      const R phi = ((b & 1) ? z.im : z.re) * inv_ntot;
-      const R y = R(coordinate(j0 + b, a.ny, a.hy)), zc = R(coordinate(n, nz, a.hz));
+      const R phi = (b & 1) ? z.im : z.re;
       const R dens = v.re * v.re + v.im * v.im;
-      const R theta = dt * (vxx + vy * y * y + vz * zc * zc + g * dens + gdd * phi);
+      const R theta = fma(dtg, dens, fma(dtgdd, phi, txy[b] + tz[n]));
       if (a.imag) {
         tile[q] = scale(v, exp_r(-theta));
       } else {
@@ -1026,7 +1085,8 @@ struct Impl {
 
   static size_t smem_z_fft(const KArgs &a) { return 2 * (size_t)a.nz * (T::kZLines / 2 + 1) * E; }
   static size_t smem_k5(const KArgs &a) {
-    return smem_z_fft(a) + (size_t)T::kZLines * cn_slots(a.nz, a.cn[2].lchunk) * E;
+    return smem_z_fft(a) + (size_t)T::kZLines * cn_slots(a.nz, a.cn[2].lchunk) * E +
+           (size_t)(a.nz + T::kZLines) * sizeof(R);
   }
   static size_t smem_y(const KArgs &a) { return 2 * (size_t)a.ny * (y_lines_per_cta<R>(a.ny) + 1) * E; }
   static size_t smem_x(const KArgs &a) { return 2 * (size_t)a.nx * T::kXCols * E; }

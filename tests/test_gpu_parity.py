@@ -202,3 +202,16 @@ def test_mixed_precision_error_vs_oracle(orc, mode):
     assert og["mu"] == pytest.approx(ow["mu"], rel=2e-5)
     assert og["energy"] == pytest.approx(ow["energy"], rel=2e-5)
     gpu.close()
+
+
+@pytest.mark.parametrize("dt", [3.0, -3.0, 0.37])
+def test_potential_step_large_phase_angles(orc, dt):
+    """theta = dt (V + g n + gdd Phi) spanning many multiples of pi/2 (both signs), which
+    exercises the argument reduction of the FP64 sine/cosine."""
+    shape, h = (16, 12, 18), 0.6
+    psi = state(shape, h)
+    gpu, p = make(orc, shape, h, dt, abi.DGPE_REAL_TIME, nu=(2.0, 1.5, 2.5), g=40.0, gdd=30.0)
+    gpu.set_psi(psi)
+    gpu.substep(abi.DGPE_SUB_POTENTIAL)
+    assert rel(gpu.get_psi(), orc.potential_step(p, psi)) < FP64_SUB_TOL
+    gpu.close()
