@@ -95,7 +95,7 @@ int check_physics(const dgpe_params *p) {
 }
 
 struct Layout {
-  size_t state, partials, tw[3], cn[3], psi, spec, total;
+  size_t state, partials, tw[3], cn[3], dtv[3], psi, spec, total;
 };
 
 Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
@@ -114,6 +114,10 @@ Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
   for (int d = 0; d < 3; ++d) {
     L.cn[d] = off;
     off += align_up((size_t)5 * kWarp * cn_chunk(n[d]) * e);   // lane-interleaved tables
+  }
+  for (int d = 0; d < 3; ++d) {
+    L.dtv[d] = off;
+    off += align_up((size_t)n[d] * (e / 2));
   }
   L.psi = off;
   off += align_up((size_t)p->nx * p->ny * p->nz * e);
@@ -154,6 +158,15 @@ void set_physics(KArgs &a, const dgpe_params *p) {
   a.vz = 0.5 * p->nu[2] * p->nu[2];
   a.inv_ntot = 1.0 / ((double)p->nx * p->ny * p->nz);
   a.imag = p->mode == DGPE_IMAG_TIME;
+  const double h[3] = {p->hx, p->hy, p->hz};
+  for (int d = 0; d < 3; ++d) {
+    a.cn_r[d] = p->dt / (4.0 * h[d] * h[d]);
+    a.cn_rf[d] = (float)a.cn_r[d];
+  }
+  a.dtg = p->dt * p->g;
+  a.dtgdd_n = p->dt * p->gdd * a.inv_ntot;
+  a.dtg_f = (float)a.dtg;
+  a.dtgdd_n_f = (float)a.dtgdd_n;
 }
 
 thread_local char g_last_cuda_error[128] = "";
@@ -300,13 +313,19 @@ int build_graph(dgpe_ctx *c) {
   return DGPE_OK;
 }
 
-int setup_tables(dgpe_ctx *c) {
+// Per-axis tables of the physics: dt v_d x^2 (always) and the Crank-Nicolson factor
+// tables (only when dt, h or the mode changed, or on the first call).
+int setup_tables(dgpe_ctx *c, bool cn_changed) {
   const dgpe_params *p = &c->p;
   const double h[3] = {p->hx, p->hy, p->hz};
+  const int n[3] = {p->nx, p->ny, p->nz};
+  const double v[3] = {c->args.vx, c->args.vy, c->args.vz};
   for (int d = 0; d < 3; ++d) {
-    const double r = p->dt / (4.0 * h[d] * h[d]);
-    const int rc = map_cuda(c->ks->cn_tables(at(c, c->L.cn[d]), c->args.cn[d].m, c->args.cn[d].chunk, r,
-                                             p->mode == DGPE_IMAG_TIME, c->stream));
+    int rc = map_cuda(c->ks->axis_potential(at(c, c->L.dtv[d]), n[d], h[d], v[d], p->dt, c->stream));
+    if (rc) return rc;
+    if (!cn_changed) continue;
+    rc = map_cuda(c->ks->cn_tables(at(c, c->L.cn[d]), c->args.cn[d].m, c->args.cn[d].chunk, c->args.cn_r[d],
+                                   p->mode == DGPE_IMAG_TIME, c->stream));
     if (rc) return rc;
   }
   return DGPE_OK;
@@ -394,12 +413,13 @@ int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out) {
   for (int d = 0; d < 3; ++d) {
     a.tw[d] = at(c, c->L.tw[d]);
     a.cn[d].tab = at(c, c->L.cn[d]);
+    a.dtv[d] = at(c, c->L.dtv[d]);
   }
   const int n[3] = {p->nx, p->ny, p->nz};
   rc = map_cuda(cudaMemsetAsync(a.psi, 0, (size_t)p->nx * p->ny * p->nz * c->ks->elem_bytes, c->stream));
   if (!rc) rc = map_cuda(c->ks->reset_state(a.state, c->stream));
   for (int d = 0; d < 3 && !rc; ++d) rc = map_cuda(c->ks->twiddles(const_cast<void *>(a.tw[d]), n[d], c->stream));
-  if (!rc) rc = setup_tables(c);
+  if (!rc) rc = setup_tables(c, true);
   if (rc) {
     dgpe_destroy(c);
     return rc;
@@ -414,6 +434,8 @@ int dgpe_set_params(dgpe_ctx *c, const dgpe_params *p) {
     return DGPE_EINVAL;
   int rc = check_physics(p);
   if (rc) return rc;
+  const bool cn_changed = p->dt != c->p.dt || p->hx != c->p.hx || p->hy != c->p.hy || p->hz != c->p.hz ||
+                          p->mode != c->p.mode;
   void *ws = c->p.workspace;
   const size_t wsb = c->p.workspace_bytes;
   c->p = *p;
@@ -421,7 +443,7 @@ int dgpe_set_params(dgpe_ctx *c, const dgpe_params *p) {
   c->p.workspace_bytes = wsb;
   set_physics(c->args, p);
   c->graph_valid = false;
-  return setup_tables(c);
+  return setup_tables(c, cn_changed);
 }
 
 int dgpe_set_psi(dgpe_ctx *c, const void *psi, int where) {

@@ -344,11 +344,11 @@ __device__ cplx<R> *fft_lines(cplx<R> *a, cplx<R> *b, const FftPlan &pl, int lw,
 // affine recurrences across lanes, resolved by warp-shuffle scans of (A, B) pairs.
 // Element n of the line is at buf[cn_slot(n, lchunk) * es].
 // ---------------------------------------------------------------------------------------
-template <typename R, typename Coef>
+template <typename R, typename Coef, int CH>
 __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m, int lchunk,
                                         const Coef *__restrict__ tab, Coef c) {
   const int t = threadIdx.x & (kWarp - 1);
-  const int chunk = 1 << lchunk;
+  constexpr int chunk = CH;
   const int s0 = t * chunk;
   const int len = max(0, min(chunk, m - s0));
   // tables are lane-interleaved: entry of interior point t*chunk + e at [e * 32 + t]
@@ -359,10 +359,10 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   const Coef *H = tab + 3 * mp + t;
   const Coef *G = tab + 4 * mp + t;
 
-  cplx<R> y[kCnMaxChunk];
+  cplx<R> y[CH];
   cplx<R> acc = czero<R>();
 #pragma unroll
-  for (int e = 0; e < kCnMaxChunk; ++e) {
+  for (int e = 0; e < CH; ++e) {
     if (e < len) {
       const int i = s0 + e;
       acc = buf[(i + 1 + t) * es] + mul(ldg(alpha + e * kWarp), acc);
@@ -386,9 +386,8 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
 
   acc = czero<R>();
 #pragma unroll
-  for (int e = kCnMaxChunk - 1; e >= 0; --e) {
+  for (int e = CH - 1; e >= 0; --e) {
     if (e < len) {
-      const int i = s0 + e;
       acc = mul(ldg(beta + e * kWarp), y[e] + mul(c, acc));
       y[e] = acc;
     }
@@ -409,7 +408,7 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   if (t == kWarp - 1) X = czero<R>();
 
 #pragma unroll
-  for (int e = 0; e < kCnMaxChunk; ++e) {
+  for (int e = 0; e < CH; ++e) {
     if (e < len) {
       const int i = s0 + e;
       const cplx<R> chi = y[e] + mul(ldg(H + e * kWarp), Y) + mul(ldg(G + e * kWarp), X);
@@ -424,16 +423,36 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   }
 }
 
+// cn_line with the chunk length as a compile-time constant (every unrolled iteration live).
+template <typename R, typename Coef>
+__device__ __forceinline__ void cn_line_any(cplx<R> *__restrict__ buf, int es, int m, int lchunk,
+                                            const Coef *__restrict__ tab, Coef c) {
+  switch (lchunk) {
+    case 1: cn_line<R, Coef, 2>(buf, es, m, lchunk, tab, c); break;
+    case 2: cn_line<R, Coef, 4>(buf, es, m, lchunk, tab, c); break;
+    case 3: cn_line<R, Coef, 8>(buf, es, m, lchunk, tab, c); break;
+    default: cn_line<R, Coef, 16>(buf, es, m, lchunk, tab, c); break;
+  }
+}
+
 template <typename R, typename Coef>
 struct CnCoef;
 template <typename R>
 struct CnCoef<R, R> {
-  __device__ static R make(double r) { return R(r); }
+  __device__ static R make(R r) { return r; }
 };
 template <typename R>
 struct CnCoef<R, cplx<R>> {
-  __device__ static cplx<R> make(double r) { return {R(0), R(r)}; }
+  __device__ static cplx<R> make(R r) { return {R(0), r}; }
 };
+
+// A host-precomputed constant in the kernel precision (no FP64 work per thread in FP32).
+template <typename R>
+__device__ __forceinline__ R pick(double d, float f);
+template <>
+__device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
 // ---------------------------------------------------------------------------------------
 // Reductions (FP64): warp shuffle, then across warps; deterministic order.
@@ -568,6 +587,16 @@ __global__ void k_cn_tables(Coef *tab, int m, int chunk, double r, int imag) {
       store_coef<R>(tab, at(3, i), h);
       store_coef<R>(tab, at(4, i), gg);
     }
+  }
+}
+
+// dt v_d x_i^2 on one axis, x_i = (i - n/2) h (the potential-step angle, per axis).
+template <typename R>
+__global__ void k_axis_potential(R *out, int n, double h, double v, double dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double x = (double)(i - n / 2) * h;
+    out[i] = R(dt * v * x * x);
   }
 }
 
@@ -873,19 +902,15 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
     // small per-CTA tables; the 1/(nx ny nz) of the inverse transform is folded into gdd.
     R *tz = reinterpret_cast<R *>(tile + BZ * LS);
     R *txy = tz + nz;
-    const double x = coordinate(i, a.nx, a.hx);
-    for (int n = threadIdx.x; n < nz; n += blockDim.x) {
-      const double zc = coordinate(n, nz, a.hz);
-      tz[n] = R(a.dt * a.vz * zc * zc);
-    }
-    if (threadIdx.x < BZ) {
-      const double y = coordinate(j0 + threadIdx.x, a.ny, a.hy);
-      txy[threadIdx.x] = R(a.dt * (a.vx * x * x + a.vy * y * y));
-    }
+    const R *dtv_x = reinterpret_cast<const R *>(a.dtv[0]);
+    const R *dtv_y = reinterpret_cast<const R *>(a.dtv[1]);
+    const R *dtv_z = reinterpret_cast<const R *>(a.dtv[2]);
+    for (int n = threadIdx.x; n < nz; n += blockDim.x) tz[n] = dtv_z[n];
+    if (threadIdx.x < nl) txy[threadIdx.x] = dtv_x[i] + dtv_y[j0 + threadIdx.x];
     __syncthreads();
     const R sr = R(s);
     const bool scaled = s != 1.0;
-    const R dtg = R(a.dt * a.g), dtgdd = R(a.dt * a.gdd * a.inv_ntot);
+    const R dtg = pick<R>(a.dtg, a.dtg_f), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f);
     for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
       const int b = e / nz, n = e - b * nz;
       const int q = b * LS + cn_slot(n, lc);
@@ -907,10 +932,10 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
   }
 
   if (zmode == kZStep || zmode == kZCnOnly) {
-    const Coef c = CnCoef<R, Coef>::make(a.dt / (4.0 * a.hz * a.hz));
+    const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[2], a.cn_rf[2]));
     const Coef *tab = reinterpret_cast<const Coef *>(a.cn[2].tab);
     for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp)
-      cn_line<R, Coef>(tile + b * LS, 1, a.cn[2].m, lc, tab, c);
+      cn_line_any<R, Coef>(tile + b * LS, 1, a.cn[2].m, lc, tab, c);
     __syncthreads();
   }
 
@@ -995,7 +1020,7 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
       const double x = coordinate(n, a.nx, a.hx);
       x2tab[n] = R(x * x);
     }
-  const Coef c = CnCoef<R, Coef>::make(a.dt / (4.0 * (AXIS == 0 ? a.hx * a.hx : a.hy * a.hy)));
+  const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[AXIS], a.cn_rf[AXIS]));
   const Coef *tab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
   double v[4] = {0, 0, 0, 0};
 
@@ -1014,7 +1039,7 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
     const size_t base = tile_origin(tile, fixed, k0);
     const int nb = min(B, a.nz - k0);
     for (int l = threadIdx.x / kWarp; l < nb; l += blockDim.x / kWarp)
-      cn_line<R, Coef>(cur + l, SB, a.cn[AXIS].m, lc, tab, c);
+      cn_line_any<R, Coef>(cur + l, SB, a.cn[AXIS].m, lc, tab, c);
     __syncthreads();
     if (b < nb) {
       RowSums<R> rs;
@@ -1157,6 +1182,11 @@ struct Impl {
     return cudaGetLastError();
   }
 
+  static cudaError_t axis_potential(void *out, int n, double h, double v, double dt, cudaStream_t st) {
+    k_axis_potential<R><<<(n + 127) / 128, 128, 0, st>>>(reinterpret_cast<R *>(out), n, h, v, dt);
+    return cudaGetLastError();
+  }
+
   static cudaError_t reset_state(DevState *s, cudaStream_t st) {
     k_reset_state<R><<<1, 32, 0, st>>>(s);
     return cudaGetLastError();
@@ -1216,8 +1246,9 @@ struct Impl {
   }
 
   static const KernelSet *set() {
-    static const KernelSet ks = {(int)E, &init, &twiddles, &cn_tables, &reset_state, &k1, &k2, &k3, &k4, &k5, &k6, &k7,
-                                 &materialize, &max_blocks};
+    static const KernelSet ks = {(int)E, &init,          &twiddles,   &cn_tables, &axis_potential, &reset_state,
+                                 &k1,        &k2,            &k3,         &k4,        &k5,             &k6,
+                                 &k7,        &materialize,   &max_blocks};
     return &ks;
   }
 };

@@ -48,6 +48,11 @@ struct KArgs {
   double vx, vy, vz;           // 0.5 * nu_d^2
   double inv_ntot;             // 1 / (nx ny nz)
   int imag;                    // 1 = imaginary time
+  double cn_r[3];              // dt / (4 h_d^2), the Crank-Nicolson coefficient magnitude
+  float cn_rf[3];
+  double dtg, dtgdd_n;         // dt g and dt gdd / (nx ny nz) (Phi's 1/N folded in)
+  float dtg_f, dtgdd_n_f;
+  const void *dtv[3];          // dt v_d x_i^2 per axis (kernel precision)
   void *psi;                   // [nx][ny][nz] complex
   void *spec;                  // [nzh][nx][ny] complex, the z-half-spectrum-major layout
   DevState *state;
@@ -87,6 +92,7 @@ struct KernelSet {
   cudaError_t (*init)();
   cudaError_t (*twiddles)(void *tw, int n, cudaStream_t st);
   cudaError_t (*cn_tables)(void *tab, int m, int chunk, double r, int imag, cudaStream_t st);
+  cudaError_t (*axis_potential)(void *out, int n, double h, double v, double dt, cudaStream_t st);
   cudaError_t (*reset_state)(DevState *st_ptr, cudaStream_t st);
   cudaError_t (*k1)(const KArgs &a, cudaStream_t st);
   cudaError_t (*k2)(const KArgs &a, cudaStream_t st);   // forward FFT along y
