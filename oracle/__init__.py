@@ -78,7 +78,9 @@ def lib():
                                ("orc_potential_step", [P(Params), dp]),
                                ("orc_cn_sweep", [P(Params), dp, ctypes.c_int]),
                                ("orc_step", [P(Params), dp, ctypes.c_int]),
-                               ("orc_observables", [P(Params), dp, P(Obs)])]:
+                               ("orc_observables", [P(Params), dp, P(Obs)]),
+                               ("orc_adjoint_step", [P(Params), dp, dp, dp]),
+                               ("orc_grad_z2", [P(Params), ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp])]:
                 f = getattr(L, name)
                 f.argtypes = args
                 f.restype = None
@@ -181,3 +183,24 @@ def observables(p, psi):
     o = Obs()
     lib().orc_observables(ctypes.byref(p), _ptr(psi), ctypes.byref(o))
     return o.as_dict()
+
+
+def adjoint_step(p, psi_k, gbar):
+    """Cotangent of the step input and (dL/dg, dL/dgdd, dL/dnu_z) of one real-time step."""
+    psi_k = _c128(psi_k)
+    g = _c128(gbar).copy()
+    grads = np.zeros(3)
+    lib().orc_adjoint_step(ctypes.byref(p), _ptr(psi_k), _ptr(g), _ptr(grads))
+    return g, grads
+
+
+def grad_z2(p, nu_z, steps_per_seg, psi0):
+    """L = h^3 sum z^2 |psi_N|^2 under a piecewise-constant nu_z schedule and its adjoint
+    gradient: returns (L, dL/dnu_z[nseg], dL/dg, dL/dgdd)."""
+    nu_z = np.ascontiguousarray(nu_z, dtype=np.float64)
+    psi0 = _c128(psi0)
+    loss, dg, dgdd = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    dnu = np.zeros(nu_z.size)
+    lib().orc_grad_z2(ctypes.byref(p), nu_z.size, int(steps_per_seg), _ptr(nu_z), _ptr(psi0),
+                      ctypes.byref(loss), _ptr(dnu), ctypes.byref(dg), ctypes.byref(dgdd))
+    return loss.value, dnu, dg.value, dgdd.value

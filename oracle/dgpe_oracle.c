@@ -343,3 +343,90 @@ void orc_observables(const orc_params *p, const double complex *psi, orc_obs *o)
   free(n);
   free(phi);
 }
+
+/* ---------------------------------------------------------------------------------------
+ * Adjoint of one real-time step psi' = Z Y X P(psi) (oracle order: potential, x, y, z).
+ *  - Each Crank-Nicolson sweep C = (1 - cD)^{-1}(1 + cD) is complex symmetric, so its adjoint
+ *    is conj(C): the same sweep with c -> conj(c), i.e. dt -> -dt.
+ *  - The potential step P(psi) = e^{-i theta} psi, theta = dt (V + g n + gdd Phi[n]),
+ *    n = |psi|^2: with s = Im(conj(gbar1) P(psi)),
+ *      gbar = e^{+i theta} gbar1 + 2 dt (g s + gdd Phi[s]) psi
+ *    (Phi is a convolution with a real even kernel, hence self-adjoint), and
+ *      dL/dg = dt sum s n, dL/dgdd = dt sum s Phi[n], dL/dnu_z = dt sum s nu_z z^2.
+ * --------------------------------------------------------------------------------------- */
+void orc_adjoint_step(const orc_params *p, const double complex *psi_k, double complex *gbar, double *grads) {
+  long ntot = (long)p->nx * p->ny * p->nz;
+  orc_params back = *p;
+  back.dt = -p->dt;
+  /* sweeps in reverse order, each adjoint = the sweep with -dt */
+  orc_cn_sweep(&back, gbar, 2);
+  orc_cn_sweep(&back, gbar, 1);
+  orc_cn_sweep(&back, gbar, 0);
+  /* potential step */
+  double *n = malloc(sizeof(double) * ntot), *phin = malloc(sizeof(double) * ntot);
+  double *sf = malloc(sizeof(double) * ntot), *phis = malloc(sizeof(double) * ntot);
+  for (long q = 0; q < ntot; ++q) n[q] = creal(psi_k[q]) * creal(psi_k[q]) + cimag(psi_k[q]) * cimag(psi_k[q]);
+  orc_dipolar_phi(p, n, phin);
+  double sg = 0, sdd = 0, snu = 0;
+  for (int i = 0; i < p->nx; ++i)
+    for (int j = 0; j < p->ny; ++j)
+      for (int k = 0; k < p->nz; ++k) {
+        long q = ((long)i * p->ny + j) * p->nz + k;
+        double theta = p->dt * (trap(p, i, j, k) + p->g * n[q] + p->gdd * phin[q]);
+        double complex out = psi_k[q] * cexp(-I * theta);          /* P(psi) */
+        double sv = cimag(conj(gbar[q]) * out);
+        double z = coord(k, p->nz, p->hz);
+        sf[q] = sv;
+        sg += sv * n[q];
+        sdd += sv * phin[q];
+        snu += sv * p->nu[2] * z * z;
+        gbar[q] = gbar[q] * cexp(I * theta);
+      }
+  orc_dipolar_phi(p, sf, phis);
+  for (long q = 0; q < ntot; ++q) gbar[q] += 2.0 * p->dt * (p->g * sf[q] + p->gdd * phis[q]) * psi_k[q];
+  grads[0] += p->dt * sg;
+  grads[1] += p->dt * sdd;
+  grads[2] += p->dt * snu;
+  free(n); free(phin); free(sf); free(phis);
+}
+
+void orc_grad_z2(const orc_params *p, int nseg, int steps_per_seg, const double *nu_z,
+                 const double complex *psi0, double *loss, double *dnu, double *dg, double *dgdd) {
+  long ntot = (long)p->nx * p->ny * p->nz;
+  int nsteps = nseg * steps_per_seg;
+  double complex *states = malloc(sizeof(double complex) * ntot * (nsteps + 1));
+  memcpy(states, psi0, sizeof(double complex) * ntot);
+  orc_params q = *p;
+  q.mode = ORC_REAL_TIME;
+  for (int t = 0; t < nsteps; ++t) {
+    q.nu[2] = nu_z[t / steps_per_seg];
+    memcpy(states + (long)(t + 1) * ntot, states + (long)t * ntot, sizeof(double complex) * ntot);
+    orc_step(&q, states + (long)(t + 1) * ntot, 1);
+  }
+  const double complex *last = states + (long)nsteps * ntot;
+  double dv = p->hx * p->hy * p->hz, l = 0;
+  double complex *gbar = malloc(sizeof(double complex) * ntot);
+  for (int i = 0; i < p->nx; ++i)
+    for (int j = 0; j < p->ny; ++j)
+      for (int k = 0; k < p->nz; ++k) {
+        long idx = ((long)i * p->ny + j) * p->nz + k;
+        double z = coord(k, p->nz, p->hz);
+        double nn = creal(last[idx]) * creal(last[idx]) + cimag(last[idx]) * cimag(last[idx]);
+        l += dv * z * z * nn;
+        gbar[idx] = 2.0 * dv * z * z * last[idx];     /* 2 dL/d conj(psi_N) */
+      }
+  *loss = l;
+  *dg = 0;
+  *dgdd = 0;
+  for (int s = 0; s < nseg; ++s) dnu[s] = 0;
+  for (int t = nsteps - 1; t >= 0; --t) {
+    double gr[3] = {0, 0, 0};
+    q.nu[2] = nu_z[t / steps_per_seg];
+    orc_adjoint_step(&q, states + (long)t * ntot, gbar, gr);
+    *dg += gr[0];
+    *dgdd += gr[1];
+    dnu[t / steps_per_seg] += gr[2];
+  }
+  free(gbar);
+  free(states);
+}

@@ -80,4 +80,19 @@ void orc_cn_sweep(const orc_params *p, double complex *psi, int axis);
 void orc_step(const orc_params *p, double complex *psi, int nsteps);
 void orc_observables(const orc_params *p, const double complex *psi, orc_obs *o);
 
+/* Discrete adjoint of one real-time step (paper's method differentiated by hand; the
+ * paper itself has no adjoint).  Real-valued loss L, cotangent gbar = 2 dL/d conj(psi), so
+ * that dL = Re sum conj(gbar) dpsi.  On entry gbar is the cotangent of the step's output,
+ * psi_k the step's input; on exit gbar is the cotangent of psi_k and
+ *   grads[0] += dL/dg,  grads[1] += dL/dgdd,  grads[2] += dL/dnu_z
+ * (the step's own contribution; nu_z of p). */
+void orc_adjoint_step(const orc_params *p, const double complex *psi_k, double complex *gbar, double *grads);
+
+/* L = hx hy hz sum z^2 |psi_N|^2 after nseg * steps_per_seg real-time steps from psi0, with
+ * nu_z = nu_z[s] during segment s (the other parameters from p), and its gradient by the
+ * adjoint: dnu[s] = dL/dnu_z[s], dg = dL/dg, dgdd = dL/dgdd.  Keeps every state in memory
+ * (meant for small grids). */
+void orc_grad_z2(const orc_params *p, int nseg, int steps_per_seg, const double *nu_z,
+                 const double complex *psi0, double *loss, double *dnu, double *dg, double *dgdd);
+
 #endif
