@@ -148,6 +148,43 @@ int dgpe_observables(dgpe_ctx *ctx, dgpe_obs *o);
  * double for FP64, float for MIXED) into host or device memory.  Synchronises for host. */
 int dgpe_get_phi(dgpe_ctx *ctx, void *out, int where);
 
+/* ---- Differentiation (real time only) ----------------------------------------------
+ * Discrete adjoint of the real-time step, written by hand (the paper has no adjoint; this
+ * differentiates the step it describes).  Cotangent convention: for a real loss L,
+ * gbar = 2 dL/d conj(psi), so that dL = Re sum conj(gbar) dpsi.  Of one step
+ * psi' = X Y Z P(psi): each Crank-Nicolson sweep's adjoint is the same sweep with
+ * dt -> -dt, and the potential step's adjoint is
+ *   gbar = e^{+i theta} gbar1 + 2 dt (g s + gdd Phi[s]) psi,  s = Im(conj(gbar1) P(psi)),
+ * with dL/dg = dt sum s |psi|^2, dL/dgdd = dt sum s Phi[|psi|^2], dL/dnu_z = dt nu_z sum s z^2.
+ */
+
+/* One adjoint step.  psi_k: device, the step's input state ([nx][ny][nz], the context's
+ * complex type), not modified.  gbar: device, in = cotangent of the step's output,
+ * out = cotangent of psi_k.  Adds the step's dL/dg, dL/dgdd, dL/dnu_z to the context's
+ * accumulators (dgpe_adjoint_grads).  Uses the context's parameters (nu_z, g, gdd, dt),
+ * which must be those of the forward step.  DGPE_EUNSUPPORTED in imaginary time. */
+int dgpe_adjoint_step(dgpe_ctx *ctx, const void *psi_k, void *gbar);
+
+/* Synchronises and copies the accumulated {dL/dg, dL/dgdd, dL/dnu_z} into out[3]; reset != 0
+ * zeroes the accumulators afterwards. */
+int dgpe_adjoint_grads(dgpe_ctx *ctx, double *out, int reset);
+
+/* Device bytes of the work buffer of dgpe_grad_z2 for nseg segments of steps_per_seg
+ * steps: sqrt(N) checkpointing keeps ceil(N/k) checkpoints plus the k states of one
+ * segment (k = ceil(sqrt(N)), N = nseg * steps_per_seg), the cotangent and nseg sums. */
+int dgpe_grad_z2_workspace_bytes(const dgpe_ctx *ctx, int nseg, int steps_per_seg, size_t *bytes);
+
+/* Gradient of L = hx hy hz sum z^2 |psi_N|^2 (= <z^2> of a unit-norm state) after
+ * N = nseg * steps_per_seg real-time steps from the current psi, with the trap frequency
+ * nu_z = nu_z[s] (host array) during steps [s*steps_per_seg, (s+1)*steps_per_seg), the other
+ * parameters fixed.  Outputs (host): *loss, dnu[s] = dL/dnu_z[s] (nseg values), *dg, *dgdd.
+ * work: device memory of dgpe_grad_z2_workspace_bytes(), 256-byte aligned, caller-owned.
+ * Cost: one forward pass storing a checkpoint every k steps, then per segment (backwards)
+ * a recomputation from its checkpoint and the adjoint steps through it.  On return the
+ * context holds the initial psi and the initial nu_z again.  Synchronises. */
+int dgpe_grad_z2(dgpe_ctx *ctx, int nseg, int steps_per_seg, const double *nu_z, void *work, size_t work_bytes,
+                 double *loss, double *dnu, double *dg, double *dgdd);
+
 /* Wait for the stream; returns a latched device error if any. */
 int dgpe_sync(dgpe_ctx *ctx);
 

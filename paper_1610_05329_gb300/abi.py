@@ -85,6 +85,12 @@ _SIGNATURES = [
     ("dgpe_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("dgpe_set_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("dgpe_kernel_times", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_kernel_time), ctypes.c_int, _P(ctypes.c_int)]),
+    ("dgpe_adjoint_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("dgpe_adjoint_grads", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("dgpe_grad_z2_workspace_bytes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _P(ctypes.c_size_t)]),
+    ("dgpe_grad_z2", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_size_t, _P(ctypes.c_double), ctypes.c_void_p, _P(ctypes.c_double),
+                                    _P(ctypes.c_double)]),
     ("dgpe_moments_noalloc", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_params), ctypes.c_void_p, ctypes.c_void_p]),
     ("dgpe_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("dgpe_last_cuda_error", ctypes.c_char_p, []),
@@ -196,6 +202,33 @@ def dgpe_kernel_times(ctx, max_kernels=16):
     _check(load().dgpe_kernel_times(ctx, arr, max_kernels, ctypes.byref(n)), "dgpe_kernel_times")
     return [{"name": arr[i].name.decode(), "total_ms": arr[i].total_ms, "launches": arr[i].launches,
              "bytes_per_launch": arr[i].bytes_per_launch} for i in range(min(n.value, max_kernels))]
+
+
+def dgpe_adjoint_step(ctx, psi_k_ptr, gbar_ptr):
+    _check(load().dgpe_adjoint_step(ctx, ctypes.c_void_p(psi_k_ptr), ctypes.c_void_p(gbar_ptr)), "dgpe_adjoint_step")
+
+
+def dgpe_adjoint_grads(ctx, reset=False):
+    out = (ctypes.c_double * 3)()
+    _check(load().dgpe_adjoint_grads(ctx, out, 1 if reset else 0), "dgpe_adjoint_grads")
+    return np.array(out[:])
+
+
+def dgpe_grad_z2_workspace_bytes(ctx, nseg, steps_per_seg):
+    n = ctypes.c_size_t(0)
+    _check(load().dgpe_grad_z2_workspace_bytes(ctx, int(nseg), int(steps_per_seg), ctypes.byref(n)),
+           "dgpe_grad_z2_workspace_bytes")
+    return n.value
+
+
+def dgpe_grad_z2(ctx, nu_z, steps_per_seg, work_ptr, work_bytes):
+    nu = np.ascontiguousarray(nu_z, dtype=np.float64)
+    dnu = np.zeros(nu.size)
+    loss, dg, dgdd = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().dgpe_grad_z2(ctx, nu.size, int(steps_per_seg), nu.ctypes.data, ctypes.c_void_p(work_ptr),
+                               int(work_bytes), ctypes.byref(loss), dnu.ctypes.data, ctypes.byref(dg),
+                               ctypes.byref(dgdd)), "dgpe_grad_z2")
+    return loss.value, dnu, dg.value, dgdd.value
 
 
 def dgpe_moments_noalloc(psi_ptr, params, out_ptr, stream=0):
@@ -317,3 +350,64 @@ class Condensate:
 
     def kernel_times(self):
         return dgpe_kernel_times(self.ctx)
+
+    def adjoint_step(self, psi_k, gbar):
+        """gbar (device tensor) <- cotangent of psi_k for one real-time step (in place)."""
+        dgpe_adjoint_step(self.ctx, psi_k.data_ptr(), gbar.data_ptr())
+
+    def adjoint_grads(self, reset=False):
+        return dgpe_adjoint_grads(self.ctx, reset)
+
+    def grad_z2(self, nu_z, steps_per_seg):
+        """(L, dL/dnu_z[nseg], dL/dg, dL/dgdd) of L = <z^2> of the final state of a real-time
+        trajectory under a piecewise-constant nu_z schedule (sqrt(N) checkpointing); the
+        checkpoint buffer is a PyTorch tensor kept between calls."""
+        nu = np.ascontiguousarray(nu_z, dtype=np.float64)
+        need = dgpe_grad_z2_workspace_bytes(self.ctx, nu.size, steps_per_seg)
+        work = getattr(self, "_grad_work", None)
+        if work is None or work.numel() < need:
+            work = self._torch.empty(need, dtype=self._torch.uint8, device=self.device)
+            self._grad_work = work
+        return dgpe_grad_z2(self.ctx, nu, steps_per_seg, work.data_ptr(), work.numel())
+
+
+def trajectory_z2(condensate, nu_z, g, gdd, steps_per_seg):
+    """Differentiable L = <z^2> of the final state of a real-time trajectory (torch autograd).
+
+    nu_z: 1-D float64 tensor (one trap frequency per segment), g, gdd: 0-d float64 tensors.
+    The trajectory starts from the condensate's current psi, which is restored afterwards.
+    Gradients come from the hand-written adjoint (dgpe_grad_z2)."""
+    return _TrajectoryZ2.apply(nu_z, g, gdd, condensate, steps_per_seg)
+
+
+def _make_autograd_function():
+    import torch
+
+    class TrajectoryZ2(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, nu_z, g, gdd, condensate, steps_per_seg):
+            condensate.set_params(g=float(g), gdd=float(gdd))
+            loss, dnu, dg, dgdd = condensate.grad_z2(nu_z.detach().cpu().numpy(), steps_per_seg)
+            ctx.save_for_backward(torch.as_tensor(dnu, dtype=torch.float64),
+                                  torch.tensor(dg, dtype=torch.float64), torch.tensor(dgdd, dtype=torch.float64))
+            return torch.tensor(loss, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            dnu, dg, dgdd = ctx.saved_tensors
+            g = grad_out.to(torch.float64)
+            return g * dnu, g * dg, g * dgdd, None, None
+
+    return TrajectoryZ2
+
+
+class _LazyFunction:
+    _fn = None
+
+    def apply(self, *args):
+        if _LazyFunction._fn is None:
+            _LazyFunction._fn = _make_autograd_function()
+        return _LazyFunction._fn.apply(*args)
+
+
+_TrajectoryZ2 = _LazyFunction()

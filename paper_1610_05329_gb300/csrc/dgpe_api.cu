@@ -95,7 +95,7 @@ int check_physics(const dgpe_params *p) {
 }
 
 struct Layout {
-  size_t state, partials, tw[3], cn[3], dtv[3], psi, spec, total;
+  size_t state, partials, tw[3], cn[3], cn_adj[3], dtv[3], psi, spec, total;
 };
 
 Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
@@ -114,6 +114,8 @@ Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
   for (int d = 0; d < 3; ++d) {
     L.cn[d] = off;
     off += align_up((size_t)5 * kWarp * cn_chunk(n[d]) * e);   // lane-interleaved tables
+    L.cn_adj[d] = off;                                          // the same for dt -> -dt (adjoint)
+    off += align_up((size_t)5 * kWarp * cn_chunk(n[d]) * e);
   }
   for (int d = 0; d < 3; ++d) {
     L.dtv[d] = off;
@@ -163,6 +165,7 @@ void set_physics(KArgs &a, const dgpe_params *p) {
     a.cn_r[d] = p->dt / (4.0 * h[d] * h[d]);
     a.cn_rf[d] = (float)a.cn_r[d];
   }
+  a.dt_nuz = p->dt * p->nu[2];
   a.dtg = p->dt * p->g;
   a.dtgdd_n = p->dt * p->gdd * a.inv_ntot;
   a.dtg_f = (float)a.dtg;
@@ -178,9 +181,10 @@ int map_cuda(cudaError_t e) {
   return DGPE_ECUDA;
 }
 
-const char *kKernelNames[kNumKernels] = {"k1_density_r2c_z",      "k2_fft_y",   "k3_fft_x_dipolar_ifft_x",
-                                         "k4_ifft_y",             "k5_c2r_z_phase_cn_z", "k6_cn_y",
-                                         "k7_cn_x_reduce",        "materialize", "observables"};
+const char *kKernelNames[kNumKernels] = {"k1_density_r2c_z",  "k2_fft_y",            "k3_fft_x_dipolar_ifft_x",
+                                         "k4_ifft_y",         "k5_c2r_z_phase_cn_z", "k6_cn_y",
+                                         "k7_cn_x_reduce",    "materialize",         "observables",
+                                         "adj_phase_r2c_z",   "adj_combine"};
 
 }  // namespace
 
@@ -225,6 +229,8 @@ double kernel_bytes(const dgpe_ctx *c, int k) {
     case kK7CnXReduce:
     case kKMaterialize: return 2 * e * ntot;
     case kKObs: return e * (nspec + 5 * ntot);
+    case kKAdjPhase: return e * (2 * nspec + 4 * ntot);
+    case kKAdjCombine: return e * (nspec + 3 * ntot);
     default: return 0;
   }
 }
@@ -327,6 +333,10 @@ int setup_tables(dgpe_ctx *c, bool cn_changed) {
     rc = map_cuda(c->ks->cn_tables(at(c, c->L.cn[d]), c->args.cn[d].m, c->args.cn[d].chunk, c->args.cn_r[d],
                                    p->mode == DGPE_IMAG_TIME, c->stream));
     if (rc) return rc;
+    if (p->mode == DGPE_REAL_TIME)   // the adjoint sweep is the sweep with dt -> -dt
+      rc = map_cuda(c->ks->cn_tables(at(c, c->L.cn_adj[d]), c->args.cn[d].m, c->args.cn[d].chunk,
+                                     -c->args.cn_r[d], 0, c->stream));
+    if (rc) return rc;
   }
   return DGPE_OK;
 }
@@ -339,6 +349,83 @@ int check_device_flags(dgpe_ctx *c) {
   if (e != cudaSuccess) return map_cuda(e);
   if (flags & kFlagNonFinite) c->latched = DGPE_ENONFINITE;
   return c->latched;
+}
+
+}  // namespace
+
+namespace {
+
+// The sweeps of the adjoint step run on the cotangent with the conjugate (dt -> -dt) tables.
+KArgs adjoint_sweep_args(dgpe_ctx *c, void *gbar) {
+  KArgs a = c->args;
+  a.psi = gbar;
+  for (int d = 0; d < 3; ++d) {
+    a.cn[d].tab = at(c, c->L.cn_adj[d]);
+    a.cn_r[d] = -a.cn_r[d];
+    a.cn_rf[d] = -a.cn_rf[d];
+  }
+  return a;
+}
+
+// Adjoint of one real-time step (GPU order P, Z, Y, X): X^H, Y^H, Z^H on gbar, then the
+// adjoint of the potential step, which needs Phi of |psi_k|^2 and then Phi of s.
+int enqueue_adjoint_step(dgpe_ctx *c, const void *psi_k, void *gbar, double *nu_slot) {
+  cudaStream_t st = c->stream;
+  const KernelSet *ks = c->ks;
+  const KArgs sw = adjoint_sweep_args(c, gbar);
+  int rc;
+  if ((rc = launch(c, st, kK7CnXReduce, [&] { return ks->k7(sw, 0, 0, st); }))) return rc;
+  if ((rc = launch(c, st, kK6CnY, [&] { return ks->k6(sw, st); }))) return rc;
+  if ((rc = launch(c, st, kK5C2RzPhaseCnz, [&] { return ks->k5(sw, kZCnOnly, st); }))) return rc;
+  KArgs fa = c->args;
+  fa.psi = const_cast<void *>(psi_k);
+  fa.gbar = gbar;
+  fa.unit_scale = 1;
+  fa.grad_nu_slot = nu_slot;
+  if ((rc = launch(c, st, kK1DensityR2Cz, [&] { return ks->k1(fa, st); }))) return rc;
+  if ((rc = launch(c, st, kK2FftY, [&] { return ks->k2(fa, st); }))) return rc;
+  if ((rc = launch(c, st, kK3FftXDipolar, [&] { return ks->k3(fa, st); }))) return rc;
+  if ((rc = launch(c, st, kK4IfftY, [&] { return ks->k4(fa, st); }))) return rc;
+  if ((rc = launch(c, st, kKAdjPhase, [&] { return ks->adj_phase(fa, st); }))) return rc;
+  if ((rc = launch(c, st, kK2FftY, [&] { return ks->k2(fa, st); }))) return rc;
+  if ((rc = launch(c, st, kK3FftXDipolar, [&] { return ks->k3(fa, st); }))) return rc;
+  if ((rc = launch(c, st, kK4IfftY, [&] { return ks->k4(fa, st); }))) return rc;
+  return launch(c, st, kKAdjCombine, [&] { return ks->adj_combine(fa, st); });
+}
+
+// nu_z during a trajectory: only the z table of dt v_z z^2 is rebuilt (the captured step
+// graph stays valid).
+int set_nu_z(dgpe_ctx *c, double v) {
+  if (v == c->p.nu[2]) return DGPE_OK;
+  c->p.nu[2] = v;
+  c->args.vz = 0.5 * v * v;
+  c->args.dt_nuz = c->p.dt * v;
+  return map_cuda(c->ks->axis_potential(at(c, c->L.dtv[2]), c->p.nz, c->p.hz, c->args.vz, c->p.dt, c->stream));
+}
+
+int grad_steps_per_checkpoint(int nsteps) {
+  int k = 1;
+  while ((long)k * k < nsteps) ++k;
+  return k;
+}
+
+struct GradLayout {
+  size_t state, ckpt, seg, gbar, dnu, total;
+  int k, nck;
+};
+
+GradLayout grad_layout(const dgpe_ctx *c, int nseg, int steps_per_seg) {
+  GradLayout g{};
+  const int n = nseg * steps_per_seg;
+  g.k = grad_steps_per_checkpoint(n);
+  g.nck = (n + g.k - 1) / g.k;
+  g.state = align_up((size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes);
+  g.ckpt = 0;
+  g.seg = g.ckpt + (size_t)g.nck * g.state;
+  g.gbar = g.seg + (size_t)g.k * g.state;
+  g.dnu = g.gbar + g.state;
+  g.total = g.dnu + align_up((size_t)nseg * sizeof(double));
+  return g;
 }
 
 }  // namespace
@@ -436,13 +523,16 @@ int dgpe_set_params(dgpe_ctx *c, const dgpe_params *p) {
   if (rc) return rc;
   const bool cn_changed = p->dt != c->p.dt || p->hx != c->p.hx || p->hy != c->p.hy || p->hz != c->p.hz ||
                           p->mode != c->p.mode;
+  const bool step_args_changed = cn_changed || p->g != c->p.g || p->gdd != c->p.gdd;
   void *ws = c->p.workspace;
   const size_t wsb = c->p.workspace_bytes;
   c->p = *p;
   c->p.workspace = ws;
   c->p.workspace_bytes = wsb;
   set_physics(c->args, p);
-  c->graph_valid = false;
+  // the step kernels read the trap only through the per-axis tables rebuilt below, so a
+  // change of nu alone keeps the captured graph valid
+  if (step_args_changed) c->graph_valid = false;
   return setup_tables(c, cn_changed);
 }
 
@@ -554,6 +644,98 @@ int dgpe_get_phi(dgpe_ctx *c, void *out, int where) {
     if (!rc) rc = check_device_flags(c);
   }
   return rc;
+}
+
+int dgpe_adjoint_step(dgpe_ctx *c, const void *psi_k, void *gbar) {
+  if (!c || !psi_k || !gbar) return DGPE_EINVAL;
+  if (c->p.mode != DGPE_REAL_TIME) return DGPE_EUNSUPPORTED;
+  return enqueue_adjoint_step(c, psi_k, gbar, nullptr);
+}
+
+int dgpe_adjoint_grads(dgpe_ctx *c, double *out, int reset) {
+  if (!c || !out) return DGPE_EINVAL;
+  double *dev = c->args.state->grads;
+  int rc = map_cuda(cudaMemcpyAsync(out, dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (!rc && reset) rc = map_cuda(cudaMemsetAsync(dev, 0, 4 * sizeof(double), c->stream));
+  if (!rc) rc = map_cuda(cudaStreamSynchronize(c->stream));
+  return rc;
+}
+
+int dgpe_grad_z2_workspace_bytes(const dgpe_ctx *c, int nseg, int steps_per_seg, size_t *bytes) {
+  if (!c || !bytes || nseg < 1 || steps_per_seg < 1) return DGPE_EINVAL;
+  *bytes = grad_layout(c, nseg, steps_per_seg).total;
+  return DGPE_OK;
+}
+
+int dgpe_grad_z2(dgpe_ctx *c, int nseg, int steps_per_seg, const double *nu_z, void *work, size_t work_bytes,
+                 double *loss, double *dnu, double *dg, double *dgdd) {
+  if (!c || !nu_z || !work || !loss || !dnu || !dg || !dgdd || nseg < 1 || steps_per_seg < 1) return DGPE_EINVAL;
+  if (c->p.mode != DGPE_REAL_TIME) return DGPE_EUNSUPPORTED;
+  for (int s = 0; s < nseg; ++s)
+    if (!isfinite(nu_z[s])) return DGPE_EINVAL;
+  const GradLayout g = grad_layout(c, nseg, steps_per_seg);
+  if (work_bytes < g.total) return DGPE_ENOMEM;
+  if (reinterpret_cast<uintptr_t>(work) % kAlign) return DGPE_EINVAL;
+  char *w = static_cast<char *>(work);
+  const int n = nseg * steps_per_seg;
+  const size_t sb = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;
+  cudaStream_t st = c->stream;
+  void *psi = c->args.psi;
+  void *gbar = w + g.gbar;
+  double *dnu_dev = reinterpret_cast<double *>(w + g.dnu);
+  const double nu_z0 = c->p.nu[2];
+  int rc = DGPE_OK;
+  auto chk = [&](int r) {
+    if (rc == DGPE_OK) rc = r;
+    return rc == DGPE_OK;
+  };
+  // absorb a pending renormalisation so that every checkpoint is the state itself
+  chk(launch(c, st, kKMaterialize, [&] { return c->ks->materialize(c->args, st); }));
+  chk(map_cuda(cudaMemsetAsync(c->args.state->grads, 0, 4 * sizeof(double), st)));
+  chk(map_cuda(cudaMemsetAsync(dnu_dev, 0, (size_t)nseg * sizeof(double), st)));
+  // forward trajectory with a checkpoint of psi every k steps
+  for (int t = 0; t < n && rc == DGPE_OK; ++t) {
+    if (t % g.k == 0) chk(map_cuda(cudaMemcpyAsync(w + g.ckpt + (size_t)(t / g.k) * g.state, psi, sb,
+                                                   cudaMemcpyDeviceToDevice, st)));
+    chk(set_nu_z(c, nu_z[t / steps_per_seg]));
+    chk(dgpe_step(c, 1));
+  }
+  // L = h^3 sum z^2 |psi_N|^2 is the last x-sweep's z^2 moment; its cotangent seeds gbar
+  double sum_z2 = 0;
+  chk(map_cuda(cudaMemcpyAsync(&sum_z2, &c->args.state->sums[3], sizeof(double), cudaMemcpyDeviceToHost, st)));
+  KArgs la = c->args;
+  la.gbar = gbar;
+  chk(map_cuda(c->ks->loss_z2(la, st)));
+  chk(map_cuda(cudaStreamSynchronize(st)));
+  *loss = c->p.hx * c->p.hy * c->p.hz * sum_z2;
+  // backward, segment by segment: recompute the states of a segment from its checkpoint,
+  // then run the adjoint steps through it in reverse
+  for (int ck = g.nck - 1; ck >= 0 && rc == DGPE_OK; --ck) {
+    const int t0 = ck * g.k, t1 = (t0 + g.k < n) ? t0 + g.k : n;
+    chk(map_cuda(cudaMemcpyAsync(psi, w + g.ckpt + (size_t)ck * g.state, sb, cudaMemcpyDeviceToDevice, st)));
+    for (int t = t0; t < t1 && rc == DGPE_OK; ++t) {
+      chk(map_cuda(cudaMemcpyAsync(w + g.seg + (size_t)(t - t0) * g.state, psi, sb, cudaMemcpyDeviceToDevice, st)));
+      if (t + 1 < t1) {   // the state after the segment's last step is not needed
+        chk(set_nu_z(c, nu_z[t / steps_per_seg]));
+        chk(dgpe_step(c, 1));
+      }
+    }
+    for (int t = t1 - 1; t >= t0 && rc == DGPE_OK; --t) {
+      chk(set_nu_z(c, nu_z[t / steps_per_seg]));
+      chk(enqueue_adjoint_step(c, w + g.seg + (size_t)(t - t0) * g.state, gbar, dnu_dev + t / steps_per_seg));
+    }
+  }
+  // leave the context at the initial state and the initial nu_z
+  chk(map_cuda(cudaMemcpyAsync(psi, w + g.ckpt, sb, cudaMemcpyDeviceToDevice, st)));
+  chk(set_nu_z(c, nu_z0));
+  double gr[4] = {0, 0, 0, 0};
+  chk(map_cuda(cudaMemcpyAsync(gr, c->args.state->grads, sizeof(gr), cudaMemcpyDeviceToHost, st)));
+  chk(map_cuda(cudaMemcpyAsync(dnu, dnu_dev, (size_t)nseg * sizeof(double), cudaMemcpyDeviceToHost, st)));
+  chk(map_cuda(cudaStreamSynchronize(st)));
+  if (rc) return rc;
+  *dg = gr[0];
+  *dgdd = gr[1];
+  return check_device_flags(c);
 }
 
 int dgpe_sync(dgpe_ctx *c) {

@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) 
   const int nl = min(BZ, a.ny - j0), np = nl >> 1;
   C *za = reinterpret_cast<C *>(smem_raw);
   C *zb = za + nz * SB;
-  const double s = a.state->s;
+  const double s = a.unit_scale ? 1.0 : a.state->s;
   const R s2 = R(s * s);
   const C *psi = reinterpret_cast<const C *>(a.psi) + ((size_t)i * a.ny + j0) * nz;
   const int total = nl * nz;
@@ -1078,6 +1078,205 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Adjoint of the real-time potential step (the paper has no adjoint; this differentiates
+// the step above by hand).  With P(psi) = e^{-i theta} psi, theta = dt (V + g n + gdd Phi[n])
+// and the cotangent gbar1 of P's output:
+//   u = e^{+i theta} gbar1,  s = Im(conj(gbar1) P(psi)) = Im(conj(u) psi),
+//   gbar = u + 2 dt (g s + gdd Phi[s]) psi,
+//   dL/dg = dt sum s n,  dL/dgdd = dt sum s Phi[n],  dL/dnu_z = dt nu_z sum s z^2.
+// k5_adj_phase: C2R of the spectrum of n -> Phi[n]; theta; u (written over gbar); the three
+// sums; then s is transformed along z (R2C, as in K1) and written back to the same
+// spectrum column (each CTA owns its (i, j0..) column, so reading and writing it is safe).
+// k5_adj_combine: C2R of the spectrum of s (after the y/x passes) -> Phi[s]; final gbar.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+struct AdjSums;
+template <>
+struct AdjSums<double> {
+  double v[3] = {0, 0, 0};
+  __device__ __forceinline__ void add(double sg, double sdd, double snu) {
+    v[0] += sg;
+    v[1] += sdd;
+    v[2] += snu;
+  }
+  __device__ __forceinline__ double get(int q) const { return v[q]; }
+};
+template <>
+struct AdjSums<float> {
+  DFAcc v[3];
+  __device__ __forceinline__ void add(float sg, float sdd, float snu) {
+    v[0].add(sg);
+    v[1].add(sdd);
+    v[2].add(snu);
+  }
+  __device__ __forceinline__ double get(int q) const { return v[q].value(); }
+};
+
+template <typename R>
+__device__ __forceinline__ void load_half_spectrum_column(const KArgs &a, cplx<R> *za, int i, int j0, int np) {
+  using C = cplx<R>;
+  constexpr int PZ = Tiles<R>::kZLines / 2;
+  constexpr int SB = PZ + 1;
+  const int nz = a.nz, half = nz / 2;
+  const C *spec = reinterpret_cast<const C *>(a.spec) + (size_t)i * a.ny + j0;
+  const size_t plane = (size_t)a.nx * a.ny;
+  const int p = threadIdx.x % PZ;
+  if (p >= np) return;
+  for (int m = threadIdx.x / PZ; m < a.nzh; m += blockDim.x / PZ) {
+    C x1 = spec[m * plane + 2 * p];
+    C x2 = spec[m * plane + 2 * p + 1];
+    if (m == 0 || m == half) {
+      x1.im = R(0);
+      x2.im = R(0);
+    }
+    za[m * SB + p] = {x1.re - x2.im, x1.im + x2.re};
+    if (m > 0 && m < half) za[(nz - m) * SB + p] = {x1.re + x2.im, x2.re - x1.im};
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void store_half_spectrum_column(const KArgs &a, const cplx<R> *res, int i, int j0, int np) {
+  using C = cplx<R>;
+  constexpr int PZ = Tiles<R>::kZLines / 2;
+  constexpr int SB = PZ + 1;
+  const int nz = a.nz;
+  C *spec = reinterpret_cast<C *>(a.spec) + (size_t)i * a.ny + j0;
+  const size_t plane = (size_t)a.nx * a.ny;
+  const int p = threadIdx.x % PZ;
+  if (p >= np) return;
+  for (int m = threadIdx.x / PZ; m < a.nzh; m += blockDim.x / PZ) {
+    const C zm = res[m * SB + p];
+    const C zc = res[((nz - m) % nz) * SB + p];
+    C *dst = spec + m * plane + 2 * p;
+    dst[0] = {R(0.5) * (zm.re + zc.re), R(0.5) * (zm.im - zc.im)};
+    dst[1] = {R(0.5) * (zm.im + zc.im), R(0.5) * (zc.re - zm.re)};
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_phase(KArgs a) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int BZ = Tiles<R>::kZLines;
+  constexpr int PZ = BZ / 2;
+  constexpr int SB = PZ + 1;
+  const int nz = a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
+  const int nl = min(BZ, a.ny - j0), np = nl >> 1;
+  C *za = reinterpret_cast<C *>(smem_raw);
+  C *zb = za + nz * SB;
+  C *pk = zb + nz * SB;      // psi_k tile [b][n]
+  C *gt = pk + BZ * nz;      // gbar tile [b][n]
+  R *tz = reinterpret_cast<R *>(gt + BZ * nz);
+  R *z2 = tz + nz;
+  R *txy = z2 + nz;
+  const size_t line0 = (size_t)i * a.ny + j0;
+  const C *psi = reinterpret_cast<const C *>(a.psi) + line0 * nz;
+  C *gb = reinterpret_cast<C *>(a.gbar) + line0 * nz;
+  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
+    cp_async(pk + e, psi + e);
+    cp_async(gt + e, gb + e);
+  }
+  const R *dtv_x = reinterpret_cast<const R *>(a.dtv[0]);
+  const R *dtv_y = reinterpret_cast<const R *>(a.dtv[1]);
+  const R *dtv_z = reinterpret_cast<const R *>(a.dtv[2]);
+  for (int n = threadIdx.x; n < nz; n += blockDim.x) {
+    tz[n] = dtv_z[n];
+    const double zc = coordinate(n, nz, a.hz);
+    z2[n] = R(zc * zc);
+  }
+  if (threadIdx.x < nl) txy[threadIdx.x] = dtv_x[i] + dtv_y[j0 + threadIdx.x];
+  load_half_spectrum_column<R>(a, za, i, j0, np);
+  __syncthreads();
+  C *res = fft_lines<R, +1>(za, zb, a.plan[2], PZ, np, SB, reinterpret_cast<const C *>(a.tw[2]));
+  C *sbuf = (res == za) ? zb : za;
+  cp_async_wait_all();
+  __syncthreads();
+  const R dtg = pick<R>(a.dtg, a.dtg_f), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f);
+  const R inv_ntot = R(a.inv_ntot);
+  AdjSums<R> acc;
+  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
+    const int b = e / nz, n = e - b * nz;
+    const C v = pk[e];
+    const C g1 = gt[e];
+    const C z = res[n * SB + (b >> 1)];
+    const R phi = (b & 1) ? z.im : z.re;
+    const R dens = v.re * v.re + v.im * v.im;
+    const R theta = fma(dtg, dens, fma(dtgdd, phi, txy[b] + tz[n]));
+    R sn, cs;
+    sin_cos(theta, &sn, &cs);
+    const C u = {g1.re * cs - g1.im * sn, g1.re * sn + g1.im * cs};
+    const R sv = u.re * v.im - u.im * v.re;
+    gt[e] = u;
+    reinterpret_cast<R *>(sbuf + n * SB + (b >> 1))[b & 1] = sv;
+    acc.add(sv * dens, sv * phi * inv_ntot, sv * z2[n]);
+  }
+  __syncthreads();
+  const C *res2 = fft_lines<R, -1>(sbuf, res, a.plan[2], PZ, np, SB, reinterpret_cast<const C *>(a.tw[2]));
+  store_half_spectrum_column<R>(a, res2, i, j0, np);
+  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) gb[e] = gt[e];
+  double v3[3] = {acc.get(0), acc.get(1), acc.get(2)};
+  if (reduce_across_blocks<3>(v3, a.partials, &a.state->ticket) && threadIdx.x == 0) {
+    a.state->grads[0] += a.dt * v3[0];
+    a.state->grads[1] += a.dt * v3[1];
+    a.state->grads[2] += a.dt_nuz * v3[2];
+    if (a.grad_nu_slot) *a.grad_nu_slot += a.dt_nuz * v3[2];
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_combine(KArgs a) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int BZ = Tiles<R>::kZLines;
+  constexpr int PZ = BZ / 2;
+  constexpr int SB = PZ + 1;
+  const int nz = a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
+  const int nl = min(BZ, a.ny - j0), np = nl >> 1;
+  C *za = reinterpret_cast<C *>(smem_raw);
+  C *zb = za + nz * SB;
+  C *pk = zb + nz * SB;
+  C *gt = pk + BZ * nz;
+  const size_t line0 = (size_t)i * a.ny + j0;
+  const C *psi = reinterpret_cast<const C *>(a.psi) + line0 * nz;
+  C *gb = reinterpret_cast<C *>(a.gbar) + line0 * nz;
+  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
+    cp_async(pk + e, psi + e);
+    cp_async(gt + e, gb + e);
+  }
+  load_half_spectrum_column<R>(a, za, i, j0, np);
+  __syncthreads();
+  const C *res = fft_lines<R, +1>(za, zb, a.plan[2], PZ, np, SB, reinterpret_cast<const C *>(a.tw[2]));
+  cp_async_wait_all();
+  __syncthreads();
+  const R dtg = pick<R>(a.dtg, a.dtg_f), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f);
+  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
+    const int b = e / nz, n = e - b * nz;
+    const C v = pk[e];
+    const C u = gt[e];
+    const C z = res[n * SB + (b >> 1)];
+    const R phis = (b & 1) ? z.im : z.re;
+    const R sv = u.re * v.im - u.im * v.re;
+    const R coef = R(2) * fma(dtg, sv, dtgdd * phis);
+    gb[e] = {fma(coef, v.re, u.re), fma(coef, v.im, u.im)};
+  }
+}
+
+// Cotangent of L = hx hy hz sum z^2 |psi|^2: gbar = 2 hx hy hz z^2 psi.
+template <typename R>
+__global__ void k_loss_z2(KArgs a, size_t count) {
+  using C = cplx<R>;
+  const C *psi = reinterpret_cast<const C *>(a.psi);
+  C *gb = reinterpret_cast<C *>(a.gbar);
+  const R w = R(2.0 * a.hx * a.hy * a.hz);
+  const R hz = R(a.hz);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < count; q += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(q % a.nz);
+    const R z = R(k - a.nz / 2) * hz;
+    gb[q] = scale(psi[q], w * z * z);
+  }
+}
+
 // psi <- s psi, then s <- 1 (set by the last block).
 template <typename R>
 __global__ void k_materialize(KArgs a, size_t count) {
@@ -1168,6 +1367,8 @@ struct Impl {
     chk(allow_smem(k_cn<R, R, 1>));
     chk(allow_smem(k_cn<R, C, 0>));
     chk(allow_smem(k_cn<R, C, 1>));
+    chk(allow_smem(k5_adj_phase<R>));
+    chk(allow_smem(k5_adj_combine<R>));
     return e;
   }
 
@@ -1238,6 +1439,25 @@ struct Impl {
     return cudaGetLastError();
   }
   // Host-only bound (no device query): the CN grid never exceeds its tile count.
+  static size_t smem_adj(const KArgs &a) {
+    return smem_z_fft(a) + 2 * (size_t)T::kZLines * a.nz * E + (size_t)(2 * a.nz + T::kZLines) * sizeof(R);
+  }
+  static cudaError_t adj_phase(const KArgs &a, cudaStream_t st) {
+    k5_adj_phase<R><<<grid_z(a), T::kZThreads, smem_adj(a), st>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t adj_combine(const KArgs &a, cudaStream_t st) {
+    k5_adj_combine<R><<<grid_z(a), T::kZThreads, smem_adj(a), st>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t loss_z2(const KArgs &a, cudaStream_t st) {
+    const size_t count = (size_t)a.nx * a.ny * a.nz;
+    size_t blocks = (count + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    k_loss_z2<R><<<(unsigned)blocks, 256, 0, st>>>(a, count);
+    return cudaGetLastError();
+  }
+
   static int max_blocks(const KArgs &a) {
     const dim3 z = grid_z(a);
     const int bz = (int)(z.x * z.y);
@@ -1248,7 +1468,8 @@ struct Impl {
   static const KernelSet *set() {
     static const KernelSet ks = {(int)E, &init,          &twiddles,   &cn_tables, &axis_potential, &reset_state,
                                  &k1,        &k2,            &k3,         &k4,        &k5,             &k6,
-                                 &k7,        &materialize,   &max_blocks};
+                                 &k7,        &materialize,   &adj_phase,  &adj_combine, &loss_z2,
+                                 &max_blocks};
     return &ks;
   }
 };

@@ -34,6 +34,7 @@ struct DevState {
   double norm;       // hx hy hz sum |psi_buf|^2 after the last full step
   double sums[8];    // last reduction (step: n, x^2 n, y^2 n, z^2 n; obs: 8 terms)
   double obs[12];    // observables of the last dgpe_observables call
+  double grads[4];      // adjoint accumulators: dL/dg, dL/dgdd, dL/dnu_z
   unsigned int flags;   // bit 0: non-finite norm
   unsigned int ticket;  // last-block-done counter of the fused reductions
   unsigned long long steps;
@@ -61,6 +62,11 @@ struct KArgs {
   FftPlan plan[3];
   CnTab cn[3];
   void *out;                   // optional output (Phi for get_phi)
+  // adjoint step
+  void *gbar;                  // cotangent field (same layout as psi)
+  double dt_nuz;               // dt * nu_z (the nu_z derivative of theta is dt nu_z z^2)
+  double *grad_nu_slot;        // optional extra accumulator of dL/dnu_z (schedule segment)
+  int unit_scale;              // K1: ignore the pending renormalisation (s = 1)
 };
 
 // Modes of the z-line kernel (C2R along z + potential step + CN along z).
@@ -83,6 +89,8 @@ enum KernelId : int {
   kK7CnXReduce,
   kKMaterialize,
   kKObs,
+  kKAdjPhase,
+  kKAdjCombine,
   kNumKernels
 };
 
@@ -102,6 +110,9 @@ struct KernelSet {
   cudaError_t (*k6)(const KArgs &a, cudaStream_t st);   // CN-y
   cudaError_t (*k7)(const KArgs &a, int reduce, int renorm, cudaStream_t st);  // CN-x
   cudaError_t (*materialize)(const KArgs &a, cudaStream_t st);
+  cudaError_t (*adj_phase)(const KArgs &a, cudaStream_t st);     // u = e^{i theta} gbar, s, R2C(s)
+  cudaError_t (*adj_combine)(const KArgs &a, cudaStream_t st);   // gbar = u + 2 dt (g s + gdd Phi[s]) psi
+  cudaError_t (*loss_z2)(const KArgs &a, cudaStream_t st);       // gbar = 2 h^3 z^2 psi
   int (*max_blocks)(const KArgs &a);   // upper bound on blocks of any reducing kernel
 };
 
