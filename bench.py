@@ -40,6 +40,48 @@ WORKLOADS = {
 }
 PREP_STEPS = 20
 
+# FP64 peak of GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA per clock per SM
+# (measured issue rate) x 2 flops x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# DRAM bytes (read + write) per launch from ncu captures (profiles/), valid while the kernel
+# source is byte-identical to the one captured (sha1 of dgpe_device.cuh).
+NCU_TRAFFIC = {
+    "275dc372c2b0d12e4128e0567f3afd54f74d95ca": {
+        ("real256_fp64", "k5_c2r_z_phase_cn_z"): 618.3e6,
+        ("real512x512x384_mixed", "k5_c2r_z_phase_cn_z"): 1960.5e6,
+    },
+}
+
+
+def kernel_source_sha1():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1610_05329_gb300", "csrc", "dgpe_device.cuh")
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def fp64_flops_per_point(kernel, shape):
+    """Algorithmic FP64 flops per grid point of each real-time FP64 kernel (FMA = 2 flops);
+    the derivation is in the design notes.  FFT of length n: 5 n log2 n per complex line;
+    the half spectrum has (nz/2+1)/nz complex values per real point."""
+    import math
+    nx, ny, nz = shape
+    half = (nz // 2 + 1) / nz
+    chunk = 2
+    while chunk * 32 < nz - 2:
+        chunk *= 2
+    cn = 8 + 12 + 16 + 4 + 140.0 / chunk        # forward, backward, fix-up, 2chi - psi, lane scans
+    return {
+        "k1_density_r2c_z": 2.5 * math.log2(nz) + 5,
+        "k2_fft_y": 5 * math.log2(ny) * half,
+        "k3_fft_x_dipolar_ifft_x": (10 * math.log2(nx) + 10) * half,
+        "k4_ifft_y": 5 * math.log2(ny) * half,
+        "k5_c2r_z_phase_cn_z": 2.5 * math.log2(nz) + 2 + 9 + 36 + 6 + (8 + 12 + 16 + 4 + 140.0 / chunk),
+        "k6_cn_y": cn,
+        "k7_cn_x_reduce": cn + 6,
+    }.get(kernel, 0.0)
+
 
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -137,9 +179,12 @@ def time_steps(c, steps, barrier):
     return e0.elapsed_time(e1)
 
 
-def kernel_profile(c, steps, hbm_peak, peak_kind):
-    """Per-kernel CUDA-event durations over `steps` instrumented steps."""
+def kernel_profile(c, steps, hbm_peak, peak_kind, workload):
+    """Per-kernel CUDA-event durations over `steps` instrumented steps (the same step
+    sequence as the timed region, with an event pair around every launch)."""
     import torch
+    wl = WORKLOADS[workload]
+    npts = wl["shape"][0] * wl["shape"][1] * wl["shape"][2]
     c.set_timing(True)
     c.kernel_times()        # reset
     t0 = time.perf_counter()
@@ -149,19 +194,35 @@ def kernel_profile(c, steps, hbm_peak, peak_kind):
     rows = c.kernel_times()
     c.set_timing(False)
     total = sum(r["total_ms"] for r in rows)
+    traffic = NCU_TRAFFIC.get(kernel_source_sha1(), {})
     out = []
     for r in rows:
         avg = r["total_ms"] / r["launches"]
         gbs = r["bytes_per_launch"] / (avg * 1e-3) / 1e9
-        out.append({"kernel": r["name"], "launches": r["launches"], "avg_ms": round(avg, 5),
-                    "share": round(r["total_ms"] / total, 4), "bytes_per_launch": r["bytes_per_launch"],
-                    "achieved_gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4)})
+        d = {"kernel": r["name"], "launches": r["launches"], "avg_ms": round(avg, 5),
+             "share": round(r["total_ms"] / total, 4), "bytes_per_launch": r["bytes_per_launch"],
+             "achieved_gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4)}
+        if wl["precision"] == "fp64":
+            fl = fp64_flops_per_point(r["name"], wl["shape"]) * npts
+            d["fp64_flops_per_launch"] = fl
+            d["fp64_tflops"] = round(fl / (avg * 1e-3) / 1e12, 4)
+            d["frac_fp64"] = round(d["fp64_tflops"] / FP64_PEAK_TFLOPS, 4)
+        out.append(d)
     out.sort(key=lambda d: -d["share"])
     top = out[0]
-    roofline = {"bound": "hbm", "kernel": top["kernel"], "achieved": top["achieved_gbs"], "peak": hbm_peak,
-                "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-                "unit": "GB/s", "frac": top["frac_hbm"], "traffic": None,
-                "instrumented_ms_per_step": round(total / steps, 4), "instrumented_wall_s": round(wall, 3)}
+    tr = traffic.get((workload, top["kernel"]))
+    hbm = {"bound": "hbm", "kernel": top["kernel"], "achieved": top["achieved_gbs"], "peak": hbm_peak,
+           "unit": "GB/s", "frac": top["frac_hbm"], "traffic": tr,
+           "peak_kind": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback")}
+    if wl["precision"] == "fp64":
+        roofline = {"bound": "alu", "kernel": top["kernel"], "achieved": top["fp64_tflops"],
+                    "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": top["frac_fp64"],
+                    "traffic": tr, "peak_kind": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz",
+                    "hbm_view": hbm}
+    else:
+        roofline = hbm
+    roofline["instrumented_ms_per_step"] = round(total / steps, 4)
+    roofline["instrumented_wall_s"] = round(wall, 3)
     return roofline, out
 
 
@@ -212,6 +273,49 @@ def cpu_baseline(wl, budget_s=20.0):
                 steps, *wl["shape"], t)}
 
 
+def differentiation_run(abi, local, precision, steps, full=True):
+    """The differentiation workload on 128^3 (h = 0.2, nu = (1, 1, nu_z(t)), g = 30,
+    gdd = 15, real time dt = 0.001): forward step vs adjoint step time (CUDA events), and
+    the whole sqrt(N)-checkpointed gradient of <z^2> over 50 segments x 40 steps with nu_z
+    drawn from U[0.8, 1.2] (SplitMix64, seed 4)."""
+    import torch
+    from paper_1610_05329_gb300 import inputs
+    shape, h = (128, 128, 128), 0.2
+    prec = abi.DGPE_FP64 if precision == "fp64" else abi.DGPE_MIXED
+    c = abi.Condensate(shape, h, 0.001, mode=abi.DGPE_IMAG_TIME, precision=prec, nu=(1.0, 1.0, 1.0), g=30.0,
+                       gdd=15.0, device=torch.device("cuda", local))
+    c.set_psi(torch.from_numpy(inputs.gaussian_psi(shape, h, noise=1e-3, seed=1)).to(device=c.device, dtype=c.cdtype))
+    c.step(PREP_STEPS)
+    c.set_params(mode=abi.DGPE_REAL_TIME)
+    c.step(3)
+    fwd = time_steps(c, steps, lambda: None)
+    psi_k = c.get_psi(host=False)
+    gbar = psi_k.clone()
+    for _ in range(3):
+        c.adjoint_step(psi_k, gbar)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(c.device)
+    e0.record(c.stream)
+    for _ in range(steps):
+        c.adjoint_step(psi_k, gbar)
+    e1.record(c.stream)
+    torch.cuda.synchronize(c.device)
+    adj = e0.elapsed_time(e1)
+    out = {"grid": list(shape), "dtype": "f64" if precision == "fp64" else "f32 (FP64 reductions)",
+           "forward_ms_per_step": round(fwd / steps, 4), "adjoint_ms_per_step": round(adj / steps, 4),
+           "adjoint_over_forward": round(adj / fwd, 3)}
+    if full:
+        nu_z = inputs.uniform(4, 50, 0.8, 1.2)
+        t0 = time.perf_counter()
+        loss, dnu, dg, dgdd = c.grad_z2(nu_z, 40)
+        wall = time.perf_counter() - t0
+        out.update({"grad_2000_steps_s": round(wall, 3), "grad_ms_per_step": round(wall / 2000 * 1e3, 4),
+                    "grad_over_forward": round(wall / 2000 * 1e3 / (fwd / steps), 3), "loss_z2": loss,
+                    "dL_dg": dg, "dL_dgdd": dgdd, "checkpoints": "sqrt(N): every 45 steps"})
+    c.close()
+    return out
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
     ws, rank, _ = dist_env()
@@ -253,6 +357,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 512x512x384 mixed-precision line item")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the 128^3 differentiation line item")
     ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
                     help="time only this workload (profiling); the default line times both")
     args = ap.parse_args()
@@ -296,7 +401,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = ws * npts * args.steps / (ms * 1e-3)
-    roofline, kernels = kernel_profile(c, min(args.steps, 50), hbm_peak, peak_kind)
+    roofline, kernels = kernel_profile(c, min(args.steps, 50), hbm_peak, peak_kind, name)
     e2e = e2e_run(abi, c, args.e2e_steps) if args.e2e_steps > 0 else None
     c.sync()
     c.close()
@@ -308,13 +413,17 @@ def main():
         nm = wlm["shape"][0] * wlm["shape"][1] * wlm["shape"][2]
         cm.step(args.warmup)
         msm = time_steps(cm, args.steps, barrier)
-        rl_m, kernels_m = kernel_profile(cm, min(args.steps, 50), hbm_peak, peak_kind)
+        rl_m, kernels_m = kernel_profile(cm, min(args.steps, 50), hbm_peak, peak_kind, "real512x512x384_mixed")
         cm.sync()
         cm.close()
         mixed = {"value": ws * nm * args.steps / (msm * 1e-3), "unit": UNIT, "ms_per_step": round(msm / args.steps, 4),
                  "dtype": "f32 (FP64 reductions)", "grid": list(wlm["shape"]), "roofline": rl_m, "kernels": kernels_m,
                  "algorithmic_bytes_per_step": sum(k["bytes_per_launch"] * k["launches"] for k in kernels_m)
                  / min(args.steps, 50)}
+
+    diff = None
+    if not args.no_adjoint and args.workload is None:
+        diff = {p: differentiation_run(abi, local, p, min(args.steps, 50)) for p in ("fp64", "mixed")}
 
     if rank != 0:
         return
@@ -329,6 +438,8 @@ def main():
             "gpu_launches": 7 * args.steps, "clocks": clk, "roofline": roofline, "kernels": kernels, "e2e": e2e}
     if mixed is not None:
         line["mixed_512x512x384"] = mixed
+    if diff is not None:
+        line["differentiation_128"] = diff
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)

@@ -115,7 +115,7 @@ def test_autograd_function():
     loss = abi.trajectory_z2(gpu, nu, g, gdd, 4)
     (3.0 * loss).backward()
     l, dnu, dg, dgdd = gpu.grad_z2(np.array([1.0, 0.9, 1.1]), 4)
-    assert float(loss) == pytest.approx(l, rel=1e-13)
+    assert float(loss.detach()) == pytest.approx(l, rel=1e-13)
     assert np.allclose(nu.grad.numpy(), 3.0 * dnu, rtol=1e-12)
     assert float(g.grad) == pytest.approx(3.0 * dg, rel=1e-12)
     assert float(gdd.grad) == pytest.approx(3.0 * dgdd, rel=1e-12)
