@@ -330,6 +330,75 @@ def differentiation_run(abi, local, precision, steps, full=True):
     return out
 
 
+def batching_run(abi, local, steps=300, count=64):
+    """The batching workload: 64 independent imaginary-time FP32-mixed condensates, cube
+    sizes drawn from {32, 48, 64, 96, 128} (SplitMix64 seed 5), h = 12.8/N, g ~ U[5, 80],
+    gdd ~ U[0, 0.9 g], nu_d ~ U[0.5, 2], dt = 0.001, `steps` steps each.  Sequential
+    per-condensate graph launches vs one batched graph (parallel branches) per step, after
+    autotuning one member per distinct size."""
+    import torch
+    from paper_1610_05329_gb300 import inputs
+    sizes = [32, 48, 64, 96, 128]
+    u = inputs.uniform(5, 6 * count)
+    members = []
+    for k in range(count):
+        n = sizes[min(int(u[6 * k] * 5), 4)]
+        g = 5.0 + 75.0 * u[6 * k + 1]
+        gdd = 0.9 * g * u[6 * k + 2]
+        nu = tuple(0.5 + 1.5 * u[6 * k + 3 + d] for d in range(3))
+        members.append(dict(n=n, h=12.8 / n, g=g, gdd=gdd, nu=nu))
+    conds, psis = [], []
+    for k, m in enumerate(members):
+        shape = (m["n"],) * 3
+        c = abi.Condensate(shape, m["h"], 0.001, mode=abi.DGPE_IMAG_TIME, precision=abi.DGPE_MIXED, nu=m["nu"],
+                           g=m["g"], gdd=m["gdd"], device=torch.device("cuda", local))
+        psi = torch.from_numpy(inputs.gaussian_psi(shape, m["h"], noise=1e-3, seed=100 + k)).to(
+            device=c.device, dtype=c.cdtype)
+        conds.append(c)
+        psis.append(psi)
+        c.set_psi(psi)
+    npts = sum(m["n"] ** 3 for m in members)
+    tunings = {}
+    for c, m in zip(conds, members):
+        if m["n"] not in tunings:
+            tunings[m["n"]] = c.autotune()
+        else:
+            c.set_tuning(tunings[m["n"]])
+    st = torch.cuda.current_stream(conds[0].device)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    for c in conds:                      # warm-up (graph capture) of the sequential path
+        c.step(1)
+    for c, psi in zip(conds, psis):
+        c.set_psi(psi)
+    seq_ms = timed(lambda: [c.step(steps) for c in conds])
+    b = abi.Batch(conds)
+    b.step(1)
+    for c, psi in zip(conds, psis):
+        c.set_psi(psi)
+    bat_ms = timed(lambda: b.step(steps))
+    b.sync()
+    b.close()
+    for c in conds:
+        c.close()
+    return {"condensates": count, "sizes": {str(n): sum(1 for m in members if m["n"] == n) for n in sizes},
+            "steps": steps, "points": npts, "dtype": "f32 (FP64 reductions)",
+            "sequential_ms": round(seq_ms, 3), "batched_ms": round(bat_ms, 3),
+            "sequential_updates_per_s": npts * steps / (seq_ms * 1e-3),
+            "batched_updates_per_s": npts * steps / (bat_ms * 1e-3),
+            "batched_speedup": round(seq_ms / bat_ms, 3),
+            "autotune": {str(n): {k: (list(v) if isinstance(v, tuple) else v) for k, v in t.items()}
+                         for n, t in tunings.items()}}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
     ws, rank, _ = dist_env()
@@ -372,6 +441,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the 512x512x384 mixed-precision line item")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 128^3 differentiation line item")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-condensate batching line item")
     ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
                     help="time only this workload (profiling); the default line times both")
     args = ap.parse_args()
@@ -436,6 +506,10 @@ def main():
     if not args.no_adjoint and args.workload is None:
         diff = {p: differentiation_run(abi, local, p, min(args.steps, 50)) for p in ("fp64", "mixed")}
 
+    batch = None
+    if not args.no_batch and args.workload is None:
+        batch = batching_run(abi, local)
+
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -451,6 +525,8 @@ def main():
         line["mixed_512x512x384"] = mixed
     if diff is not None:
         line["differentiation_128"] = diff
+    if batch is not None:
+        line["batching_64"] = batch
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)

@@ -185,6 +185,41 @@ int dgpe_grad_z2_workspace_bytes(const dgpe_ctx *ctx, int nseg, int steps_per_se
 int dgpe_grad_z2(dgpe_ctx *ctx, int nseg, int steps_per_seg, const double *nu_z, void *work, size_t work_bytes,
                  double *loss, double *dnu, double *dg, double *dgdd);
 
+/* ---- Batching and launch-shape tuning -----------------------------------------------
+ * Many independent condensates (different shapes and parameters) advanced together: one
+ * CUDA graph holds every context's step kernels as parallel branches, so small grids that
+ * cannot fill the GPU alone run concurrently.  The paper runs one condensate per program;
+ * this serves many small independent ones (parameter scans). */
+typedef struct dgpe_batch dgpe_batch;
+
+/* n >= 1 distinct contexts on the current device; they must outlive the batch.  The batch
+ * launches on cuda_stream; do not enqueue work on a context's own stream while a batch step
+ * may still run (synchronise first). */
+int dgpe_batch_create(dgpe_ctx *const *ctxs, int n, void *cuda_stream, dgpe_batch **out);
+/* nsteps SSCN steps of every context (one graph launch per step; the graph is rebuilt
+ * when a context's step changed through dgpe_set_params or tuning).  Asynchronous. */
+int dgpe_batch_step(dgpe_batch *b, int nsteps);
+/* Wait for the batch stream; the first latched device error of any context. */
+int dgpe_batch_sync(dgpe_batch *b);
+void dgpe_batch_destroy(dgpe_batch *b);
+
+/* Launch shape of a context's step. */
+typedef struct dgpe_tuning {
+  int plan_style[3];     /* FFT radix order per axis: 0 radix-8 first, 1 radix-4, 2 radix-3 first */
+  int ylines;            /* lines per CTA of the y transforms: 2, 4, 8, 16 or 32 */
+  int fft_threads;       /* threads per CTA of the y/x transforms: 128 or 256 */
+  int cn_per_sm;         /* CTAs per SM of the persistent Crank-Nicolson sweeps: 1 or 2 */
+  double step_ms_default, step_ms_tuned;  /* measured by dgpe_autotune (0 otherwise) */
+} dgpe_tuning;
+
+/* Time candidate launch shapes on this context's own shape (a few steps each, with CUDA
+ * events per kernel), choose the fastest per kernel class, apply it and report it in *out.
+ * psi and the device state are restored afterwards.  Synchronises; allocates one
+ * psi-sized temporary with cudaMallocAsync. */
+int dgpe_autotune(dgpe_ctx *ctx, dgpe_tuning *out);
+/* Apply a tuning (e.g. one found earlier for the same shape). DGPE_EINVAL if invalid. */
+int dgpe_set_tuning(dgpe_ctx *ctx, const dgpe_tuning *t);
+
 /* Wait for the stream; returns a latched device error if any. */
 int dgpe_sync(dgpe_ctx *ctx);
 

@@ -58,6 +58,23 @@ class dgpe_kernel_time(ctypes.Structure):
                 ("launches", ctypes.c_longlong), ("bytes_per_launch", ctypes.c_double)]
 
 
+class dgpe_tuning(ctypes.Structure):
+    _fields_ = [("plan_style", ctypes.c_int * 3), ("ylines", ctypes.c_int), ("fft_threads", ctypes.c_int),
+                ("cn_per_sm", ctypes.c_int), ("step_ms_default", ctypes.c_double), ("step_ms_tuned", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"plan_style": tuple(self.plan_style), "ylines": self.ylines, "fft_threads": self.fft_threads,
+                "cn_per_sm": self.cn_per_sm, "step_ms_default": self.step_ms_default,
+                "step_ms_tuned": self.step_ms_tuned}
+
+    @classmethod
+    def from_dict(cls, d):
+        t = cls()
+        t.plan_style[0], t.plan_style[1], t.plan_style[2] = d["plan_style"]
+        t.ylines, t.fft_threads, t.cn_per_sm = d["ylines"], d["fft_threads"], d["cn_per_sm"]
+        return t
+
+
 class DgpeError(RuntimeError):
     def __init__(self, code, what):
         msg = "%s: %s (%d)" % (what, strerror(code), code)
@@ -91,6 +108,12 @@ _SIGNATURES = [
     ("dgpe_grad_z2", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_size_t, _P(ctypes.c_double), ctypes.c_void_p, _P(ctypes.c_double),
                                     _P(ctypes.c_double)]),
+    ("dgpe_batch_create", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, _P(ctypes.c_void_p)]),
+    ("dgpe_batch_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("dgpe_batch_sync", ctypes.c_int, [ctypes.c_void_p]),
+    ("dgpe_batch_destroy", None, [ctypes.c_void_p]),
+    ("dgpe_autotune", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_tuning)]),
+    ("dgpe_set_tuning", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_tuning)]),
     ("dgpe_moments_noalloc", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_params), ctypes.c_void_p, ctypes.c_void_p]),
     ("dgpe_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("dgpe_last_cuda_error", ctypes.c_char_p, []),
@@ -231,6 +254,38 @@ def dgpe_grad_z2(ctx, nu_z, steps_per_seg, work_ptr, work_bytes):
     return loss.value, dnu, dg.value, dgdd.value
 
 
+def dgpe_autotune(ctx):
+    t = dgpe_tuning()
+    _check(load().dgpe_autotune(ctx, ctypes.byref(t)), "dgpe_autotune")
+    return t.as_dict()
+
+
+def dgpe_set_tuning(ctx, tuning):
+    t = dgpe_tuning.from_dict(tuning)
+    _check(load().dgpe_set_tuning(ctx, ctypes.byref(t)), "dgpe_set_tuning")
+
+
+def dgpe_batch_create(ctxs, stream=0):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    b = ctypes.c_void_p()
+    _check(load().dgpe_batch_create(arr, len(ctxs), ctypes.c_void_p(stream or None), ctypes.byref(b)),
+           "dgpe_batch_create")
+    return b
+
+
+def dgpe_batch_step(b, nsteps):
+    _check(load().dgpe_batch_step(b, int(nsteps)), "dgpe_batch_step")
+
+
+def dgpe_batch_sync(b):
+    _check(load().dgpe_batch_sync(b), "dgpe_batch_sync")
+
+
+def dgpe_batch_destroy(b):
+    if b:
+        load().dgpe_batch_destroy(b)
+
+
 def dgpe_moments_noalloc(psi_ptr, params, out_ptr, stream=0):
     """Norm and rms sizes of a device psi into 4 device doubles, allocating nothing (for
     callers whose device memory is owned elsewhere or who must not allocate mid-run)."""
@@ -351,6 +406,12 @@ class Condensate:
     def kernel_times(self):
         return dgpe_kernel_times(self.ctx)
 
+    def autotune(self):
+        return dgpe_autotune(self.ctx)
+
+    def set_tuning(self, tuning):
+        dgpe_set_tuning(self.ctx, tuning)
+
     def adjoint_step(self, psi_k, gbar):
         """gbar (device tensor) <- cotangent of psi_k for one real-time step (in place)."""
         dgpe_adjoint_step(self.ctx, psi_k.data_ptr(), gbar.data_ptr())
@@ -369,6 +430,34 @@ class Condensate:
             work = self._torch.empty(need, dtype=self._torch.uint8, device=self.device)
             self._grad_work = work
         return dgpe_grad_z2(self.ctx, nu, steps_per_seg, work.data_ptr(), work.numel())
+
+
+class Batch:
+    """Independent condensates advanced together by one CUDA graph per step (their kernels
+    run as parallel graph branches) on PyTorch's current stream."""
+
+    def __init__(self, condensates):
+        import torch
+        self.members = list(condensates)
+        self.stream = torch.cuda.current_stream()
+        self.handle = dgpe_batch_create([c.ctx for c in self.members], self.stream.cuda_stream)
+
+    def step(self, nsteps=1):
+        dgpe_batch_step(self.handle, nsteps)
+
+    def sync(self):
+        dgpe_batch_sync(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            dgpe_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def trajectory_z2(condensate, nu_z, g, gdd, steps_per_seg):

@@ -29,17 +29,24 @@ bool is_2a3b(int n) {
 
 bool finite(double v) { return isfinite(v) != 0; }
 
-// Radix plan: as many radix-8 stages as possible, then one radix-4 or radix-2 stage for
-// the rest of the power of two, then the radix-3 stages.
-FftPlan make_plan(int n) {
+// Radix plan.  style 0: as many radix-8 stages as possible, then one radix-4 or radix-2
+// stage for the rest of the power of two, then the radix-3 stages.  style 1: radix-4 stages
+// (and one radix-2), then radix-3.  style 2: radix-3 stages first, then as style 0.
+FftPlan make_plan(int n, int style = 0) {
   FftPlan p{};
   p.n = n;
   int m = n, k = 0;
-  while (m % 8 == 0) {
-    p.radix[k++] = 8;
-    m /= 8;
-  }
-  if (m % 4 == 0) {
+  if (style == 2)
+    while (m % 3 == 0) {
+      p.radix[k++] = 3;
+      m /= 3;
+    }
+  if (style != 1)
+    while (m % 8 == 0) {
+      p.radix[k++] = 8;
+      m /= 8;
+    }
+  while (m % 4 == 0) {
     p.radix[k++] = 4;
     m /= 4;
   }
@@ -140,7 +147,7 @@ KArgs base_args(const dgpe_params *p) {
   a.nzh = p->nz / 2 + 1;
   for (int d = 0; d < 3; ++d) {
     const int n = d == 0 ? p->nx : d == 1 ? p->ny : p->nz;
-    a.plan[d] = make_plan(n);
+    a.plan[d] = make_plan(n, 0);
     a.cn[d].m = n - 2;
     a.cn[d].chunk = cn_chunk(n);
     a.cn[d].lchunk = log2_int(a.cn[d].chunk);
@@ -209,6 +216,18 @@ struct dgpe_ctx {
   double total_ms[kNumKernels];
   long long launches[kNumKernels];
   int latched;
+  int plan_style[3];
+  unsigned generation;   // bumped whenever the captured step would change (batches rebuild)
+};
+
+struct dgpe_batch {
+  std::vector<dgpe_ctx *> ctxs;
+  std::vector<unsigned> gens;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> branches;
+  std::vector<cudaEvent_t> events;
+  cudaGraphExec_t graph = nullptr;
 };
 
 namespace {
@@ -430,6 +449,56 @@ GradLayout grad_layout(const dgpe_ctx *c, int nseg, int steps_per_seg) {
 
 }  // namespace
 
+namespace {
+
+// Drain the timing events of the launches enqueued with timing on: per-kernel milliseconds.
+int drain_kernel_times(dgpe_ctx *c, double *ms) {
+  int rc = map_cuda(cudaStreamSynchronize(c->stream));
+  for (int q = 0; q < kNumKernels; ++q) ms[q] = 0;
+  for (const auto &pd : c->pending) {
+    float t = 0.f;
+    if (rc == DGPE_OK && cudaEventElapsedTime(&t, pd.a, pd.b) == cudaSuccess) ms[pd.kernel] += t;
+    c->ev_free.push_back(pd.a);
+    c->ev_free.push_back(pd.b);
+  }
+  c->pending.clear();
+  return rc;
+}
+
+void apply_tuning(dgpe_ctx *c, const dgpe_tuning &t) {
+  const int n[3] = {c->p.nx, c->p.ny, c->p.nz};
+  for (int d = 0; d < 3; ++d) {
+    c->plan_style[d] = t.plan_style[d];
+    c->args.plan[d] = make_plan(n[d], t.plan_style[d]);
+  }
+  c->args.ylines = t.ylines;
+  c->args.fft_threads = t.fft_threads;
+  c->args.cn_per_sm = t.cn_per_sm;
+  c->graph_valid = false;
+  ++c->generation;
+}
+
+bool tuning_valid(const dgpe_ctx *c, const dgpe_tuning &t) {
+  for (int d = 0; d < 3; ++d)
+    if (t.plan_style[d] < 0 || t.plan_style[d] > 2) return false;
+  if (t.fft_threads != 128 && t.fft_threads != 256) return false;
+  if (t.ylines < 2 || t.ylines > 32 || (t.ylines & (t.ylines - 1))) return false;
+  if (c->ks->y_smem(c->p.ny, t.ylines) + 8192 > 227 * 1024) return false;
+  if (t.cn_per_sm < 1 || t.cn_per_sm > 2) return false;
+  return true;
+}
+
+dgpe_tuning current_tuning(const dgpe_ctx *c) {
+  dgpe_tuning t{};
+  for (int d = 0; d < 3; ++d) t.plan_style[d] = c->plan_style[d];
+  t.ylines = c->args.ylines;
+  t.fft_threads = c->args.fft_threads;
+  t.cn_per_sm = c->args.cn_per_sm;
+  return t;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *dgpe_strerror(int code) {
@@ -477,6 +546,9 @@ int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out) {
   c->args = base_args(p);
   set_physics(c->args, p);
   c->L = layout_of(p, c->ks, c->ks->max_blocks(c->args));
+  c->args.ylines = c->ks->default_ylines(p->ny);
+  c->args.fft_threads = 256;
+  c->args.cn_per_sm = 2;
   rc = map_cuda(c->ks->init());
   if (!rc) rc = map_cuda(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   if (!rc) {
@@ -532,7 +604,10 @@ int dgpe_set_params(dgpe_ctx *c, const dgpe_params *p) {
   set_physics(c->args, p);
   // the step kernels read the trap only through the per-axis tables rebuilt below, so a
   // change of nu alone keeps the captured graph valid
-  if (step_args_changed) c->graph_valid = false;
+  if (step_args_changed) {
+    c->graph_valid = false;
+    ++c->generation;
+  }
   return setup_tables(c, cn_changed);
 }
 
@@ -736,6 +811,207 @@ int dgpe_grad_z2(dgpe_ctx *c, int nseg, int steps_per_seg, const double *nu_z, v
   *dg = gr[0];
   *dgdd = gr[1];
   return check_device_flags(c);
+}
+
+int dgpe_set_tuning(dgpe_ctx *c, const dgpe_tuning *t) {
+  if (!c || !t || !tuning_valid(c, *t)) return DGPE_EINVAL;
+  apply_tuning(c, *t);
+  return DGPE_OK;
+}
+
+int dgpe_autotune(dgpe_ctx *c, dgpe_tuning *out) {
+  if (!c || !out) return DGPE_EINVAL;
+  const size_t sb = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;
+  void *saved = nullptr;
+  DevState st_saved;
+  int rc = map_cuda(cudaMallocAsync(&saved, sb, c->stream));
+  if (!rc) rc = map_cuda(cudaMemcpyAsync(saved, c->args.psi, sb, cudaMemcpyDeviceToDevice, c->stream));
+  if (!rc) rc = map_cuda(cudaMemcpyAsync(&st_saved, c->args.state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+  if (!rc) rc = map_cuda(cudaStreamSynchronize(c->stream));
+  if (rc) {
+    if (saved) cudaFreeAsync(saved, c->stream);
+    return rc;
+  }
+  const dgpe_tuning base = current_tuning(c);
+  const int ylines_opts[5] = {2, 4, 8, 16, 32};
+  const int threads_opts[2] = {256, 128};
+  const int steps = 3;
+  // per option, the summed time of the kernels it affects
+  double t_style[3][3] = {{1e30, 1e30, 1e30}, {1e30, 1e30, 1e30}, {1e30, 1e30, 1e30}};
+  double t_y[5][2], t_x[2] = {1e30, 1e30}, t_cn[2] = {1e30, 1e30};
+  for (auto &r : t_y) r[0] = r[1] = 1e30;
+  double default_ms = 0;
+  const bool timing = c->timing;
+  c->timing = true;
+  for (int round = 0; round < 10 && rc == DGPE_OK; ++round) {
+    dgpe_tuning t = base;
+    const int yi = round % 5, ti = (round / 5) % 2, si = round % 3, ci = round % 2;
+    if (round > 0) {
+      t.ylines = ylines_opts[yi];
+      t.fft_threads = threads_opts[ti];
+      for (int d = 0; d < 3; ++d) t.plan_style[d] = si;
+      t.cn_per_sm = 1 + ci;
+    }
+    if (!tuning_valid(c, t)) continue;
+    apply_tuning(c, t);
+    rc = enqueue_step(c, c->stream);   // warm-up step of this configuration
+    double ms[kNumKernels];
+    if (!rc) rc = drain_kernel_times(c, ms);
+    for (int s = 0; s < steps && rc == DGPE_OK; ++s) rc = enqueue_step(c, c->stream);
+    if (!rc) rc = drain_kernel_times(c, ms);
+    if (rc) break;
+    double total = 0;
+    for (int q = 0; q < kNumKernels; ++q) total += ms[q];
+    if (round == 0) default_ms = total / steps;
+    const double tz = ms[kK1DensityR2Cz] + ms[kK5C2RzPhaseCnz], ty = ms[kK2FftY] + ms[kK4IfftY],
+                 tx = ms[kK3FftXDipolar], tcn = ms[kK6CnY] + ms[kK7CnXReduce];
+    const int sidx[3] = {t.plan_style[0], t.plan_style[1], t.plan_style[2]};
+    t_style[0][sidx[0]] = fmin(t_style[0][sidx[0]], tx);
+    t_style[1][sidx[1]] = fmin(t_style[1][sidx[1]], ty);
+    t_style[2][sidx[2]] = fmin(t_style[2][sidx[2]], tz);
+    int yk = 0;
+    while (ylines_opts[yk] != t.ylines) ++yk;
+    const int tk = t.fft_threads == 256 ? 0 : 1;
+    t_y[yk][tk] = fmin(t_y[yk][tk], ty);
+    t_x[tk] = fmin(t_x[tk], tx);
+    t_cn[t.cn_per_sm - 1] = fmin(t_cn[t.cn_per_sm - 1], tcn);
+  }
+  dgpe_tuning best = base;
+  if (rc == DGPE_OK) {
+    for (int d = 0; d < 3; ++d) {
+      int b = base.plan_style[d];
+      for (int k = 0; k < 3; ++k)
+        if (t_style[d][k] < t_style[d][b]) b = k;
+      best.plan_style[d] = b;
+    }
+    // y-pass shape and transform threads: the (ylines, threads) pair with the least y + x time
+    double bestv = 1e30;
+    for (int yk = 0; yk < 5; ++yk)
+      for (int tk = 0; tk < 2; ++tk) {
+        const double v = t_y[yk][tk] + t_x[tk];
+        if (v < bestv) {
+          bestv = v;
+          best.ylines = ylines_opts[yk];
+          best.fft_threads = threads_opts[tk];
+        }
+      }
+    best.cn_per_sm = t_cn[1] < t_cn[0] ? 2 : 1;
+    if (!tuning_valid(c, best)) best = base;
+    apply_tuning(c, best);
+    for (int s = 0; s < 1 + steps && rc == DGPE_OK; ++s) {
+      rc = enqueue_step(c, c->stream);
+      if (s == 0 && !rc) {
+        double ms0[kNumKernels];
+        rc = drain_kernel_times(c, ms0);
+      }
+    }
+    double ms[kNumKernels];
+    if (!rc) rc = drain_kernel_times(c, ms);
+    double total = 0;
+    for (int q = 0; q < kNumKernels; ++q) total += ms[q];
+    best.step_ms_default = default_ms;
+    best.step_ms_tuned = total / steps;
+  }
+  c->timing = timing;
+  // restore the state the tuning steps advanced
+  int rc2 = map_cuda(cudaMemcpyAsync(c->args.psi, saved, sb, cudaMemcpyDeviceToDevice, c->stream));
+  if (!rc2) rc2 = map_cuda(cudaMemcpyAsync(c->args.state, &st_saved, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+  cudaFreeAsync(saved, c->stream);
+  if (!rc2) rc2 = map_cuda(cudaStreamSynchronize(c->stream));
+  if (rc == DGPE_OK) rc = rc2;
+  if (rc == DGPE_OK) *out = best;
+  return rc;
+}
+
+int dgpe_batch_create(dgpe_ctx *const *ctxs, int n, void *cuda_stream, dgpe_batch **out) {
+  if (!ctxs || n < 1 || !out) return DGPE_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return DGPE_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return DGPE_EINVAL;
+  }
+  dgpe_batch *b = new (std::nothrow) dgpe_batch();
+  if (!b) return DGPE_ENOMEM;
+  b->ctxs.assign(ctxs, ctxs + n);
+  b->gens.assign(n, ~0u);
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  int rc = map_cuda(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  b->branches.assign(n, nullptr);
+  b->events.assign(n + 1, nullptr);
+  for (int i = 0; i < n && !rc; ++i) rc = map_cuda(cudaStreamCreateWithFlags(&b->branches[i], cudaStreamNonBlocking));
+  for (int i = 0; i <= n && !rc; ++i) rc = map_cuda(cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming));
+  if (rc) {
+    dgpe_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return DGPE_OK;
+}
+
+// One graph: a fork from the capture stream to one branch per context, each branch the
+// context's seven step kernels, then a join.  Independent branches run concurrently.
+static int batch_build(dgpe_batch *b) {
+  bool stale = b->graph == nullptr;
+  for (size_t i = 0; i < b->ctxs.size(); ++i) stale = stale || b->gens[i] != b->ctxs[i]->generation;
+  if (!stale) return DGPE_OK;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  const int n = (int)b->ctxs.size();
+  std::vector<char> timing(n);
+  for (int i = 0; i < n; ++i) {
+    timing[i] = b->ctxs[i]->timing;
+    b->ctxs[i]->timing = false;
+  }
+  int rc = map_cuda(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  if (!rc) rc = map_cuda(cudaEventRecord(b->events[n], b->cap));
+  for (int i = 0; i < n && !rc; ++i) {
+    rc = map_cuda(cudaStreamWaitEvent(b->branches[i], b->events[n], 0));
+    if (!rc) rc = enqueue_step(b->ctxs[i], b->branches[i]);
+    if (!rc) rc = map_cuda(cudaEventRecord(b->events[i], b->branches[i]));
+    if (!rc) rc = map_cuda(cudaStreamWaitEvent(b->cap, b->events[i], 0));
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+  for (int i = 0; i < n; ++i) b->ctxs[i]->timing = timing[i];
+  if (!rc) rc = map_cuda(e);
+  if (!rc) rc = map_cuda(cudaGraphInstantiate(&b->graph, g, 0));
+  if (g) cudaGraphDestroy(g);
+  if (rc) {
+    b->graph = nullptr;
+    return rc;
+  }
+  for (int i = 0; i < n; ++i) b->gens[i] = b->ctxs[i]->generation;
+  return DGPE_OK;
+}
+
+int dgpe_batch_step(dgpe_batch *b, int nsteps) {
+  if (!b || nsteps < 0) return DGPE_EINVAL;
+  if (nsteps == 0) return DGPE_OK;
+  int rc = batch_build(b);
+  for (int s = 0; s < nsteps && !rc; ++s) rc = map_cuda(cudaGraphLaunch(b->graph, b->stream));
+  return rc;
+}
+
+int dgpe_batch_sync(dgpe_batch *b) {
+  if (!b) return DGPE_EINVAL;
+  int rc = map_cuda(cudaStreamSynchronize(b->stream));
+  for (size_t i = 0; i < b->ctxs.size() && !rc; ++i) rc = check_device_flags(b->ctxs[i]);
+  return rc;
+}
+
+void dgpe_batch_destroy(dgpe_batch *b) {
+  if (!b) return;
+  if (b->stream || b->cap) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (cudaEvent_t e : b->events)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t st : b->branches)
+    if (st) cudaStreamDestroy(st);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
 }
 
 int dgpe_sync(dgpe_ctx *c) {

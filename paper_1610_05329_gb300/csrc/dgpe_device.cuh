@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = a.ny;
-  const int L = y_lines_per_cta<R>(n);
+  const int L = a.ylines;
   const int SB = L + 1;
   const size_t total = (size_t)a.nzh * a.nx;
   const size_t l0 = (size_t)blockIdx.x * L;
@@ -1312,7 +1312,7 @@ struct Impl {
     return smem_z_fft(a) + (size_t)T::kZLines * cn_slots(a.nz, a.cn[2].lchunk) * E +
            (size_t)(a.nz + T::kZLines) * sizeof(R);
   }
-  static size_t smem_y(const KArgs &a) { return 2 * (size_t)a.ny * (y_lines_per_cta<R>(a.ny) + 1) * E; }
+  static size_t smem_y(const KArgs &a) { return 2 * (size_t)a.ny * (a.ylines + 1) * E; }
   static size_t smem_x(const KArgs &a) { return 2 * (size_t)a.nx * T::kXCols * E; }
   static size_t smem_cn(int n, int lchunk) {
     return 2 * (size_t)cn_slots(n, lchunk) * (T::kCnCols + 1) * E + (size_t)n * sizeof(R);
@@ -1334,7 +1334,8 @@ struct Impl {
     const int tiles = ((a.nz + T::kCnCols - 1) / T::kCnCols) * (axis == 0 ? a.ny : a.nx);
     const int n = a.cn[axis].m + 2;
     const size_t sm = smem_cn(n, a.cn[axis].lchunk);
-    const int per_sm = sm * 2 + 4096 <= 227 * 1024 ? 2 : 1;
+    const int fit = sm * 2 + 4096 <= 227 * 1024 ? 2 : 1;
+    const int per_sm = a.cn_per_sm < fit ? (a.cn_per_sm < 1 ? 1 : a.cn_per_sm) : fit;
     const int cap = sm_count() * per_sm;
     return dim3(tiles < cap ? tiles : cap);
   }
@@ -1399,19 +1400,19 @@ struct Impl {
   }
   static cudaError_t k2(const KArgs &a, cudaStream_t st) {
     const size_t lines = (size_t)a.nzh * a.nx;
-    const int L = y_lines_per_cta<R>(a.ny);
-    k_ffty<R, -1><<<(unsigned)((lines + L - 1) / L), kFftThreads, smem_y(a), st>>>(a);
+    const int L = a.ylines;
+    k_ffty<R, -1><<<(unsigned)((lines + L - 1) / L), a.fft_threads, smem_y(a), st>>>(a);
     return cudaGetLastError();
   }
   static cudaError_t k3(const KArgs &a, cudaStream_t st) {
     dim3 grid((a.ny + T::kXCols - 1) / T::kXCols, a.nzh);
-    k3_fftx_dipolar<R><<<grid, kFftThreads, smem_x(a), st>>>(a);
+    k3_fftx_dipolar<R><<<grid, a.fft_threads, smem_x(a), st>>>(a);
     return cudaGetLastError();
   }
   static cudaError_t k4(const KArgs &a, cudaStream_t st) {
     const size_t lines = (size_t)a.nzh * a.nx;
-    const int L = y_lines_per_cta<R>(a.ny);
-    k_ffty<R, +1><<<(unsigned)((lines + L - 1) / L), kFftThreads, smem_y(a), st>>>(a);
+    const int L = a.ylines;
+    k_ffty<R, +1><<<(unsigned)((lines + L - 1) / L), a.fft_threads, smem_y(a), st>>>(a);
     return cudaGetLastError();
   }
   static cudaError_t k5(const KArgs &a, int zmode, cudaStream_t st) {
@@ -1458,6 +1459,9 @@ struct Impl {
     return cudaGetLastError();
   }
 
+  static int default_ylines(int ny) { return y_lines_per_cta<R>(ny); }
+  static size_t y_smem(int ny, int ylines) { return 2 * (size_t)ny * (ylines + 1) * E; }
+
   static int max_blocks(const KArgs &a) {
     const dim3 z = grid_z(a);
     const int bz = (int)(z.x * z.y);
@@ -1469,7 +1473,7 @@ struct Impl {
     static const KernelSet ks = {(int)E, &init,          &twiddles,   &cn_tables, &axis_potential, &reset_state,
                                  &k1,        &k2,            &k3,         &k4,        &k5,             &k6,
                                  &k7,        &materialize,   &adj_phase,  &adj_combine, &loss_z2,
-                                 &max_blocks};
+                                 &max_blocks, &default_ylines, &y_smem};
     return &ks;
   }
 };

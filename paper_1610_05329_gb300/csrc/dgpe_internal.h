@@ -67,6 +67,10 @@ struct KArgs {
   double dt_nuz;               // dt * nu_z (the nu_z derivative of theta is dt nu_z z^2)
   double *grad_nu_slot;        // optional extra accumulator of dL/dnu_z (schedule segment)
   int unit_scale;              // K1: ignore the pending renormalisation (s = 1)
+  // launch shapes (defaults set at create; dgpe_autotune may change them)
+  int ylines;                  // K2/K4 lines per CTA (power of two, <= 32)
+  int fft_threads;             // K2/K3/K4 threads per CTA (128 or 256)
+  int cn_per_sm;               // K6/K7 persistent CTAs per SM (1 or 2; capped by shared memory)
 };
 
 // Modes of the z-line kernel (C2R along z + potential step + CN along z).
@@ -114,6 +118,8 @@ struct KernelSet {
   cudaError_t (*adj_combine)(const KArgs &a, cudaStream_t st);   // gbar = u + 2 dt (g s + gdd Phi[s]) psi
   cudaError_t (*loss_z2)(const KArgs &a, cudaStream_t st);       // gbar = 2 h^3 z^2 psi
   int (*max_blocks)(const KArgs &a);   // upper bound on blocks of any reducing kernel
+  int (*default_ylines)(int ny);
+  size_t (*y_smem)(int ny, int ylines);
 };
 
 const KernelSet *kernels_f64();

@@ -1,0 +1,75 @@
+"""Batched condensates (one CUDA graph, one branch per condensate) and the launch-shape
+autotuner: batching must not change any result (bitwise), tuning must leave the state
+untouched and the results within the parity tolerance of the oracle."""
+import numpy as np
+import pytest
+
+from paper_1610_05329_gb300 import abi, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1610_05329_gb300 import build
+    build.build()
+    abi.load()
+
+
+MEMBERS = [((16, 16, 16), 0.6, abi.DGPE_IMAG_TIME, (1.0, 1.3, 0.7), 12.0, 6.0),
+           ((24, 24, 24), 0.45, abi.DGPE_IMAG_TIME, (0.6, 1.0, 1.8), 60.0, 40.0),
+           ((32, 18, 12), 0.5, abi.DGPE_REAL_TIME, (1.0, 1.0, 1.0), 30.0, 10.0),
+           ((12, 48, 24), 0.35, abi.DGPE_REAL_TIME, (2.0, 0.5, 1.1), 5.0, 4.0)]
+
+
+@pytest.mark.parametrize("precision", [abi.DGPE_FP64, abi.DGPE_MIXED])
+def test_batch_equals_individual_steps(precision):
+    cdt = np.complex128 if precision == abi.DGPE_FP64 else np.complex64
+    batched, alone = [], []
+    for k, (shape, h, mode, nu, g, gdd) in enumerate(MEMBERS):
+        psi = inputs.gaussian_psi(shape, h, seed=20 + k).astype(cdt)
+        for group in (batched, alone):
+            c = abi.Condensate(shape, h, 0.005, mode=mode, precision=precision, nu=nu, g=g, gdd=gdd)
+            c.set_psi(psi)
+            group.append(c)
+    b = abi.Batch(batched)
+    b.step(7)
+    b.sync()
+    for c in alone:
+        c.step(7)
+    for x, y in zip(batched, alone):
+        assert np.array_equal(x.get_psi(), y.get_psi())
+    # a parameter change rebuilds the batch graph
+    batched[0].set_params(g=20.0)
+    alone[0].set_params(g=20.0)
+    b.step(3)
+    b.sync()
+    alone[0].step(3)
+    assert np.array_equal(batched[0].get_psi(), alone[0].get_psi())
+    b.close()
+    for c in batched + alone:
+        c.close()
+
+
+def test_autotune_restores_state_and_keeps_parity(orc):
+    shape, h, dt = (32, 48, 24), 0.3, 0.005
+    psi = inputs.gaussian_psi(shape, h, seed=31)
+    c = abi.Condensate(shape, h, dt, mode=abi.DGPE_REAL_TIME, nu=(1.0, 1.1, 0.9), g=25.0, gdd=15.0)
+    c.set_psi(psi)
+    t = c.autotune()
+    assert t["step_ms_tuned"] > 0 and t["step_ms_default"] > 0
+    assert np.array_equal(c.get_psi(), psi)
+    c.step(6)
+    p = orc.make_params(shape, h, dt, orc.REAL_TIME, (1.0, 1.1, 0.9), 25.0, 15.0)
+    want = orc.step(p, psi, 6)
+    got = c.get_psi()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-10
+    # every radix order gives the same step within the FP64 parity bar
+    for style in (0, 1, 2):
+        c.set_tuning(dict(t, plan_style=(style, style, style)))
+        c.set_psi(psi)
+        c.step(6)
+        assert np.linalg.norm(c.get_psi() - want) / np.linalg.norm(want) < 1e-10
+    with pytest.raises(abi.DgpeError):
+        c.set_tuning(dict(t, ylines=3))
+    c.close()
