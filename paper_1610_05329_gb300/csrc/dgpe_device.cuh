@@ -164,6 +164,26 @@ __host__ __device__ inline int y_lines_per_cta(int ny) {
   return l;
 }
 
+// Walks the flat index e = b * n + k of contiguous lines of length n in steps of `step`
+// (the block size), keeping (b, k) up to date without an integer division per step.
+struct LinePos {
+  int b, k, sb, sk, n;
+  __device__ __forceinline__ LinePos(int e0, int n_, int step) : n(n_) {
+    b = e0 / n;
+    k = e0 - b * n;
+    sb = step / n;
+    sk = step - sb * n;
+  }
+  __device__ __forceinline__ void next() {
+    k += sk;
+    b += sb;
+    if (k >= n) {
+      k -= n;
+      ++b;
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------------------
 // Asynchronous global -> shared copies (cp.async): every copy of a tile is in flight at
 // once instead of one dependent load per loop iteration.
@@ -632,6 +652,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) 
   const R s2 = R(s * s);
   const C *psi = reinterpret_cast<const C *>(a.psi) + ((size_t)i * a.ny + j0) * nz;
   const int total = nl * nz;
+  LinePos pos(threadIdx.x, nz, blockDim.x);
   for (int e0 = threadIdx.x; e0 < total; e0 += kUnroll * blockDim.x) {
     C v[kUnroll];
 #pragma unroll
@@ -643,10 +664,10 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) 
     for (int u = 0; u < kUnroll; ++u) {
       const int e = e0 + u * blockDim.x;
       if (e < total) {
-        const int b = e / nz, n = e - b * nz;
-        R *z = reinterpret_cast<R *>(za + n * SB + (b >> 1));
-        z[b & 1] = s2 * (v[u].re * v[u].re + v[u].im * v[u].im);
+        R *z = reinterpret_cast<R *>(za + pos.k * SB + (pos.b >> 1));
+        z[pos.b & 1] = s2 * (v[u].re * v[u].re + v[u].im * v[u].im);
       }
+      pos.next();
     }
   }
   __syncthreads();
@@ -683,18 +704,16 @@ __global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a) {
   C *za = reinterpret_cast<C *>(smem_raw);
   C *zb = za + n * SB;
   C *spec = reinterpret_cast<C *>(a.spec) + l0 * n;
-  for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
-    const int l = e / n, k = e - l * n;
-    cp_async(za + k * SB + l, spec + e);
+  {
+    LinePos pos(threadIdx.x, n, blockDim.x);
+    for (int e = threadIdx.x; e < nl * n; e += blockDim.x, pos.next()) cp_async(za + pos.k * SB + pos.b, spec + e);
   }
   cp_async_wait_all();
   __syncthreads();
   const C *res = fft_lines<R, DIR>(za, zb, a.plan[1], L, nl, SB, reinterpret_cast<const C *>(a.tw[1]));
+  LinePos pos(threadIdx.x, n, blockDim.x);
 #pragma unroll 4
-  for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
-    const int l = e / n, k = e - l * n;
-    spec[e] = res[k * SB + l];
-  }
+  for (int e = threadIdx.x; e < nl * n; e += blockDim.x, pos.next()) spec[e] = res[pos.k * SB + pos.b];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -785,10 +804,9 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
 
   // psi tile: asynchronous copies, overlapped with the spectrum load and the C2R transform
   if (zmode != kZPhi) {
-    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
-      const int b = e / nz, n = e - b * nz;
-      cp_async(tile + b * LS + cn_slot(n, lc), psi + e);
-    }
+    LinePos pos(threadIdx.x, nz, blockDim.x);
+    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next())
+      cp_async(tile + pos.b * LS + cn_slot(pos.k, lc), psi + e);
   }
 
   if (zmode != kZCnOnly) {
@@ -828,10 +846,10 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
 
   if (zmode == kZPhi) {
     R *out = reinterpret_cast<R *>(a.out) + line0 * nz;
-    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
-      const int b = e / nz, n = e - b * nz;
-      const C z = res[n * SB + (b >> 1)];
-      out[e] = ((b & 1) ? z.im : z.re) * inv_ntot;
+    LinePos pos(threadIdx.x, nz, blockDim.x);
+    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
+      const C z = res[pos.k * SB + (pos.b >> 1)];
+      out[e] = ((pos.b & 1) ? z.im : z.re) * inv_ntot;
     }
     return;
   }
@@ -845,8 +863,9 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
     const R ihx2 = R(1.0 / (a.hx * a.hx)), ihy2 = R(1.0 / (a.hy * a.hy)), ihz2 = R(1.0 / (a.hz * a.hz));
     const C *gpsi = reinterpret_cast<const C *>(a.psi);
     const size_t sx = (size_t)a.ny * nz;
-    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
-      const int b = e / nz, n = e - b * nz;
+    LinePos pos(threadIdx.x, nz, blockDim.x);
+    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
+      const int b = pos.b, n = pos.k;
       const int j = j0 + b;
       const C *row = tile + b * LS;
       const C c = scale(row[cn_slot(n, lc)], sr);
@@ -911,8 +930,9 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
     const R sr = R(s);
     const bool scaled = s != 1.0;
     const R dtg = pick<R>(a.dtg, a.dtg_f), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f);
-    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
-      const int b = e / nz, n = e - b * nz;
+    LinePos pos(threadIdx.x, nz, blockDim.x);
+    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
+      const int b = pos.b, n = pos.k;
       const int q = b * LS + cn_slot(n, lc);
       C v = tile[q];
       if (scaled) v = scale(v, sr);
@@ -939,11 +959,9 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
     __syncthreads();
   }
 
+  LinePos pos(threadIdx.x, nz, blockDim.x);
 #pragma unroll 4
-  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
-    const int b = e / nz, n = e - b * nz;
-    psi[e] = tile[b * LS + cn_slot(n, lc)];
-  }
+  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) psi[e] = tile[pos.b * LS + cn_slot(pos.k, lc)];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1195,8 +1213,9 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_phase(KArgs a) {
   const R dtg = pick<R>(a.dtg, a.dtg_f), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f);
   const R inv_ntot = R(a.inv_ntot);
   AdjSums<R> acc;
-  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
-    const int b = e / nz, n = e - b * nz;
+  LinePos pos(threadIdx.x, nz, blockDim.x);
+  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
+    const int b = pos.b, n = pos.k;
     const C v = pk[e];
     const C g1 = gt[e];
     const C z = res[n * SB + (b >> 1)];
@@ -1250,8 +1269,9 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_combine(KArgs a) {
   cp_async_wait_all();
   __syncthreads();
   const R dtg = pick<R>(a.dtg, a.dtg_f), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f);
-  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
-    const int b = e / nz, n = e - b * nz;
+  LinePos pos(threadIdx.x, nz, blockDim.x);
+  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
+    const int b = pos.b, n = pos.k;
     const C v = pk[e];
     const C u = gt[e];
     const C z = res[n * SB + (b >> 1)];
