@@ -150,7 +150,7 @@ struct Tiles<float> {
   static constexpr int kZThreads = 256;
   static constexpr int kXCols = 8;
   static constexpr int kCnCols = 16;
-  static constexpr int kCnThreads = 256;
+  static constexpr int kCnThreads = 512;  // 16 warps, one line per warp
   static constexpr int kYBudget = 4096;
 };
 constexpr int kFftThreads = 256;
@@ -309,22 +309,29 @@ __device__ __forceinline__ void fft_stage(const cplx<R> *__restrict__ src, cplx<
   const int jstep = blockDim.x / lw;
   const int twstep = n / (ns * P);
   const bool pow2 = (ns & (ns - 1)) == 0;
+  // strides (in elements) between the P inputs and between the P outputs of a butterfly
+  const int in_stride = nbf * sb, out_stride = ns * sb;
+  const cplx<R> *s0 = src + line;
+  cplx<R> *d0 = dst + line;
   for (int j = threadIdx.x / lw; j < nbf; j += jstep) {
     const int k = pow2 ? (j & (ns - 1)) : (j % ns);
+    const cplx<R> *in = s0 + j * sb;
     cplx<R> v[P];
 #pragma unroll
-    for (int r = 0; r < P; ++r) v[r] = src[(j + r * nbf) * sb + line];
+    for (int r = 0; r < P; ++r) v[r] = in[r * in_stride];
     if (ns > 1) {
+      const cplx<R> *w = tw + k * twstep;
+      const int wstep = k * twstep;
 #pragma unroll
       for (int r = 1; r < P; ++r) {
-        const cplx<R> w = ldg(tw + r * k * twstep);
-        v[r] = DIR < 0 ? v[r] * w : mul_conj(v[r], w);
+        const cplx<R> t = ldg(w + (r - 1) * wstep);
+        v[r] = DIR < 0 ? v[r] * t : mul_conj(v[r], t);
       }
     }
     butterfly<R, DIR, P>(v);
-    const int base = (j - k) * P + k;
+    cplx<R> *out = d0 + ((j - k) * P + k) * sb;
 #pragma unroll
-    for (int s = 0; s < P; ++s) dst[(base + s * ns) * sb + line] = v[s];
+    for (int s = 0; s < P; ++s) out[s * out_stride] = v[s];
   }
 }
 
@@ -381,16 +388,17 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
 
   cplx<R> y[CH];
   cplx<R> acc = czero<R>();
+  // (the factor tables may live in global or shared memory: plain loads)
 #pragma unroll
   for (int e = 0; e < CH; ++e) {
     if (e < len) {
       const int i = s0 + e;
-      acc = buf[(i + 1 + t) * es] + mul(ldg(alpha + e * kWarp), acc);
+      acc = buf[(i + 1 + t) * es] + mul(alpha[e * kWarp], acc);
       y[e] = acc;
     }
   }
   // forward carries: Y_{t+1} = A_t Y_t + B_t, Y_0 = 0
-  Coef A = len > 0 ? ldg(P + (len - 1) * kWarp) : coef_one<Coef>();
+  Coef A = len > 0 ? P[(len - 1) * kWarp] : coef_one<Coef>();
   cplx<R> B = acc;
 #pragma unroll
   for (int d = 1; d < kWarp; d <<= 1) {
@@ -408,13 +416,13 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
 #pragma unroll
   for (int e = CH - 1; e >= 0; --e) {
     if (e < len) {
-      acc = mul(ldg(beta + e * kWarp), y[e] + mul(c, acc));
+      acc = mul(beta[e * kWarp], y[e] + mul(c, acc));
       y[e] = acc;
     }
   }
   // backward carries: X_t = G_{s0} X_{t+1} + (chi0_{s0} + H_{s0} Y_t), X_32 = 0
-  Coef A2 = len > 0 ? ldg(G) : coef_one<Coef>();
-  cplx<R> B2 = len > 0 ? acc + mul(ldg(H), Y) : czero<R>();
+  Coef A2 = len > 0 ? G[0] : coef_one<Coef>();
+  cplx<R> B2 = len > 0 ? acc + mul(H[0], Y) : czero<R>();
 #pragma unroll
   for (int d = 1; d < kWarp; d <<= 1) {
     const Coef An = shfl_down(A2, d);
@@ -431,7 +439,7 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   for (int e = 0; e < CH; ++e) {
     if (e < len) {
       const int i = s0 + e;
-      const cplx<R> chi = y[e] + mul(ldg(H + e * kWarp), Y) + mul(ldg(G + e * kWarp), X);
+      const cplx<R> chi = y[e] + mul(H[e * kWarp], Y) + mul(G[e * kWarp], X);
       const int q = (i + 1 + t) * es;
       const cplx<R> v = buf[q];
       buf[q] = {R(2) * chi.re - v.re, R(2) * chi.im - v.im};
@@ -1011,7 +1019,9 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
   const int slots = cn_slots(N, lc);
   C *cur = reinterpret_cast<C *>(smem_raw);
   C *nxt = cur + slots * SB;
-  R *x2tab = reinterpret_cast<R *>(nxt + slots * SB);
+  Coef *stab = reinterpret_cast<Coef *>(nxt + slots * SB);     // factor tables, staged once
+  const int ntab = 5 * (kWarp << lc);
+  R *x2tab = reinterpret_cast<R *>(stab + ntab);
   const size_t stride = AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
   C *gpsi = reinterpret_cast<C *>(a.psi);
   const int b = threadIdx.x % B;   // B divides the block size: the column is fixed per thread
@@ -1039,7 +1049,11 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
       x2tab[n] = R(x * x);
     }
   const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[AXIS], a.cn_rf[AXIS]));
-  const Coef *tab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
+  {
+    const Coef *gtab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
+    for (int q = threadIdx.x; q < ntab; q += blockDim.x) stab[q] = gtab[q];
+  }
+  const Coef *tab = stab;
   double v[4] = {0, 0, 0, 0};
 
   int tile = blockIdx.x;
@@ -1335,7 +1349,8 @@ struct Impl {
   static size_t smem_y(const KArgs &a) { return 2 * (size_t)a.ny * (a.ylines + 1) * E; }
   static size_t smem_x(const KArgs &a) { return 2 * (size_t)a.nx * T::kXCols * E; }
   static size_t smem_cn(int n, int lchunk) {
-    return 2 * (size_t)cn_slots(n, lchunk) * (T::kCnCols + 1) * E + (size_t)n * sizeof(R);
+    return 2 * (size_t)cn_slots(n, lchunk) * (T::kCnCols + 1) * E + (size_t)5 * (kWarp << lchunk) * E +
+           (size_t)n * sizeof(R);
   }
 
   static dim3 grid_z(const KArgs &a) { return dim3((a.ny + T::kZLines - 1) / T::kZLines, a.nx); }
