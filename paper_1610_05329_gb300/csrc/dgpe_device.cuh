@@ -371,7 +371,7 @@ __device__ cplx<R> *fft_lines(cplx<R> *a, cplx<R> *b, const FftPlan &pl, int lw,
 // affine recurrences across lanes, resolved by warp-shuffle scans of (A, B) pairs.
 // Element n of the line is at buf[cn_slot(n, lchunk) * es].
 // ---------------------------------------------------------------------------------------
-template <typename R, typename Coef, int CH>
+template <typename R, typename Coef, int CH, bool SHARED_TAB>
 __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m, int lchunk,
                                         const Coef *__restrict__ tab, Coef c) {
   const int t = threadIdx.x & (kWarp - 1);
@@ -388,17 +388,21 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
 
   cplx<R> y[CH];
   cplx<R> acc = czero<R>();
-  // (the factor tables may live in global or shared memory: plain loads)
+  // factor tables: shared memory (plain loads) or global memory (read-only path)
+  auto T = [](const Coef *q) -> Coef {
+    if constexpr (SHARED_TAB) return *q;
+    else return ldg(q);
+  };
 #pragma unroll
   for (int e = 0; e < CH; ++e) {
     if (e < len) {
       const int i = s0 + e;
-      acc = buf[(i + 1 + t) * es] + mul(alpha[e * kWarp], acc);
+      acc = buf[(i + 1 + t) * es] + mul(T(alpha + e * kWarp), acc);
       y[e] = acc;
     }
   }
   // forward carries: Y_{t+1} = A_t Y_t + B_t, Y_0 = 0
-  Coef A = len > 0 ? P[(len - 1) * kWarp] : coef_one<Coef>();
+  Coef A = len > 0 ? T(P + (len - 1) * kWarp) : coef_one<Coef>();
   cplx<R> B = acc;
 #pragma unroll
   for (int d = 1; d < kWarp; d <<= 1) {
@@ -416,13 +420,13 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
 #pragma unroll
   for (int e = CH - 1; e >= 0; --e) {
     if (e < len) {
-      acc = mul(beta[e * kWarp], y[e] + mul(c, acc));
+      acc = mul(T(beta + e * kWarp), y[e] + mul(c, acc));
       y[e] = acc;
     }
   }
   // backward carries: X_t = G_{s0} X_{t+1} + (chi0_{s0} + H_{s0} Y_t), X_32 = 0
-  Coef A2 = len > 0 ? G[0] : coef_one<Coef>();
-  cplx<R> B2 = len > 0 ? acc + mul(H[0], Y) : czero<R>();
+  Coef A2 = len > 0 ? T(G) : coef_one<Coef>();
+  cplx<R> B2 = len > 0 ? acc + mul(T(H), Y) : czero<R>();
 #pragma unroll
   for (int d = 1; d < kWarp; d <<= 1) {
     const Coef An = shfl_down(A2, d);
@@ -439,7 +443,7 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   for (int e = 0; e < CH; ++e) {
     if (e < len) {
       const int i = s0 + e;
-      const cplx<R> chi = y[e] + mul(H[e * kWarp], Y) + mul(G[e * kWarp], X);
+      const cplx<R> chi = y[e] + mul(T(H + e * kWarp), Y) + mul(T(G + e * kWarp), X);
       const int q = (i + 1 + t) * es;
       const cplx<R> v = buf[q];
       buf[q] = {R(2) * chi.re - v.re, R(2) * chi.im - v.im};
@@ -452,14 +456,14 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
 }
 
 // cn_line with the chunk length as a compile-time constant (every unrolled iteration live).
-template <typename R, typename Coef>
+template <typename R, typename Coef, bool SHARED_TAB>
 __device__ __forceinline__ void cn_line_any(cplx<R> *__restrict__ buf, int es, int m, int lchunk,
                                             const Coef *__restrict__ tab, Coef c) {
   switch (lchunk) {
-    case 1: cn_line<R, Coef, 2>(buf, es, m, lchunk, tab, c); break;
-    case 2: cn_line<R, Coef, 4>(buf, es, m, lchunk, tab, c); break;
-    case 3: cn_line<R, Coef, 8>(buf, es, m, lchunk, tab, c); break;
-    default: cn_line<R, Coef, 16>(buf, es, m, lchunk, tab, c); break;
+    case 1: cn_line<R, Coef, 2, SHARED_TAB>(buf, es, m, lchunk, tab, c); break;
+    case 2: cn_line<R, Coef, 4, SHARED_TAB>(buf, es, m, lchunk, tab, c); break;
+    case 3: cn_line<R, Coef, 8, SHARED_TAB>(buf, es, m, lchunk, tab, c); break;
+    default: cn_line<R, Coef, 16, SHARED_TAB>(buf, es, m, lchunk, tab, c); break;
   }
 }
 
@@ -963,7 +967,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
     const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[2], a.cn_rf[2]));
     const Coef *tab = reinterpret_cast<const Coef *>(a.cn[2].tab);
     for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp)
-      cn_line_any<R, Coef>(tile + b * LS, 1, a.cn[2].m, lc, tab, c);
+      cn_line_any<R, Coef, false>(tile + b * LS, 1, a.cn[2].m, lc, tab, c);
     __syncthreads();
   }
 
@@ -1071,7 +1075,7 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
     const size_t base = tile_origin(tile, fixed, k0);
     const int nb = min(B, a.nz - k0);
     for (int l = threadIdx.x / kWarp; l < nb; l += blockDim.x / kWarp)
-      cn_line_any<R, Coef>(cur + l, SB, a.cn[AXIS].m, lc, tab, c);
+      cn_line_any<R, Coef, true>(cur + l, SB, a.cn[AXIS].m, lc, tab, c);
     __syncthreads();
     if (b < nb) {
       RowSums<R> rs;
