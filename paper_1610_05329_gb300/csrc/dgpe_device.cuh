@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int BZ = Tiles<R>::kZLines;
   constexpr int PZ = BZ / 2;
-  constexpr int SB = PZ + 1;
+  constexpr int SB = PZ;   // unpadded: the butterflies (pair fastest) and the line-fastest phase loop are conflict-free
   const int nz = a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
   const int nl = min(BZ, a.ny - j0), np = nl >> 1;
   const int lc = a.cn[2].lchunk;
@@ -942,9 +942,11 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
     const R sr = R(s);
     const bool scaled = s != 1.0;
     const R dtg = pick<R>(a.dtg, a.dtg_f), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f);
-    LinePos pos(threadIdx.x, nz, blockDim.x);
+    // lines fastest: the padded tile rows (odd stride LS) and the pair-interleaved Phi are
+    // read without bank conflicts
+    LinePos pos(threadIdx.x, nl, blockDim.x);   // pos.b = z index n, pos.k = line b
     for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
-      const int b = pos.b, n = pos.k;
+      const int n = pos.b, b = pos.k;
       const int q = b * LS + cn_slot(n, lc);
       C v = tile[q];
       if (scaled) v = scale(v, sr);
@@ -1347,7 +1349,7 @@ struct Impl {
 
   static size_t smem_z_fft(const KArgs &a) { return 2 * (size_t)a.nz * (T::kZLines / 2 + 1) * E; }
   static size_t smem_k5(const KArgs &a) {
-    return smem_z_fft(a) + (size_t)T::kZLines * cn_slots(a.nz, a.cn[2].lchunk) * E +
+    return 2 * (size_t)a.nz * (T::kZLines / 2) * E + (size_t)T::kZLines * cn_slots(a.nz, a.cn[2].lchunk) * E +
            (size_t)(a.nz + T::kZLines) * sizeof(R);
   }
   static size_t smem_y(const KArgs &a) { return 2 * (size_t)a.ny * (a.ylines + 1) * E; }
