@@ -34,8 +34,11 @@ def test_real_time_256cubed_fp64(orc):
     want = orc.step(p, psi0, 2)
     assert rel(got, want) < 1e-10
     ow = orc.observables(p, want)
-    for k in ("norm", "mu", "energy"):
-        assert o[k] == pytest.approx(ow[k], rel=1e-11)
+    # mu and E weight the psi difference by the discrete Laplacian (spectral radius
+    # 4(1/hx^2 + 1/hy^2 + 1/hz^2) = 1200 at h = 0.1), so their bound is looser than psi's
+    assert o["norm"] == pytest.approx(ow["norm"], rel=1e-11)
+    for k in ("mu", "energy"):
+        assert o[k] == pytest.approx(ow[k], rel=1e-9)
 
 
 def test_imaginary_time_256cubed_fp64(orc):
