@@ -69,8 +69,9 @@ extern "C" {
 #define DGPE_SUB_CN_Z 3
 
 /*
- * Problem description.  Sizes: 4 <= n <= 512, n even, n = 2^a 3^b (every size of the
- * paper's "FFT-friendly" advice that this build's radix-2/3/4/8 transforms cover).
+ * Problem description.  Sizes: 4 <= n <= 512, n even, n = 2^a 3^b 5^c 7^d (the paper's
+ * "FFT-friendly" sizes, except factors 11 and 13; radix-2/3/4/5/7/8 transforms), e.g.
+ * the paper's own 480 x 480 x 500 and 480 x 480 x 250 grids.
  * h, dt > 0 and finite; nu, g, gdd finite.  workspace: NULL, or device memory of at least
  * workspace_bytes >= dgpe_workspace_bytes(p) bytes, 256-byte aligned, owned by the caller
  * and kept alive until dgpe_destroy.

@@ -21,17 +21,20 @@ namespace {
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-bool is_2a3b(int n) {
+bool is_2a3b5c7d(int n) {
   while (n % 2 == 0) n /= 2;
   while (n % 3 == 0) n /= 3;
+  while (n % 5 == 0) n /= 5;
+  while (n % 7 == 0) n /= 7;
   return n == 1;
 }
 
 bool finite(double v) { return isfinite(v) != 0; }
 
 // Radix plan.  style 0: as many radix-8 stages as possible, then one radix-4 or radix-2
-// stage for the rest of the power of two, then the radix-3 stages.  style 1: radix-4 stages
-// (and one radix-2), then radix-3.  style 2: radix-3 stages first, then as style 0.
+// stage for the rest of the power of two, then the radix-3, 5 and 7 stages.  style 1:
+// radix-4 stages (and one radix-2), then the odd radices.  style 2: radix-3 stages first,
+// then as style 0.
 FftPlan make_plan(int n, int style = 0) {
   FftPlan p{};
   p.n = n;
@@ -58,6 +61,14 @@ FftPlan make_plan(int n, int style = 0) {
     p.radix[k++] = 3;
     m /= 3;
   }
+  while (m % 5 == 0) {
+    p.radix[k++] = 5;
+    m /= 5;
+  }
+  while (m % 7 == 0) {
+    p.radix[k++] = 7;
+    m /= 7;
+  }
   p.nstages = k;
   return p;
 }
@@ -82,7 +93,7 @@ int check_shape(const dgpe_params *p) {
   const int dims[3] = {p->nx, p->ny, p->nz};
   for (int d = 0; d < 3; ++d) {
     const int n = dims[d];
-    if (n < 4 || n > 512 || n % 2 != 0 || !is_2a3b(n)) return DGPE_EINVAL;
+    if (n < 4 || n > 512 || n % 2 != 0 || !is_2a3b5c7d(n)) return DGPE_EINVAL;
     if (cn_chunk(n) > kCnMaxChunk) return DGPE_EUNSUPPORTED;
   }
   if (p->precision != DGPE_FP64 && p->precision != DGPE_MIXED) return DGPE_EINVAL;

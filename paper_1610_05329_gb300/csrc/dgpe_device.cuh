@@ -223,7 +223,7 @@ __host__ __device__ inline int cn_slot(int n, int lchunk) { return n + (max(n - 
 __host__ __device__ inline int cn_slots(int n, int lchunk) { return n + ((n - 2) >> lchunk); }
 
 // ---------------------------------------------------------------------------------------
-// FFT: radix-2/3/4/8 butterflies (DIR = -1 forward e^{-i..}, +1 inverse, unnormalised)
+// FFT: radix-2/3/4/5/7/8 butterflies (DIR = -1 forward e^{-i..}, +1 inverse, unnormalised)
 // ---------------------------------------------------------------------------------------
 template <typename R, int DIR>
 __device__ __forceinline__ void bf2(cplx<R> *v) {
@@ -287,11 +287,60 @@ __device__ __forceinline__ void bf3(cplx<R> *v) {
   }
 }
 
+// Radix 5 and 7 (odd primes): with t_k = v_k + v_{P-k}, u_k = v_k - v_{P-k},
+// X_m = v_0 + sum_k cos(2 pi k m / P) t_k  -/+  i sum_k sin(2 pi k m / P) u_k  (m, P - m),
+// the sign of i being DIR's.
+template <typename R, int DIR>
+__device__ __forceinline__ void bf5(cplx<R> *v) {
+  const R c1 = R(0.30901699437494745), c2 = R(-0.8090169943749475);
+  const R s1 = R(0.9510565162951535), s2 = R(0.5877852522924731);
+  const cplx<R> t1 = v[1] + v[4], t2 = v[2] + v[3], t3 = v[1] - v[4], t4 = v[2] - v[3];
+  const cplx<R> a = {v[0].re + c1 * t1.re + c2 * t2.re, v[0].im + c1 * t1.im + c2 * t2.im};
+  const cplx<R> b = {v[0].re + c2 * t1.re + c1 * t2.re, v[0].im + c2 * t1.im + c1 * t2.im};
+  const cplx<R> d = {s1 * t3.re + s2 * t4.re, s1 * t3.im + s2 * t4.im};
+  const cplx<R> e = {s2 * t3.re - s1 * t4.re, s2 * t3.im - s1 * t4.im};
+  const cplx<R> id = DIR < 0 ? mul_mi(d) : mul_i(d), ie = DIR < 0 ? mul_mi(e) : mul_i(e);
+  v[0] = v[0] + t1 + t2;
+  v[1] = a + id;
+  v[4] = a - id;
+  v[2] = b + ie;
+  v[3] = b - ie;
+}
+
+template <typename R, int DIR>
+__device__ __forceinline__ void bf7(cplx<R> *v) {
+  const R C1 = R(0.6234898018587335), C2 = R(-0.2225209339563144), C3 = R(-0.9009688679024191);
+  const R S1 = R(0.7818314824680298), S2 = R(0.9749279121818236), S3 = R(0.4338837391175581);
+  const cplx<R> t1 = v[1] + v[6], t2 = v[2] + v[5], t3 = v[3] + v[4];
+  const cplx<R> u1 = v[1] - v[6], u2 = v[2] - v[5], u3 = v[3] - v[4];
+  auto lin3 = [](R p, cplx<R> x, R q, cplx<R> y, R r, cplx<R> z) {
+    return cplx<R>{p * x.re + q * y.re + r * z.re, p * x.im + q * y.im + r * z.im};
+  };
+  const cplx<R> a1 = v[0] + lin3(C1, t1, C2, t2, C3, t3);
+  const cplx<R> a2 = v[0] + lin3(C2, t1, C3, t2, C1, t3);
+  const cplx<R> a3 = v[0] + lin3(C3, t1, C1, t2, C2, t3);
+  const cplx<R> d1 = lin3(S1, u1, S2, u2, S3, u3);
+  const cplx<R> d2 = lin3(S2, u1, -S3, u2, -S1, u3);
+  const cplx<R> d3 = lin3(S3, u1, -S1, u2, S2, u3);
+  const cplx<R> i1 = DIR < 0 ? mul_mi(d1) : mul_i(d1);
+  const cplx<R> i2 = DIR < 0 ? mul_mi(d2) : mul_i(d2);
+  const cplx<R> i3 = DIR < 0 ? mul_mi(d3) : mul_i(d3);
+  v[0] = v[0] + t1 + t2 + t3;
+  v[1] = a1 + i1;
+  v[6] = a1 - i1;
+  v[2] = a2 + i2;
+  v[5] = a2 - i2;
+  v[3] = a3 + i3;
+  v[4] = a3 - i3;
+}
+
 template <typename R, int DIR, int P>
 __device__ __forceinline__ void butterfly(cplx<R> *v) {
-  if (P == 2) bf2<R, DIR>(v);
-  else if (P == 3) bf3<R, DIR>(v);
-  else if (P == 4) bf4<R, DIR>(v[0], v[1], v[2], v[3]);
+  if constexpr (P == 2) bf2<R, DIR>(v);
+  else if constexpr (P == 3) bf3<R, DIR>(v);
+  else if constexpr (P == 4) bf4<R, DIR>(v[0], v[1], v[2], v[3]);
+  else if constexpr (P == 5) bf5<R, DIR>(v);
+  else if constexpr (P == 7) bf7<R, DIR>(v);
   else bf8<R, DIR>(v);
 }
 
@@ -346,6 +395,8 @@ __device__ cplx<R> *fft_lines(cplx<R> *a, cplx<R> *b, const FftPlan &pl, int lw,
     if (p == 8) fft_stage<R, DIR, 8>(a, b, pl.n, ns, lw, nlines, sb, tw);
     else if (p == 4) fft_stage<R, DIR, 4>(a, b, pl.n, ns, lw, nlines, sb, tw);
     else if (p == 3) fft_stage<R, DIR, 3>(a, b, pl.n, ns, lw, nlines, sb, tw);
+    else if (p == 5) fft_stage<R, DIR, 5>(a, b, pl.n, ns, lw, nlines, sb, tw);
+    else if (p == 7) fft_stage<R, DIR, 7>(a, b, pl.n, ns, lw, nlines, sb, tw);
     else fft_stage<R, DIR, 2>(a, b, pl.n, ns, lw, nlines, sb, tw);
     __syncthreads();
     cplx<R> *t = a;

@@ -59,8 +59,8 @@ def test_workspace_bytes(lib):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(shape=(5, 16, 16)), dict(shape=(16, 14, 16)), dict(shape=(16, 16, 2)), dict(shape=(1024, 16, 16)),
-    dict(shape=(16, 16, 10)), dict(h=0.0), dict(h=(0.2, -0.1, 0.2)), dict(h=float("nan")), dict(dt=0.0),
+    dict(shape=(5, 16, 16)), dict(shape=(16, 22, 16)), dict(shape=(16, 16, 2)), dict(shape=(1024, 16, 16)),
+    dict(shape=(16, 16, 26)), dict(h=0.0), dict(h=(0.2, -0.1, 0.2)), dict(h=float("nan")), dict(dt=0.0),
     dict(dt=-0.01), dict(dt=float("inf")), dict(mode=2), dict(precision=7), dict(g=float("nan")),
     dict(nu=(1, float("inf"), 1)),
 ])

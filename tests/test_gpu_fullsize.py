@@ -108,3 +108,16 @@ def test_batching_sizes_mixed(orc, n):
     gpu.close()
     want = orc.step(orc.make_params((n, n, n), h, 0.001, orc.IMAG_TIME, nu, g, gdd), psi0.astype(np.complex128), 10)
     assert rel(got, want) < 5e-6
+
+
+def test_paper_grid_480x480x250_fp64(orc):
+    """The grid of the paper's CUDA/MPI timings (Table 3): 480 x 480 x 250 (radix 2, 3, 5)."""
+    shape, h, nu, g, gdd, dt = (480, 480, 250), 0.05, (1.0, 1.0, 1.5), 40.0, 20.0, 5e-4
+    psi0 = inputs.gaussian_psi(shape, h, noise=1e-3, seed=2)
+    gpu = abi.Condensate(shape, h, dt, mode=abi.DGPE_REAL_TIME, nu=nu, g=g, gdd=gdd)
+    gpu.set_psi(psi0)
+    gpu.step(1)
+    got = gpu.get_psi()
+    gpu.close()
+    want = orc.step(orc.make_params(shape, h, dt, orc.REAL_TIME, nu, g, gdd), psi0, 1)
+    assert rel(got, want) < 1e-10

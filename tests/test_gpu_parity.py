@@ -215,3 +215,16 @@ def test_potential_step_large_phase_angles(orc, dt):
     gpu.substep(abi.DGPE_SUB_POTENTIAL)
     assert rel(gpu.get_psi(), orc.potential_step(p, psi)) < FP64_SUB_TOL
     gpu.close()
+
+
+@pytest.mark.parametrize("shape,h", [((10, 20, 14), 0.5), ((40, 28, 30), 0.3), ((70, 10, 50), 0.25)])
+@pytest.mark.parametrize("mode", [abi.DGPE_REAL_TIME, abi.DGPE_IMAG_TIME])
+def test_radix5_radix7_sizes(orc, shape, h, mode):
+    """Grid sizes with factors 5 and 7 (the paper's FFT-friendly sizes 2^a 3^b 5^c 7^d)."""
+    psi = state(shape, h)
+    gpu, p = make(orc, shape, h, 0.005, mode)
+    gpu.set_psi(psi)
+    assert rel(gpu.phi(), orc.dipolar_phi(p, np.abs(psi) ** 2)) < FP64_SUB_TOL
+    gpu.step(6)
+    assert rel(gpu.get_psi(), orc.step(p, psi, 6)) < FP64_STEP_TOL
+    gpu.close()
