@@ -399,6 +399,40 @@ def batching_run(abi, local, steps=300, count=64):
                          for n, t in tunings.items()}}
 
 
+# The paper's own 3D timing grids and times for 1000 iterations (its Tables 1-3; precision
+# unstated (C doubles), physics unstated): context only.
+PAPER_GRIDS = {
+    "480x480x480": {"shape": (480, 480, 480), "paper": "Table 1: imag3d-th 888 s, real3d-th 1466 s (16 cores, T=16)"},
+    "480x480x500": {"shape": (480, 480, 500), "paper": "Table 2: imag3d-mpi 1124 s (1 node) / 96 s (32 nodes); real3d-mpi 2140 / 129 s"},
+    "480x480x250": {"shape": (480, 480, 250), "paper": "Table 3: imag3d CUDA 579 s, real3d CUDA 800 s (1 Tesla M2090); 61 / 80 s on 32 GPUs"},
+}
+
+
+def paper_grid_run(abi, local, steps=5):
+    """FP64 imaginary- and real-time steps on the paper's timing grids (h = 0.05, trap
+    (1, 1, 1.5), g = 40, gdd = 20, dt = 5e-4): ms/step and the time of 1000 iterations."""
+    import torch
+    from paper_1610_05329_gb300 import inputs
+    out = {}
+    for name, spec in PAPER_GRIDS.items():
+        shape = spec["shape"]
+        c = abi.Condensate(shape, 0.05, 5e-4, mode=abi.DGPE_IMAG_TIME, nu=(1.0, 1.0, 1.5), g=40.0, gdd=20.0,
+                           device=torch.device("cuda", local))
+        c.set_psi(torch.from_numpy(inputs.gaussian_psi(shape, 0.05, noise=1e-3, seed=1)).to(device=c.device,
+                                                                                            dtype=c.cdtype))
+        c.step(2)
+        ms_imag = time_steps(c, steps, lambda: None) / steps
+        c.set_params(mode=abi.DGPE_REAL_TIME)
+        c.step(2)
+        ms_real = time_steps(c, steps, lambda: None) / steps
+        c.close()
+        npts = shape[0] * shape[1] * shape[2]
+        out[name] = {"imag_ms_per_step": round(ms_imag, 3), "real_ms_per_step": round(ms_real, 3),
+                     "imag_1000_steps_s": round(ms_imag, 3), "real_1000_steps_s": round(ms_real, 3),
+                     "real_updates_per_s": npts / (ms_real * 1e-3), "paper": spec["paper"]}
+    return out
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
     ws, rank, _ = dist_env()
@@ -442,6 +476,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 128^3 differentiation line item")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-condensate batching line item")
+    ap.add_argument("--no-paper-grids", action="store_true", help="skip the paper-grid context line item")
     ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
                     help="time only this workload (profiling); the default line times both")
     args = ap.parse_args()
@@ -509,6 +544,9 @@ def main():
     batch = None
     if not args.no_batch and args.workload is None:
         batch = batching_run(abi, local)
+    paper = None
+    if not args.no_paper_grids and args.workload is None:
+        paper = paper_grid_run(abi, local)
 
     if rank != 0:
         return
@@ -527,6 +565,8 @@ def main():
         line["differentiation_128"] = diff
     if batch is not None:
         line["batching_64"] = batch
+    if paper is not None:
+        line["paper_grids_fp64"] = paper
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
