@@ -85,6 +85,9 @@ typedef struct dgpe_params {
   double nu[3];       /* trap frequencies nu_x, nu_y, nu_z */
   double g;           /* contact strength */
   double gdd;         /* dipolar strength (dipoles along z) */
+  double cutoff;      /* spherical cutoff radius R of the dipolar interaction (interaction
+                         restricted to r < R: Ut(k) times 1 + 3cos(kR)/(kR)^2 - 3sin(kR)/(kR)^3);
+                         <= 0: no cutoff */
   void *workspace;    /* optional caller-owned device memory */
   size_t workspace_bytes;
 } dgpe_params;

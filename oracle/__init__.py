@@ -33,7 +33,8 @@ class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
                 ("dt", ctypes.c_double), ("mode", ctypes.c_int),
-                ("nu", ctypes.c_double * 3), ("g", ctypes.c_double), ("gdd", ctypes.c_double)]
+                ("nu", ctypes.c_double * 3), ("g", ctypes.c_double), ("gdd", ctypes.c_double),
+                ("cutoff", ctypes.c_double)]
 
 
 class Obs(ctypes.Structure):
@@ -68,6 +69,8 @@ def lib():
             P = ctypes.POINTER
             dp = ctypes.c_void_p
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_cutoff_factor.restype = ctypes.c_double
+            L.orc_cutoff_factor.argtypes = [ctypes.c_double]
             for name, args in [("orc_fft", [dp, ctypes.c_int, ctypes.c_int]),
                                ("orc_dft", [dp, ctypes.c_int, ctypes.c_int]),
                                ("orc_fft3", [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -92,8 +95,9 @@ def num_threads():
     return lib().orc_num_threads()
 
 
-def make_params(shape, h, dt, mode, nu, g, gdd):
-    """shape = (nx, ny, nz); h = scalar or (hx, hy, hz); mode = REAL_TIME / IMAG_TIME."""
+def make_params(shape, h, dt, mode, nu, g, gdd, cutoff=0.0):
+    """shape = (nx, ny, nz); h = scalar or (hx, hy, hz); mode = REAL_TIME / IMAG_TIME;
+    cutoff = spherical cutoff radius of the dipolar interaction (<= 0: none)."""
     hx, hy, hz = (h, h, h) if np.isscalar(h) else tuple(h)
     p = Params()
     p.nx, p.ny, p.nz = (int(v) for v in shape)
@@ -102,6 +106,7 @@ def make_params(shape, h, dt, mode, nu, g, gdd):
     p.mode = int(mode)
     p.nu[0], p.nu[1], p.nu[2] = (float(v) for v in nu)
     p.g, p.gdd = float(g), float(gdd)
+    p.cutoff = float(cutoff)
     return p
 
 
@@ -204,3 +209,7 @@ def grad_z2(p, nu_z, steps_per_seg, psi0):
     lib().orc_grad_z2(ctypes.byref(p), nu_z.size, int(steps_per_seg), _ptr(nu_z), _ptr(psi0),
                       ctypes.byref(loss), _ptr(dnu), ctypes.byref(dg), ctypes.byref(dgdd))
     return loss.value, dnu, dg.value, dgdd.value
+
+
+def cutoff_factor(x):
+    return lib().orc_cutoff_factor(float(x))

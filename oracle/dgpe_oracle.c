@@ -127,7 +127,21 @@ static double wavenumber(int m, int n, double h) {
   return TWO_PI * (double)ms / ((double)n * h);
 }
 
-/* Ut(k) = 3 kz^2 / |k|^2 - 1 (dipoles along z), Ut(0) = 0 [S2, S3, S4]. */
+/* c(x) = 1 + 3 cos x / x^2 - 3 sin x / x^3; below x = 0.5 its Taylor series
+ * sum_{n>=2} (-1)^n 6n x^(2n-2) / (2n+1)! (the closed form cancels there). */
+double orc_cutoff_factor(double x) {
+  if (x >= 0.5) return 1.0 + 3.0 * cos(x) / (x * x) - 3.0 * sin(x) / (x * x * x);
+  double sum = 0, fact = 120.0; /* (2n+1)! for n = 2 */
+  double xp = x * x;            /* x^(2n-2) for n = 2 */
+  for (int n = 2; n <= 12; ++n) {
+    sum += ((n % 2) ? -1.0 : 1.0) * 6.0 * n * xp / fact;
+    fact *= (2.0 * n + 2.0) * (2.0 * n + 3.0);
+    xp *= x * x;
+  }
+  return sum;
+}
+
+/* Ut(k) = 3 kz^2 / |k|^2 - 1 (dipoles along z), Ut(0) = 0 [S2, S3, S4]; optional cutoff [S5]. */
 void orc_dipolar_kernel(const orc_params *p, double *ut) {
   for (int i = 0; i < p->nx; ++i)
     for (int j = 0; j < p->ny; ++j)
@@ -136,7 +150,9 @@ void orc_dipolar_kernel(const orc_params *p, double *ut) {
         double ky = wavenumber(j, p->ny, p->hy);
         double kz = wavenumber(k, p->nz, p->hz);
         double k2 = kx * kx + ky * ky + kz * kz;
-        ut[((long)i * p->ny + j) * p->nz + k] = (k2 == 0.0) ? 0.0 : 3.0 * kz * kz / k2 - 1.0;
+        double u = (k2 == 0.0) ? 0.0 : 3.0 * kz * kz / k2 - 1.0;
+        if (p->cutoff > 0 && k2 > 0.0) u *= orc_cutoff_factor(sqrt(k2) * p->cutoff);
+        ut[((long)i * p->ny + j) * p->nz + k] = u;
       }
 }
 

@@ -41,6 +41,7 @@ typedef struct {
   int mode;            /* ORC_REAL_TIME or ORC_IMAG_TIME */
   double nu[3];        /* trap frequencies nu_x, nu_y, nu_z */
   double g, gdd;       /* contact and dipolar strengths */
+  double cutoff;       /* spherical cutoff radius R of the dipolar interaction; <= 0: none */
 } orc_params;
 
 typedef struct {
@@ -59,7 +60,10 @@ void orc_dft(double complex *x, int n, int sign);   /* naive O(n^2) definition *
 /* 3D transform of a [nx][ny][nz] array (unnormalised), built from orc_fft along each axis. */
 void orc_fft3(double complex *x, int nx, int ny, int nz, int sign);
 
-/* Momentum-space dipolar kernel Ut on the full [nx][ny][nz] FFT grid. */
+/* Momentum-space dipolar kernel Ut on the full [nx][ny][nz] FFT grid.  With a spherical
+ * cutoff R > 0 (the interaction restricted to r < R), Ut is multiplied by
+ * c(kR) = 1 + 3 cos(kR)/(kR)^2 - 3 sin(kR)/(kR)^3 = 3 int_0^{kR} j_2(x)/x dx. */
+double orc_cutoff_factor(double x);
 void orc_dipolar_kernel(const orc_params *p, double *ut);
 /* Phi = Re IDFT[ Ut DFT(n) ] for a real density n.  Uses orc_fft3. */
 void orc_dipolar_phi(const orc_params *p, const double *n, double *phi);

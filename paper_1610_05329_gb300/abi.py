@@ -39,7 +39,7 @@ class dgpe_params(ctypes.Structure):
                 ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
                 ("dt", ctypes.c_double), ("mode", ctypes.c_int), ("precision", ctypes.c_int),
                 ("nu", ctypes.c_double * 3), ("g", ctypes.c_double), ("gdd", ctypes.c_double),
-                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+                ("cutoff", ctypes.c_double), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
 class dgpe_obs(ctypes.Structure):
@@ -152,7 +152,7 @@ def dgpe_last_cuda_error():
 
 
 def make_params(shape, h, dt, mode=DGPE_IMAG_TIME, precision=DGPE_FP64, nu=(1.0, 1.0, 1.0), g=0.0, gdd=0.0,
-                workspace=None, workspace_bytes=0):
+                workspace=None, workspace_bytes=0, cutoff=0.0):
     hx, hy, hz = (h, h, h) if np.isscalar(h) else tuple(h)
     p = dgpe_params()
     p.nx, p.ny, p.nz = (int(v) for v in shape)
@@ -162,6 +162,7 @@ def make_params(shape, h, dt, mode=DGPE_IMAG_TIME, precision=DGPE_FP64, nu=(1.0,
     p.precision = int(precision)
     p.nu[0], p.nu[1], p.nu[2] = (float(v) for v in nu)
     p.g, p.gdd = float(g), float(gdd)
+    p.cutoff = float(cutoff)
     p.workspace = workspace
     p.workspace_bytes = int(workspace_bytes)
     return p
@@ -307,7 +308,7 @@ class Condensate:
     """
 
     def __init__(self, shape, h, dt, mode=DGPE_IMAG_TIME, precision=DGPE_FP64, nu=(1.0, 1.0, 1.0),
-                 g=0.0, gdd=0.0, device=None):
+                 g=0.0, gdd=0.0, device=None, cutoff=0.0):
         import torch
         self._torch = torch
         self.shape = tuple(int(v) for v in shape)
@@ -316,7 +317,7 @@ class Condensate:
         self.cdtype = torch.complex128 if precision == DGPE_FP64 else torch.complex64
         self.rdtype = torch.float64 if precision == DGPE_FP64 else torch.float32
         self.np_cdtype = np.complex128 if precision == DGPE_FP64 else np.complex64
-        self._params = make_params(shape, h, dt, mode, precision, nu, g, gdd)
+        self._params = make_params(shape, h, dt, mode, precision, nu, g, gdd, cutoff=cutoff)
         nbytes = dgpe_workspace_bytes(self._params)
         self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self._params.workspace = self._ws.data_ptr()
@@ -350,7 +351,7 @@ class Condensate:
                 p.hx, p.hy, p.hz = hx, hy, hz
             elif k == "nu":
                 p.nu[0], p.nu[1], p.nu[2] = (float(x) for x in v)
-            elif k in ("dt", "g", "gdd"):
+            elif k in ("dt", "g", "gdd", "cutoff"):
                 setattr(p, k, float(v))
             elif k == "mode":
                 p.mode = int(v)

@@ -108,7 +108,7 @@ int check_physics(const dgpe_params *p) {
   if (p->mode == DGPE_IMAG_TIME && !(p->dt > 0)) return DGPE_EINVAL;
   for (int d = 0; d < 3; ++d)
     if (!finite(p->nu[d])) return DGPE_EINVAL;
-  if (!finite(p->g) || !finite(p->gdd)) return DGPE_EINVAL;
+  if (!finite(p->g) || !finite(p->gdd) || !finite(p->cutoff)) return DGPE_EINVAL;
   return DGPE_OK;
 }
 
@@ -171,6 +171,7 @@ void set_physics(KArgs &a, const dgpe_params *p) {
   a.hy = p->hy;
   a.hz = p->hz;
   a.dt = p->dt;
+  a.cutoff = p->cutoff;
   a.g = p->g;
   a.gdd = p->gdd;
   a.vx = 0.5 * p->nu[0] * p->nu[0];
@@ -606,7 +607,7 @@ int dgpe_set_params(dgpe_ctx *c, const dgpe_params *p) {
   if (rc) return rc;
   const bool cn_changed = p->dt != c->p.dt || p->hx != c->p.hx || p->hy != c->p.hy || p->hz != c->p.hz ||
                           p->mode != c->p.mode;
-  const bool step_args_changed = cn_changed || p->g != c->p.g || p->gdd != c->p.gdd;
+  const bool step_args_changed = cn_changed || p->g != c->p.g || p->gdd != c->p.gdd || p->cutoff != c->p.cutoff;
   void *ws = c->p.workspace;
   const size_t wsb = c->p.workspace_bytes;
   c->p = *p;

@@ -784,25 +784,52 @@ __global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a) {
 // forward FFT along x, multiply by Ut(kx, ky, kz) = 3 kz^2 / |k|^2 - 1 (Ut(0) = 0),
 // inverse FFT along x.
 // ---------------------------------------------------------------------------------------
+// Cutoff factor c(x) = 1 + 3 cos x / x^2 - 3 sin x / x^3 = 3 int_0^x j_2(t)/t dt of the
+// spherically truncated dipolar interaction; below x = 0.5 its Taylor series
+// sum_{n>=2} (-1)^n 6n x^(2n-2) / (2n+1)!, where the closed form cancels.
+template <typename R>
+__device__ __forceinline__ R cutoff_factor(R x) {
+  if (x >= R(0.5)) {
+    R sn, cs;
+    sin_cos(x, &sn, &cs);
+    const R ix2 = R(1) / (x * x);
+    return R(1) + R(3) * cs * ix2 - R(3) * sn * ix2 / x;
+  }
+  const R u = x * x;
+  // coefficients 6n/(2n+1)! for n = 2..9 (alternating signs)
+  R p = R(6.0 * 9 / 121645100408832000.0);
+  p = fma(p, -u, R(6.0 * 8 / 355687428096000.0));
+  p = fma(p, -u, R(6.0 * 7 / 1307674368000.0));
+  p = fma(p, -u, R(6.0 * 6 / 6227020800.0));
+  p = fma(p, -u, R(6.0 * 5 / 39916800.0));
+  p = fma(p, -u, R(6.0 * 4 / 362880.0));
+  p = fma(p, -u, R(6.0 * 3 / 5040.0));
+  p = fma(p, -u, R(6.0 * 2 / 120.0));
+  return p * u;
+}
+
 template <typename R>
 __device__ __forceinline__ R dipolar_kernel(int ix, int iy, int iz, const KArgs &a) {
   const double two_pi = 6.283185307179586476925286766559;
   const int mx = ix <= a.nx / 2 ? ix : ix - a.nx;
   const int my = iy <= a.ny / 2 ? iy : iy - a.ny;
+  R u, k2r;
   if constexpr (sizeof(R) == 8) {
     const double kx = two_pi * (double)mx / ((double)a.nx * a.hx);
     const double ky = two_pi * (double)my / ((double)a.ny * a.hy);
     const double kz = two_pi * (double)iz / ((double)a.nz * a.hz);
-    const double k2 = kx * kx + ky * ky + kz * kz;
-    return k2 > 0.0 ? 3.0 * kz * kz / k2 - 1.0 : 0.0;
+    k2r = kx * kx + ky * ky + kz * kz;
+    u = k2r > 0.0 ? 3.0 * kz * kz / k2r - 1.0 : 0.0;
   } else {
     const float tp = 6.283185307f;
     const float kx = tp * (float)mx / ((float)a.nx * (float)a.hx);
     const float ky = tp * (float)my / ((float)a.ny * (float)a.hy);
     const float kz = tp * (float)iz / ((float)a.nz * (float)a.hz);
-    const float k2 = kx * kx + ky * ky + kz * kz;
-    return k2 > 0.0f ? 3.0f * kz * kz / k2 - 1.0f : 0.0f;
+    k2r = kx * kx + ky * ky + kz * kz;
+    u = k2r > 0.0f ? 3.0f * kz * kz / k2r - 1.0f : 0.0f;
   }
+  if (a.cutoff > 0.0 && k2r > R(0)) u *= cutoff_factor<R>(sqrt(k2r) * R(a.cutoff));
+  return u;
 }
 
 template <typename R>

@@ -46,6 +46,7 @@ struct KArgs {
   int nx, ny, nz, nzh;         // nzh = nz/2 + 1 (half-spectrum length along z)
   double hx, hy, hz;
   double dt, g, gdd;
+  double cutoff;               // spherical cutoff radius of the dipolar kernel (<= 0: none)
   double vx, vy, vz;           // 0.5 * nu_d^2
   double inv_ntot;             // 1 / (nx ny nz)
   int imag;                    // 1 = imaginary time

@@ -228,3 +228,21 @@ def test_radix5_radix7_sizes(orc, shape, h, mode):
     gpu.step(6)
     assert rel(gpu.get_psi(), orc.step(p, psi, 6)) < FP64_STEP_TOL
     gpu.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(abi.DGPE_FP64, FP64_STEP_TOL), (abi.DGPE_MIXED, 2e-5)])
+def test_spherical_cutoff(orc, precision, tol):
+    """Dipolar interaction restricted to r < R (R = 3.1, inside the box of 9.6)."""
+    shape, h, R = (24, 32, 36), (0.4, 0.3, 0.27), 3.1
+    psi = state(shape, h)
+    gpu = abi.Condensate(shape, h, 0.005, mode=abi.DGPE_REAL_TIME, precision=precision, nu=(1.0, 1.1, 0.9),
+                         g=25.0, gdd=15.0, cutoff=R)
+    p = orc.make_params(shape, h, 0.005, orc.REAL_TIME, (1.0, 1.1, 0.9), 25.0, 15.0, cutoff=R)
+    cdt = np.complex128 if precision == abi.DGPE_FP64 else np.complex64
+    gpu.set_psi(psi.astype(cdt))
+    want_phi = orc.dipolar_phi(p, np.abs(psi.astype(cdt).astype(np.complex128)) ** 2)
+    assert rel(gpu.phi(), want_phi) < (FP64_SUB_TOL if precision == abi.DGPE_FP64 else 1e-5)
+    gpu.step(8)
+    want = orc.step(p, psi.astype(cdt).astype(np.complex128), 8)
+    assert rel(gpu.get_psi().astype(np.complex128), want) < tol
+    gpu.close()

@@ -89,3 +89,24 @@ def test_gaussian_dipolar_energy(orc, sr, sz):
 
 def test_isotropic_density_has_no_dipolar_energy(orc):
     assert abs(grid_e_dd(orc, 32, 0.3, 1.0, 1.0)) < 1e-15
+
+
+@pytest.mark.parametrize("x", [1e-3, 0.1, 0.49, 0.5, 0.51, 1.0, 3.7, 12.0, 40.0])
+def test_cutoff_factor_is_the_j2_integral(orc, x):
+    """Spherical cutoff (interaction restricted to r < R): the kernel factor is
+    3 int_0^{kR} j_2(t)/t dt (partial-wave expansion of the truncated 1/r^3 kernel),
+    computed here by quadrature of the spherical Bessel function."""
+    from scipy.special import spherical_jn
+    val, _ = integrate.quad(lambda t: spherical_jn(2, t) / t, 0, x, limit=400, epsabs=1e-15, epsrel=1e-13)
+    assert orc.cutoff_factor(x) == pytest.approx(3 * val, rel=1e-10, abs=1e-16)
+
+
+def test_cutoff_tends_to_the_uncut_kernel(orc):
+    # a cutoff much larger than the box changes only the lowest wavenumbers; R -> 0 removes
+    # the interaction
+    p0 = orc.make_params((8, 8, 8), 0.5, 1e-3, orc.REAL_TIME, (1, 1, 1), 0, 1)
+    big = orc.make_params((8, 8, 8), 0.5, 1e-3, orc.REAL_TIME, (1, 1, 1), 0, 1, cutoff=1e4)
+    tiny = orc.make_params((8, 8, 8), 0.5, 1e-3, orc.REAL_TIME, (1, 1, 1), 0, 1, cutoff=1e-6)
+    u0, ub, ut = orc.dipolar_kernel(p0), orc.dipolar_kernel(big), orc.dipolar_kernel(tiny)
+    assert np.max(np.abs(ub - u0)) < 1e-6
+    assert np.max(np.abs(ut)) < 1e-11
