@@ -62,6 +62,13 @@ extern "C" {
 #define DGPE_HOST 0
 #define DGPE_DEVICE 1
 
+/* Quadrature of the norm (hence the imaginary-time renormalisation) and of the observables. */
+#define DGPE_RECTANGLE 0  /* h^3 sum over all points */
+#define DGPE_SIMPSON 1    /* composite Simpson (1,4,2,...,4,1)/3 per axis on indices 0..n-2 (the last point is a wall) */
+/* Kinetic-energy form of the observables. */
+#define DGPE_KINETIC_LAPLACIAN3 0  /* 1/2 Re conj(psi)(-lap psi), the step's own 3-point Laplacian */
+#define DGPE_KINETIC_GRADIENT5 1   /* 1/2 |grad psi|^2 with 4th-order 5-point first derivatives */
+
 /* Sub-steps for dgpe_substep (each is one factor of the split step). */
 #define DGPE_SUB_POTENTIAL 0  /* psi <- psi e^{-i theta} (or e^{-theta}); no renormalisation */
 #define DGPE_SUB_CN_X 1
@@ -88,12 +95,15 @@ typedef struct dgpe_params {
   double cutoff;      /* spherical cutoff radius R of the dipolar interaction (interaction
                          restricted to r < R: Ut(k) times 1 + 3cos(kR)/(kR)^2 - 3sin(kR)/(kR)^3);
                          <= 0: no cutoff */
+  int integration;    /* DGPE_RECTANGLE (default 0) or DGPE_SIMPSON */
+  int kinetic;        /* DGPE_KINETIC_LAPLACIAN3 (default 0) or DGPE_KINETIC_GRADIENT5 */
   void *workspace;    /* optional caller-owned device memory */
   size_t workspace_bytes;
 } dgpe_params;
 
-/* Observables of the current state, FP64.  norm = h^3 sum |psi|^2; the energy terms use the
- * 3-point Laplacian with zero values outside the grid:
+/* Observables of the current state, FP64.  norm = h^3 sum |psi|^2 (sums weighted by the
+ * chosen quadrature); the energy terms use the 3-point Laplacian with zero values outside
+ * the grid (or the 5-point gradient, see dgpe_params.kinetic):
  *   e_kin = h^3 sum 1/2 Re conj(psi) (-lap psi),  e_trap = h^3 sum V n,
  *   e_contact = h^3 sum g n^2 / 2,  e_dipolar = h^3 sum gdd Phi n / 2,
  *   energy = e_kin + e_trap + e_contact + e_dipolar,

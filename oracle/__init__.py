@@ -34,7 +34,7 @@ class Params(ctypes.Structure):
                 ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
                 ("dt", ctypes.c_double), ("mode", ctypes.c_int),
                 ("nu", ctypes.c_double * 3), ("g", ctypes.c_double), ("gdd", ctypes.c_double),
-                ("cutoff", ctypes.c_double)]
+                ("cutoff", ctypes.c_double), ("integration", ctypes.c_int), ("kinetic", ctypes.c_int)]
 
 
 class Obs(ctypes.Structure):
@@ -71,6 +71,8 @@ def lib():
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_cutoff_factor.restype = ctypes.c_double
             L.orc_cutoff_factor.argtypes = [ctypes.c_double]
+            L.orc_norm.restype = ctypes.c_double
+            L.orc_norm.argtypes = [ctypes.POINTER(Params), ctypes.c_void_p]
             for name, args in [("orc_fft", [dp, ctypes.c_int, ctypes.c_int]),
                                ("orc_dft", [dp, ctypes.c_int, ctypes.c_int]),
                                ("orc_fft3", [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -95,7 +97,7 @@ def num_threads():
     return lib().orc_num_threads()
 
 
-def make_params(shape, h, dt, mode, nu, g, gdd, cutoff=0.0):
+def make_params(shape, h, dt, mode, nu, g, gdd, cutoff=0.0, integration=0, kinetic=0):
     """shape = (nx, ny, nz); h = scalar or (hx, hy, hz); mode = REAL_TIME / IMAG_TIME;
     cutoff = spherical cutoff radius of the dipolar interaction (<= 0: none)."""
     hx, hy, hz = (h, h, h) if np.isscalar(h) else tuple(h)
@@ -107,6 +109,8 @@ def make_params(shape, h, dt, mode, nu, g, gdd, cutoff=0.0):
     p.nu[0], p.nu[1], p.nu[2] = (float(v) for v in nu)
     p.g, p.gdd = float(g), float(gdd)
     p.cutoff = float(cutoff)
+    p.integration = int(integration)
+    p.kinetic = int(kinetic)
     return p
 
 
@@ -213,3 +217,8 @@ def grad_z2(p, nu_z, steps_per_seg, psi0):
 
 def cutoff_factor(x):
     return lib().orc_cutoff_factor(float(x))
+
+
+def norm(p, psi):
+    psi = _c128(psi)
+    return lib().orc_norm(ctypes.byref(p), _ptr(psi))

@@ -295,12 +295,29 @@ void orc_cn_sweep(const orc_params *p, double complex *psi, int axis) {
   }
 }
 
-static double grid_norm(const orc_params *p, const double complex *psi) {
-  long ntot = (long)p->nx * p->ny * p->nz;
-  double s = 0;
-  for (long q = 0; q < ntot; ++q) s += creal(psi[q]) * creal(psi[q]) + cimag(psi[q]) * cimag(psi[q]);
-  return s * p->hx * p->hy * p->hz; /* rectangle rule [S13] */
+/* Quadrature weight of grid index i on an axis of n points (times h): 1 for the rectangle
+ * rule [S13]; composite Simpson (1, 4, 2, 4, ..., 4, 1)/3 on indices 0..n-2 (n - 2
+ * intervals, n even) and 0 on the last point, a wall. */
+static double quad_weight(const orc_params *p, int i, int n) {
+  if (p->integration == 0) return 1.0;
+  if (i > n - 2) return 0.0;
+  if (i == 0 || i == n - 2) return 1.0 / 3.0;
+  return (i % 2) ? 4.0 / 3.0 : 2.0 / 3.0;
 }
+
+static double grid_norm(const orc_params *p, const double complex *psi) {
+  double s = 0;
+  for (int i = 0; i < p->nx; ++i)
+    for (int j = 0; j < p->ny; ++j)
+      for (int k = 0; k < p->nz; ++k) {
+        long q = ((long)i * p->ny + j) * p->nz + k;
+        double w = quad_weight(p, i, p->nx) * quad_weight(p, j, p->ny) * quad_weight(p, k, p->nz);
+        s += w * (creal(psi[q]) * creal(psi[q]) + cimag(psi[q]) * cimag(psi[q]));
+      }
+  return s * p->hx * p->hy * p->hz;
+}
+
+double orc_norm(const orc_params *p, const double complex *psi) { return grid_norm(p, psi); }
 
 void orc_step(const orc_params *p, double complex *psi, int nsteps) {
   long ntot = (long)p->nx * p->ny * p->nz;
@@ -316,10 +333,13 @@ void orc_step(const orc_params *p, double complex *psi, int nsteps) {
   }
 }
 
-/* Discrete observables [S14] with the same 3-point Laplacian (zero outside the grid). */
+/* Discrete observables [S14] with the same 3-point Laplacian (zero outside the grid), or
+ * with the 5-point first derivative (f(i-2) - 8 f(i-1) + 8 f(i+1) - f(i+2)) / (12 h); sums
+ * weighted by the quadrature rule. */
 void orc_observables(const orc_params *p, const double complex *psi, orc_obs *o) {
   int nx = p->nx, ny = p->ny, nz = p->nz;
   long ntot = (long)nx * ny * nz;
+  long sx_ = (long)ny * nz, sy_ = nz;
   double dv = p->hx * p->hy * p->hz;
   double *n = malloc(sizeof(double) * ntot);
   double *phi = malloc(sizeof(double) * ntot);
@@ -330,21 +350,34 @@ void orc_observables(const orc_params *p, const double complex *psi, orc_obs *o)
     for (int j = 0; j < ny; ++j)
       for (int k = 0; k < nz; ++k) {
         long q = ((long)i * ny + j) * nz + k;
+        double w = quad_weight(p, i, nx) * quad_weight(p, j, ny) * quad_weight(p, k, nz);
         double complex c = psi[q];
-        double complex xm = i > 0 ? psi[q - (long)ny * nz] : 0, xp = i < nx - 1 ? psi[q + (long)ny * nz] : 0;
-        double complex ym = j > 0 ? psi[q - nz] : 0, yp = j < ny - 1 ? psi[q + nz] : 0;
-        double complex zm = k > 0 ? psi[q - 1] : 0, zp = k < nz - 1 ? psi[q + 1] : 0;
-        double complex lap = (xm - 2.0 * c + xp) / (p->hx * p->hx) + (ym - 2.0 * c + yp) / (p->hy * p->hy) +
-                             (zm - 2.0 * c + zp) / (p->hz * p->hz);
+#define AT(di, dj, dk)                                                                          \
+  ((i + (di) >= 0 && i + (di) < nx && j + (dj) >= 0 && j + (dj) < ny && k + (dk) >= 0 && k + (dk) < nz) \
+       ? psi[q + (di) * sx_ + (dj) * sy_ + (dk)]                                                \
+       : 0)
+        double ekin;
+        if (p->kinetic == 0) {
+          double complex lap = (AT(-1, 0, 0) - 2.0 * c + AT(1, 0, 0)) / (p->hx * p->hx) +
+                               (AT(0, -1, 0) - 2.0 * c + AT(0, 1, 0)) / (p->hy * p->hy) +
+                               (AT(0, 0, -1) - 2.0 * c + AT(0, 0, 1)) / (p->hz * p->hz);
+          ekin = 0.5 * creal(conj(c) * (-lap));
+        } else {
+          double complex gx = (AT(-2, 0, 0) - 8.0 * AT(-1, 0, 0) + 8.0 * AT(1, 0, 0) - AT(2, 0, 0)) / (12.0 * p->hx);
+          double complex gy = (AT(0, -2, 0) - 8.0 * AT(0, -1, 0) + 8.0 * AT(0, 1, 0) - AT(0, 2, 0)) / (12.0 * p->hy);
+          double complex gz = (AT(0, 0, -2) - 8.0 * AT(0, 0, -1) + 8.0 * AT(0, 0, 1) - AT(0, 0, 2)) / (12.0 * p->hz);
+          ekin = 0.5 * (creal(gx * conj(gx)) + creal(gy * conj(gy)) + creal(gz * conj(gz)));
+        }
+#undef AT
         double x = coord(i, nx, p->hx), y = coord(j, ny, p->hy), z = coord(k, nz, p->hz);
-        sn += n[q];
-        skin += 0.5 * creal(conj(c) * (-lap));
-        strap += trap(p, i, j, k) * n[q];
-        sint += p->g * n[q] * n[q];
-        sdd += p->gdd * phi[q] * n[q];
-        sx += x * x * n[q];
-        sy += y * y * n[q];
-        sz += z * z * n[q];
+        sn += w * n[q];
+        skin += w * ekin;
+        strap += w * trap(p, i, j, k) * n[q];
+        sint += w * p->g * n[q] * n[q];
+        sdd += w * p->gdd * phi[q] * n[q];
+        sx += w * x * x * n[q];
+        sy += w * y * y * n[q];
+        sz += w * z * z * n[q];
       }
   o->norm = dv * sn;
   o->e_kin = dv * skin;

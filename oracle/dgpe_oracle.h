@@ -42,6 +42,9 @@ typedef struct {
   double nu[3];        /* trap frequencies nu_x, nu_y, nu_z */
   double g, gdd;       /* contact and dipolar strengths */
   double cutoff;       /* spherical cutoff radius R of the dipolar interaction; <= 0: none */
+  int integration;     /* 0: rectangle rule [S13]; 1: composite Simpson on indices 0..N-2 */
+  int kinetic;         /* 0: E_kin = h^3 sum 1/2 Re conj(psi)(-lap psi), 3-point Laplacian [S14];
+                          1: E_kin = h^3 sum 1/2 |grad psi|^2, 5-point 4th-order gradient */
 } orc_params;
 
 typedef struct {
@@ -83,6 +86,8 @@ void orc_cn_sweep(const orc_params *p, double complex *psi, int axis);
 /* Full steps: potential, CN x, CN y, CN z, then renormalisation in imaginary time. */
 void orc_step(const orc_params *p, double complex *psi, int nsteps);
 void orc_observables(const orc_params *p, const double complex *psi, orc_obs *o);
+/* hx hy hz sum w |psi|^2 with the quadrature weights of p->integration. */
+double orc_norm(const orc_params *p, const double complex *psi);
 
 /* Discrete adjoint of one real-time step (paper's method differentiated by hand; the
  * paper itself has no adjoint).  Real-valued loss L, cotangent gbar = 2 dL/d conj(psi), so

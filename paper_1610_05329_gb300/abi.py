@@ -32,6 +32,10 @@ DGPE_SUB_POTENTIAL = 0
 DGPE_SUB_CN_X = 1
 DGPE_SUB_CN_Y = 2
 DGPE_SUB_CN_Z = 3
+DGPE_RECTANGLE = 0
+DGPE_SIMPSON = 1
+DGPE_KINETIC_LAPLACIAN3 = 0
+DGPE_KINETIC_GRADIENT5 = 1
 
 
 class dgpe_params(ctypes.Structure):
@@ -39,7 +43,8 @@ class dgpe_params(ctypes.Structure):
                 ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
                 ("dt", ctypes.c_double), ("mode", ctypes.c_int), ("precision", ctypes.c_int),
                 ("nu", ctypes.c_double * 3), ("g", ctypes.c_double), ("gdd", ctypes.c_double),
-                ("cutoff", ctypes.c_double), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+                ("cutoff", ctypes.c_double), ("integration", ctypes.c_int), ("kinetic", ctypes.c_int),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
 class dgpe_obs(ctypes.Structure):
@@ -152,7 +157,8 @@ def dgpe_last_cuda_error():
 
 
 def make_params(shape, h, dt, mode=DGPE_IMAG_TIME, precision=DGPE_FP64, nu=(1.0, 1.0, 1.0), g=0.0, gdd=0.0,
-                workspace=None, workspace_bytes=0, cutoff=0.0):
+                workspace=None, workspace_bytes=0, cutoff=0.0, integration=DGPE_RECTANGLE,
+                kinetic=DGPE_KINETIC_LAPLACIAN3):
     hx, hy, hz = (h, h, h) if np.isscalar(h) else tuple(h)
     p = dgpe_params()
     p.nx, p.ny, p.nz = (int(v) for v in shape)
@@ -163,6 +169,8 @@ def make_params(shape, h, dt, mode=DGPE_IMAG_TIME, precision=DGPE_FP64, nu=(1.0,
     p.nu[0], p.nu[1], p.nu[2] = (float(v) for v in nu)
     p.g, p.gdd = float(g), float(gdd)
     p.cutoff = float(cutoff)
+    p.integration = int(integration)
+    p.kinetic = int(kinetic)
     p.workspace = workspace
     p.workspace_bytes = int(workspace_bytes)
     return p
@@ -308,7 +316,8 @@ class Condensate:
     """
 
     def __init__(self, shape, h, dt, mode=DGPE_IMAG_TIME, precision=DGPE_FP64, nu=(1.0, 1.0, 1.0),
-                 g=0.0, gdd=0.0, device=None, cutoff=0.0):
+                 g=0.0, gdd=0.0, device=None, cutoff=0.0, integration=DGPE_RECTANGLE,
+                 kinetic=DGPE_KINETIC_LAPLACIAN3):
         import torch
         self._torch = torch
         self.shape = tuple(int(v) for v in shape)
@@ -317,7 +326,8 @@ class Condensate:
         self.cdtype = torch.complex128 if precision == DGPE_FP64 else torch.complex64
         self.rdtype = torch.float64 if precision == DGPE_FP64 else torch.float32
         self.np_cdtype = np.complex128 if precision == DGPE_FP64 else np.complex64
-        self._params = make_params(shape, h, dt, mode, precision, nu, g, gdd, cutoff=cutoff)
+        self._params = make_params(shape, h, dt, mode, precision, nu, g, gdd, cutoff=cutoff,
+                                   integration=integration, kinetic=kinetic)
         nbytes = dgpe_workspace_bytes(self._params)
         self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self._params.workspace = self._ws.data_ptr()
@@ -353,8 +363,8 @@ class Condensate:
                 p.nu[0], p.nu[1], p.nu[2] = (float(x) for x in v)
             elif k in ("dt", "g", "gdd", "cutoff"):
                 setattr(p, k, float(v))
-            elif k == "mode":
-                p.mode = int(v)
+            elif k in ("mode", "integration", "kinetic"):
+                setattr(p, k, int(v))
             else:
                 raise KeyError(k)
         dgpe_set_params(self.ctx, p)

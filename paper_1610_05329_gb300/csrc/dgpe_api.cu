@@ -109,6 +109,8 @@ int check_physics(const dgpe_params *p) {
   for (int d = 0; d < 3; ++d)
     if (!finite(p->nu[d])) return DGPE_EINVAL;
   if (!finite(p->g) || !finite(p->gdd) || !finite(p->cutoff)) return DGPE_EINVAL;
+  if (p->integration != DGPE_RECTANGLE && p->integration != DGPE_SIMPSON) return DGPE_EINVAL;
+  if (p->kinetic != DGPE_KINETIC_LAPLACIAN3 && p->kinetic != DGPE_KINETIC_GRADIENT5) return DGPE_EINVAL;
   return DGPE_OK;
 }
 
@@ -172,6 +174,8 @@ void set_physics(KArgs &a, const dgpe_params *p) {
   a.hz = p->hz;
   a.dt = p->dt;
   a.cutoff = p->cutoff;
+  a.simpson = p->integration == DGPE_SIMPSON;
+  a.kinetic5 = p->kinetic == DGPE_KINETIC_GRADIENT5;
   a.g = p->g;
   a.gdd = p->gdd;
   a.vx = 0.5 * p->nu[0] * p->nu[0];
@@ -607,7 +611,8 @@ int dgpe_set_params(dgpe_ctx *c, const dgpe_params *p) {
   if (rc) return rc;
   const bool cn_changed = p->dt != c->p.dt || p->hx != c->p.hx || p->hy != c->p.hy || p->hz != c->p.hz ||
                           p->mode != c->p.mode;
-  const bool step_args_changed = cn_changed || p->g != c->p.g || p->gdd != c->p.gdd || p->cutoff != c->p.cutoff;
+  const bool step_args_changed = cn_changed || p->g != c->p.g || p->gdd != c->p.gdd || p->cutoff != c->p.cutoff ||
+                                 p->integration != c->p.integration;
   void *ws = c->p.workspace;
   const size_t wsb = c->p.workspace_bytes;
   c->p = *p;

@@ -592,6 +592,15 @@ __device__ bool reduce_across_blocks(double (&v)[NV], double *partials, unsigned
 
 __device__ __forceinline__ double coordinate(int i, int n, double h) { return (double)(i - n / 2) * h; }
 
+// Quadrature weight (times h) of index i on an axis of n points: 1 (rectangle rule), or
+// composite Simpson (1, 4, 2, ..., 4, 1)/3 on indices 0..n-2 and 0 on the last point (a wall).
+__device__ __forceinline__ double quad_weight(int i, int n, int simpson) {
+  if (!simpson) return 1.0;
+  if (i > n - 2) return 0.0;
+  if (i == 0 || i == n - 2) return 1.0 / 3.0;
+  return (i & 1) ? 4.0 / 3.0 : 2.0 / 3.0;
+}
+
 // ---------------------------------------------------------------------------------------
 // Set-up kernels
 // ---------------------------------------------------------------------------------------
@@ -950,6 +959,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
     double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const R sr = R(s);
     const double x = coordinate(i, a.nx, a.hx);
+    const double wxi = quad_weight(i, a.nx, a.simpson);
     const R ihx2 = R(1.0 / (a.hx * a.hx)), ihy2 = R(1.0 / (a.hy * a.hy)), ihz2 = R(1.0 / (a.hz * a.hz));
     const C *gpsi = reinterpret_cast<const C *>(a.psi);
     const size_t sx = (size_t)a.ny * nz;
@@ -966,22 +976,42 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
       const C yp = j < a.ny - 1 ? scale(gpsi[q + nz], sr) : czero<R>();
       const C xm = i > 0 ? scale(gpsi[q - sx], sr) : czero<R>();
       const C xp = i < a.nx - 1 ? scale(gpsi[q + sx], sr) : czero<R>();
-      const C lap = {(xm.re - R(2) * c.re + xp.re) * ihx2 + (ym.re - R(2) * c.re + yp.re) * ihy2 +
-                         (zm.re - R(2) * c.re + zp.re) * ihz2,
-                     (xm.im - R(2) * c.im + xp.im) * ihx2 + (ym.im - R(2) * c.im + yp.im) * ihy2 +
-                         (zm.im - R(2) * c.im + zp.im) * ihz2};
+      double ekin;
+      if (!a.kinetic5) {
+        const C lap = {(xm.re - R(2) * c.re + xp.re) * ihx2 + (ym.re - R(2) * c.re + yp.re) * ihy2 +
+                           (zm.re - R(2) * c.re + zp.re) * ihz2,
+                       (xm.im - R(2) * c.im + xp.im) * ihx2 + (ym.im - R(2) * c.im + yp.im) * ihy2 +
+                           (zm.im - R(2) * c.im + zp.im) * ihz2};
+        ekin = -0.5 * ((double)c.re * lap.re + (double)c.im * lap.im);
+      } else {
+        // 4th-order first derivatives (f(-2) - 8 f(-1) + 8 f(1) - f(2)) / (12 h), zero outside
+        const C zm2 = n > 1 ? scale(row[cn_slot(n - 2, lc)], sr) : czero<R>();
+        const C zp2 = n < nz - 2 ? scale(row[cn_slot(n + 2, lc)], sr) : czero<R>();
+        const C ym2 = j > 1 ? scale(gpsi[q - 2 * nz], sr) : czero<R>();
+        const C yp2 = j < a.ny - 2 ? scale(gpsi[q + 2 * nz], sr) : czero<R>();
+        const C xm2 = i > 1 ? scale(gpsi[q - 2 * sx], sr) : czero<R>();
+        const C xp2 = i < a.nx - 2 ? scale(gpsi[q + 2 * sx], sr) : czero<R>();
+        auto d1 = [](C m2, C m1, C p1, C p2, double h) {
+          const double f = 1.0 / (12.0 * h);
+          const double re = ((double)m2.re - 8.0 * m1.re + 8.0 * p1.re - p2.re) * f;
+          const double im = ((double)m2.im - 8.0 * m1.im + 8.0 * p1.im - p2.im) * f;
+          return re * re + im * im;
+        };
+        ekin = 0.5 * (d1(xm2, xm, xp, xp2, a.hx) + d1(ym2, ym, yp, yp2, a.hy) + d1(zm2, zm, zp, zp2, a.hz));
+      }
       const C z = res[n * SB + (b >> 1)];
       const double phi = (double)(((b & 1) ? z.im : z.re) * inv_ntot);
       const double dens = (double)c.re * c.re + (double)c.im * c.im;
       const double y = coordinate(j, a.ny, a.hy), zc = coordinate(n, nz, a.hz);
-      v[0] += dens;
-      v[1] += -0.5 * ((double)c.re * lap.re + (double)c.im * lap.im);
-      v[2] += (a.vx * x * x + a.vy * y * y + a.vz * zc * zc) * dens;
-      v[3] += a.g * dens * dens;
-      v[4] += a.gdd * phi * dens;
-      v[5] += x * x * dens;
-      v[6] += y * y * dens;
-      v[7] += zc * zc * dens;
+      const double w = wxi * quad_weight(j, a.ny, a.simpson) * quad_weight(n, nz, a.simpson);
+      v[0] += w * dens;
+      v[1] += w * ekin;
+      v[2] += w * (a.vx * x * x + a.vy * y * y + a.vz * zc * zc) * dens;
+      v[3] += w * a.g * dens * dens;
+      v[4] += w * a.gdd * phi * dens;
+      v[5] += w * x * x * dens;
+      v[6] += w * y * y * dens;
+      v[7] += w * zc * zc * dens;
     }
     if (reduce_across_blocks<8>(v, a.partials, &a.state->ticket) && threadIdx.x == 0) {
       const double dv = a.hx * a.hy * a.hz;
@@ -1106,6 +1136,7 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
   Coef *stab = reinterpret_cast<Coef *>(nxt + slots * SB);     // factor tables, staged once
   const int ntab = 5 * (kWarp << lc);
   R *x2tab = reinterpret_cast<R *>(stab + ntab);
+  R *wxtab = x2tab + N;                                         // quadrature weights along x
   const size_t stride = AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
   C *gpsi = reinterpret_cast<C *>(a.psi);
   const int b = threadIdx.x % B;   // B divides the block size: the column is fixed per thread
@@ -1131,6 +1162,7 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
       const double x = coordinate(n, a.nx, a.hx);
       x2tab[n] = R(x * x);
+      wxtab[n] = R(quad_weight(n, a.nx, a.simpson));
     }
   const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[AXIS], a.cn_rf[AXIS]));
   {
@@ -1164,13 +1196,18 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
       for (int n = n0; n < N; n += nstep, dst += nstep * stride) {
         const C w = cur[cn_slot(n, lc) * SB + b];
         *dst = w;
-        if (do_reduce) rs.add(w.re * w.re + w.im * w.im, x2tab[n]);
+        if (do_reduce) {
+          R d = w.re * w.re + w.im * w.im;
+          if (a.simpson) d *= wxtab[n];
+          rs.add(d, x2tab[n]);
+        }
       }
       if (do_reduce) {
-        const double t = rs.total();
+        const double wyz = quad_weight(fixed, a.ny, a.simpson) * quad_weight(k0 + b, a.nz, a.simpson);
+        const double t = wyz * rs.total();
         const double z = coordinate(k0 + b, a.nz, a.hz), y = coordinate(fixed, a.ny, a.hy);
         v[0] += t;
-        v[1] += rs.xmoment();
+        v[1] += wyz * rs.xmoment();
         v[2] += y * y * t;
         v[3] += z * z * t;
       }
@@ -1434,7 +1471,7 @@ struct Impl {
   static size_t smem_x(const KArgs &a) { return 2 * (size_t)a.nx * T::kXCols * E; }
   static size_t smem_cn(int n, int lchunk) {
     return 2 * (size_t)cn_slots(n, lchunk) * (T::kCnCols + 1) * E + (size_t)5 * (kWarp << lchunk) * E +
-           (size_t)n * sizeof(R);
+           2 * (size_t)n * sizeof(R);
   }
 
   static dim3 grid_z(const KArgs &a) { return dim3((a.ny + T::kZLines - 1) / T::kZLines, a.nx); }

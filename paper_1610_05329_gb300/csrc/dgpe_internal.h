@@ -47,6 +47,8 @@ struct KArgs {
   double hx, hy, hz;
   double dt, g, gdd;
   double cutoff;               // spherical cutoff radius of the dipolar kernel (<= 0: none)
+  int simpson;                 // 1: composite Simpson weights in the norm and observables
+  int kinetic5;                // 1: kinetic energy from the 5-point gradient
   double vx, vy, vz;           // 0.5 * nu_d^2
   double inv_ntot;             // 1 / (nx ny nz)
   int imag;                    // 1 = imaginary time

@@ -246,3 +246,26 @@ def test_spherical_cutoff(orc, precision, tol):
     want = orc.step(p, psi.astype(cdt).astype(np.complex128), 8)
     assert rel(gpu.get_psi().astype(np.complex128), want) < tol
     gpu.close()
+
+
+@pytest.mark.parametrize("integration,kinetic", [(1, 0), (0, 1), (1, 1)])
+def test_simpson_and_gradient_observables(orc, integration, kinetic):
+    """The quadrature/derivative options: imaginary-time steps renormalised with Simpson
+    weights, and the observables with Simpson weights and/or the 5-point gradient."""
+    shape, h = (24, 18, 36), 0.35
+    psi = state(shape, h)
+    gpu = abi.Condensate(shape, h, 0.005, mode=abi.DGPE_IMAG_TIME, nu=(1.0, 1.1, 0.9), g=25.0, gdd=15.0,
+                         integration=integration, kinetic=kinetic)
+    p = orc.make_params(shape, h, 0.005, orc.IMAG_TIME, (1.0, 1.1, 0.9), 25.0, 15.0, integration=integration,
+                        kinetic=kinetic)
+    gpu.set_psi(psi)
+    gpu.step(10)
+    got, want = gpu.get_psi(), orc.step(p, psi, 10)
+    assert rel(got, want) < FP64_STEP_TOL
+    og, ow = gpu.observables(), orc.observables(p, want)
+    for k in ("norm", "mu", "energy", "e_kin"):
+        assert og[k] == pytest.approx(ow[k], rel=1e-11), k
+    for d in range(3):
+        assert og["rms"][d] == pytest.approx(ow["rms"][d], rel=1e-11)
+    assert og["norm"] == pytest.approx(1.0, abs=1e-12)
+    gpu.close()
