@@ -70,6 +70,12 @@ FftPlan make_plan(int n, int style = 0) {
     m /= 7;
   }
   p.nstages = k;
+  int off = 0, ns = 1;
+  for (int s = 0; s < k; ++s) {
+    p.twoff[s] = off;
+    off += ns * (p.radix[s] - 1);
+    ns *= p.radix[s];
+  }
   return p;
 }
 
@@ -481,17 +487,22 @@ int drain_kernel_times(dgpe_ctx *c, double *ms) {
   return rc;
 }
 
-void apply_tuning(dgpe_ctx *c, const dgpe_tuning &t) {
+int apply_tuning(dgpe_ctx *c, const dgpe_tuning &t) {
   const int n[3] = {c->p.nx, c->p.ny, c->p.nz};
+  int rc = DGPE_OK;
   for (int d = 0; d < 3; ++d) {
+    const bool changed = c->plan_style[d] != t.plan_style[d];
     c->plan_style[d] = t.plan_style[d];
     c->args.plan[d] = make_plan(n[d], t.plan_style[d]);
+    // the twiddle tables are laid out per stage of the plan
+    if (changed && !rc) rc = map_cuda(c->ks->twiddles(const_cast<void *>(c->args.tw[d]), c->args.plan[d], c->stream));
   }
   c->args.ylines = t.ylines;
   c->args.fft_threads = t.fft_threads;
   c->args.cn_per_sm = t.cn_per_sm;
   c->graph_valid = false;
   ++c->generation;
+  return rc;
 }
 
 bool tuning_valid(const dgpe_ctx *c, const dgpe_tuning &t) {
@@ -593,7 +604,8 @@ int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out) {
   const int n[3] = {p->nx, p->ny, p->nz};
   rc = map_cuda(cudaMemsetAsync(a.psi, 0, (size_t)p->nx * p->ny * p->nz * c->ks->elem_bytes, c->stream));
   if (!rc) rc = map_cuda(c->ks->reset_state(a.state, c->stream));
-  for (int d = 0; d < 3 && !rc; ++d) rc = map_cuda(c->ks->twiddles(const_cast<void *>(a.tw[d]), n[d], c->stream));
+  for (int d = 0; d < 3 && !rc; ++d) rc = map_cuda(c->ks->twiddles(const_cast<void *>(a.tw[d]), a.plan[d], c->stream));
+  (void)n;
   if (!rc) rc = setup_tables(c, true);
   if (rc) {
     dgpe_destroy(c);
@@ -832,8 +844,7 @@ int dgpe_grad_z2(dgpe_ctx *c, int nseg, int steps_per_seg, const double *nu_z, v
 
 int dgpe_set_tuning(dgpe_ctx *c, const dgpe_tuning *t) {
   if (!c || !t || !tuning_valid(c, *t)) return DGPE_EINVAL;
-  apply_tuning(c, *t);
-  return DGPE_OK;
+  return apply_tuning(c, *t);
 }
 
 int dgpe_autotune(dgpe_ctx *c, dgpe_tuning *out) {
@@ -870,8 +881,8 @@ int dgpe_autotune(dgpe_ctx *c, dgpe_tuning *out) {
       t.cn_per_sm = 1 + ci;
     }
     if (!tuning_valid(c, t)) continue;
-    apply_tuning(c, t);
-    rc = enqueue_step(c, c->stream);   // warm-up step of this configuration
+    rc = apply_tuning(c, t);
+    if (!rc) rc = enqueue_step(c, c->stream);   // warm-up step of this configuration
     double ms[kNumKernels];
     if (!rc) rc = drain_kernel_times(c, ms);
     for (int s = 0; s < steps && rc == DGPE_OK; ++s) rc = enqueue_step(c, c->stream);
@@ -914,7 +925,7 @@ int dgpe_autotune(dgpe_ctx *c, dgpe_tuning *out) {
       }
     best.cn_per_sm = t_cn[1] < t_cn[0] ? 2 : 1;
     if (!tuning_valid(c, best)) best = base;
-    apply_tuning(c, best);
+    rc = apply_tuning(c, best);
     for (int s = 0; s < 1 + steps && rc == DGPE_OK; ++s) {
       rc = enqueue_step(c, c->stream);
       if (s == 0 && !rc) {

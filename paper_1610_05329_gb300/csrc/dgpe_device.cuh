@@ -356,7 +356,6 @@ __device__ __forceinline__ void fft_stage(const cplx<R> *__restrict__ src, cplx<
   const int line = threadIdx.x % lw;
   if (line >= nlines) return;
   const int jstep = blockDim.x / lw;
-  const int twstep = n / (ns * P);
   const bool pow2 = (ns & (ns - 1)) == 0;
   // strides (in elements) between the P inputs and between the P outputs of a butterfly
   const int in_stride = nbf * sb, out_stride = ns * sb;
@@ -369,11 +368,10 @@ __device__ __forceinline__ void fft_stage(const cplx<R> *__restrict__ src, cplx<
 #pragma unroll
     for (int r = 0; r < P; ++r) v[r] = in[r * in_stride];
     if (ns > 1) {
-      const cplx<R> *w = tw + k * twstep;
-      const int wstep = k * twstep;
+      const cplx<R> *w = tw + k * (P - 1);   // this stage's table: the P-1 twiddles of k
 #pragma unroll
       for (int r = 1; r < P; ++r) {
-        const cplx<R> t = ldg(w + (r - 1) * wstep);
+        const cplx<R> t = ldg(w + r - 1);
         v[r] = DIR < 0 ? v[r] * t : mul_conj(v[r], t);
       }
     }
@@ -392,12 +390,13 @@ __device__ cplx<R> *fft_lines(cplx<R> *a, cplx<R> *b, const FftPlan &pl, int lw,
   int ns = 1;
   for (int st = 0; st < pl.nstages; ++st) {
     const int p = pl.radix[st];
-    if (p == 8) fft_stage<R, DIR, 8>(a, b, pl.n, ns, lw, nlines, sb, tw);
-    else if (p == 4) fft_stage<R, DIR, 4>(a, b, pl.n, ns, lw, nlines, sb, tw);
-    else if (p == 3) fft_stage<R, DIR, 3>(a, b, pl.n, ns, lw, nlines, sb, tw);
-    else if (p == 5) fft_stage<R, DIR, 5>(a, b, pl.n, ns, lw, nlines, sb, tw);
-    else if (p == 7) fft_stage<R, DIR, 7>(a, b, pl.n, ns, lw, nlines, sb, tw);
-    else fft_stage<R, DIR, 2>(a, b, pl.n, ns, lw, nlines, sb, tw);
+    const cplx<R> *tws = tw + pl.twoff[st];
+    if (p == 8) fft_stage<R, DIR, 8>(a, b, pl.n, ns, lw, nlines, sb, tws);
+    else if (p == 4) fft_stage<R, DIR, 4>(a, b, pl.n, ns, lw, nlines, sb, tws);
+    else if (p == 3) fft_stage<R, DIR, 3>(a, b, pl.n, ns, lw, nlines, sb, tws);
+    else if (p == 5) fft_stage<R, DIR, 5>(a, b, pl.n, ns, lw, nlines, sb, tws);
+    else if (p == 7) fft_stage<R, DIR, 7>(a, b, pl.n, ns, lw, nlines, sb, tws);
+    else fft_stage<R, DIR, 2>(a, b, pl.n, ns, lw, nlines, sb, tws);
     __syncthreads();
     cplx<R> *t = a;
     a = b;
@@ -604,14 +603,23 @@ __device__ __forceinline__ double quad_weight(int i, int n, int simpson) {
 // ---------------------------------------------------------------------------------------
 // Set-up kernels
 // ---------------------------------------------------------------------------------------
+// Per-stage twiddle tables of a plan (layout in FftPlan): entry twoff[s] + k (P-1) + r - 1
+// = e^{-2 pi i r k / (ns P)}.
 template <typename R>
-__global__ void k_twiddles(cplx<R> *tw, int n) {
+__global__ void k_twiddles(cplx<R> *tw, FftPlan pl) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) {
-    double s, c;
-    sincospi(2.0 * (double)t / (double)n, &s, &c);
-    tw[t] = {R(c), R(-s)};
+  if (t >= pl.n - 1) return;
+  int st = 0, ns = 1;
+  while (st + 1 < pl.nstages && t >= pl.twoff[st + 1]) {
+    ns *= pl.radix[st];
+    ++st;
   }
+  const int p = pl.radix[st];
+  const int q = t - pl.twoff[st];
+  const int k = q / (p - 1), r = q - k * (p - 1) + 1;
+  double s, c;
+  sincospi(2.0 * (double)(r * k) / (double)(ns * p), &s, &c);
+  tw[t] = {R(c), R(-s)};
 }
 
 // LU factors of tridiag(-c, 1 + 2c, -c) (order m) and the chunk response tables P, H, G
@@ -1529,8 +1537,8 @@ struct Impl {
     return e;
   }
 
-  static cudaError_t twiddles(void *tw, int n, cudaStream_t st) {
-    k_twiddles<R><<<(n + 127) / 128, 128, 0, st>>>(reinterpret_cast<C *>(tw), n);
+  static cudaError_t twiddles(void *tw, const FftPlan &pl, cudaStream_t st) {
+    k_twiddles<R><<<(pl.n + 127) / 128, 128, 0, st>>>(reinterpret_cast<C *>(tw), pl);
     return cudaGetLastError();
   }
 

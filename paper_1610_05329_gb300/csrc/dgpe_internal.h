@@ -11,10 +11,14 @@ constexpr int kWarp = 32;
 constexpr int kCnMaxChunk = 16;   // interior points per lane of the chunked Thomas solve
 
 // Mixed-radix plan of one transform length: n = radix[0] * radix[1] * ...
+// Twiddles are stored per stage: stage s (radix P, ns = product of the earlier radices)
+// keeps e^{-2 pi i r k / (ns P)} for k < ns, r = 1..P-1 at twoff[s] + k (P - 1) + r - 1;
+// the stages together hold n - 1 entries.
 struct FftPlan {
   int n;
   int nstages;
   int radix[kMaxStages];
+  int twoff[kMaxStages];
 };
 
 // Crank-Nicolson factor tables of one direction (interior size m = n - 2, chunk length c):
@@ -105,7 +109,7 @@ enum KernelId : int {
 struct KernelSet {
   int elem_bytes;  // sizeof complex element
   cudaError_t (*init)();
-  cudaError_t (*twiddles)(void *tw, int n, cudaStream_t st);
+  cudaError_t (*twiddles)(void *tw, const FftPlan &pl, cudaStream_t st);
   cudaError_t (*cn_tables)(void *tab, int m, int chunk, double r, int imag, cudaStream_t st);
   cudaError_t (*axis_potential)(void *out, int n, double h, double v, double dt, cudaStream_t st);
   cudaError_t (*reset_state)(DevState *st_ptr, cudaStream_t st);
