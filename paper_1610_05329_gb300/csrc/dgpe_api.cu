@@ -121,7 +121,7 @@ int check_physics(const dgpe_params *p) {
 }
 
 struct Layout {
-  size_t state, partials, tw[3], cn[3], cn_adj[3], dtv[3], psi, spec, total;
+  size_t state, partials, tw[3], cn[3], cn_adj[3], dtv[3], ksq[3], psi, spec, total;
 };
 
 Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
@@ -145,6 +145,8 @@ Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
   }
   for (int d = 0; d < 3; ++d) {
     L.dtv[d] = off;
+    off += align_up((size_t)n[d] * (e / 2));
+    L.ksq[d] = off;
     off += align_up((size_t)n[d] * (e / 2));
   }
   L.psi = off;
@@ -369,6 +371,7 @@ int setup_tables(dgpe_ctx *c, bool cn_changed) {
   const double v[3] = {c->args.vx, c->args.vy, c->args.vz};
   for (int d = 0; d < 3; ++d) {
     int rc = map_cuda(c->ks->axis_potential(at(c, c->L.dtv[d]), n[d], h[d], v[d], p->dt, c->stream));
+    if (!rc) rc = map_cuda(c->ks->axis_ksq(at(c, c->L.ksq[d]), n[d], h[d], c->stream));
     if (rc) return rc;
     if (!cn_changed) continue;
     rc = map_cuda(c->ks->cn_tables(at(c, c->L.cn[d]), c->args.cn[d].m, c->args.cn[d].chunk, c->args.cn_r[d],
@@ -600,6 +603,7 @@ int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out) {
     a.tw[d] = at(c, c->L.tw[d]);
     a.cn[d].tab = at(c, c->L.cn[d]);
     a.dtv[d] = at(c, c->L.dtv[d]);
+    a.ksq[d] = at(c, c->L.ksq[d]);
   }
   const int n[3] = {p->nx, p->ny, p->nz};
   rc = map_cuda(cudaMemsetAsync(a.psi, 0, (size_t)p->nx * p->ny * p->nz * c->ks->elem_bytes, c->stream));

@@ -112,7 +112,38 @@ __device__ __forceinline__ void sin_cos(double x, double *s, double *c) {
     default: *s = -cr; *c = sr; break;
   }
 }
-__device__ __forceinline__ void sin_cos(float x, float *s, float *c) { sincosf(x, s, c); }
+// FP32 sine and cosine by the same method: r = x - k pi/2 with k = rint(2x/pi) taken from
+// the low bits of the FP32 sum 2x/pi + 1.5 * 2^23 (no conversion instruction), pi/2 split
+// into three floats and subtracted by FMAs; Taylor series through r^9 (sine) and r^10
+// (cosine) on |r| <= pi/4, first omitted terms below 2e-9.  |x| >= 2^16 and non-finite x
+// go to the general routine.
+__device__ __forceinline__ void sin_cos(float x, float *s, float *c) {
+  if (!(fabsf(x) < 65536.0f)) {
+    sincosf(x, s, c);
+    return;
+  }
+  const float kb = fmaf(x, 0.63661974668502808f, 12582912.0f);
+  const int q = __float_as_int(kb) & 3;
+  const float k = kb - 12582912.0f;
+  float r = fmaf(-k, 1.5707963705062866f, x);
+  r = fmaf(-k, -4.371138828673793e-08f, r);
+  r = fmaf(-k, -1.7151245100058819e-15f, r);
+  const float u = r * r;
+  float ps = 2.7557319223985893e-06f;
+  ps = fmaf(ps, u, -0.0001984126984126984f);
+  ps = fmaf(ps, u, 0.008333333333333333f);
+  ps = fmaf(ps, u, -0.16666666666666666f);
+  const float sr = fmaf(r * u, ps, r);
+  float pc = -2.755731922398589e-07f;
+  pc = fmaf(pc, u, 2.48015873015873e-05f);
+  pc = fmaf(pc, u, -0.001388888888888889f);
+  pc = fmaf(pc, u, 0.041666666666666664f);
+  pc = fmaf(pc, u, -0.5f);
+  const float cr = fmaf(u, pc, 1.0f);
+  const float ss = (q & 1) ? cr : sr, cc = (q & 1) ? sr : cr;
+  *s = (q & 2) ? -ss : ss;
+  *c = ((q + 1) & 2) ? -cc : cc;
+}
 __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 __device__ __forceinline__ float exp_r(float x) { return expf(x); }
 
@@ -600,6 +631,14 @@ __device__ __forceinline__ double quad_weight(int i, int n, int simpson) {
   return (i & 1) ? 4.0 / 3.0 : 2.0 / 3.0;
 }
 
+template <typename R>
+__device__ __forceinline__ R quad_weight_r(int i, int n, int simpson) {
+  if (!simpson) return R(1);
+  if (i > n - 2) return R(0);
+  if (i == 0 || i == n - 2) return R(1.0 / 3.0);
+  return (i & 1) ? R(4.0 / 3.0) : R(2.0 / 3.0);
+}
+
 // ---------------------------------------------------------------------------------------
 // Set-up kernels
 // ---------------------------------------------------------------------------------------
@@ -697,6 +736,17 @@ __global__ void k_axis_potential(R *out, int n, double h, double v, double dt) {
   if (i < n) {
     const double x = (double)(i - n / 2) * h;
     out[i] = R(dt * v * x * x);
+  }
+}
+
+// k_m^2 on one axis, k_m = 2 pi m / (n h) with m signed (m <= n/2: m, else m - n).
+template <typename R>
+__global__ void k_axis_ksq(R *out, int n, double h) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const int m = i <= n / 2 ? i : i - n;
+    const double k = 6.283185307179586476925286766559 * (double)m / ((double)n * h);
+    out[i] = R(k * k);
   }
 }
 
@@ -825,27 +875,13 @@ __device__ __forceinline__ R cutoff_factor(R x) {
   return p * u;
 }
 
+// Ut(k) = 3 kz^2 / |k|^2 - 1 (Ut(0) = 0) from the per-axis k^2 tables, times the cutoff
+// factor when a cutoff is set.
 template <typename R>
-__device__ __forceinline__ R dipolar_kernel(int ix, int iy, int iz, const KArgs &a) {
-  const double two_pi = 6.283185307179586476925286766559;
-  const int mx = ix <= a.nx / 2 ? ix : ix - a.nx;
-  const int my = iy <= a.ny / 2 ? iy : iy - a.ny;
-  R u, k2r;
-  if constexpr (sizeof(R) == 8) {
-    const double kx = two_pi * (double)mx / ((double)a.nx * a.hx);
-    const double ky = two_pi * (double)my / ((double)a.ny * a.hy);
-    const double kz = two_pi * (double)iz / ((double)a.nz * a.hz);
-    k2r = kx * kx + ky * ky + kz * kz;
-    u = k2r > 0.0 ? 3.0 * kz * kz / k2r - 1.0 : 0.0;
-  } else {
-    const float tp = 6.283185307f;
-    const float kx = tp * (float)mx / ((float)a.nx * (float)a.hx);
-    const float ky = tp * (float)my / ((float)a.ny * (float)a.hy);
-    const float kz = tp * (float)iz / ((float)a.nz * (float)a.hz);
-    k2r = kx * kx + ky * ky + kz * kz;
-    u = k2r > 0.0f ? 3.0f * kz * kz / k2r - 1.0f : 0.0f;
-  }
-  if (a.cutoff > 0.0 && k2r > R(0)) u *= cutoff_factor<R>(sqrt(k2r) * R(a.cutoff));
+__device__ __forceinline__ R dipolar_kernel(R kx2, R ky2, R kz2, const KArgs &a) {
+  const R k2 = kx2 + ky2 + kz2;
+  R u = k2 > R(0) ? R(3) * kz2 / k2 - R(1) : R(0);
+  if (a.cutoff > 0.0 && k2 > R(0)) u *= cutoff_factor<R>(sqrt(k2) * R(a.cutoff));
   return u;
 }
 
@@ -868,9 +904,15 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
   __syncthreads();
   const C *tw = reinterpret_cast<const C *>(a.tw[0]);
   C *res = fft_lines<R, -1>(za, zb, a.plan[0], BX, nb, SB, tw);
-  for (int e = threadIdx.x; e < n * BX; e += blockDim.x) {
-    const int b = e % BX, k = e / BX;
-    if (b < nb) res[k * SB + b] = scale(res[k * SB + b], dipolar_kernel<R>(k, j0 + b, m, a));
+  {
+    const R *kx2 = reinterpret_cast<const R *>(a.ksq[0]);
+    const R kz2 = reinterpret_cast<const R *>(a.ksq[2])[m];
+    const int b = threadIdx.x % BX;
+    if (b < nb) {
+      const R kyz2 = reinterpret_cast<const R *>(a.ksq[1])[j0 + b];
+      for (int k = threadIdx.x / BX; k < n; k += blockDim.x / BX)
+        res[k * SB + b] = scale(res[k * SB + b], dipolar_kernel<R>(ldg(kx2 + k), kyz2, kz2, a));
+    }
   }
   __syncthreads();
   C *other = (res == za) ? zb : za;
@@ -1097,32 +1139,23 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
 // ---------------------------------------------------------------------------------------
 // K6 / K7: Crank-Nicolson along y (AXIS = 1, lines psi[i][:][k]) or x (AXIS = 0, lines
 // psi[:][j][k]) for kCnCols consecutive k per CTA (one warp per line).  K7 (x) also sums
-// n, x^2 n, y^2 n, z^2 n (FP64 totals; per-thread partial sums in FP64 for FP64 data and
-// in double-float for FP32 data) and, in the last block, sets the norm and the pending
+// n, x^2 n, y^2 n, z^2 n (FP64 totals; per-thread sums in FP64 for FP64 data; for FP32
+// data, FP32 sums over the points of one tile column, accumulated across tiles in
+// double-float) and, in the last block, sets the norm and the pending
 // renormalisation factor s = 1/sqrt(norm) (imaginary time) or 1 (real time).
 // ---------------------------------------------------------------------------------------
+// Running sums of the reduction: FP64 for FP64 data; for FP32 data, double-float (FP32
+// instructions only), fed once per tile column with that column's FP32 partial sums.
 template <typename R>
-struct RowSums;
+struct SumAcc;
 template <>
-struct RowSums<double> {
-  double s0 = 0.0, sx = 0.0;
-  __device__ __forceinline__ void add(double d, double x2) {
-    s0 += d;
-    sx = fma(x2, d, sx);
-  }
-  __device__ __forceinline__ double total() const { return s0; }
-  __device__ __forceinline__ double xmoment() const { return sx; }
+struct SumAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double t) { v += t; }
+  __device__ __forceinline__ double value() const { return v; }
 };
 template <>
-struct RowSums<float> {
-  DFAcc s0, sx;
-  __device__ __forceinline__ void add(float d, float x2) {
-    s0.add(d);
-    sx.add(__fmul_rn(x2, d));
-  }
-  __device__ __forceinline__ double total() const { return s0.value(); }
-  __device__ __forceinline__ double xmoment() const { return sx.value(); }
-};
+struct SumAcc<float> : DFAcc {};
 
 // Persistent, double-buffered: each CTA walks the tiles (fixed index, k-tile)
 // blockIdx.x, blockIdx.x + gridDim.x, ...; the cp.async copies of the next tile are in
@@ -1178,7 +1211,8 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
     for (int q = threadIdx.x; q < ntab; q += blockDim.x) stab[q] = gtab[q];
   }
   const Coef *tab = stab;
-  double v[4] = {0, 0, 0, 0};
+  SumAcc<R> acc[4];
+  const R hy = R(a.hy), hz = R(a.hz);
 
   int tile = blockIdx.x;
   if (tile < ntiles) issue(tile, cur);
@@ -1198,7 +1232,7 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
       cn_line_any<R, Coef, true>(cur + l, SB, a.cn[AXIS].m, lc, tab, c);
     __syncthreads();
     if (b < nb) {
-      RowSums<R> rs;
+      R s0 = R(0), sx = R(0);   // this column's partial sums of n and x^2 n
       C *dst = gpsi + base + b + (size_t)n0 * stride;
 #pragma unroll 4
       for (int n = n0; n < N; n += nstep, dst += nstep * stride) {
@@ -1207,17 +1241,18 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
         if (do_reduce) {
           R d = w.re * w.re + w.im * w.im;
           if (a.simpson) d *= wxtab[n];
-          rs.add(d, x2tab[n]);
+          s0 += d;
+          sx = fma(x2tab[n], d, sx);
         }
       }
       if (do_reduce) {
-        const double wyz = quad_weight(fixed, a.ny, a.simpson) * quad_weight(k0 + b, a.nz, a.simpson);
-        const double t = wyz * rs.total();
-        const double z = coordinate(k0 + b, a.nz, a.hz), y = coordinate(fixed, a.ny, a.hy);
-        v[0] += t;
-        v[1] += wyz * rs.xmoment();
-        v[2] += y * y * t;
-        v[3] += z * z * t;
+        const R wyz = quad_weight_r<R>(fixed, a.ny, a.simpson) * quad_weight_r<R>(k0 + b, a.nz, a.simpson);
+        const R y = R(fixed - a.ny / 2) * hy, z = R(k0 + b - a.nz / 2) * hz;
+        const R t = wyz * s0;
+        acc[0].add(t);
+        acc[1].add(wyz * sx);
+        acc[2].add(y * y * t);
+        acc[3].add(z * z * t);
       }
     }
     __syncthreads();   // `cur` is refilled by the prefetch two tiles ahead
@@ -1226,6 +1261,7 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
     nxt = t;
   }
   if (do_reduce) {
+    double v[4] = {acc[0].value(), acc[1].value(), acc[2].value(), acc[3].value()};
     if (reduce_across_blocks<4>(v, a.partials, &a.state->ticket) && threadIdx.x == 0) {
       DevState *st = a.state;
       const double norm = a.hx * a.hy * a.hz * v[0];
@@ -1553,6 +1589,11 @@ struct Impl {
     return cudaGetLastError();
   }
 
+  static cudaError_t axis_ksq(void *out, int n, double h, cudaStream_t st) {
+    k_axis_ksq<R><<<(n + 127) / 128, 128, 0, st>>>(reinterpret_cast<R *>(out), n, h);
+    return cudaGetLastError();
+  }
+
   static cudaError_t reset_state(DevState *s, cudaStream_t st) {
     k_reset_state<R><<<1, 32, 0, st>>>(s);
     return cudaGetLastError();
@@ -1634,7 +1675,7 @@ struct Impl {
   }
 
   static const KernelSet *set() {
-    static const KernelSet ks = {(int)E, &init,          &twiddles,   &cn_tables, &axis_potential, &reset_state,
+    static const KernelSet ks = {(int)E, &init,          &twiddles,   &cn_tables, &axis_potential, &axis_ksq, &reset_state,
                                  &k1,        &k2,            &k3,         &k4,        &k5,             &k6,
                                  &k7,        &materialize,   &adj_phase,  &adj_combine, &loss_z2,
                                  &max_blocks, &default_ylines, &y_smem};

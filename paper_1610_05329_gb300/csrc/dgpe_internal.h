@@ -61,6 +61,7 @@ struct KArgs {
   double dtg, dtgdd_n;         // dt g and dt gdd / (nx ny nz) (Phi's 1/N folded in)
   float dtg_f, dtgdd_n_f;
   const void *dtv[3];          // dt v_d x_i^2 per axis (kernel precision)
+  const void *ksq[3];          // k_m^2 per axis, m = FFT index (kernel precision)
   void *psi;                   // [nx][ny][nz] complex
   void *spec;                  // [nzh][nx][ny] complex, the z-half-spectrum-major layout
   DevState *state;
@@ -112,6 +113,7 @@ struct KernelSet {
   cudaError_t (*twiddles)(void *tw, const FftPlan &pl, cudaStream_t st);
   cudaError_t (*cn_tables)(void *tab, int m, int chunk, double r, int imag, cudaStream_t st);
   cudaError_t (*axis_potential)(void *out, int n, double h, double v, double dt, cudaStream_t st);
+  cudaError_t (*axis_ksq)(void *out, int n, double h, cudaStream_t st);
   cudaError_t (*reset_state)(DevState *st_ptr, cudaStream_t st);
   cudaError_t (*k1)(const KArgs &a, cudaStream_t st);
   cudaError_t (*k2)(const KArgs &a, cudaStream_t st);   // forward FFT along y

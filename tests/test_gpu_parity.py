@@ -217,6 +217,27 @@ def test_potential_step_large_phase_angles(orc, dt):
     gpu.close()
 
 
+@pytest.mark.parametrize("dt", [3.0, -3.0, 0.37, 0.004])
+def test_potential_step_large_phase_angles_fp32(orc, dt):
+    """The FP32 sine/cosine (three-float pi/2 reduction, Taylor series) over angles up to a
+    few hundred radians of both signs.  Bound: theta is formed in FP32 from four rounded
+    terms (a few ulp of |theta|max), then reduced and evaluated to ~1e-7."""
+    shape, h, nu, g, gdd = (16, 12, 18), 0.6, (2.0, 1.5, 2.5), 40.0, 30.0
+    psi = state(shape, h).astype(np.complex64).astype(np.complex128)
+    gpu, p = make(orc, shape, h, dt, abi.DGPE_REAL_TIME, nu=nu, g=g, gdd=gdd, precision=abi.DGPE_MIXED)
+    gpu.set_psi(psi.astype(np.complex64))
+    gpu.substep(abi.DGPE_SUB_POTENTIAL)
+    got = gpu.get_psi().astype(np.complex128)
+    want = orc.potential_step(p, psi)
+    x, y, z = inputs.grid_axes(shape, (h, h, h))
+    vmax = 0.5 * (nu[0] ** 2 * np.max(x ** 2) + nu[1] ** 2 * np.max(y ** 2) + nu[2] ** 2 * np.max(z ** 2))
+    n = np.abs(psi) ** 2
+    theta_max = abs(dt) * (vmax + g * n.max() + gdd * np.abs(orc.dipolar_phi(p, n)).max())
+    assert theta_max > 1.0 or dt == 0.004
+    assert rel(got, want) < 5e-7 * theta_max + 1e-6, (rel(got, want), theta_max)
+    gpu.close()
+
+
 @pytest.mark.parametrize("shape,h", [((10, 20, 14), 0.5), ((40, 28, 30), 0.3), ((70, 10, 50), 0.25)])
 @pytest.mark.parametrize("mode", [abi.DGPE_REAL_TIME, abi.DGPE_IMAG_TIME])
 def test_radix5_radix7_sizes(orc, shape, h, mode):
