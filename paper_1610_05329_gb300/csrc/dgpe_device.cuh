@@ -45,6 +45,12 @@ template <typename R>
 __device__ __forceinline__ cplx<R> mul(R a, cplx<R> v) { return {a * v.re, a * v.im}; }
 template <typename R>
 __device__ __forceinline__ cplx<R> mul(cplx<R> a, cplx<R> v) { return a * v; }
+// c v for the Crank-Nicolson coefficient c: real r (imaginary time) or i r (real time; the
+// complex Coef holds {0, r}, so only its imaginary part enters).
+template <typename R>
+__device__ __forceinline__ cplx<R> mul_c(R c, cplx<R> v) { return {c * v.re, c * v.im}; }
+template <typename R>
+__device__ __forceinline__ cplx<R> mul_c(cplx<R> c, cplx<R> v) { return {-c.im * v.im, c.im * v.re}; }
 template <typename T>
 __device__ __forceinline__ T coef_one();
 template <>
@@ -449,23 +455,27 @@ __device__ cplx<R> *fft_lines(cplx<R> *a, cplx<R> *b, const FftPlan &pl, int lw,
 //   y_i   = y0_i + P_i Y_t,                   Y_t = y at the point before the chunk,
 //   chi_i = chi0_i + Y_t H_i + X_{t+1} G_i,   X_{t+1} = chi at the point after the chunk,
 // with P, H, G precomputed per position (see k_cn_tables).  The carries Y_t and X_t are
-// affine recurrences across lanes, resolved by warp-shuffle scans of (A, B) pairs.
+// affine recurrences across lanes, resolved by warp-shuffle scans of (A, B) pairs; the A
+// factors of every lane and scan step depend only on the position, so they come from the
+// tables as well (only B is scanned).
 // Element n of the line is at buf[cn_slot(n, lchunk) * es].
+// Table layout (lane-interleaved, mp = 32 * chunk): [alpha | beta | H | G] at q * mp + e * 32
+// + t for interior point t * chunk + e, then the scan factors: forward step k (offset
+// 2^k) at 4 mp + k * 32 + t, backward step k at 4 mp + (5 + k) * 32 + t.
 // ---------------------------------------------------------------------------------------
 template <typename R, typename Coef, int CH, bool SHARED_TAB>
 __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m, int lchunk,
-                                        const Coef *__restrict__ tab, Coef c) {
+                                        const Coef *__restrict__ tab, const Coef *__restrict__ scan_s, Coef c) {
   const int t = threadIdx.x & (kWarp - 1);
   constexpr int chunk = CH;
   const int s0 = t * chunk;
   const int len = max(0, min(chunk, m - s0));
-  // tables are lane-interleaved: entry of interior point t*chunk + e at [e * 32 + t]
   const int mp = kWarp << lchunk;
   const Coef *alpha = tab + t;
   const Coef *beta = tab + mp + t;
-  const Coef *P = tab + 2 * mp + t;
-  const Coef *H = tab + 3 * mp + t;
-  const Coef *G = tab + 4 * mp + t;
+  const Coef *H = tab + 2 * mp + t;
+  const Coef *G = tab + 3 * mp + t;
+  const Coef *scan = scan_s + t;   // the scan factors, staged in shared memory by the caller
 
   cplx<R> y[CH];
   cplx<R> acc = czero<R>();
@@ -483,16 +493,11 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
     }
   }
   // forward carries: Y_{t+1} = A_t Y_t + B_t, Y_0 = 0
-  Coef A = len > 0 ? T(P + (len - 1) * kWarp) : coef_one<Coef>();
   cplx<R> B = acc;
 #pragma unroll
-  for (int d = 1; d < kWarp; d <<= 1) {
-    const Coef Ap = shfl_up(A, d);
-    const cplx<R> Bp = shfl_up(B, d);
-    if (t >= d) {
-      B = mul(A, Bp) + B;
-      A = A * Ap;
-    }
+  for (int k = 0; k < 5; ++k) {
+    const cplx<R> Bp = shfl_up(B, 1 << k);
+    if (t >= (1 << k)) B = mul(scan[k * kWarp], Bp) + B;
   }
   cplx<R> Y = shfl_up(B, 1);
   if (t == 0) Y = czero<R>();
@@ -501,21 +506,16 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
 #pragma unroll
   for (int e = CH - 1; e >= 0; --e) {
     if (e < len) {
-      acc = mul(T(beta + e * kWarp), y[e] + mul(c, acc));
+      acc = mul(T(beta + e * kWarp), y[e] + mul_c(c, acc));
       y[e] = acc;
     }
   }
   // backward carries: X_t = G_{s0} X_{t+1} + (chi0_{s0} + H_{s0} Y_t), X_32 = 0
-  Coef A2 = len > 0 ? T(G) : coef_one<Coef>();
   cplx<R> B2 = len > 0 ? acc + mul(T(H), Y) : czero<R>();
 #pragma unroll
-  for (int d = 1; d < kWarp; d <<= 1) {
-    const Coef An = shfl_down(A2, d);
-    const cplx<R> Bn = shfl_down(B2, d);
-    if (t + d < kWarp) {
-      B2 = mul(A2, Bn) + B2;
-      A2 = A2 * An;
-    }
+  for (int k = 0; k < 5; ++k) {
+    const cplx<R> Bn = shfl_down(B2, 1 << k);
+    if (t + (1 << k) < kWarp) B2 = mul(scan[(5 + k) * kWarp], Bn) + B2;
   }
   cplx<R> X = shfl_down(B2, 1);
   if (t == kWarp - 1) X = czero<R>();
@@ -539,12 +539,12 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
 // cn_line with the chunk length as a compile-time constant (every unrolled iteration live).
 template <typename R, typename Coef, bool SHARED_TAB>
 __device__ __forceinline__ void cn_line_any(cplx<R> *__restrict__ buf, int es, int m, int lchunk,
-                                            const Coef *__restrict__ tab, Coef c) {
+                                            const Coef *__restrict__ tab, const Coef *__restrict__ scan_s, Coef c) {
   switch (lchunk) {
-    case 1: cn_line<R, Coef, 2, SHARED_TAB>(buf, es, m, lchunk, tab, c); break;
-    case 2: cn_line<R, Coef, 4, SHARED_TAB>(buf, es, m, lchunk, tab, c); break;
-    case 3: cn_line<R, Coef, 8, SHARED_TAB>(buf, es, m, lchunk, tab, c); break;
-    default: cn_line<R, Coef, 16, SHARED_TAB>(buf, es, m, lchunk, tab, c); break;
+    case 1: cn_line<R, Coef, 2, SHARED_TAB>(buf, es, m, lchunk, tab, scan_s, c); break;
+    case 2: cn_line<R, Coef, 4, SHARED_TAB>(buf, es, m, lchunk, tab, scan_s, c); break;
+    case 3: cn_line<R, Coef, 8, SHARED_TAB>(buf, es, m, lchunk, tab, scan_s, c); break;
+    default: cn_line<R, Coef, 16, SHARED_TAB>(buf, es, m, lchunk, tab, scan_s, c); break;
   }
 }
 
@@ -666,7 +666,9 @@ __global__ void k_twiddles(cplx<R> *tw, FftPlan pl) {
 //   e_0 = 1 + 2c, e_i = 1 + 2c - c alpha_i, alpha_i = c / e_{i-1}, beta_i = 1 / e_i;
 //   per chunk [s0, end]: P_s0 = alpha_s0, P_i = alpha_i P_{i-1};
 //   H_end = beta_end P_end, H_i = beta_i (P_i + c H_{i+1});
-//   G_end = beta_end c,     G_i = beta_i c G_{i+1}.
+//   G_end = beta_end c,     G_i = beta_i c G_{i+1};
+// alpha, beta, H and G are stored; P only enters the forward scan factors (P at each chunk
+// end, then the running products of the scan), stored after them with the backward ones.
 struct Z64 {
   double re, im;
 };
@@ -693,6 +695,8 @@ __global__ void k_cn_tables(Coef *tab, int m, int chunk, double r, int imag) {
   const Z64 diag = {1.0 + 2.0 * c.re, 2.0 * c.im};
   const Z64 one = {1.0, 0.0};
   Z64 al[kCnMaxChunk], be[kCnMaxChunk], pv[kCnMaxChunk];
+  Z64 fa[kWarp], ba[kWarp];   // per lane: P at the chunk end, G at the chunk start
+  for (int t = 0; t < kWarp; ++t) fa[t] = ba[t] = one;
   Z64 e_prev = diag;
   for (int s0 = 0; s0 < m; s0 += chunk) {
     const int end = min(s0 + chunk, m) - 1;
@@ -715,17 +719,28 @@ __global__ void k_cn_tables(Coef *tab, int m, int chunk, double r, int imag) {
       p = zmul(p, al[i - s0]);
       pv[i - s0] = p;
     }
-    for (int i = s0; i <= end; ++i) store_coef<R>(tab, at(2, i), pv[i - s0]);
     Z64 h = zmul(be[end - s0], pv[end - s0]);
     Z64 gg = zmul(be[end - s0], c);
-    store_coef<R>(tab, at(3, end), h);
-    store_coef<R>(tab, at(4, end), gg);
+    store_coef<R>(tab, at(2, end), h);
+    store_coef<R>(tab, at(3, end), gg);
     for (int i = end - 1; i >= s0; --i) {
       h = zmul(be[i - s0], zadd(pv[i - s0], zmul(c, h)));
       gg = zmul(be[i - s0], zmul(c, gg));
-      store_coef<R>(tab, at(3, i), h);
-      store_coef<R>(tab, at(4, i), gg);
+      store_coef<R>(tab, at(2, i), h);
+      store_coef<R>(tab, at(3, i), gg);
     }
+    fa[s0 / chunk] = pv[end - s0];
+    ba[s0 / chunk] = gg;
+  }
+  // Kogge-Stone scan factors: before step k (offset d = 2^k) lane t holds the product of
+  // the factors of lanes t - 2^k + 1 .. t (forward) or t .. t + 2^k - 1 (backward).
+  for (int k = 0, d = 1; d < kWarp; ++k, d <<= 1) {
+    for (int t = 0; t < kWarp; ++t) {
+      store_coef<R>(tab, 4 * mp + k * kWarp + t, fa[t]);
+      store_coef<R>(tab, 4 * mp + (5 + k) * kWarp + t, ba[t]);
+    }
+    for (int t = kWarp - 1; t >= d; --t) fa[t] = zmul(fa[t], fa[t - d]);
+    for (int t = 0; t + d < kWarp; ++t) ba[t] = zmul(ba[t], ba[t + d]);
   }
 }
 
@@ -951,6 +966,13 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
   C *psi = reinterpret_cast<C *>(a.psi) + line0 * nz;
   const C *res = nullptr;
 
+  // the CN-z scan factors, staged after the per-CTA potential tables
+  Coef *scan_s = reinterpret_cast<Coef *>(reinterpret_cast<R *>(tile + BZ * LS) + nz + BZ);
+  if (zmode == kZStep || zmode == kZCnOnly) {
+    const Coef *gscan = reinterpret_cast<const Coef *>(a.cn[2].tab) + 4 * (kWarp << lc);
+    for (int q = threadIdx.x; q < 10 * kWarp; q += blockDim.x) scan_s[q] = gscan[q];
+  }
+
   // psi tile: asynchronous copies, overlapped with the spectrum load and the C2R transform
   if (zmode != kZPhi) {
     LinePos pos(threadIdx.x, nz, blockDim.x);
@@ -1127,7 +1149,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmo
     const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[2], a.cn_rf[2]));
     const Coef *tab = reinterpret_cast<const Coef *>(a.cn[2].tab);
     for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp)
-      cn_line_any<R, Coef, false>(tile + b * LS, 1, a.cn[2].m, lc, tab, c);
+      cn_line_any<R, Coef, false>(tile + b * LS, 1, a.cn[2].m, lc, tab, scan_s, c);
     __syncthreads();
   }
 
@@ -1175,7 +1197,7 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
   C *cur = reinterpret_cast<C *>(smem_raw);
   C *nxt = cur + slots * SB;
   Coef *stab = reinterpret_cast<Coef *>(nxt + slots * SB);     // factor tables, staged once
-  const int ntab = 5 * (kWarp << lc);
+  const int ntab = 4 * (kWarp << lc) + 10 * kWarp;
   R *x2tab = reinterpret_cast<R *>(stab + ntab);
   R *wxtab = x2tab + N;                                         // quadrature weights along x
   const size_t stride = AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
@@ -1229,7 +1251,7 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
     const size_t base = tile_origin(tile, fixed, k0);
     const int nb = min(B, a.nz - k0);
     for (int l = threadIdx.x / kWarp; l < nb; l += blockDim.x / kWarp)
-      cn_line_any<R, Coef, true>(cur + l, SB, a.cn[AXIS].m, lc, tab, c);
+      cn_line_any<R, Coef, true>(cur + l, SB, a.cn[AXIS].m, lc, tab, tab + 4 * (kWarp << lc), c);
     __syncthreads();
     if (b < nb) {
       R s0 = R(0), sx = R(0);   // this column's partial sums of n and x^2 n
@@ -1509,12 +1531,12 @@ struct Impl {
   static size_t smem_z_fft(const KArgs &a) { return 2 * (size_t)a.nz * (T::kZLines / 2 + 1) * E; }
   static size_t smem_k5(const KArgs &a) {
     return 2 * (size_t)a.nz * (T::kZLines / 2) * E + (size_t)T::kZLines * cn_slots(a.nz, a.cn[2].lchunk) * E +
-           (size_t)(a.nz + T::kZLines) * sizeof(R);
+           (size_t)(a.nz + T::kZLines) * sizeof(R) + (size_t)10 * kWarp * E;
   }
   static size_t smem_y(const KArgs &a) { return 2 * (size_t)a.ny * (a.ylines + 1) * E; }
   static size_t smem_x(const KArgs &a) { return 2 * (size_t)a.nx * T::kXCols * E; }
   static size_t smem_cn(int n, int lchunk) {
-    return 2 * (size_t)cn_slots(n, lchunk) * (T::kCnCols + 1) * E + (size_t)5 * (kWarp << lchunk) * E +
+    return 2 * (size_t)cn_slots(n, lchunk) * (T::kCnCols + 1) * E + (size_t)(4 * (kWarp << lchunk) + 10 * kWarp) * E +
            2 * (size_t)n * sizeof(R);
   }
 

@@ -22,9 +22,10 @@ struct FftPlan {
 };
 
 // Crank-Nicolson factor tables of one direction (interior size m = n - 2, chunk length c):
-// five arrays [alpha | beta | P | H | G] of 32*c coefficients each (complex in real time,
+// four arrays [alpha | beta | H | G] of 32*c coefficients each (complex in real time,
 // real in imaginary time, in the kernel precision), lane-interleaved: the entry of interior
-// point t*c + e sits at e*32 + t, so the 32 lanes of a warp read one contiguous segment.
+// point t*c + e sits at e*32 + t, so the 32 lanes of a warp read one contiguous segment;
+// then 10 x 32 scan factors of the lane carries (5 forward steps, 5 backward).
 struct CnTab {
   const void *tab;
   int m;
