@@ -121,7 +121,7 @@ int check_physics(const dgpe_params *p) {
 }
 
 struct Layout {
-  size_t state, partials, tw[3], cn[3], cn_adj[3], dtv[3], ksq[3], psi, spec, total;
+  size_t state, partials, tw[3], cn[3], cn_adj[3], dtv[3], psi, spec, utab, total;
 };
 
 Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
@@ -146,13 +146,13 @@ Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
   for (int d = 0; d < 3; ++d) {
     L.dtv[d] = off;
     off += align_up((size_t)n[d] * (e / 2));
-    L.ksq[d] = off;
-    off += align_up((size_t)n[d] * (e / 2));
   }
   L.psi = off;
   off += align_up((size_t)p->nx * p->ny * p->nz * e);
   L.spec = off;
   off += align_up((size_t)(p->nz / 2 + 1) * p->nx * p->ny * e);
+  L.utab = off;   // FP64 only: the FP32 kernels evaluate the dipolar kernel in place
+  if (p->precision == DGPE_FP64) off += align_up((size_t)(p->nz / 2 + 1) * p->nx * p->ny * sizeof(double));
   L.total = off;
   (void)ks;
   return L;
@@ -182,6 +182,9 @@ void set_physics(KArgs &a, const dgpe_params *p) {
   a.hz = p->hz;
   a.dt = p->dt;
   a.cutoff = p->cutoff;
+  a.kf[0] = (float)(2.0 * M_PI / (p->nx * p->hx));
+  a.kf[1] = (float)(2.0 * M_PI / (p->ny * p->hy));
+  a.kf[2] = (float)(2.0 * M_PI / (p->nz * p->hz));
   a.simpson = p->integration == DGPE_SIMPSON;
   a.kinetic5 = p->kinetic == DGPE_KINETIC_GRADIENT5;
   a.g = p->g;
@@ -362,16 +365,16 @@ int build_graph(dgpe_ctx *c) {
   return DGPE_OK;
 }
 
-// Per-axis tables of the physics: dt v_d x^2 (always) and the Crank-Nicolson factor
-// tables (only when dt, h or the mode changed, or on the first call).
-int setup_tables(dgpe_ctx *c, bool cn_changed) {
+// Per-axis tables of the physics: dt v_d x^2 (always), the Crank-Nicolson factor tables
+// (only when dt, h or the mode changed, or on the first call) and the dipolar kernel on the
+// half spectrum (only when h or the cutoff changed, or on the first call).
+int setup_tables(dgpe_ctx *c, bool cn_changed, bool ut_changed) {
   const dgpe_params *p = &c->p;
   const double h[3] = {p->hx, p->hy, p->hz};
   const int n[3] = {p->nx, p->ny, p->nz};
   const double v[3] = {c->args.vx, c->args.vy, c->args.vz};
   for (int d = 0; d < 3; ++d) {
     int rc = map_cuda(c->ks->axis_potential(at(c, c->L.dtv[d]), n[d], h[d], v[d], p->dt, c->stream));
-    if (!rc) rc = map_cuda(c->ks->axis_ksq(at(c, c->L.ksq[d]), n[d], h[d], c->stream));
     if (rc) return rc;
     if (!cn_changed) continue;
     rc = map_cuda(c->ks->cn_tables(at(c, c->L.cn[d]), c->args.cn[d].m, c->args.cn[d].chunk, c->args.cn_r[d],
@@ -382,6 +385,7 @@ int setup_tables(dgpe_ctx *c, bool cn_changed) {
                                      -c->args.cn_r[d], 0, c->stream));
     if (rc) return rc;
   }
+  if (ut_changed) return map_cuda(c->ks->dipolar_table(c->args, c->stream));
   return DGPE_OK;
 }
 
@@ -603,14 +607,14 @@ int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out) {
     a.tw[d] = at(c, c->L.tw[d]);
     a.cn[d].tab = at(c, c->L.cn[d]);
     a.dtv[d] = at(c, c->L.dtv[d]);
-    a.ksq[d] = at(c, c->L.ksq[d]);
   }
+  a.utab = at(c, c->L.utab);
   const int n[3] = {p->nx, p->ny, p->nz};
   rc = map_cuda(cudaMemsetAsync(a.psi, 0, (size_t)p->nx * p->ny * p->nz * c->ks->elem_bytes, c->stream));
   if (!rc) rc = map_cuda(c->ks->reset_state(a.state, c->stream));
   for (int d = 0; d < 3 && !rc; ++d) rc = map_cuda(c->ks->twiddles(const_cast<void *>(a.tw[d]), a.plan[d], c->stream));
   (void)n;
-  if (!rc) rc = setup_tables(c, true);
+  if (!rc) rc = setup_tables(c, true, true);
   if (rc) {
     dgpe_destroy(c);
     return rc;
@@ -627,6 +631,7 @@ int dgpe_set_params(dgpe_ctx *c, const dgpe_params *p) {
   if (rc) return rc;
   const bool cn_changed = p->dt != c->p.dt || p->hx != c->p.hx || p->hy != c->p.hy || p->hz != c->p.hz ||
                           p->mode != c->p.mode;
+  const bool ut_changed = p->hx != c->p.hx || p->hy != c->p.hy || p->hz != c->p.hz || p->cutoff != c->p.cutoff;
   const bool step_args_changed = cn_changed || p->g != c->p.g || p->gdd != c->p.gdd || p->cutoff != c->p.cutoff ||
                                  p->integration != c->p.integration;
   void *ws = c->p.workspace;
@@ -641,7 +646,7 @@ int dgpe_set_params(dgpe_ctx *c, const dgpe_params *p) {
     c->graph_valid = false;
     ++c->generation;
   }
-  return setup_tables(c, cn_changed);
+  return setup_tables(c, cn_changed, ut_changed);
 }
 
 int dgpe_set_psi(dgpe_ctx *c, const void *psi, int where) {

@@ -45,12 +45,21 @@ template <typename R>
 __device__ __forceinline__ cplx<R> mul(R a, cplx<R> v) { return {a * v.re, a * v.im}; }
 template <typename R>
 __device__ __forceinline__ cplx<R> mul(cplx<R> a, cplx<R> v) { return a * v; }
-// c v for the Crank-Nicolson coefficient c: real r (imaginary time) or i r (real time; the
-// complex Coef holds {0, r}, so only its imaginary part enters).
+// a b + d as a chain of FMAs (2 per component for complex a, 1 for real a).
 template <typename R>
-__device__ __forceinline__ cplx<R> mul_c(R c, cplx<R> v) { return {c * v.re, c * v.im}; }
+__device__ __forceinline__ cplx<R> cfma(R a, cplx<R> b, cplx<R> d) { return {fma(a, b.re, d.re), fma(a, b.im, d.im)}; }
 template <typename R>
-__device__ __forceinline__ cplx<R> mul_c(cplx<R> c, cplx<R> v) { return {-c.im * v.im, c.im * v.re}; }
+__device__ __forceinline__ cplx<R> cfma(cplx<R> a, cplx<R> b, cplx<R> d) {
+  return {fma(a.re, b.re, fma(-a.im, b.im, d.re)), fma(a.re, b.im, fma(a.im, b.re, d.im))};
+}
+// c v + d for the Crank-Nicolson coefficient c: real r (imaginary time) or i r (real time;
+// the complex Coef holds {0, r}, so only its imaginary part enters).
+template <typename R>
+__device__ __forceinline__ cplx<R> cfma_c(R c, cplx<R> v, cplx<R> d) { return cfma(c, v, d); }
+template <typename R>
+__device__ __forceinline__ cplx<R> cfma_c(cplx<R> c, cplx<R> v, cplx<R> d) {
+  return {fma(-c.im, v.im, d.re), fma(c.im, v.re, d.im)};
+}
 template <typename T>
 __device__ __forceinline__ T coef_one();
 template <>
@@ -488,7 +497,7 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   for (int e = 0; e < CH; ++e) {
     if (e < len) {
       const int i = s0 + e;
-      acc = buf[(i + 1 + t) * es] + mul(T(alpha + e * kWarp), acc);
+      acc = cfma(T(alpha + e * kWarp), acc, buf[(i + 1 + t) * es]);
       y[e] = acc;
     }
   }
@@ -497,7 +506,7 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const cplx<R> Bp = shfl_up(B, 1 << k);
-    if (t >= (1 << k)) B = mul(scan[k * kWarp], Bp) + B;
+    if (t >= (1 << k)) B = cfma(scan[k * kWarp], Bp, B);
   }
   cplx<R> Y = shfl_up(B, 1);
   if (t == 0) Y = czero<R>();
@@ -506,16 +515,16 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
 #pragma unroll
   for (int e = CH - 1; e >= 0; --e) {
     if (e < len) {
-      acc = mul(T(beta + e * kWarp), y[e] + mul_c(c, acc));
+      acc = mul(T(beta + e * kWarp), cfma_c(c, acc, y[e]));
       y[e] = acc;
     }
   }
   // backward carries: X_t = G_{s0} X_{t+1} + (chi0_{s0} + H_{s0} Y_t), X_32 = 0
-  cplx<R> B2 = len > 0 ? acc + mul(T(H), Y) : czero<R>();
+  cplx<R> B2 = len > 0 ? cfma(T(H), Y, acc) : czero<R>();
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const cplx<R> Bn = shfl_down(B2, 1 << k);
-    if (t + (1 << k) < kWarp) B2 = mul(scan[(5 + k) * kWarp], Bn) + B2;
+    if (t + (1 << k) < kWarp) B2 = cfma(scan[(5 + k) * kWarp], Bn, B2);
   }
   cplx<R> X = shfl_down(B2, 1);
   if (t == kWarp - 1) X = czero<R>();
@@ -524,10 +533,10 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   for (int e = 0; e < CH; ++e) {
     if (e < len) {
       const int i = s0 + e;
-      const cplx<R> chi = y[e] + mul(T(H + e * kWarp), Y) + mul(T(G + e * kWarp), X);
+      const cplx<R> chi = cfma(T(H + e * kWarp), Y, cfma(T(G + e * kWarp), X, y[e]));
       const int q = (i + 1 + t) * es;
       const cplx<R> v = buf[q];
-      buf[q] = {R(2) * chi.re - v.re, R(2) * chi.im - v.im};
+      buf[q] = {fma(R(2), chi.re, -v.re), fma(R(2), chi.im, -v.im)};
     }
   }
   if (t == 0) {
@@ -754,14 +763,47 @@ __global__ void k_axis_potential(R *out, int n, double h, double v, double dt) {
   }
 }
 
-// k_m^2 on one axis, k_m = 2 pi m / (n h) with m signed (m <= n/2: m, else m - n).
+// Cutoff factor c(x) = 1 + 3 cos x / x^2 - 3 sin x / x^3 = 3 int_0^x j_2(t)/t dt of the
+// spherically truncated dipolar interaction; below x = 0.5 its Taylor series
+// sum_{n>=2} (-1)^n 6n x^(2n-2) / (2n+1)!, where the closed form cancels.
 template <typename R>
-__global__ void k_axis_ksq(R *out, int n, double h) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    const int m = i <= n / 2 ? i : i - n;
-    const double k = 6.283185307179586476925286766559 * (double)m / ((double)n * h);
-    out[i] = R(k * k);
+__device__ __forceinline__ R cutoff_factor(R x) {
+  if (x >= R(0.5)) {
+    R sn, cs;
+    sin_cos(x, &sn, &cs);
+    const R ix2 = R(1) / (x * x);
+    return R(1) + R(3) * cs * ix2 - R(3) * sn * ix2 / x;
+  }
+  const R u = x * x;
+  // coefficients 6n/(2n+1)! for n = 2..9 (alternating signs)
+  R p = R(6.0 * 9 / 121645100408832000.0);
+  p = fma(p, -u, R(6.0 * 8 / 355687428096000.0));
+  p = fma(p, -u, R(6.0 * 7 / 1307674368000.0));
+  p = fma(p, -u, R(6.0 * 6 / 6227020800.0));
+  p = fma(p, -u, R(6.0 * 5 / 39916800.0));
+  p = fma(p, -u, R(6.0 * 4 / 362880.0));
+  p = fma(p, -u, R(6.0 * 3 / 5040.0));
+  p = fma(p, -u, R(6.0 * 2 / 120.0));
+  return p * u;
+}
+
+// Ut(k) = 3 kz^2 / |k|^2 - 1 (Ut(0) = 0), times the cutoff factor when a cutoff is set, on
+// the half spectrum [m][i][j] (kz index m <= nz/2, kx index i, ky index j), computed in
+// FP64: k_d = 2 pi q / (n_d h_d) with the signed frequency q (q <= n/2: q, else q - n).
+template <typename R>
+__global__ void k_dipolar_table(R *ut, KArgs a) {
+  const size_t total = (size_t)a.nzh * a.nx * a.ny;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e % a.ny);
+    const size_t r = e / a.ny;
+    const int i = (int)(r % a.nx), m = (int)(r / a.nx);
+    const int qx = i <= a.nx / 2 ? i : i - a.nx, qy = j <= a.ny / 2 ? j : j - a.ny;
+    const double kx = two_pi * qx / (a.nx * a.hx), ky = two_pi * qy / (a.ny * a.hy), kz = two_pi * m / (a.nz * a.hz);
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    double u = k2 > 0.0 ? 3.0 * kz * kz / k2 - 1.0 : 0.0;
+    if (a.cutoff > 0.0 && k2 > 0.0) u *= cutoff_factor<double>(sqrt(k2) * a.cutoff);
+    ut[e] = R(u);
   }
 }
 
@@ -866,40 +908,6 @@ __global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a) {
 // forward FFT along x, multiply by Ut(kx, ky, kz) = 3 kz^2 / |k|^2 - 1 (Ut(0) = 0),
 // inverse FFT along x.
 // ---------------------------------------------------------------------------------------
-// Cutoff factor c(x) = 1 + 3 cos x / x^2 - 3 sin x / x^3 = 3 int_0^x j_2(t)/t dt of the
-// spherically truncated dipolar interaction; below x = 0.5 its Taylor series
-// sum_{n>=2} (-1)^n 6n x^(2n-2) / (2n+1)!, where the closed form cancels.
-template <typename R>
-__device__ __forceinline__ R cutoff_factor(R x) {
-  if (x >= R(0.5)) {
-    R sn, cs;
-    sin_cos(x, &sn, &cs);
-    const R ix2 = R(1) / (x * x);
-    return R(1) + R(3) * cs * ix2 - R(3) * sn * ix2 / x;
-  }
-  const R u = x * x;
-  // coefficients 6n/(2n+1)! for n = 2..9 (alternating signs)
-  R p = R(6.0 * 9 / 121645100408832000.0);
-  p = fma(p, -u, R(6.0 * 8 / 355687428096000.0));
-  p = fma(p, -u, R(6.0 * 7 / 1307674368000.0));
-  p = fma(p, -u, R(6.0 * 6 / 6227020800.0));
-  p = fma(p, -u, R(6.0 * 5 / 39916800.0));
-  p = fma(p, -u, R(6.0 * 4 / 362880.0));
-  p = fma(p, -u, R(6.0 * 3 / 5040.0));
-  p = fma(p, -u, R(6.0 * 2 / 120.0));
-  return p * u;
-}
-
-// Ut(k) = 3 kz^2 / |k|^2 - 1 (Ut(0) = 0) from the per-axis k^2 tables, times the cutoff
-// factor when a cutoff is set.
-template <typename R>
-__device__ __forceinline__ R dipolar_kernel(R kx2, R ky2, R kz2, const KArgs &a) {
-  const R k2 = kx2 + ky2 + kz2;
-  R u = k2 > R(0) ? R(3) * kz2 / k2 - R(1) : R(0);
-  if (a.cutoff > 0.0 && k2 > R(0)) u *= cutoff_factor<R>(sqrt(k2) * R(a.cutoff));
-  return u;
-}
-
 template <typename R>
 __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
   using C = cplx<R>;
@@ -919,14 +927,26 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
   __syncthreads();
   const C *tw = reinterpret_cast<const C *>(a.tw[0]);
   C *res = fft_lines<R, -1>(za, zb, a.plan[0], BX, nb, SB, tw);
-  {
-    const R *kx2 = reinterpret_cast<const R *>(a.ksq[0]);
-    const R kz2 = reinterpret_cast<const R *>(a.ksq[2])[m];
-    const int b = threadIdx.x % BX;
-    if (b < nb) {
-      const R kyz2 = reinterpret_cast<const R *>(a.ksq[1])[j0 + b];
+  const int b = threadIdx.x % BX;
+  if (b < nb) {
+    if constexpr (sizeof(R) == 8) {
+      // FP64: the table (its FP64 division and cutoff factor would cost more than the read)
+      const R *ut = reinterpret_cast<const R *>(a.utab) + (size_t)m * a.nx * a.ny + j0;
       for (int k = threadIdx.x / BX; k < n; k += blockDim.x / BX)
-        res[k * SB + b] = scale(res[k * SB + b], dipolar_kernel<R>(ldg(kx2 + k), kyz2, kz2, a));
+        res[k * SB + b] = scale(res[k * SB + b], ldg(ut + (size_t)k * a.ny + b));
+    } else {
+      // FP32: in place, k_d = q_d * (2 pi / (n_d h_d)) with the signed frequency q_d
+      const R fx = a.kf[0], fy = a.kf[1], fz = a.kf[2];
+      const int jy = j0 + b;
+      const R ky = R(jy <= a.ny / 2 ? jy : jy - a.ny) * fy, kz = R(m) * fz;
+      const R kz2 = kz * kz, kyz2 = fma(ky, ky, kz2);
+      for (int k = threadIdx.x / BX; k < n; k += blockDim.x / BX) {
+        const R kx = R(k <= n / 2 ? k : k - n) * fx;
+        const R k2 = fma(kx, kx, kyz2);
+        R u = k2 > R(0) ? __fdividef(R(3) * kz2, k2) - R(1) : R(0);
+        if (a.cutoff > 0.0 && k2 > R(0)) u *= cutoff_factor<R>(sqrt(k2) * R(a.cutoff));
+        res[k * SB + b] = scale(res[k * SB + b], u);
+      }
     }
   }
   __syncthreads();
@@ -1611,8 +1631,12 @@ struct Impl {
     return cudaGetLastError();
   }
 
-  static cudaError_t axis_ksq(void *out, int n, double h, cudaStream_t st) {
-    k_axis_ksq<R><<<(n + 127) / 128, 128, 0, st>>>(reinterpret_cast<R *>(out), n, h);
+  static cudaError_t dipolar_table(const KArgs &a, cudaStream_t st) {
+    if (sizeof(R) != 8) return cudaSuccess;   // FP32 evaluates the kernel in K3
+    const size_t total = (size_t)a.nzh * a.nx * a.ny;
+    const size_t want = (total + 255) / 256, cap = (size_t)sm_count() * 8;
+    const int blocks = (int)(want < cap ? want : cap);
+    k_dipolar_table<R><<<blocks, 256, 0, st>>>(reinterpret_cast<R *>(const_cast<void *>(a.utab)), a);
     return cudaGetLastError();
   }
 
@@ -1697,7 +1721,7 @@ struct Impl {
   }
 
   static const KernelSet *set() {
-    static const KernelSet ks = {(int)E, &init,          &twiddles,   &cn_tables, &axis_potential, &axis_ksq, &reset_state,
+    static const KernelSet ks = {(int)E, &init,          &twiddles,   &cn_tables, &axis_potential, &dipolar_table, &reset_state,
                                  &k1,        &k2,            &k3,         &k4,        &k5,             &k6,
                                  &k7,        &materialize,   &adj_phase,  &adj_combine, &loss_z2,
                                  &max_blocks, &default_ylines, &y_smem};

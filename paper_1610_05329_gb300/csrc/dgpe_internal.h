@@ -62,9 +62,10 @@ struct KArgs {
   double dtg, dtgdd_n;         // dt g and dt gdd / (nx ny nz) (Phi's 1/N folded in)
   float dtg_f, dtgdd_n_f;
   const void *dtv[3];          // dt v_d x_i^2 per axis (kernel precision)
-  const void *ksq[3];          // k_m^2 per axis, m = FFT index (kernel precision)
   void *psi;                   // [nx][ny][nz] complex
   void *spec;                  // [nzh][nx][ny] complex, the z-half-spectrum-major layout
+  const void *utab;            // Ut(k) (times the cutoff factor) on [nzh][nx][ny], FP64 only
+  float kf[3];                 // 2 pi / (n_d h_d): wavenumber per frequency index (FP32 K3)
   DevState *state;
   double *partials;            // per-block reduction partials
   const void *tw[3];           // twiddles e^{-2 pi i t / n_d}, t < n_d, for d = x, y, z
@@ -114,7 +115,7 @@ struct KernelSet {
   cudaError_t (*twiddles)(void *tw, const FftPlan &pl, cudaStream_t st);
   cudaError_t (*cn_tables)(void *tab, int m, int chunk, double r, int imag, cudaStream_t st);
   cudaError_t (*axis_potential)(void *out, int n, double h, double v, double dt, cudaStream_t st);
-  cudaError_t (*axis_ksq)(void *out, int n, double h, cudaStream_t st);
+  cudaError_t (*dipolar_table)(const KArgs &a, cudaStream_t st);   // fills utab
   cudaError_t (*reset_state)(DevState *st_ptr, cudaStream_t st);
   cudaError_t (*k1)(const KArgs &a, cudaStream_t st);
   cudaError_t (*k2)(const KArgs &a, cudaStream_t st);   // forward FFT along y
