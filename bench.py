@@ -71,13 +71,14 @@ def fp64_flops_per_point(kernel, shape):
     chunk = 2
     while chunk * 32 < nz - 2:
         chunk *= 2
-    cn = 8 + 12 + 16 + 4 + 140.0 / chunk        # forward, backward, fix-up, 2chi - psi, lane scans
+    cn = 8 + 10 + 16 + 4 + 88.0 / chunk         # forward, backward, fix-up, 2chi - psi, lane scans
     return {
         "k1_density_r2c_z": 2.5 * math.log2(nz) + 5,
         "k2_fft_y": 5 * math.log2(ny) * half,
-        "k3_fft_x_dipolar_ifft_x": (10 * math.log2(nx) + 10) * half,
+        "k3_fft_x_dipolar_ifft_x": (10 * math.log2(nx) + 2) * half,
         "k4_ifft_y": 5 * math.log2(ny) * half,
-        "k5_c2r_z_phase_cn_z": 2.5 * math.log2(nz) + 2 + 9 + 36 + 6 + (8 + 12 + 16 + 4 + 140.0 / chunk),
+        # sine/cosine: 24 flops for |theta| <= 1/4 (every point of this workload), else 36 + reduction
+        "k5_c2r_z_phase_cn_z": 2.5 * math.log2(nz) + 2 + 9 + 24 + 6 + cn,
         "k6_cn_y": cn,
         "k7_cn_x_reduce": cn + 6,
     }.get(kernel, 0.0)
