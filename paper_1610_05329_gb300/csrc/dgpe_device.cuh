@@ -203,6 +203,7 @@ template <>
 struct Tiles<double> {
   static constexpr int kZLines = 8;       // z-lines per CTA in K1/K5 (4 pairs)
   static constexpr int kZThreads = 256;   // 8 warps: one z-line per warp in the CN-z solve
+  static constexpr int kZMinBlocks = 2;   // K5: two CTAs per SM (at most 128 registers)
   static constexpr int kXCols = 4;        // consecutive y columns per K3 tile
   static constexpr int kCnCols = 8;       // consecutive z columns per K6/K7 tile (128 B rows)
   static constexpr int kCnThreads = 128;  // 4 warps, two lines per warp
@@ -212,6 +213,7 @@ template <>
 struct Tiles<float> {
   static constexpr int kZLines = 16;
   static constexpr int kZThreads = 256;
+  static constexpr int kZMinBlocks = 2;
   static constexpr int kXCols = 8;
   static constexpr int kCnCols = 16;
   static constexpr int kCnThreads = 512;  // 16 warps, one line per warp
@@ -984,8 +986,10 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
 // step psi <- s psi e^{-i theta} (real time) or s psi e^{-theta} (imaginary time) with
 // theta = dt (V + g s^2 |psi|^2 + gdd Phi), and the Crank-Nicolson solve along z.
 // ---------------------------------------------------------------------------------------
-template <typename R, typename Coef>
-__global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_zline(KArgs a, int zmode) {
+template <typename R, typename Coef, int ZM>
+__global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R>::kZMinBlocks)
+    k5_zline(KArgs a) {
+  constexpr int zmode = ZM;   // one instance per mode: each gets its own register allocation
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int BZ = Tiles<R>::kZLines;
@@ -1622,8 +1626,14 @@ struct Impl {
     chk(allow_smem(k_ffty<R, -1>));
     chk(allow_smem(k_ffty<R, +1>));
     chk(allow_smem(k3_fftx_dipolar<R>));
-    chk(allow_smem(k5_zline<R, R>));
-    chk(allow_smem(k5_zline<R, C>));
+    chk(allow_smem(k5_zline<R, R, kZStep>));
+    chk(allow_smem(k5_zline<R, C, kZStep>));
+    chk(allow_smem(k5_zline<R, R, kZPhaseOnly>));
+    chk(allow_smem(k5_zline<R, C, kZPhaseOnly>));
+    chk(allow_smem(k5_zline<R, R, kZCnOnly>));
+    chk(allow_smem(k5_zline<R, C, kZCnOnly>));
+    chk(allow_smem(k5_zline<R, R, kZPhi>));
+    chk(allow_smem(k5_zline<R, R, kZObs>));
     chk(allow_smem(k_cn<R, R, 0>));
     chk(allow_smem(k_cn<R, R, 1>));
     chk(allow_smem(k_cn<R, C, 0>));
@@ -1685,8 +1695,25 @@ struct Impl {
     return cudaGetLastError();
   }
   static cudaError_t k5(const KArgs &a, int zmode, cudaStream_t st) {
-    if (a.imag) k5_zline<R, R><<<grid_z(a), T::kZThreads, smem_k5(a), st>>>(a, zmode);
-    else k5_zline<R, C><<<grid_z(a), T::kZThreads, smem_k5(a), st>>>(a, zmode);
+    const dim3 g = grid_z(a);
+    const size_t sm = smem_k5(a);
+    switch (zmode) {
+      case kZStep:
+        if (a.imag) k5_zline<R, R, kZStep><<<g, T::kZThreads, sm, st>>>(a);
+        else k5_zline<R, C, kZStep><<<g, T::kZThreads, sm, st>>>(a);
+        break;
+      case kZPhaseOnly:
+        if (a.imag) k5_zline<R, R, kZPhaseOnly><<<g, T::kZThreads, sm, st>>>(a);
+        else k5_zline<R, C, kZPhaseOnly><<<g, T::kZThreads, sm, st>>>(a);
+        break;
+      case kZCnOnly:
+        if (a.imag) k5_zline<R, R, kZCnOnly><<<g, T::kZThreads, sm, st>>>(a);
+        else k5_zline<R, C, kZCnOnly><<<g, T::kZThreads, sm, st>>>(a);
+        break;
+      case kZPhi: k5_zline<R, R, kZPhi><<<g, T::kZThreads, sm, st>>>(a); break;
+      case kZObs: k5_zline<R, R, kZObs><<<g, T::kZThreads, sm, st>>>(a); break;
+      default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
   }
   static cudaError_t k6(const KArgs &a, cudaStream_t st) {
