@@ -182,6 +182,8 @@ void set_physics(KArgs &a, const dgpe_params *p) {
   a.hz = p->hz;
   a.dt = p->dt;
   a.cutoff = p->cutoff;
+  a.has_cutoff = p->cutoff > 0.0;
+  a.cutoff_f = (float)p->cutoff;
   a.kf[0] = (float)(2.0 * M_PI / (p->nx * p->hx));
   a.kf[1] = (float)(2.0 * M_PI / (p->ny * p->hy));
   a.kf[2] = (float)(2.0 * M_PI / (p->nz * p->hz));
@@ -193,6 +195,7 @@ void set_physics(KArgs &a, const dgpe_params *p) {
   a.vy = 0.5 * p->nu[1] * p->nu[1];
   a.vz = 0.5 * p->nu[2] * p->nu[2];
   a.inv_ntot = 1.0 / ((double)p->nx * p->ny * p->nz);
+  a.inv_ntot_f = (float)a.inv_ntot;
   a.imag = p->mode == DGPE_IMAG_TIME;
   const double h[3] = {p->hx, p->hy, p->hz};
   for (int d = 0; d < 3; ++d) {

@@ -596,6 +596,24 @@ __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 template <>
 __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
+// The pending renormalisation factor s of the device state (and s^2) in the kernel
+// precision; the FP32 kernels read the FP32 copies, so they issue no FP64 instruction.
+__device__ __forceinline__ void set_scale(DevState *st, double s) {
+  st->s = s;
+  st->sf = (float)s;
+  st->s2f = (float)(s * s);
+}
+template <typename R>
+__device__ __forceinline__ R scale_of(const DevState *st) {
+  if constexpr (sizeof(R) == 8) return st->s;
+  else return st->sf;
+}
+template <typename R>
+__device__ __forceinline__ R scale_sq_of(const DevState *st) {
+  if constexpr (sizeof(R) == 8) return st->s * st->s;
+  else return st->s2f;
+}
+
 // ---------------------------------------------------------------------------------------
 // Reductions (FP64): warp shuffle, then across warps; deterministic order.
 // ---------------------------------------------------------------------------------------
@@ -830,7 +848,7 @@ __global__ void k_dipolar_table(R *ut, KArgs a) {
 template <typename R>
 __global__ void k_reset_state(DevState *st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    st->s = 1.0;
+    set_scale(st, 1.0);
     st->norm = 0.0;
     st->flags = 0u;
     st->ticket = 0u;
@@ -855,8 +873,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) 
   const int nl = min(BZ, a.ny - j0), np = nl >> 1;
   C *za = reinterpret_cast<C *>(smem_raw);
   C *zb = za + nz * SB;
-  const double s = a.unit_scale ? 1.0 : a.state->s;
-  const R s2 = R(s * s);
+  const R s2 = a.unit_scale ? R(1) : scale_sq_of<R>(a.state);
   const C *psi = reinterpret_cast<const C *>(a.psi) + ((size_t)i * a.ny + j0) * nz;
   const int total = nl * nz;
   LinePos pos(threadIdx.x, nz, blockDim.x);
@@ -964,7 +981,7 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
         const R kx = R(k <= n / 2 ? k : k - n) * fx;
         const R k2 = fma(kx, kx, kyz2);
         R u = k2 > R(0) ? __fdividef(R(3) * kz2, k2) - R(1) : R(0);
-        if (a.cutoff > 0.0 && k2 > R(0)) u *= cutoff_factor<R>(sqrt(k2) * R(a.cutoff));
+        if (a.has_cutoff && k2 > R(0)) u *= cutoff_factor<R>(sqrt(k2) * a.cutoff_f);
         res[k * SB + b] = scale(res[k * SB + b], u);
       }
     }
@@ -1002,8 +1019,8 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R
   C *za = reinterpret_cast<C *>(smem_raw);
   C *zb = za + nz * SB;
   C *tile = zb + nz * SB;
-  const double s = a.state->s;
-  const R inv_ntot = R(a.inv_ntot);
+  const R s = scale_of<R>(a.state);
+  const R inv_ntot = pick<R>(a.inv_ntot, a.inv_ntot_f);
   const size_t line0 = (size_t)i * a.ny + j0;
   C *psi = reinterpret_cast<C *>(a.psi) + line0 * nz;
   const C *res = nullptr;
@@ -1162,7 +1179,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R
     if (threadIdx.x < nl) txy[threadIdx.x] = dtv_x[i] + dtv_y[j0 + threadIdx.x];
     __syncthreads();
     const R sr = R(s);
-    const bool scaled = s != 1.0;
+    const bool scaled = s != R(1);
     const R dtg = pick<R>(a.dtg, a.dtg_f), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f);
     // lines fastest: the padded tile rows (odd stride LS) and the pair-interleaved Phi are
     // read without bank conflicts
@@ -1333,7 +1350,7 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
       st->norm = norm;
       const bool ok = isfinite(norm) && norm > 0.0;
       if (!ok) st->flags |= kFlagNonFinite;
-      st->s = (renorm && ok) ? 1.0 / sqrt(norm) : 1.0;
+      set_scale(st, (renorm && ok) ? 1.0 / sqrt(norm) : 1.0);
       st->steps += 1ull;
     }
   }
@@ -1454,7 +1471,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_phase(KArgs a) {
   cp_async_wait_all();
   __syncthreads();
   const R dtg = pick<R>(a.dtg, a.dtg_f), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f);
-  const R inv_ntot = R(a.inv_ntot);
+  const R inv_ntot = pick<R>(a.inv_ntot, a.inv_ntot_f);
   AdjSums<R> acc;
   LinePos pos(threadIdx.x, nz, blockDim.x);
   for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
@@ -1544,7 +1561,7 @@ __global__ void k_loss_z2(KArgs a, size_t count) {
 template <typename R>
 __global__ void k_materialize(KArgs a, size_t count) {
   using C = cplx<R>;
-  const R s = R(a.state->s);
+  const R s = scale_of<R>(a.state);
   C *psi = reinterpret_cast<C *>(a.psi);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < count; q += (size_t)gridDim.x * blockDim.x)
     psi[q] = scale(psi[q], s);
@@ -1556,7 +1573,7 @@ __global__ void k_materialize(KArgs a, size_t count) {
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
-    a.state->s = 1.0;
+    set_scale(a.state, 1.0);
     a.state->ticket = 0u;
   }
 }

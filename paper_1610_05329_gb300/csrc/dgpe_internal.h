@@ -36,6 +36,7 @@ struct CnTab {
 // Device-resident solver state (lives in the workspace).
 struct DevState {
   double s;          // pending renormalisation factor: the state is s * psi_buf
+  float sf, s2f;     // s and s^2 rounded to FP32 (read by the FP32 kernels)
   double norm;       // hx hy hz sum |psi_buf|^2 after the last full step
   double sums[8];    // last reduction (step: n, x^2 n, y^2 n, z^2 n; obs: 8 terms)
   double obs[12];    // observables of the last dgpe_observables call
@@ -52,10 +53,13 @@ struct KArgs {
   double hx, hy, hz;
   double dt, g, gdd;
   double cutoff;               // spherical cutoff radius of the dipolar kernel (<= 0: none)
+  int has_cutoff;              // cutoff > 0
+  float cutoff_f;
   int simpson;                 // 1: composite Simpson weights in the norm and observables
   int kinetic5;                // 1: kinetic energy from the 5-point gradient
   double vx, vy, vz;           // 0.5 * nu_d^2
   double inv_ntot;             // 1 / (nx ny nz)
+  float inv_ntot_f;
   int imag;                    // 1 = imaginary time
   double cn_r[3];              // dt / (4 h_d^2), the Crank-Nicolson coefficient magnitude
   float cn_rf[3];
