@@ -271,8 +271,9 @@ double kernel_bytes(const dgpe_ctx *c, int k) {
   switch (k) {
     case kK1DensityR2Cz: return e * (ntot + nspec);
     case kK2FftY:
-    case kK3FftXDipolar:
     case kK4IfftY: return 2 * e * nspec;
+    // FP64 reads the dipolar kernel table (one real value per spectral point) as well
+    case kK3FftXDipolar: return 2 * e * nspec + (c->p.precision == DGPE_FP64 ? e / 2 * nspec : 0.0);
     case kK5C2RzPhaseCnz: return e * (nspec + 2 * ntot);
     case kK6CnY:
     case kK7CnXReduce:
