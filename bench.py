@@ -47,9 +47,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch from ncu captures (profiles/), valid while the kernel
 # source is byte-identical to the one captured (sha1 of dgpe_device.cuh).
 NCU_TRAFFIC = {
-    "275dc372c2b0d12e4128e0567f3afd54f74d95ca": {
-        ("real256_fp64", "k5_c2r_z_phase_cn_z"): 618.3e6,
-        ("real512x512x384_mixed", "k5_c2r_z_phase_cn_z"): 1960.5e6,
+    "bf44810458dc45b4e897554e1bc9451921f60803": {
+        ("real256_fp64", "k5_c2r_z_phase_cn_z"): 624.64e6,
+        ("real512x512x384_mixed", "k5_c2r_z_phase_cn_z"): 1959.97e6,
     },
 }
 
