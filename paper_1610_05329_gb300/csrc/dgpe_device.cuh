@@ -224,7 +224,7 @@ constexpr int kUnroll = 8;  // loads in flight per thread in the register-staged
 
 // K2/K4 lines per CTA: a power of two in [2, 32] (it must divide the block size).
 template <typename R>
-__host__ __device__ inline int y_lines_per_cta(int ny) {
+__host__ __device__ constexpr int y_lines_per_cta(int ny) {
   int l = 2;
   while (l * 2 <= 32 && l * 2 * ny <= Tiles<R>::kYBudget) l *= 2;
   return l;
@@ -470,6 +470,96 @@ __device__ cplx<R> *fft_lines(cplx<R> *a, cplx<R> *b, const FftPlan &pl, int lw,
     ns *= p;
   }
   return a;
+}
+
+// The same transform with the length, the line layout and the block size fixed at compile
+// time (the radix order is make_plan's default: radix 8 first, then 4, 2, 3, 5, 7): every
+// stride, trip count and twiddle offset is a constant, the loops unroll, and the shared-
+// memory accesses of a butterfly share one base address.
+__host__ __device__ constexpr int ct_radix(int n, int st) {
+  int m = n, k = 0;
+  while (m % 8 == 0) {
+    if (k++ == st) return 8;
+    m /= 8;
+  }
+  while (m % 4 == 0) {
+    if (k++ == st) return 4;
+    m /= 4;
+  }
+  if (m % 2 == 0) {
+    if (k++ == st) return 2;
+    m /= 2;
+  }
+  const int odd[3] = {3, 5, 7};
+  for (int q = 0; q < 3; ++q)
+    while (m % odd[q] == 0) {
+      if (k++ == st) return odd[q];
+      m /= odd[q];
+    }
+  return 0;
+}
+__host__ __device__ constexpr int ct_ns(int n, int st) {
+  int ns = 1;
+  for (int s = 0; s < st; ++s) ns *= ct_radix(n, s);
+  return ns;
+}
+__host__ __device__ constexpr int ct_twoff(int n, int st) {
+  int off = 0;
+  for (int s = 0; s < st; ++s) off += ct_ns(n, s) * (ct_radix(n, s) - 1);
+  return off;
+}
+
+template <typename R, int DIR, int P, int N, int NS, int LW, int SB, int NT>
+__device__ __forceinline__ void fft_stage_ct(const cplx<R> *__restrict__ src, cplx<R> *__restrict__ dst, int nlines,
+                                             const cplx<R> *__restrict__ tw) {
+  constexpr int NBF = N / P, JSTEP = NT / LW;
+  static_assert(NT % LW == 0, "the line count divides the block size");
+  const int line = threadIdx.x % LW;
+  if (line >= nlines) return;
+  const int j0 = threadIdx.x / LW;
+#pragma unroll
+  for (int it = 0; it < (NBF + JSTEP - 1) / JSTEP; ++it) {
+    const int j = j0 + it * JSTEP;
+    if (NBF % JSTEP != 0 && j >= NBF) break;
+    const int k = j % NS;
+    const cplx<R> *in = src + j * SB + line;
+    cplx<R> v[P];
+#pragma unroll
+    for (int r = 0; r < P; ++r) v[r] = in[r * NBF * SB];
+    if constexpr (NS > 1) {
+      const cplx<R> *w = tw + k * (P - 1);
+#pragma unroll
+      for (int r = 1; r < P; ++r) {
+        const cplx<R> t = ldg(w + r - 1);
+        v[r] = DIR < 0 ? v[r] * t : mul_conj(v[r], t);
+      }
+    }
+    butterfly<R, DIR, P>(v);
+    cplx<R> *out = dst + ((j - k) * P + k) * SB + line;
+#pragma unroll
+    for (int s = 0; s < P; ++s) out[s * NS * SB] = v[s];
+  }
+}
+
+template <typename R, int DIR, int N, int LW, int SB, int NT, int ST = 0>
+__device__ __forceinline__ cplx<R> *fft_lines_ct(cplx<R> *a, cplx<R> *b, int nlines, const cplx<R> *tw) {
+  constexpr int P = ct_radix(N, ST);
+  if constexpr (P == 0) {
+    return a;
+  } else {
+    fft_stage_ct<R, DIR, P, N, ct_ns(N, ST), LW, SB, NT>(a, b, nlines, tw + ct_twoff(N, ST));
+    __syncthreads();
+    return fft_lines_ct<R, DIR, N, LW, SB, NT, ST + 1>(b, a, nlines, tw);
+  }
+}
+
+// The compile-time transform when N > 0 (the caller checked that the plan is the default
+// one of length N and that the block has NT threads), else the runtime plan.
+template <typename R, int DIR, int N, int LW, int SB, int NT>
+__device__ __forceinline__ cplx<R> *fft_lines_n(cplx<R> *a, cplx<R> *b, const FftPlan &pl, int nlines,
+                                                const cplx<R> *tw) {
+  if constexpr (N > 0) return fft_lines_ct<R, DIR, N, LW, SB, NT>(a, b, nlines, tw);
+  else return fft_lines<R, DIR>(a, b, pl, LW, nlines, SB, tw);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -862,14 +952,14 @@ __global__ void k_reset_state(DevState *st) {
 // spectra are separated (X1 = (Z_m + conj Z_{N-m})/2, X2 = (Z_m - conj Z_{N-m})/2i) and
 // the half spectrum m = 0..nz/2 is stored to spec[m][i][j].
 // ---------------------------------------------------------------------------------------
-template <typename R>
+template <typename R, int N>
 __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int BZ = Tiles<R>::kZLines;
   constexpr int PZ = BZ / 2;
   constexpr int SB = PZ + 1;
-  const int nz = a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
+  const int nz = N > 0 ? N : a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
   const int nl = min(BZ, a.ny - j0), np = nl >> 1;
   C *za = reinterpret_cast<C *>(smem_raw);
   C *zb = za + nz * SB;
@@ -895,7 +985,8 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) 
     }
   }
   __syncthreads();
-  const C *res = fft_lines<R, -1>(za, zb, a.plan[2], PZ, np, SB, reinterpret_cast<const C *>(a.tw[2]));
+  const C *res = fft_lines_n<R, -1, N, PZ, SB, Tiles<R>::kZThreads>(za, zb, a.plan[2], np,
+                                                                   reinterpret_cast<const C *>(a.tw[2]));
   C *spec = reinterpret_cast<C *>(a.spec) + (size_t)i * a.ny + j0;
   const size_t plane = (size_t)a.nx * a.ny;
   const int p = threadIdx.x % PZ;
@@ -915,12 +1006,14 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) 
 // ---------------------------------------------------------------------------------------
 // K2 / K4: FFT along y of the contiguous lines spec[m][i][:].
 // ---------------------------------------------------------------------------------------
-template <typename R, int DIR>
+template <typename R, int DIR, int N>
 __global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = a.ny;
-  const int L = a.ylines;
+  // N > 0: ny = N with the default lines per CTA and 256 threads, fixed at compile time
+  constexpr int LC = N > 0 ? y_lines_per_cta<R>(N) : 0;
+  const int n = N > 0 ? N : a.ny;
+  const int L = N > 0 ? LC : a.ylines;
   const int SB = L + 1;
   const size_t total = (size_t)a.nzh * a.nx;
   const size_t l0 = (size_t)blockIdx.x * L;
@@ -934,7 +1027,11 @@ __global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a) {
   }
   cp_async_wait_all();
   __syncthreads();
-  const C *res = fft_lines<R, DIR>(za, zb, a.plan[1], L, nl, SB, reinterpret_cast<const C *>(a.tw[1]));
+  const C *res;
+  if constexpr (N > 0)
+    res = fft_lines_ct<R, DIR, N, LC, LC + 1, kFftThreads>(za, zb, nl, reinterpret_cast<const C *>(a.tw[1]));
+  else
+    res = fft_lines<R, DIR>(za, zb, a.plan[1], L, nl, SB, reinterpret_cast<const C *>(a.tw[1]));
   LinePos pos(threadIdx.x, n, blockDim.x);
 #pragma unroll 4
   for (int e = threadIdx.x; e < nl * n; e += blockDim.x, pos.next()) spec[e] = res[pos.k * SB + pos.b];
@@ -945,13 +1042,13 @@ __global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a) {
 // forward FFT along x, multiply by Ut(kx, ky, kz) = 3 kz^2 / |k|^2 - 1 (Ut(0) = 0),
 // inverse FFT along x.
 // ---------------------------------------------------------------------------------------
-template <typename R>
+template <typename R, int N>
 __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int BX = Tiles<R>::kXCols;
   constexpr int SB = BX;
-  const int n = a.nx, m = blockIdx.y, j0 = blockIdx.x * BX;
+  const int n = N > 0 ? N : a.nx, m = blockIdx.y, j0 = blockIdx.x * BX;
   const int nb = min(BX, a.ny - j0);
   C *za = reinterpret_cast<C *>(smem_raw);
   C *zb = za + n * SB;
@@ -963,7 +1060,7 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
   cp_async_wait_all();
   __syncthreads();
   const C *tw = reinterpret_cast<const C *>(a.tw[0]);
-  C *res = fft_lines<R, -1>(za, zb, a.plan[0], BX, nb, SB, tw);
+  C *res = fft_lines_n<R, -1, N, BX, SB, kFftThreads>(za, zb, a.plan[0], nb, tw);
   const int b = threadIdx.x % BX;
   if (b < nb) {
     if constexpr (sizeof(R) == 8) {
@@ -988,7 +1085,7 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
   }
   __syncthreads();
   C *other = (res == za) ? zb : za;
-  const C *out = fft_lines<R, +1>(res, other, a.plan[0], BX, nb, SB, tw);
+  const C *out = fft_lines_n<R, +1, N, BX, SB, kFftThreads>(res, other, a.plan[0], nb, tw);
 #pragma unroll 4
   for (int e = threadIdx.x; e < n * BX; e += blockDim.x) {
     const int b = e % BX, k = e / BX;
@@ -1003,7 +1100,7 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
 // step psi <- s psi e^{-i theta} (real time) or s psi e^{-theta} (imaginary time) with
 // theta = dt (V + g s^2 |psi|^2 + gdd Phi), and the Crank-Nicolson solve along z.
 // ---------------------------------------------------------------------------------------
-template <typename R, typename Coef, int ZM>
+template <typename R, typename Coef, int ZM, int N>
 __global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R>::kZMinBlocks)
     k5_zline(KArgs a) {
   constexpr int zmode = ZM;   // one instance per mode: each gets its own register allocation
@@ -1012,7 +1109,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R
   constexpr int BZ = Tiles<R>::kZLines;
   constexpr int PZ = BZ / 2;
   constexpr int SB = PZ;   // unpadded: the butterflies (pair fastest) and the line-fastest phase loop are conflict-free
-  const int nz = a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
+  const int nz = N > 0 ? N : a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
   const int nl = min(BZ, a.ny - j0), np = nl >> 1;
   const int lc = a.cn[2].lchunk;
   const int LS = cn_slots(nz, lc);
@@ -1071,7 +1168,8 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R
       }
     }
     __syncthreads();
-    res = fft_lines<R, +1>(za, zb, a.plan[2], PZ, np, SB, reinterpret_cast<const C *>(a.tw[2]));
+    res = fft_lines_n<R, +1, N, PZ, SB, Tiles<R>::kZThreads>(za, zb, a.plan[2], np,
+                                                             reinterpret_cast<const C *>(a.tw[2]));
   }
 
   if (zmode == kZPhi) {
@@ -1639,18 +1737,40 @@ struct Impl {
     auto chk = [&](cudaError_t r) {
       if (e == cudaSuccess) e = r;
     };
-    chk(allow_smem(k1_density_r2cz<R>));
-    chk(allow_smem(k_ffty<R, -1>));
-    chk(allow_smem(k_ffty<R, +1>));
-    chk(allow_smem(k3_fftx_dipolar<R>));
-    chk(allow_smem(k5_zline<R, R, kZStep>));
-    chk(allow_smem(k5_zline<R, C, kZStep>));
-    chk(allow_smem(k5_zline<R, R, kZPhaseOnly>));
-    chk(allow_smem(k5_zline<R, C, kZPhaseOnly>));
-    chk(allow_smem(k5_zline<R, R, kZCnOnly>));
-    chk(allow_smem(k5_zline<R, C, kZCnOnly>));
-    chk(allow_smem(k5_zline<R, R, kZPhi>));
-    chk(allow_smem(k5_zline<R, R, kZObs>));
+    chk(allow_smem(k1_density_r2cz<R, 0>));
+    chk(allow_smem(k1_density_r2cz<R, 512>));
+    chk(allow_smem(k1_density_r2cz<R, 384>));
+    chk(allow_smem(k1_density_r2cz<R, 256>));
+    chk(allow_smem(k1_density_r2cz<R, 128>));
+    chk(allow_smem(k_ffty<R, -1, 0>));
+    chk(allow_smem(k_ffty<R, +1, 0>));
+    chk(allow_smem(k_ffty<R, -1, 512>));
+    chk(allow_smem(k_ffty<R, +1, 512>));
+    chk(allow_smem(k_ffty<R, -1, 384>));
+    chk(allow_smem(k_ffty<R, +1, 384>));
+    chk(allow_smem(k_ffty<R, -1, 256>));
+    chk(allow_smem(k_ffty<R, +1, 256>));
+    chk(allow_smem(k_ffty<R, -1, 128>));
+    chk(allow_smem(k_ffty<R, +1, 128>));
+    chk(allow_smem(k3_fftx_dipolar<R, 0>));
+    chk(allow_smem(k3_fftx_dipolar<R, 512>));
+    chk(allow_smem(k3_fftx_dipolar<R, 384>));
+    chk(allow_smem(k3_fftx_dipolar<R, 256>));
+    chk(allow_smem(k3_fftx_dipolar<R, 128>));
+    chk(allow_smem(k5_zline<R, R, kZStep, 0>));
+    chk(allow_smem(k5_zline<R, C, kZStep, 0>));
+    chk(allow_smem(k5_zline<R, R, kZStep, 512>));
+    chk(allow_smem(k5_zline<R, C, kZStep, 512>));
+    chk(allow_smem(k5_zline<R, R, kZStep, 384>));
+    chk(allow_smem(k5_zline<R, C, kZStep, 384>));
+    chk(allow_smem(k5_zline<R, R, kZStep, 256>));
+    chk(allow_smem(k5_zline<R, C, kZStep, 256>));
+    chk(allow_smem(k5_zline<R, R, kZPhaseOnly, 0>));
+    chk(allow_smem(k5_zline<R, C, kZPhaseOnly, 0>));
+    chk(allow_smem(k5_zline<R, R, kZCnOnly, 0>));
+    chk(allow_smem(k5_zline<R, C, kZCnOnly, 0>));
+    chk(allow_smem(k5_zline<R, R, kZPhi, 0>));
+    chk(allow_smem(k5_zline<R, R, kZObs, 0>));
     chk(allow_smem(k_cn<R, R, 0>));
     chk(allow_smem(k_cn<R, R, 1>));
     chk(allow_smem(k_cn<R, C, 0>));
@@ -1690,45 +1810,84 @@ struct Impl {
     return cudaGetLastError();
   }
 
+  // the plan of length n is make_plan's default (the compile-time transforms follow it)
+  static bool plan_ct(const FftPlan &pl, int n) {
+    if (pl.n != n) return false;
+    for (int st = 0; st < kMaxStages; ++st) {
+      const int p = st < pl.nstages ? pl.radix[st] : 0;
+      if (p != ct_radix(n, st)) return false;
+      if (p == 0) break;
+    }
+    return true;
+  }
   static cudaError_t k1(const KArgs &a, cudaStream_t st) {
-    k1_density_r2cz<R><<<grid_z(a), T::kZThreads, smem_z_fft(a), st>>>(a);
+    const dim3 g = grid_z(a);
+    const size_t sm = smem_z_fft(a);
+    if (plan_ct(a.plan[2], 512)) k1_density_r2cz<R, 512><<<g, T::kZThreads, sm, st>>>(a);
+    else if (plan_ct(a.plan[2], 384)) k1_density_r2cz<R, 384><<<g, T::kZThreads, sm, st>>>(a);
+    else if (plan_ct(a.plan[2], 256)) k1_density_r2cz<R, 256><<<g, T::kZThreads, sm, st>>>(a);
+    else if (plan_ct(a.plan[2], 128)) k1_density_r2cz<R, 128><<<g, T::kZThreads, sm, st>>>(a);
+    else k1_density_r2cz<R, 0><<<g, T::kZThreads, sm, st>>>(a);
     return cudaGetLastError();
   }
-  static cudaError_t k2(const KArgs &a, cudaStream_t st) {
+  // the compile-time transform applies when the y plan, lines per CTA and block size are
+  // the defaults for that length
+  static bool y_fixed(const KArgs &a, int n) {
+    return a.ylines == y_lines_per_cta<R>(n) && a.fft_threads == kFftThreads && plan_ct(a.plan[1], n);
+  }
+  template <int DIR>
+  static cudaError_t ffty(const KArgs &a, cudaStream_t st) {
     const size_t lines = (size_t)a.nzh * a.nx;
     const int L = a.ylines;
-    k_ffty<R, -1><<<(unsigned)((lines + L - 1) / L), a.fft_threads, smem_y(a), st>>>(a);
+    const dim3 g((unsigned)((lines + L - 1) / L));
+    const size_t sm = smem_y(a);
+    if (y_fixed(a, 512)) k_ffty<R, DIR, 512><<<g, kFftThreads, sm, st>>>(a);
+    else if (y_fixed(a, 384)) k_ffty<R, DIR, 384><<<g, kFftThreads, sm, st>>>(a);
+    else if (y_fixed(a, 256)) k_ffty<R, DIR, 256><<<g, kFftThreads, sm, st>>>(a);
+    else if (y_fixed(a, 128)) k_ffty<R, DIR, 128><<<g, kFftThreads, sm, st>>>(a);
+    else k_ffty<R, DIR, 0><<<g, a.fft_threads, sm, st>>>(a);
     return cudaGetLastError();
   }
+  static cudaError_t k2(const KArgs &a, cudaStream_t st) { return ffty<-1>(a, st); }
   static cudaError_t k3(const KArgs &a, cudaStream_t st) {
     dim3 grid((a.ny + T::kXCols - 1) / T::kXCols, a.nzh);
-    k3_fftx_dipolar<R><<<grid, a.fft_threads, smem_x(a), st>>>(a);
+    const size_t sm = smem_x(a);
+    const bool fixed = a.fft_threads == kFftThreads;
+    if (fixed && plan_ct(a.plan[0], 512)) k3_fftx_dipolar<R, 512><<<grid, kFftThreads, sm, st>>>(a);
+    else if (fixed && plan_ct(a.plan[0], 384)) k3_fftx_dipolar<R, 384><<<grid, kFftThreads, sm, st>>>(a);
+    else if (fixed && plan_ct(a.plan[0], 256)) k3_fftx_dipolar<R, 256><<<grid, kFftThreads, sm, st>>>(a);
+    else if (fixed && plan_ct(a.plan[0], 128)) k3_fftx_dipolar<R, 128><<<grid, kFftThreads, sm, st>>>(a);
+    else k3_fftx_dipolar<R, 0><<<grid, a.fft_threads, sm, st>>>(a);
     return cudaGetLastError();
   }
-  static cudaError_t k4(const KArgs &a, cudaStream_t st) {
-    const size_t lines = (size_t)a.nzh * a.nx;
-    const int L = a.ylines;
-    k_ffty<R, +1><<<(unsigned)((lines + L - 1) / L), a.fft_threads, smem_y(a), st>>>(a);
-    return cudaGetLastError();
-  }
+  static cudaError_t k4(const KArgs &a, cudaStream_t st) { return ffty<+1>(a, st); }
   static cudaError_t k5(const KArgs &a, int zmode, cudaStream_t st) {
     const dim3 g = grid_z(a);
     const size_t sm = smem_k5(a);
     switch (zmode) {
       case kZStep:
-        if (a.imag) k5_zline<R, R, kZStep><<<g, T::kZThreads, sm, st>>>(a);
-        else k5_zline<R, C, kZStep><<<g, T::kZThreads, sm, st>>>(a);
+        if (a.imag) {
+          if (plan_ct(a.plan[2], 512)) k5_zline<R, R, kZStep, 512><<<g, T::kZThreads, sm, st>>>(a);
+          else if (plan_ct(a.plan[2], 384)) k5_zline<R, R, kZStep, 384><<<g, T::kZThreads, sm, st>>>(a);
+          else if (plan_ct(a.plan[2], 256)) k5_zline<R, R, kZStep, 256><<<g, T::kZThreads, sm, st>>>(a);
+          else k5_zline<R, R, kZStep, 0><<<g, T::kZThreads, sm, st>>>(a);
+        } else {
+          if (plan_ct(a.plan[2], 512)) k5_zline<R, C, kZStep, 512><<<g, T::kZThreads, sm, st>>>(a);
+          else if (plan_ct(a.plan[2], 384)) k5_zline<R, C, kZStep, 384><<<g, T::kZThreads, sm, st>>>(a);
+          else if (plan_ct(a.plan[2], 256)) k5_zline<R, C, kZStep, 256><<<g, T::kZThreads, sm, st>>>(a);
+          else k5_zline<R, C, kZStep, 0><<<g, T::kZThreads, sm, st>>>(a);
+        }
         break;
       case kZPhaseOnly:
-        if (a.imag) k5_zline<R, R, kZPhaseOnly><<<g, T::kZThreads, sm, st>>>(a);
-        else k5_zline<R, C, kZPhaseOnly><<<g, T::kZThreads, sm, st>>>(a);
+        if (a.imag) k5_zline<R, R, kZPhaseOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
+        else k5_zline<R, C, kZPhaseOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
         break;
       case kZCnOnly:
-        if (a.imag) k5_zline<R, R, kZCnOnly><<<g, T::kZThreads, sm, st>>>(a);
-        else k5_zline<R, C, kZCnOnly><<<g, T::kZThreads, sm, st>>>(a);
+        if (a.imag) k5_zline<R, R, kZCnOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
+        else k5_zline<R, C, kZCnOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
         break;
-      case kZPhi: k5_zline<R, R, kZPhi><<<g, T::kZThreads, sm, st>>>(a); break;
-      case kZObs: k5_zline<R, R, kZObs><<<g, T::kZThreads, sm, st>>>(a); break;
+      case kZPhi: k5_zline<R, R, kZPhi, 0><<<g, T::kZThreads, sm, st>>>(a); break;
+      case kZObs: k5_zline<R, R, kZObs, 0><<<g, T::kZThreads, sm, st>>>(a); break;
       default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
