@@ -949,7 +949,8 @@ __global__ void k_reset_state(DevState *st) {
 // ---------------------------------------------------------------------------------------
 // K1: n = s^2 |psi|^2 of kZLines consecutive z-lines (i, j0..), packed in pairs as the
 // real and imaginary parts of one complex line, forward FFT along z, then the two real
-// spectra are separated (X1 = (Z_m + conj Z_{N-m})/2, X2 = (Z_m - conj Z_{N-m})/2i) and
+// spectra are separated (X1 = (Z_m + conj Z_{N-m})/2, X2 = (Z_m - conj Z_{N-m})/2i; the 1/2
+// is applied exactly to the packed density instead) and
 // the half spectrum m = 0..nz/2 is stored to spec[m][i][j].
 // ---------------------------------------------------------------------------------------
 template <typename R, int N>
@@ -963,7 +964,8 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) 
   const int nl = min(BZ, a.ny - j0), np = nl >> 1;
   C *za = reinterpret_cast<C *>(smem_raw);
   C *zb = za + nz * SB;
-  const R s2 = a.unit_scale ? R(1) : scale_sq_of<R>(a.state);
+  // the packed density carries a factor 1/2 (exact), so the separation below needs none
+  const R s2 = R(0.5) * (a.unit_scale ? R(1) : scale_sq_of<R>(a.state));
   const C *psi = reinterpret_cast<const C *>(a.psi) + ((size_t)i * a.ny + j0) * nz;
   const int total = nl * nz;
   LinePos pos(threadIdx.x, nz, blockDim.x);
@@ -994,8 +996,8 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) 
     for (int m = threadIdx.x / PZ; m < a.nzh; m += blockDim.x / PZ) {
       const C zm = res[m * SB + p];
       const C zc = res[((nz - m) % nz) * SB + p];
-      const C x1 = {R(0.5) * (zm.re + zc.re), R(0.5) * (zm.im - zc.im)};
-      const C x2 = {R(0.5) * (zm.im + zc.im), R(0.5) * (zc.re - zm.re)};
+      const C x1 = {zm.re + zc.re, zm.im - zc.im};
+      const C x2 = {zm.im + zc.im, zc.re - zm.re};
       C *dst = spec + m * plane + 2 * p;
       dst[0] = x1;
       dst[1] = x2;
@@ -1525,8 +1527,8 @@ __device__ __forceinline__ void store_half_spectrum_column(const KArgs &a, const
     const C zm = res[m * SB + p];
     const C zc = res[((nz - m) % nz) * SB + p];
     C *dst = spec + m * plane + 2 * p;
-    dst[0] = {R(0.5) * (zm.re + zc.re), R(0.5) * (zm.im - zc.im)};
-    dst[1] = {R(0.5) * (zm.im + zc.im), R(0.5) * (zc.re - zm.re)};
+    dst[0] = {zm.re + zc.re, zm.im - zc.im};   // the packed input carries the factor 1/2
+    dst[1] = {zm.im + zc.im, zc.re - zm.re};
   }
 }
 
@@ -1585,7 +1587,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_phase(KArgs a) {
     const C u = {g1.re * cs - g1.im * sn, g1.re * sn + g1.im * cs};
     const R sv = u.re * v.im - u.im * v.re;
     gt[e] = u;
-    reinterpret_cast<R *>(sbuf + n * SB + (b >> 1))[b & 1] = sv;
+    reinterpret_cast<R *>(sbuf + n * SB + (b >> 1))[b & 1] = R(0.5) * sv;   // 1/2 of the R2C separation
     acc.add(sv * dens, sv * phi * inv_ntot, sv * z2[n]);
   }
   __syncthreads();

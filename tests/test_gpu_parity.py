@@ -290,3 +290,26 @@ def test_simpson_and_gradient_observables(orc, integration, kinetic):
         assert og["rms"][d] == pytest.approx(ow["rms"][d], rel=1e-11)
     assert og["norm"] == pytest.approx(1.0, abs=1e-12)
     gpu.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(abi.DGPE_FP64, FP64_STEP_TOL), (abi.DGPE_MIXED, 2e-5)])
+def test_compile_time_transforms_match_runtime_plans(orc, precision, tol):
+    """Lengths 128 and 256 with the default radix order run the compile-time transforms (K1,
+    K2, K3, K4 and K5's step); the radix-4-first and radix-3-first orders run the runtime
+    plans.  Both agree with the oracle after three real-time steps."""
+    shape, h, dt = (128, 128, 256), 0.12, 0.002
+    cdt = np.complex128 if precision == abi.DGPE_FP64 else np.complex64
+    psi = state(shape, h).astype(cdt)
+    gpu, p = make(orc, shape, h, dt, abi.DGPE_REAL_TIME, precision=precision)
+    want = orc.step(p, psi.astype(np.complex128), 3)
+    ylines = 16 if precision == abi.DGPE_FP64 else 32   # the default for ny = 128
+    got = {}
+    for style in (0, 1, 2):
+        gpu.set_tuning(dict(plan_style=(style, style, style), ylines=ylines, fft_threads=256, cn_per_sm=2,
+                            step_ms_default=0.0, step_ms_tuned=0.0))
+        gpu.set_psi(psi)
+        gpu.step(3)
+        got[style] = gpu.get_psi().astype(np.complex128)
+        assert rel(got[style], want) < tol, (style, rel(got[style], want))
+    assert rel(got[0], got[1]) < tol and rel(got[0], got[2]) < tol
+    gpu.close()
