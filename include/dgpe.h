@@ -233,6 +233,9 @@ typedef struct dgpe_tuning {
 int dgpe_autotune(dgpe_ctx *ctx, dgpe_tuning *out);
 /* Apply a tuning (e.g. one found earlier for the same shape). DGPE_EINVAL if invalid. */
 int dgpe_set_tuning(dgpe_ctx *ctx, const dgpe_tuning *t);
+/* The launch shape in use (the defaults of dgpe_create until dgpe_autotune or
+ * dgpe_set_tuning changes it); step_ms_default and step_ms_tuned are 0.  No CUDA call. */
+int dgpe_get_tuning(const dgpe_ctx *ctx, dgpe_tuning *out);
 
 /* Wait for the stream; returns a latched device error if any. */
 int dgpe_sync(dgpe_ctx *ctx);

@@ -118,6 +118,7 @@ _SIGNATURES = [
     ("dgpe_batch_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("dgpe_batch_destroy", None, [ctypes.c_void_p]),
     ("dgpe_autotune", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_tuning)]),
+    ("dgpe_get_tuning", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_tuning)]),
     ("dgpe_set_tuning", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_tuning)]),
     ("dgpe_moments_noalloc", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_params), ctypes.c_void_p, ctypes.c_void_p]),
     ("dgpe_strerror", ctypes.c_char_p, [ctypes.c_int]),
@@ -266,6 +267,12 @@ def dgpe_grad_z2(ctx, nu_z, steps_per_seg, work_ptr, work_bytes):
 def dgpe_autotune(ctx):
     t = dgpe_tuning()
     _check(load().dgpe_autotune(ctx, ctypes.byref(t)), "dgpe_autotune")
+    return t.as_dict()
+
+
+def dgpe_get_tuning(ctx):
+    t = dgpe_tuning()
+    _check(load().dgpe_get_tuning(ctx, ctypes.byref(t)), "dgpe_get_tuning")
     return t.as_dict()
 
 
@@ -422,6 +429,9 @@ class Condensate:
 
     def set_tuning(self, tuning):
         dgpe_set_tuning(self.ctx, tuning)
+
+    def tuning(self):
+        return dgpe_get_tuning(self.ctx)
 
     def adjoint_step(self, psi_k, gbar):
         """gbar (device tensor) <- cotangent of psi_k for one real-time step (in place)."""

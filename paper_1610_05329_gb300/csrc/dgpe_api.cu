@@ -860,6 +860,12 @@ int dgpe_set_tuning(dgpe_ctx *c, const dgpe_tuning *t) {
   return apply_tuning(c, *t);
 }
 
+int dgpe_get_tuning(const dgpe_ctx *c, dgpe_tuning *out) {
+  if (!c || !out) return DGPE_EINVAL;
+  *out = current_tuning(c);
+  return DGPE_OK;
+}
+
 int dgpe_autotune(dgpe_ctx *c, dgpe_tuning *out) {
   if (!c || !out) return DGPE_EINVAL;
   const size_t sb = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;

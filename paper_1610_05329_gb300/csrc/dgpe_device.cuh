@@ -207,7 +207,7 @@ struct Tiles<double> {
   static constexpr int kXCols = 4;        // consecutive y columns per K3 tile
   static constexpr int kCnCols = 8;       // consecutive z columns per K6/K7 tile (128 B rows)
   static constexpr int kCnThreads = 128;  // 4 warps, two lines per warp
-  static constexpr int kYBudget = 2048;   // K2/K4: lines per CTA ~ budget / ny
+  static constexpr int kYBudget = 1024;   // K2/K4: lines per CTA ~ budget / ny
 };
 template <>
 struct Tiles<float> {

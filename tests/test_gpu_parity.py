@@ -302,11 +302,11 @@ def test_compile_time_transforms_match_runtime_plans(orc, precision, tol):
     psi = state(shape, h).astype(cdt)
     gpu, p = make(orc, shape, h, dt, abi.DGPE_REAL_TIME, precision=precision)
     want = orc.step(p, psi.astype(np.complex128), 3)
-    ylines = 16 if precision == abi.DGPE_FP64 else 32   # the default for ny = 128
+    default = gpu.tuning()
+    assert default["plan_style"] == (0, 0, 0) and default["fft_threads"] == 256
     got = {}
     for style in (0, 1, 2):
-        gpu.set_tuning(dict(plan_style=(style, style, style), ylines=ylines, fft_threads=256, cn_per_sm=2,
-                            step_ms_default=0.0, step_ms_tuned=0.0))
+        gpu.set_tuning(dict(default, plan_style=(style, style, style)))
         gpu.set_psi(psi)
         gpu.step(3)
         got[style] = gpu.get_psi().astype(np.complex128)
