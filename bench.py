@@ -37,7 +37,11 @@ WORKLOADS = {
                          dt_prep=0.004, dt=5e-4, precision="fp64"),
     "real512x512x384_mixed": dict(shape=(512, 512, 384), h=0.05, nu=(1.0, 1.0, 2.0), g_prep=100.0, g=100.0,
                                   gdd=60.0, dt_prep=0.001, dt=5e-4, precision="mixed"),
+    # the 256^3 workload in double-float (FP32 pairs on the FP32 pipe)
+    "real256_df64": dict(shape=(256, 256, 256), h=0.1, nu=(0.5, 1.0, 1.5), g_prep=50.0, g=40.0, gdd=25.0,
+                         dt_prep=0.004, dt=5e-4, precision="df64"),
 }
+PRECISIONS = {"fp64": 0, "mixed": 1, "df64": 2}   # DGPE_FP64, DGPE_MIXED, DGPE_DF64
 PREP_STEPS = 20
 
 # FP64 peak of GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA per clock per SM
@@ -156,7 +160,7 @@ def measured_peaks():
 def make_condensate(abi, wl, local):
     import torch
     from paper_1610_05329_gb300 import inputs
-    prec = abi.DGPE_FP64 if wl["precision"] == "fp64" else abi.DGPE_MIXED
+    prec = PRECISIONS[wl["precision"]]
     c = abi.Condensate(wl["shape"], wl["h"], wl["dt_prep"], mode=abi.DGPE_IMAG_TIME, precision=prec,
                        nu=wl["nu"], g=wl["g_prep"], gdd=wl["gdd"], device=torch.device("cuda", local))
     psi0 = inputs.gaussian_psi(wl["shape"], wl["h"], noise=1e-3, seed=1)
@@ -217,7 +221,7 @@ def kernel_profile(c, steps, hbm_peak, peak_kind, workload):
         d = {"kernel": r["name"], "launches": r["launches"], "avg_ms": round(avg, 5),
              "share": round(r["total_ms"] / total, 4), "bytes_per_launch": r["bytes_per_launch"],
              "achieved_gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4)}
-        if wl["precision"] == "fp64":
+        if wl["precision"] in ("fp64", "df64"):
             fl = fp64_flops_per_point(r["name"], wl["shape"]) * npts
             d["fp64_flops_per_launch"] = fl
             d["fp64_tflops"] = round(fl / (avg * 1e-3) / 1e12, 4)
@@ -229,7 +233,13 @@ def kernel_profile(c, steps, hbm_peak, peak_kind, workload):
     hbm = {"bound": "hbm", "kernel": top["kernel"], "achieved": top["achieved_gbs"], "peak": hbm_peak,
            "unit": "GB/s", "frac": top["frac_hbm"], "traffic": tr,
            "peak_kind": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback")}
-    if wl["precision"] == "fp64":
+    if wl["precision"] == "df64":
+        # FP64-class arithmetic on the FP32 pipe: the same algorithmic FP64 flops, compared
+        # with what the FP64 pipe could do at most
+        roofline = dict(hbm, fp64_equivalent={"achieved": top["fp64_tflops"], "unit": "TFLOP/s",
+                                              "fp64_pipe_peak": round(FP64_PEAK_TFLOPS, 4),
+                                              "ratio_to_fp64_peak": top["frac_fp64"]})
+    elif wl["precision"] == "fp64":
         roofline = {"bound": "alu", "kernel": top["kernel"], "achieved": top["fp64_tflops"],
                     "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": top["frac_fp64"],
                     "traffic": tr, "peak_kind": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz",
@@ -474,6 +484,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 512x512x384 mixed-precision line item")
+    ap.add_argument("--no-df64", action="store_true", help="skip the 256^3 double-float line item")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 128^3 differentiation line item")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-condensate batching line item")
@@ -509,6 +520,7 @@ def main():
     wl = WORKLOADS[name]
     if args.workload is not None:
         args.no_mixed = True
+        args.no_df64 = True
     c = make_condensate(abi, wl, local)
     npts = wl["shape"][0] * wl["shape"][1] * wl["shape"][2]
     c.step(args.warmup)
@@ -538,6 +550,21 @@ def main():
                  "algorithmic_bytes_per_step": sum(k["bytes_per_launch"] * k["launches"] for k in kernels_m)
                  / min(args.steps, 50)}
 
+    dfl = None
+    if not args.no_df64:
+        wld = WORKLOADS["real256_df64"]
+        cd = make_condensate(abi, wld, local)
+        nd = wld["shape"][0] * wld["shape"][1] * wld["shape"][2]
+        cd.step(args.warmup)
+        msd = time_steps(cd, args.steps, barrier)
+        value_d, msd = aggregate_over_ranks(msd, nd * args.steps, dist, cd.device)
+        rl_d, kernels_d = kernel_profile(cd, min(args.steps, 50), hbm_peak, peak_kind, "real256_df64")
+        cd.sync()
+        cd.close()
+        dfl = {"value": value_d, "unit": UNIT, "ms_per_step": round(msd / args.steps, 4),
+               "dtype": "df64 (pairs of FP32, ~48 significant bits; parity with the FP64 oracle <= 1e-10)",
+               "grid": list(wld["shape"]), "roofline": rl_d, "kernels": kernels_d}
+
     diff = None
     if not args.no_adjoint and args.workload is None:
         diff = {p: differentiation_run(abi, local, p, min(args.steps, 50)) for p in ("fp64", "mixed")}
@@ -557,11 +584,13 @@ def main():
             "config": {"workload": name, "grid": list(wl["shape"]), "mode": "real", "h": wl["h"],
                        "dt": wl["dt"], "g": wl["g"], "gdd": wl["gdd"], "nu": list(wl["nu"]),
                        "prep": "%d imaginary-time steps at g=%g from the seeded Gaussian" % (PREP_STEPS, wl["g_prep"]),
-                       "l2": "inputs larger than L2 (psi %d MB > 129 MB)" % (npts * (16 if wl["precision"] == "fp64" else 8) >> 20),
+                       "l2": "inputs larger than L2 (psi %d MB > 129 MB)" % (npts * (8 if wl["precision"] == "mixed" else 16) >> 20),
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
             "gpu_launches": 7 * args.steps, "clocks": clk, "roofline": roofline, "kernels": kernels, "e2e": e2e}
     if mixed is not None:
         line["mixed_512x512x384"] = mixed
+    if dfl is not None:
+        line["df64_256"] = dfl
     if diff is not None:
         line["differentiation_128"] = diff
     if batch is not None:

@@ -24,7 +24,8 @@
  * them in any order.
  *
  * Memory and layout.  psi is row-major [nx][ny][nz] (z fastest), complex values stored as
- * interleaved (re, im) pairs: complex128 for DGPE_FP64, complex64 for DGPE_MIXED.  All
+ * interleaved (re, im) pairs: complex128 for DGPE_FP64 and DGPE_DF64, complex64 for
+ * DGPE_MIXED.  All
  * device memory the solver uses is one workspace of dgpe_workspace_bytes() bytes: the
  * caller may own it (params.workspace, e.g. a PyTorch tensor) or let dgpe_create allocate
  * it with cudaMalloc.  Nothing is kept in global variables: one context per stream.
@@ -58,6 +59,12 @@ extern "C" {
 
 #define DGPE_FP64 0   /* complex128 psi; FFT, phase and CN in FP64 */
 #define DGPE_MIXED 1  /* complex64 psi; FFT, phase and CN in FP32; norm/mu/E sums in FP64 */
+/* Double-float: every value is a pair of FP32 numbers hi + lo (about 48 significant bits)
+ * and every operation runs on the FP32 pipe, which GB300 issues 64 times as fast as FP64.
+ * The caller sees complex128 (dgpe_set_psi/dgpe_get_psi convert at the boundary) and FP64
+ * observables; the differentiation calls return DGPE_EUNSUPPORTED.  The paper has no
+ * counterpart: this is an implementation choice for FP64-starved hardware. */
+#define DGPE_DF64 2
 
 #define DGPE_HOST 0
 #define DGPE_DEVICE 1
@@ -88,7 +95,7 @@ typedef struct dgpe_params {
   double hx, hy, hz;
   double dt;
   int mode;           /* DGPE_REAL_TIME or DGPE_IMAG_TIME */
-  int precision;      /* DGPE_FP64 or DGPE_MIXED */
+  int precision;      /* DGPE_FP64, DGPE_MIXED or DGPE_DF64 */
   double nu[3];       /* trap frequencies nu_x, nu_y, nu_z */
   double g;           /* contact strength */
   double gdd;         /* dipolar strength (dipoles along z) */

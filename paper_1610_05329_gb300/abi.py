@@ -26,6 +26,7 @@ DGPE_REAL_TIME = 0
 DGPE_IMAG_TIME = 1
 DGPE_FP64 = 0
 DGPE_MIXED = 1
+DGPE_DF64 = 2   # double-float pairs on the FP32 pipe; complex128 at the boundary
 DGPE_HOST = 0
 DGPE_DEVICE = 1
 DGPE_SUB_POTENTIAL = 0
@@ -318,7 +319,7 @@ def dgpe_destroy(ctx):
 class Condensate:
     """One solver context on the current CUDA device and PyTorch's current stream.
 
-    psi arrays are [nx][ny][nz] complex128 (FP64) or complex64 (MIXED); numpy arrays are
+    psi arrays are [nx][ny][nz] complex128 (FP64, DF64) or complex64 (MIXED); numpy arrays are
     host memory, torch CUDA tensors device memory.
     """
 
@@ -330,9 +331,10 @@ class Condensate:
         self.shape = tuple(int(v) for v in shape)
         self.precision = precision
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        self.cdtype = torch.complex128 if precision == DGPE_FP64 else torch.complex64
-        self.rdtype = torch.float64 if precision == DGPE_FP64 else torch.float32
-        self.np_cdtype = np.complex128 if precision == DGPE_FP64 else np.complex64
+        wide = precision != DGPE_MIXED   # FP64 and double-float exchange complex128
+        self.cdtype = torch.complex128 if wide else torch.complex64
+        self.rdtype = torch.float64 if wide else torch.float32
+        self.np_cdtype = np.complex128 if wide else np.complex64
         self._params = make_params(shape, h, dt, mode, precision, nu, g, gdd, cutoff=cutoff,
                                    integration=integration, kinetic=kinetic)
         nbytes = dgpe_workspace_bytes(self._params)
@@ -399,7 +401,7 @@ class Condensate:
 
     def phi(self, host=True):
         if host:
-            out = np.empty(self.shape, dtype=np.float64 if self.precision == DGPE_FP64 else np.float32)
+            out = np.empty(self.shape, dtype=np.float32 if self.precision == DGPE_MIXED else np.float64)
             dgpe_get_phi(self.ctx, out.ctypes.data, DGPE_HOST)
             return out
         out = self._torch.empty(self.shape, dtype=self.rdtype, device=self.device)

@@ -1,6 +1,7 @@
 """Build the CUDA library libdgpe.so in-tree (nvcc, sm_103a only).
 
-The translation units (the C-ABI host code, one kernel set per precision, and the
+The translation units (the C-ABI host code, one kernel set per precision (FP64, FP32,
+double-float), and the
 allocation-free moments call) compile in parallel, then link into paper_1610_05329_gb300/_build/libdgpe.so with the CUDA runtime
 linked statically.  nvcc cross-compiles, so this also runs on a machine without a GPU.
 """
@@ -15,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdgpe.so")
-SOURCES = ["dgpe_api.cu", "kernels_f64.cu", "kernels_f32.cu", "dgpe_noalloc.cu"]
-HEADERS = ["dgpe_device.cuh", "dgpe_internal.h"]
+SOURCES = ["dgpe_api.cu", "kernels_f64.cu", "kernels_f32.cu", "kernels_df64.cu", "dgpe_noalloc.cu"]
+HEADERS = ["dgpe_device.cuh", "dgpe_internal.h", "dgpe_df64.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -102,7 +102,7 @@ int check_shape(const dgpe_params *p) {
     if (n < 4 || n > 512 || n % 2 != 0 || !is_2a3b5c7d(n)) return DGPE_EINVAL;
     if (cn_chunk(n) > kCnMaxChunk) return DGPE_EUNSUPPORTED;
   }
-  if (p->precision != DGPE_FP64 && p->precision != DGPE_MIXED) return DGPE_EINVAL;
+  if (p->precision != DGPE_FP64 && p->precision != DGPE_MIXED && p->precision != DGPE_DF64) return DGPE_EINVAL;
   return DGPE_OK;
 }
 
@@ -125,7 +125,7 @@ struct Layout {
 };
 
 Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
-  const size_t e = (size_t)(p->precision == DGPE_FP64 ? 16 : 8);
+  const size_t e = (size_t)(p->precision == DGPE_MIXED ? 8 : 16);
   const int n[3] = {p->nx, p->ny, p->nz};
   Layout L{};
   size_t off = 0;
@@ -151,14 +151,22 @@ Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
   off += align_up((size_t)p->nx * p->ny * p->nz * e);
   L.spec = off;
   off += align_up((size_t)(p->nz / 2 + 1) * p->nx * p->ny * e);
-  L.utab = off;   // FP64 only: the FP32 kernels evaluate the dipolar kernel in place
-  if (p->precision == DGPE_FP64) off += align_up((size_t)(p->nz / 2 + 1) * p->nx * p->ny * sizeof(double));
+  L.utab = off;   // FP64 and double-float (8-byte entries); the FP32 kernels evaluate it in place
+  if (p->precision != DGPE_MIXED) off += align_up((size_t)(p->nz / 2 + 1) * p->nx * p->ny * 8);
   L.total = off;
   (void)ks;
   return L;
 }
 
-const KernelSet *kernel_set(int precision) { return precision == DGPE_FP64 ? kernels_f64() : kernels_f32(); }
+const KernelSet *kernel_set(int precision) {
+  return precision == DGPE_FP64 ? kernels_f64() : precision == DGPE_DF64 ? kernels_df64() : kernels_f32();
+}
+
+// d = f + l: f its FP32 rounding, l = fl32(d - f) (the double-float pair of d)
+void split_df(double d, float *f, float *l) {
+  *f = (float)d;
+  *l = (float)(d - (double)*f);
+}
 
 KArgs base_args(const dgpe_params *p) {
   KArgs a{};
@@ -195,18 +203,18 @@ void set_physics(KArgs &a, const dgpe_params *p) {
   a.vy = 0.5 * p->nu[1] * p->nu[1];
   a.vz = 0.5 * p->nu[2] * p->nu[2];
   a.inv_ntot = 1.0 / ((double)p->nx * p->ny * p->nz);
-  a.inv_ntot_f = (float)a.inv_ntot;
+  split_df(a.inv_ntot, &a.inv_ntot_f, &a.inv_ntot_l);
   a.imag = p->mode == DGPE_IMAG_TIME;
   const double h[3] = {p->hx, p->hy, p->hz};
   for (int d = 0; d < 3; ++d) {
     a.cn_r[d] = p->dt / (4.0 * h[d] * h[d]);
-    a.cn_rf[d] = (float)a.cn_r[d];
+    split_df(a.cn_r[d], &a.cn_rf[d], &a.cn_rl[d]);
   }
   a.dt_nuz = p->dt * p->nu[2];
   a.dtg = p->dt * p->g;
   a.dtgdd_n = p->dt * p->gdd * a.inv_ntot;
-  a.dtg_f = (float)a.dtg;
-  a.dtgdd_n_f = (float)a.dtgdd_n;
+  split_df(a.dtg, &a.dtg_f, &a.dtg_l);
+  split_df(a.dtgdd_n, &a.dtgdd_n_f, &a.dtgdd_n_l);
 }
 
 thread_local char g_last_cuda_error[128] = "";
@@ -273,7 +281,7 @@ double kernel_bytes(const dgpe_ctx *c, int k) {
     case kK2FftY:
     case kK4IfftY: return 2 * e * nspec;
     // FP64 reads the dipolar kernel table (one real value per spectral point) as well
-    case kK3FftXDipolar: return 2 * e * nspec + (c->p.precision == DGPE_FP64 ? e / 2 * nspec : 0.0);
+    case kK3FftXDipolar: return 2 * e * nspec + (c->p.precision != DGPE_MIXED ? e / 2 * nspec : 0.0);
     case kK5C2RzPhaseCnz: return e * (nspec + 2 * ntot);
     case kK6CnY:
     case kK7CnXReduce:
@@ -415,6 +423,7 @@ KArgs adjoint_sweep_args(dgpe_ctx *c, void *gbar) {
     a.cn[d].tab = at(c, c->L.cn_adj[d]);
     a.cn_r[d] = -a.cn_r[d];
     a.cn_rf[d] = -a.cn_rf[d];
+    a.cn_rl[d] = -a.cn_rl[d];
   }
   return a;
 }
@@ -655,9 +664,19 @@ int dgpe_set_params(dgpe_ctx *c, const dgpe_params *p) {
 
 int dgpe_set_psi(dgpe_ctx *c, const void *psi, int where) {
   if (!c || !psi || (where != DGPE_HOST && where != DGPE_DEVICE)) return DGPE_EINVAL;
-  const size_t bytes = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;
-  int rc = map_cuda(cudaMemcpyAsync(c->args.psi, psi, bytes,
-                                    where == DGPE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+  const size_t n = (size_t)c->p.nx * c->p.ny * c->p.nz;
+  const size_t bytes = n * c->ks->elem_bytes;
+  int rc;
+  if (c->p.precision == DGPE_DF64) {
+    // complex128 in, double-float pairs (same 16 bytes per value) in the workspace: copy,
+    // then split in place
+    rc = map_cuda(cudaMemcpyAsync(c->args.psi, psi, bytes,
+                                  where == DGPE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    if (!rc) rc = map_cuda(c->ks->from_c128(c->args.psi, c->args.psi, n, c->stream));
+  } else {
+    rc = map_cuda(cudaMemcpyAsync(c->args.psi, psi, bytes,
+                                  where == DGPE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+  }
   if (!rc) rc = map_cuda(c->ks->reset_state(c->args.state, c->stream));
   if (!rc && where == DGPE_HOST) rc = map_cuda(cudaStreamSynchronize(c->stream));
   if (!rc) c->latched = DGPE_OK;
@@ -669,8 +688,22 @@ int dgpe_get_psi(dgpe_ctx *c, void *out, int where) {
   const size_t bytes = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;
   int rc = launch(c, c->stream, kKMaterialize, [&] { return c->ks->materialize(c->args, c->stream); });
   if (rc) return rc;
-  rc = map_cuda(cudaMemcpyAsync(out, c->args.psi, bytes,
-                                where == DGPE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+  if (c->p.precision == DGPE_DF64) {
+    // double-float pairs -> complex128, through a stream-ordered temporary for a host buffer
+    const size_t n = (size_t)c->p.nx * c->p.ny * c->p.nz;
+    if (where == DGPE_DEVICE) {
+      rc = map_cuda(c->ks->to_c128(c->args.psi, out, n, c->stream));
+    } else {
+      void *tmp = nullptr;
+      rc = map_cuda(cudaMallocAsync(&tmp, bytes, c->stream));
+      if (!rc) rc = map_cuda(c->ks->to_c128(c->args.psi, tmp, n, c->stream));
+      if (!rc) rc = map_cuda(cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, c->stream));
+      if (tmp) cudaFreeAsync(tmp, c->stream);
+    }
+  } else {
+    rc = map_cuda(cudaMemcpyAsync(out, c->args.psi, bytes,
+                                  where == DGPE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+  }
   if (rc) return rc;
   if (where == DGPE_HOST) {
     rc = map_cuda(cudaStreamSynchronize(c->stream));
@@ -765,7 +798,7 @@ int dgpe_get_phi(dgpe_ctx *c, void *out, int where) {
 
 int dgpe_adjoint_step(dgpe_ctx *c, const void *psi_k, void *gbar) {
   if (!c || !psi_k || !gbar) return DGPE_EINVAL;
-  if (c->p.mode != DGPE_REAL_TIME) return DGPE_EUNSUPPORTED;
+  if (c->p.mode != DGPE_REAL_TIME || c->p.precision == DGPE_DF64) return DGPE_EUNSUPPORTED;
   return enqueue_adjoint_step(c, psi_k, gbar, nullptr);
 }
 
@@ -787,7 +820,7 @@ int dgpe_grad_z2_workspace_bytes(const dgpe_ctx *c, int nseg, int steps_per_seg,
 int dgpe_grad_z2(dgpe_ctx *c, int nseg, int steps_per_seg, const double *nu_z, void *work, size_t work_bytes,
                  double *loss, double *dnu, double *dg, double *dgdd) {
   if (!c || !nu_z || !work || !loss || !dnu || !dg || !dgdd || nseg < 1 || steps_per_seg < 1) return DGPE_EINVAL;
-  if (c->p.mode != DGPE_REAL_TIME) return DGPE_EUNSUPPORTED;
+  if (c->p.mode != DGPE_REAL_TIME || c->p.precision == DGPE_DF64) return DGPE_EUNSUPPORTED;
   for (int s = 0; s < nseg; ++s)
     if (!isfinite(nu_z[s])) return DGPE_EINVAL;
   const GradLayout g = grad_layout(c, nseg, steps_per_seg);

@@ -1,14 +1,34 @@
 // Device code of the SSCN step: complex arithmetic, shared-memory Stockham FFT stages,
 // the chunked Thomas solver of the Crank-Nicolson sweeps, and the kernel templates.
-// Instantiated once per precision by kernels_f64.cu and kernels_f32.cu.
+// Instantiated once per real type by kernels_f64.cu (double), kernels_f32.cu (float) and
+// kernels_df64.cu (df, the double-float pair of dgpe_df64.cuh).
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <type_traits>
+
+#include "dgpe_df64.cuh"
 #include "dgpe_internal.h"
 
 namespace dgpe {
+
+// FP64-class real types (double and df) take the FP64 design choices: the dipolar kernel
+// from a table, FP64-accuracy copies of the scalars.
+template <typename R>
+struct Fp64Class {
+  static constexpr bool value = false;
+};
+template <>
+struct Fp64Class<double> {
+  static constexpr bool value = true;
+};
+template <>
+struct Fp64Class<df> {
+  static constexpr bool value = true;
+};
 
 // ---------------------------------------------------------------------------------------
 // Complex arithmetic
@@ -60,21 +80,13 @@ template <typename R>
 __device__ __forceinline__ cplx<R> cfma_c(cplx<R> c, cplx<R> v, cplx<R> d) {
   return {fma(-c.im, v.im, d.re), fma(c.im, v.re, d.im)};
 }
-template <typename T>
-__device__ __forceinline__ T coef_one();
-template <>
-__device__ __forceinline__ double coef_one<double>() { return 1.0; }
-template <>
-__device__ __forceinline__ float coef_one<float>() { return 1.0f; }
-template <>
-__device__ __forceinline__ cplx<double> coef_one<cplx<double>>() { return {1.0, 0.0}; }
-template <>
-__device__ __forceinline__ cplx<float> coef_one<cplx<float>>() { return {1.0f, 0.0f}; }
 
 __device__ __forceinline__ double shfl_up(double v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
 __device__ __forceinline__ float shfl_up(float v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
 __device__ __forceinline__ double shfl_down(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
 __device__ __forceinline__ float shfl_down(float v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ df shfl_up(df v, int d) { return {shfl_up(v.hi, d), shfl_up(v.lo, d)}; }
+__device__ __forceinline__ df shfl_down(df v, int d) { return {shfl_down(v.hi, d), shfl_down(v.lo, d)}; }
 template <typename R>
 __device__ __forceinline__ cplx<R> shfl_up(cplx<R> v, int d) { return {shfl_up(v.re, d), shfl_up(v.im, d)}; }
 template <typename R>
@@ -192,6 +204,16 @@ __device__ __forceinline__ cplx<float> ldg(const cplx<float> *p) {
   float2 v = __ldg(reinterpret_cast<const float2 *>(p));
   return {v.x, v.y};
 }
+template <>
+__device__ __forceinline__ df ldg(const df *p) {
+  float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+  return {v.x, v.y};
+}
+template <>
+__device__ __forceinline__ cplx<df> ldg(const cplx<df> *p) {
+  float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  return {df{v.x, v.y}, df{v.z, v.w}};
+}
 
 // ---------------------------------------------------------------------------------------
 // Tile shapes per precision.  Rows of strided tiles are 128 B (8 complex128 or 16
@@ -209,6 +231,8 @@ struct Tiles<double> {
   static constexpr int kCnThreads = 128;  // 4 warps, two lines per warp
   static constexpr int kYBudget = 1024;   // K2/K4: lines per CTA ~ budget / ny
 };
+template <>
+struct Tiles<df> : Tiles<double> {};   // the same 16-byte complex values
 template <>
 struct Tiles<float> {
   static constexpr int kZLines = 16;
@@ -678,29 +702,37 @@ struct CnCoef<R, cplx<R>> {
   __device__ static cplx<R> make(R r) { return {R(0), r}; }
 };
 
-// A host-precomputed constant in the kernel precision (no FP64 work per thread in FP32).
+// A host-precomputed constant in the kernel precision (no FP64 work per thread in FP32 and
+// double-float): the double d, its FP32 rounding f and the FP32 remainder l = fl32(d - f).
 template <typename R>
-__device__ __forceinline__ R pick(double d, float f);
+__device__ __forceinline__ R pick(double d, float f, float l);
 template <>
-__device__ __forceinline__ double pick<double>(double d, float) { return d; }
+__device__ __forceinline__ double pick<double>(double d, float, float) { return d; }
 template <>
-__device__ __forceinline__ float pick<float>(double, float f) { return f; }
+__device__ __forceinline__ float pick<float>(double, float f, float) { return f; }
+template <>
+__device__ __forceinline__ df pick<df>(double, float f, float l) { return {f, l}; }
 
 // The pending renormalisation factor s of the device state (and s^2) in the kernel
 // precision; the FP32 kernels read the FP32 copies, so they issue no FP64 instruction.
 __device__ __forceinline__ void set_scale(DevState *st, double s) {
   st->s = s;
   st->sf = (float)s;
-  st->s2f = (float)(s * s);
+  st->sl = (float)(s - (double)st->sf);
+  const double s2 = s * s;
+  st->s2f = (float)s2;
+  st->s2l = (float)(s2 - (double)st->s2f);
 }
 template <typename R>
 __device__ __forceinline__ R scale_of(const DevState *st) {
-  if constexpr (sizeof(R) == 8) return st->s;
+  if constexpr (std::is_same<R, double>::value) return st->s;
+  else if constexpr (std::is_same<R, df>::value) return df{st->sf, st->sl};
   else return st->sf;
 }
 template <typename R>
 __device__ __forceinline__ R scale_sq_of(const DevState *st) {
-  if constexpr (sizeof(R) == 8) return st->s * st->s;
+  if constexpr (std::is_same<R, double>::value) return st->s * st->s;
+  else if constexpr (std::is_same<R, df>::value) return df{st->s2f, st->s2l};
   else return st->s2f;
 }
 
@@ -935,6 +967,24 @@ __global__ void k_dipolar_table(R *ut, KArgs a) {
   }
 }
 
+// Double-float boundary: complex128 values split into (hi, lo) pairs (in place allowed:
+// each thread reads its 16 bytes before writing them), and pairs summed back to complex128
+// (after the pending renormalisation has been applied by k_materialize).
+template <typename R>
+__global__ void k_c128_to_pair(const double2 *src, cplx<R> *psi, size_t n) {
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = src[q];
+    psi[q] = {R(v.x), R(v.y)};
+  }
+}
+template <typename R>
+__global__ void k_pair_to_c128(const cplx<R> *psi, double2 *dst, size_t n) {
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const cplx<R> v = psi[q];
+    dst[q] = make_double2((double)v.re, (double)v.im);
+  }
+}
+
 template <typename R>
 __global__ void k_reset_state(DevState *st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -1065,8 +1115,9 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
   C *res = fft_lines_n<R, -1, N, BX, SB, kFftThreads>(za, zb, a.plan[0], nb, tw);
   const int b = threadIdx.x % BX;
   if (b < nb) {
-    if constexpr (sizeof(R) == 8) {
-      // FP64: the table (its FP64 division and cutoff factor would cost more than the read)
+    if constexpr (Fp64Class<R>::value) {
+      // FP64 (and double-float): the table (the division and the cutoff factor would cost
+      // more than the read)
       const R *ut = reinterpret_cast<const R *>(a.utab) + (size_t)m * a.nx * a.ny + j0;
       for (int k = threadIdx.x / BX; k < n; k += blockDim.x / BX)
         res[k * SB + b] = scale(res[k * SB + b], ldg(ut + (size_t)k * a.ny + b));
@@ -1119,7 +1170,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R
   C *zb = za + nz * SB;
   C *tile = zb + nz * SB;
   const R s = scale_of<R>(a.state);
-  const R inv_ntot = pick<R>(a.inv_ntot, a.inv_ntot_f);
+  const R inv_ntot = pick<R>(a.inv_ntot, a.inv_ntot_f, a.inv_ntot_l);
   const size_t line0 = (size_t)i * a.ny + j0;
   C *psi = reinterpret_cast<C *>(a.psi) + line0 * nz;
   const C *res = nullptr;
@@ -1175,11 +1226,13 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R
   }
 
   if (zmode == kZPhi) {
-    R *out = reinterpret_cast<R *>(a.out) + line0 * nz;
+    // Phi in the kernel precision; double for double-float
+    using O = typename std::conditional<std::is_same<R, df>::value, double, R>::type;
+    O *out = reinterpret_cast<O *>(a.out) + line0 * nz;
     LinePos pos(threadIdx.x, nz, blockDim.x);
     for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
       const C z = res[pos.k * SB + (pos.b >> 1)];
-      out[e] = ((pos.b & 1) ? z.im : z.re) * inv_ntot;
+      out[e] = O(((pos.b & 1) ? z.im : z.re) * inv_ntot);
     }
     return;
   }
@@ -1213,7 +1266,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R
                            (zm.re - R(2) * c.re + zp.re) * ihz2,
                        (xm.im - R(2) * c.im + xp.im) * ihx2 + (ym.im - R(2) * c.im + yp.im) * ihy2 +
                            (zm.im - R(2) * c.im + zp.im) * ihz2};
-        ekin = -0.5 * ((double)c.re * lap.re + (double)c.im * lap.im);
+        ekin = -0.5 * ((double)c.re * (double)lap.re + (double)c.im * (double)lap.im);
       } else {
         // 4th-order first derivatives (f(-2) - 8 f(-1) + 8 f(1) - f(2)) / (12 h), zero outside
         const C zm2 = n > 1 ? scale(row[cn_slot(n - 2, lc)], sr) : czero<R>();
@@ -1224,15 +1277,15 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R
         const C xp2 = i < a.nx - 2 ? scale(gpsi[q + 2 * sx], sr) : czero<R>();
         auto d1 = [](C m2, C m1, C p1, C p2, double h) {
           const double f = 1.0 / (12.0 * h);
-          const double re = ((double)m2.re - 8.0 * m1.re + 8.0 * p1.re - p2.re) * f;
-          const double im = ((double)m2.im - 8.0 * m1.im + 8.0 * p1.im - p2.im) * f;
+          const double re = ((double)m2.re - 8.0 * (double)m1.re + 8.0 * (double)p1.re - (double)p2.re) * f;
+          const double im = ((double)m2.im - 8.0 * (double)m1.im + 8.0 * (double)p1.im - (double)p2.im) * f;
           return re * re + im * im;
         };
         ekin = 0.5 * (d1(xm2, xm, xp, xp2, a.hx) + d1(ym2, ym, yp, yp2, a.hy) + d1(zm2, zm, zp, zp2, a.hz));
       }
       const C z = res[n * SB + (b >> 1)];
       const double phi = (double)(((b & 1) ? z.im : z.re) * inv_ntot);
-      const double dens = (double)c.re * c.re + (double)c.im * c.im;
+      const double dens = (double)c.re * (double)c.re + (double)c.im * (double)c.im;
       const double y = coordinate(j, a.ny, a.hy), zc = coordinate(n, nz, a.hz);
       const double w = wxi * quad_weight(j, a.ny, a.simpson) * quad_weight(n, nz, a.simpson);
       v[0] += w * dens;
@@ -1280,7 +1333,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R
     __syncthreads();
     const R sr = R(s);
     const bool scaled = s != R(1);
-    const R dtg = pick<R>(a.dtg, a.dtg_f), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f);
+    const R dtg = pick<R>(a.dtg, a.dtg_f, a.dtg_l), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f, a.dtgdd_n_l);
     // lines fastest: the padded tile rows (odd stride LS) and the pair-interleaved Phi are
     // read without bank conflicts
     LinePos pos(threadIdx.x, nl, blockDim.x);   // pos.b = z index n, pos.k = line b
@@ -1305,7 +1358,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R
   }
 
   if (zmode == kZStep || zmode == kZCnOnly) {
-    const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[2], a.cn_rf[2]));
+    const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[2], a.cn_rf[2], a.cn_rl[2]));
     const Coef *tab = reinterpret_cast<const Coef *>(a.cn[2].tab);
     for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp)
       cn_line_any<R, Coef, false>(tile + b * LS, 1, a.cn[2].m, lc, tab, scan_s, c);
@@ -1337,6 +1390,12 @@ struct SumAcc<double> {
 };
 template <>
 struct SumAcc<float> : DFAcc {};
+template <>
+struct SumAcc<df> {
+  df v{0.0f, 0.0f};
+  __device__ __forceinline__ void add(df t) { v = v + t; }
+  __device__ __forceinline__ double value() const { return (double)v; }
+};
 
 // Persistent, double-buffered: each CTA walks the tiles (fixed index, k-tile)
 // blockIdx.x, blockIdx.x + gridDim.x, ...; the cp.async copies of the next tile are in
@@ -1386,7 +1445,7 @@ __global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce
       x2tab[n] = R(x * x);
       wxtab[n] = R(quad_weight(n, a.nx, a.simpson));
     }
-  const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[AXIS], a.cn_rf[AXIS]));
+  const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[AXIS], a.cn_rf[AXIS], a.cn_rl[AXIS]));
   {
     const Coef *gtab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
     for (int q = threadIdx.x; q < ntab; q += blockDim.x) stab[q] = gtab[q];
@@ -1481,6 +1540,16 @@ struct AdjSums<double> {
   __device__ __forceinline__ double get(int q) const { return v[q]; }
 };
 template <>
+struct AdjSums<df> {
+  df v[3] = {df{0.0f, 0.0f}, df{0.0f, 0.0f}, df{0.0f, 0.0f}};
+  __device__ __forceinline__ void add(df sg, df sdd, df snu) {
+    v[0] = v[0] + sg;
+    v[1] = v[1] + sdd;
+    v[2] = v[2] + snu;
+  }
+  __device__ __forceinline__ double get(int q) const { return (double)v[q]; }
+};
+template <>
 struct AdjSums<float> {
   DFAcc v[3];
   __device__ __forceinline__ void add(float sg, float sdd, float snu) {
@@ -1570,8 +1639,8 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_phase(KArgs a) {
   C *sbuf = (res == za) ? zb : za;
   cp_async_wait_all();
   __syncthreads();
-  const R dtg = pick<R>(a.dtg, a.dtg_f), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f);
-  const R inv_ntot = pick<R>(a.inv_ntot, a.inv_ntot_f);
+  const R dtg = pick<R>(a.dtg, a.dtg_f, a.dtg_l), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f, a.dtgdd_n_l);
+  const R inv_ntot = pick<R>(a.inv_ntot, a.inv_ntot_f, a.inv_ntot_l);
   AdjSums<R> acc;
   LinePos pos(threadIdx.x, nz, blockDim.x);
   for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
@@ -1628,7 +1697,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_combine(KArgs a) {
   const C *res = fft_lines<R, +1>(za, zb, a.plan[2], PZ, np, SB, reinterpret_cast<const C *>(a.tw[2]));
   cp_async_wait_all();
   __syncthreads();
-  const R dtg = pick<R>(a.dtg, a.dtg_f), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f);
+  const R dtg = pick<R>(a.dtg, a.dtg_f, a.dtg_l), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f, a.dtgdd_n_l);
   LinePos pos(threadIdx.x, nz, blockDim.x);
   for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
     const int b = pos.b, n = pos.k;
@@ -1686,6 +1755,9 @@ struct Impl {
   using C = cplx<R>;
   using T = Tiles<R>;
   static constexpr size_t E = sizeof(C);
+  // compile-time transforms of lengths 128-512 (not for double-float, whose kernels take
+  // many times longer to compile)
+  static constexpr bool kCtSizes = !std::is_same<R, df>::value;
 
   static size_t smem_z_fft(const KArgs &a) { return 2 * (size_t)a.nz * (T::kZLines / 2 + 1) * E; }
   static size_t smem_k5(const KArgs &a) {
@@ -1740,45 +1812,47 @@ struct Impl {
       if (e == cudaSuccess) e = r;
     };
     chk(allow_smem(k1_density_r2cz<R, 0>));
-    chk(allow_smem(k1_density_r2cz<R, 512>));
-    chk(allow_smem(k1_density_r2cz<R, 384>));
-    chk(allow_smem(k1_density_r2cz<R, 256>));
-    chk(allow_smem(k1_density_r2cz<R, 128>));
     chk(allow_smem(k_ffty<R, -1, 0>));
     chk(allow_smem(k_ffty<R, +1, 0>));
-    chk(allow_smem(k_ffty<R, -1, 512>));
-    chk(allow_smem(k_ffty<R, +1, 512>));
-    chk(allow_smem(k_ffty<R, -1, 384>));
-    chk(allow_smem(k_ffty<R, +1, 384>));
-    chk(allow_smem(k_ffty<R, -1, 256>));
-    chk(allow_smem(k_ffty<R, +1, 256>));
-    chk(allow_smem(k_ffty<R, -1, 128>));
-    chk(allow_smem(k_ffty<R, +1, 128>));
     chk(allow_smem(k3_fftx_dipolar<R, 0>));
-    chk(allow_smem(k3_fftx_dipolar<R, 512>));
-    chk(allow_smem(k3_fftx_dipolar<R, 384>));
-    chk(allow_smem(k3_fftx_dipolar<R, 256>));
-    chk(allow_smem(k3_fftx_dipolar<R, 128>));
     chk(allow_smem(k5_zline<R, R, kZStep, 0>));
     chk(allow_smem(k5_zline<R, C, kZStep, 0>));
-    chk(allow_smem(k5_zline<R, R, kZStep, 512>));
-    chk(allow_smem(k5_zline<R, C, kZStep, 512>));
-    chk(allow_smem(k5_zline<R, R, kZStep, 384>));
-    chk(allow_smem(k5_zline<R, C, kZStep, 384>));
-    chk(allow_smem(k5_zline<R, R, kZStep, 256>));
-    chk(allow_smem(k5_zline<R, C, kZStep, 256>));
     chk(allow_smem(k5_zline<R, R, kZPhaseOnly, 0>));
     chk(allow_smem(k5_zline<R, C, kZPhaseOnly, 0>));
     chk(allow_smem(k5_zline<R, R, kZCnOnly, 0>));
     chk(allow_smem(k5_zline<R, C, kZCnOnly, 0>));
     chk(allow_smem(k5_zline<R, R, kZPhi, 0>));
     chk(allow_smem(k5_zline<R, R, kZObs, 0>));
+    if constexpr (kCtSizes) {
+      chk(allow_smem(k1_density_r2cz<R, 512>));
+      chk(allow_smem(k1_density_r2cz<R, 384>));
+      chk(allow_smem(k1_density_r2cz<R, 256>));
+      chk(allow_smem(k1_density_r2cz<R, 128>));
+      chk(allow_smem(k_ffty<R, -1, 512>));
+      chk(allow_smem(k_ffty<R, +1, 512>));
+      chk(allow_smem(k_ffty<R, -1, 384>));
+      chk(allow_smem(k_ffty<R, +1, 384>));
+      chk(allow_smem(k_ffty<R, -1, 256>));
+      chk(allow_smem(k_ffty<R, +1, 256>));
+      chk(allow_smem(k_ffty<R, -1, 128>));
+      chk(allow_smem(k_ffty<R, +1, 128>));
+      chk(allow_smem(k3_fftx_dipolar<R, 512>));
+      chk(allow_smem(k3_fftx_dipolar<R, 384>));
+      chk(allow_smem(k3_fftx_dipolar<R, 256>));
+      chk(allow_smem(k3_fftx_dipolar<R, 128>));
+      chk(allow_smem(k5_zline<R, R, kZStep, 512>));
+      chk(allow_smem(k5_zline<R, C, kZStep, 512>));
+      chk(allow_smem(k5_zline<R, R, kZStep, 384>));
+      chk(allow_smem(k5_zline<R, C, kZStep, 384>));
+      chk(allow_smem(k5_zline<R, R, kZStep, 256>));
+      chk(allow_smem(k5_zline<R, C, kZStep, 256>));
+    }
     chk(allow_smem(k_cn<R, R, 0>));
     chk(allow_smem(k_cn<R, R, 1>));
     chk(allow_smem(k_cn<R, C, 0>));
     chk(allow_smem(k_cn<R, C, 1>));
-    chk(allow_smem(k5_adj_phase<R>));
-    chk(allow_smem(k5_adj_combine<R>));
+    if constexpr (kAdjoint) chk(allow_smem(k5_adj_phase<R>));
+    if constexpr (kAdjoint) chk(allow_smem(k5_adj_combine<R>));
     return e;
   }
 
@@ -1799,12 +1873,31 @@ struct Impl {
   }
 
   static cudaError_t dipolar_table(const KArgs &a, cudaStream_t st) {
-    if (sizeof(R) != 8) return cudaSuccess;   // FP32 evaluates the kernel in K3
+    if (!Fp64Class<R>::value) return cudaSuccess;   // FP32 evaluates the kernel in K3
     const size_t total = (size_t)a.nzh * a.nx * a.ny;
     const size_t want = (total + 255) / 256, cap = (size_t)sm_count() * 8;
     const int blocks = (int)(want < cap ? want : cap);
     k_dipolar_table<R><<<blocks, 256, 0, st>>>(reinterpret_cast<R *>(const_cast<void *>(a.utab)), a);
     return cudaGetLastError();
+  }
+
+  static cudaError_t from_c128(const void *src, void *psi, size_t n, cudaStream_t st) {
+    if constexpr (!std::is_same<R, df>::value) {
+      return cudaErrorNotSupported;
+    } else {
+      const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)sm_count() * 16);
+      k_c128_to_pair<R><<<blocks, 256, 0, st>>>(static_cast<const double2 *>(src), static_cast<C *>(psi), n);
+      return cudaGetLastError();
+    }
+  }
+  static cudaError_t to_c128(const void *psi, void *dst, size_t n, cudaStream_t st) {
+    if constexpr (!std::is_same<R, df>::value) {
+      return cudaErrorNotSupported;
+    } else {
+      const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)sm_count() * 16);
+      k_pair_to_c128<R><<<blocks, 256, 0, st>>>(static_cast<const C *>(psi), static_cast<double2 *>(dst), n);
+      return cudaGetLastError();
+    }
   }
 
   static cudaError_t reset_state(DevState *s, cudaStream_t st) {
@@ -1825,11 +1918,15 @@ struct Impl {
   static cudaError_t k1(const KArgs &a, cudaStream_t st) {
     const dim3 g = grid_z(a);
     const size_t sm = smem_z_fft(a);
-    if (plan_ct(a.plan[2], 512)) k1_density_r2cz<R, 512><<<g, T::kZThreads, sm, st>>>(a);
-    else if (plan_ct(a.plan[2], 384)) k1_density_r2cz<R, 384><<<g, T::kZThreads, sm, st>>>(a);
-    else if (plan_ct(a.plan[2], 256)) k1_density_r2cz<R, 256><<<g, T::kZThreads, sm, st>>>(a);
-    else if (plan_ct(a.plan[2], 128)) k1_density_r2cz<R, 128><<<g, T::kZThreads, sm, st>>>(a);
-    else k1_density_r2cz<R, 0><<<g, T::kZThreads, sm, st>>>(a);
+    if constexpr (kCtSizes) {
+      if (plan_ct(a.plan[2], 512)) k1_density_r2cz<R, 512><<<g, T::kZThreads, sm, st>>>(a);
+      else if (plan_ct(a.plan[2], 384)) k1_density_r2cz<R, 384><<<g, T::kZThreads, sm, st>>>(a);
+      else if (plan_ct(a.plan[2], 256)) k1_density_r2cz<R, 256><<<g, T::kZThreads, sm, st>>>(a);
+      else if (plan_ct(a.plan[2], 128)) k1_density_r2cz<R, 128><<<g, T::kZThreads, sm, st>>>(a);
+      else k1_density_r2cz<R, 0><<<g, T::kZThreads, sm, st>>>(a);
+    } else {
+      k1_density_r2cz<R, 0><<<g, T::kZThreads, sm, st>>>(a);
+    }
     return cudaGetLastError();
   }
   // the compile-time transform applies when the y plan, lines per CTA and block size are
@@ -1843,11 +1940,15 @@ struct Impl {
     const int L = a.ylines;
     const dim3 g((unsigned)((lines + L - 1) / L));
     const size_t sm = smem_y(a);
-    if (y_fixed(a, 512)) k_ffty<R, DIR, 512><<<g, kFftThreads, sm, st>>>(a);
-    else if (y_fixed(a, 384)) k_ffty<R, DIR, 384><<<g, kFftThreads, sm, st>>>(a);
-    else if (y_fixed(a, 256)) k_ffty<R, DIR, 256><<<g, kFftThreads, sm, st>>>(a);
-    else if (y_fixed(a, 128)) k_ffty<R, DIR, 128><<<g, kFftThreads, sm, st>>>(a);
-    else k_ffty<R, DIR, 0><<<g, a.fft_threads, sm, st>>>(a);
+    if constexpr (kCtSizes) {
+      if (y_fixed(a, 512)) k_ffty<R, DIR, 512><<<g, kFftThreads, sm, st>>>(a);
+      else if (y_fixed(a, 384)) k_ffty<R, DIR, 384><<<g, kFftThreads, sm, st>>>(a);
+      else if (y_fixed(a, 256)) k_ffty<R, DIR, 256><<<g, kFftThreads, sm, st>>>(a);
+      else if (y_fixed(a, 128)) k_ffty<R, DIR, 128><<<g, kFftThreads, sm, st>>>(a);
+      else k_ffty<R, DIR, 0><<<g, a.fft_threads, sm, st>>>(a);
+    } else {
+      k_ffty<R, DIR, 0><<<g, a.fft_threads, sm, st>>>(a);
+    }
     return cudaGetLastError();
   }
   static cudaError_t k2(const KArgs &a, cudaStream_t st) { return ffty<-1>(a, st); }
@@ -1855,11 +1956,15 @@ struct Impl {
     dim3 grid((a.ny + T::kXCols - 1) / T::kXCols, a.nzh);
     const size_t sm = smem_x(a);
     const bool fixed = a.fft_threads == kFftThreads;
-    if (fixed && plan_ct(a.plan[0], 512)) k3_fftx_dipolar<R, 512><<<grid, kFftThreads, sm, st>>>(a);
-    else if (fixed && plan_ct(a.plan[0], 384)) k3_fftx_dipolar<R, 384><<<grid, kFftThreads, sm, st>>>(a);
-    else if (fixed && plan_ct(a.plan[0], 256)) k3_fftx_dipolar<R, 256><<<grid, kFftThreads, sm, st>>>(a);
-    else if (fixed && plan_ct(a.plan[0], 128)) k3_fftx_dipolar<R, 128><<<grid, kFftThreads, sm, st>>>(a);
-    else k3_fftx_dipolar<R, 0><<<grid, a.fft_threads, sm, st>>>(a);
+    if constexpr (kCtSizes) {
+      if (fixed && plan_ct(a.plan[0], 512)) k3_fftx_dipolar<R, 512><<<grid, kFftThreads, sm, st>>>(a);
+      else if (fixed && plan_ct(a.plan[0], 384)) k3_fftx_dipolar<R, 384><<<grid, kFftThreads, sm, st>>>(a);
+      else if (fixed && plan_ct(a.plan[0], 256)) k3_fftx_dipolar<R, 256><<<grid, kFftThreads, sm, st>>>(a);
+      else if (fixed && plan_ct(a.plan[0], 128)) k3_fftx_dipolar<R, 128><<<grid, kFftThreads, sm, st>>>(a);
+      else k3_fftx_dipolar<R, 0><<<grid, a.fft_threads, sm, st>>>(a);
+    } else {
+      k3_fftx_dipolar<R, 0><<<grid, a.fft_threads, sm, st>>>(a);
+    }
     return cudaGetLastError();
   }
   static cudaError_t k4(const KArgs &a, cudaStream_t st) { return ffty<+1>(a, st); }
@@ -1868,15 +1973,20 @@ struct Impl {
     const size_t sm = smem_k5(a);
     switch (zmode) {
       case kZStep:
-        if (a.imag) {
-          if (plan_ct(a.plan[2], 512)) k5_zline<R, R, kZStep, 512><<<g, T::kZThreads, sm, st>>>(a);
-          else if (plan_ct(a.plan[2], 384)) k5_zline<R, R, kZStep, 384><<<g, T::kZThreads, sm, st>>>(a);
-          else if (plan_ct(a.plan[2], 256)) k5_zline<R, R, kZStep, 256><<<g, T::kZThreads, sm, st>>>(a);
-          else k5_zline<R, R, kZStep, 0><<<g, T::kZThreads, sm, st>>>(a);
+        if constexpr (kCtSizes) {
+          if (a.imag) {
+            if (plan_ct(a.plan[2], 512)) k5_zline<R, R, kZStep, 512><<<g, T::kZThreads, sm, st>>>(a);
+            else if (plan_ct(a.plan[2], 384)) k5_zline<R, R, kZStep, 384><<<g, T::kZThreads, sm, st>>>(a);
+            else if (plan_ct(a.plan[2], 256)) k5_zline<R, R, kZStep, 256><<<g, T::kZThreads, sm, st>>>(a);
+            else k5_zline<R, R, kZStep, 0><<<g, T::kZThreads, sm, st>>>(a);
+          } else {
+            if (plan_ct(a.plan[2], 512)) k5_zline<R, C, kZStep, 512><<<g, T::kZThreads, sm, st>>>(a);
+            else if (plan_ct(a.plan[2], 384)) k5_zline<R, C, kZStep, 384><<<g, T::kZThreads, sm, st>>>(a);
+            else if (plan_ct(a.plan[2], 256)) k5_zline<R, C, kZStep, 256><<<g, T::kZThreads, sm, st>>>(a);
+            else k5_zline<R, C, kZStep, 0><<<g, T::kZThreads, sm, st>>>(a);
+          }
         } else {
-          if (plan_ct(a.plan[2], 512)) k5_zline<R, C, kZStep, 512><<<g, T::kZThreads, sm, st>>>(a);
-          else if (plan_ct(a.plan[2], 384)) k5_zline<R, C, kZStep, 384><<<g, T::kZThreads, sm, st>>>(a);
-          else if (plan_ct(a.plan[2], 256)) k5_zline<R, C, kZStep, 256><<<g, T::kZThreads, sm, st>>>(a);
+          if (a.imag) k5_zline<R, R, kZStep, 0><<<g, T::kZThreads, sm, st>>>(a);
           else k5_zline<R, C, kZStep, 0><<<g, T::kZThreads, sm, st>>>(a);
         }
         break;
@@ -1917,20 +2027,34 @@ struct Impl {
   static size_t smem_adj(const KArgs &a) {
     return smem_z_fft(a) + 2 * (size_t)T::kZLines * a.nz * E + (size_t)(2 * a.nz + T::kZLines) * sizeof(R);
   }
+  // the differentiation kernels exist for FP64 and FP32 only
+  static constexpr bool kAdjoint = !std::is_same<R, df>::value;
   static cudaError_t adj_phase(const KArgs &a, cudaStream_t st) {
-    k5_adj_phase<R><<<grid_z(a), T::kZThreads, smem_adj(a), st>>>(a);
-    return cudaGetLastError();
+    if constexpr (!kAdjoint) {
+      return cudaErrorNotSupported;
+    } else {
+      k5_adj_phase<R><<<grid_z(a), T::kZThreads, smem_adj(a), st>>>(a);
+      return cudaGetLastError();
+    }
   }
   static cudaError_t adj_combine(const KArgs &a, cudaStream_t st) {
-    k5_adj_combine<R><<<grid_z(a), T::kZThreads, smem_adj(a), st>>>(a);
-    return cudaGetLastError();
+    if constexpr (!kAdjoint) {
+      return cudaErrorNotSupported;
+    } else {
+      k5_adj_combine<R><<<grid_z(a), T::kZThreads, smem_adj(a), st>>>(a);
+      return cudaGetLastError();
+    }
   }
   static cudaError_t loss_z2(const KArgs &a, cudaStream_t st) {
-    const size_t count = (size_t)a.nx * a.ny * a.nz;
-    size_t blocks = (count + 255) / 256;
-    if (blocks > 8192) blocks = 8192;
-    k_loss_z2<R><<<(unsigned)blocks, 256, 0, st>>>(a, count);
-    return cudaGetLastError();
+    if constexpr (!kAdjoint) {
+      return cudaErrorNotSupported;
+    } else {
+      const size_t count = (size_t)a.nx * a.ny * a.nz;
+      size_t blocks = (count + 255) / 256;
+      if (blocks > 8192) blocks = 8192;
+      k_loss_z2<R><<<(unsigned)blocks, 256, 0, st>>>(a, count);
+      return cudaGetLastError();
+    }
   }
 
   static int default_ylines(int ny) { return y_lines_per_cta<R>(ny); }
@@ -1944,7 +2068,7 @@ struct Impl {
   }
 
   static const KernelSet *set() {
-    static const KernelSet ks = {(int)E, &init,          &twiddles,   &cn_tables, &axis_potential, &dipolar_table, &reset_state,
+    static const KernelSet ks = {(int)E, &init,          &twiddles,   &cn_tables, &axis_potential, &dipolar_table, &from_c128, &to_c128, &reset_state,
                                  &k1,        &k2,            &k3,         &k4,        &k5,             &k6,
                                  &k7,        &materialize,   &adj_phase,  &adj_combine, &loss_z2,
                                  &max_blocks, &default_ylines, &y_smem};

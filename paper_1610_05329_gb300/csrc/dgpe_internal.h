@@ -37,6 +37,7 @@ struct CnTab {
 struct DevState {
   double s;          // pending renormalisation factor: the state is s * psi_buf
   float sf, s2f;     // s and s^2 rounded to FP32 (read by the FP32 kernels)
+  float sl, s2l;     // the FP32 remainders: (sf, sl) and (s2f, s2l) are double-float pairs
   double norm;       // hx hy hz sum |psi_buf|^2 after the last full step
   double sums[8];    // last reduction (step: n, x^2 n, y^2 n, z^2 n; obs: 8 terms)
   double obs[12];    // observables of the last dgpe_observables call
@@ -59,12 +60,12 @@ struct KArgs {
   int kinetic5;                // 1: kinetic energy from the 5-point gradient
   double vx, vy, vz;           // 0.5 * nu_d^2
   double inv_ntot;             // 1 / (nx ny nz)
-  float inv_ntot_f;
+  float inv_ntot_f, inv_ntot_l;   // FP32 rounding and remainder (the double-float pair)
   int imag;                    // 1 = imaginary time
   double cn_r[3];              // dt / (4 h_d^2), the Crank-Nicolson coefficient magnitude
-  float cn_rf[3];
+  float cn_rf[3], cn_rl[3];
   double dtg, dtgdd_n;         // dt g and dt gdd / (nx ny nz) (Phi's 1/N folded in)
-  float dtg_f, dtgdd_n_f;
+  float dtg_f, dtgdd_n_f, dtg_l, dtgdd_n_l;
   const void *dtv[3];          // dt v_d x_i^2 per axis (kernel precision)
   void *psi;                   // [nx][ny][nz] complex
   void *spec;                  // [nzh][nx][ny] complex, the z-half-spectrum-major layout
@@ -120,6 +121,10 @@ struct KernelSet {
   cudaError_t (*cn_tables)(void *tab, int m, int chunk, double r, int imag, cudaStream_t st);
   cudaError_t (*axis_potential)(void *out, int n, double h, double v, double dt, cudaStream_t st);
   cudaError_t (*dipolar_table)(const KArgs &a, cudaStream_t st);   // fills utab
+  // double-float only: complex128 -> the kernels' pairs (in place allowed), and back with the
+  // pending renormalisation applied
+  cudaError_t (*from_c128)(const void *src, void *psi, size_t n, cudaStream_t st);
+  cudaError_t (*to_c128)(const void *psi, void *dst, size_t n, cudaStream_t st);
   cudaError_t (*reset_state)(DevState *st_ptr, cudaStream_t st);
   cudaError_t (*k1)(const KArgs &a, cudaStream_t st);
   cudaError_t (*k2)(const KArgs &a, cudaStream_t st);   // forward FFT along y
@@ -139,5 +144,6 @@ struct KernelSet {
 
 const KernelSet *kernels_f64();
 const KernelSet *kernels_f32();
+const KernelSet *kernels_df64();
 
 }  // namespace dgpe

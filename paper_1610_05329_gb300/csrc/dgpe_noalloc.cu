@@ -89,7 +89,7 @@ extern "C" int dgpe_moments_noalloc(const void *psi, const dgpe_params *p, doubl
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return DGPE_EINVAL;
   if (!(p->hx > 0 && p->hy > 0 && p->hz > 0) || !isfinite(p->hx) || !isfinite(p->hy) || !isfinite(p->hz))
     return DGPE_EINVAL;
-  if (p->precision != DGPE_FP64 && p->precision != DGPE_MIXED) return DGPE_EINVAL;
+  if (p->precision != DGPE_FP64 && p->precision != DGPE_MIXED && p->precision != DGPE_DF64) return DGPE_EINVAL;
   const long long npts = (long long)p->nx * p->ny * p->nz;
   if (npts > kNoAllocMaxPoints) return DGPE_EUNSUPPORTED;   // beyond the fixed scratch
   NoAllocScratch *scr = nullptr;
@@ -99,7 +99,7 @@ extern "C" int dgpe_moments_noalloc(const void *psi, const dgpe_params *p, doubl
   // the counter must start at zero (a reduction that was cut short may have left it set)
   if (cudaMemsetAsync(&scr->ticket, 0, sizeof(unsigned int), st) != cudaSuccess) return DGPE_ECUDA;
   const unsigned blocks = (unsigned)((npts + kNoAllocPointsPerBlock - 1) / kNoAllocPointsPerBlock);
-  if (p->precision == DGPE_FP64)
+  if (p->precision != DGPE_MIXED)   // complex128 (FP64, and the double-float mode's caller format)
     k_moments_noalloc<double><<<blocks, kNoAllocThreads, 0, st>>>(static_cast<const cplx<double> *>(psi), p->nx,
                                                                   p->ny, p->nz, p->hx, p->hy, p->hz, npts, scr, out);
   else
