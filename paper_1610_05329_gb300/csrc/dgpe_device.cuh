@@ -231,8 +231,14 @@ struct Tiles<double> {
   static constexpr int kCnThreads = 128;  // 4 warps, two lines per warp
   static constexpr int kYBudget = 1024;   // K2/K4: lines per CTA ~ budget / ny
 };
+// double-float: the 16-byte values of FP64; its CN sweeps take the 16-warp CTAs of FP32
+// (the long FP32 dependency chains want the warps; the 128-register cap costs a few spills)
+// whenever the two 16-column tiles fit in shared memory, else the FP64 shape.
 template <>
-struct Tiles<df> : Tiles<double> {};   // the same 16-byte complex values
+struct Tiles<df> : Tiles<double> {
+  static constexpr int kCnColsWide = 16;
+  static constexpr int kCnThreadsWide = 512;
+};
 template <>
 struct Tiles<float> {
   static constexpr int kZLines = 16;
@@ -1400,11 +1406,11 @@ struct SumAcc<df> {
 // Persistent, double-buffered: each CTA walks the tiles (fixed index, k-tile)
 // blockIdx.x, blockIdx.x + gridDim.x, ...; the cp.async copies of the next tile are in
 // flight while the current tile is solved and stored.
-template <typename R, typename Coef, int AXIS>
-__global__ void __launch_bounds__(Tiles<R>::kCnThreads) k_cn(KArgs a, int reduce, int renorm) {
+// B columns (z) per tile, NT threads (B divides NT; one or two lines per warp).
+template <typename R, typename Coef, int AXIS, int B = Tiles<R>::kCnCols, int NT = Tiles<R>::kCnThreads>
+__global__ void __launch_bounds__(NT) k_cn(KArgs a, int reduce, int renorm) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int B = Tiles<R>::kCnCols;
   constexpr int SB = B + 1;
   const int N = AXIS == 0 ? a.nx : a.ny;
   const int nfixed = AXIS == 0 ? a.ny : a.nx;
@@ -1766,9 +1772,19 @@ struct Impl {
   }
   static size_t smem_y(const KArgs &a) { return 2 * (size_t)a.ny * (a.ylines + 1) * E; }
   static size_t smem_x(const KArgs &a) { return 2 * (size_t)a.nx * T::kXCols * E; }
-  static size_t smem_cn(int n, int lchunk) {
-    return 2 * (size_t)cn_slots(n, lchunk) * (T::kCnCols + 1) * E + (size_t)(4 * (kWarp << lchunk) + 10 * kWarp) * E +
+  static size_t smem_cn(int n, int lchunk, int cols = T::kCnCols) {
+    return 2 * (size_t)cn_slots(n, lchunk) * (cols + 1) * E + (size_t)(4 * (kWarp << lchunk) + 10 * kWarp) * E +
            2 * (size_t)n * sizeof(R);
+  }
+  // double-float sweeps in the wide shape when its tiles fit (static shared memory of the
+  // reduction included)
+  static bool cn_wide(const KArgs &a, int axis) {
+    if constexpr (!std::is_same<R, df>::value) {
+      return false;
+    } else {
+      const int n = a.cn[axis].m + 2;
+      return smem_cn(n, a.cn[axis].lchunk, T::kCnColsWide) + 4096 <= 227 * 1024;
+    }
   }
 
   static dim3 grid_z(const KArgs &a) { return dim3((a.ny + T::kZLines - 1) / T::kZLines, a.nx); }
@@ -1783,10 +1799,10 @@ struct Impl {
     }
     return n;
   }
-  static dim3 grid_cn(const KArgs &a, int axis) {
-    const int tiles = ((a.nz + T::kCnCols - 1) / T::kCnCols) * (axis == 0 ? a.ny : a.nx);
+  static dim3 grid_cn(const KArgs &a, int axis, int cols = T::kCnCols) {
+    const int tiles = ((a.nz + cols - 1) / cols) * (axis == 0 ? a.ny : a.nx);
     const int n = a.cn[axis].m + 2;
-    const size_t sm = smem_cn(n, a.cn[axis].lchunk);
+    const size_t sm = smem_cn(n, a.cn[axis].lchunk, cols);
     const int fit = sm * 2 + 4096 <= 227 * 1024 ? 2 : 1;
     const int per_sm = a.cn_per_sm < fit ? (a.cn_per_sm < 1 ? 1 : a.cn_per_sm) : fit;
     const int cap = sm_count() * per_sm;
@@ -1851,6 +1867,13 @@ struct Impl {
     chk(allow_smem(k_cn<R, R, 1>));
     chk(allow_smem(k_cn<R, C, 0>));
     chk(allow_smem(k_cn<R, C, 1>));
+    if constexpr (std::is_same<R, df>::value) {
+      constexpr int B = T::kCnColsWide, NT = T::kCnThreadsWide;
+      chk(allow_smem(k_cn<R, R, 0, B, NT>));
+      chk(allow_smem(k_cn<R, R, 1, B, NT>));
+      chk(allow_smem(k_cn<R, C, 0, B, NT>));
+      chk(allow_smem(k_cn<R, C, 1, B, NT>));
+    }
     if constexpr (kAdjoint) chk(allow_smem(k5_adj_phase<R>));
     if constexpr (kAdjoint) chk(allow_smem(k5_adj_combine<R>));
     return e;
@@ -2004,18 +2027,25 @@ struct Impl {
     }
     return cudaGetLastError();
   }
-  static cudaError_t k6(const KArgs &a, cudaStream_t st) {
-    const size_t sm = smem_cn(a.ny, a.cn[1].lchunk);
-    if (a.imag) k_cn<R, R, 1><<<grid_cn(a, 1), T::kCnThreads, sm, st>>>(a, 0, 0);
-    else k_cn<R, C, 1><<<grid_cn(a, 1), T::kCnThreads, sm, st>>>(a, 0, 0);
+  template <int AXIS>
+  static cudaError_t cn(const KArgs &a, int reduce, int renorm, cudaStream_t st) {
+    const int n = AXIS == 0 ? a.nx : a.ny;
+    if constexpr (std::is_same<R, df>::value) {
+      if (cn_wide(a, AXIS)) {
+        constexpr int B = T::kCnColsWide, NT = T::kCnThreadsWide;
+        const size_t sm = smem_cn(n, a.cn[AXIS].lchunk, B);
+        if (a.imag) k_cn<R, R, AXIS, B, NT><<<grid_cn(a, AXIS, B), NT, sm, st>>>(a, reduce, renorm);
+        else k_cn<R, C, AXIS, B, NT><<<grid_cn(a, AXIS, B), NT, sm, st>>>(a, reduce, renorm);
+        return cudaGetLastError();
+      }
+    }
+    const size_t sm = smem_cn(n, a.cn[AXIS].lchunk);
+    if (a.imag) k_cn<R, R, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, reduce, renorm);
+    else k_cn<R, C, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, reduce, renorm);
     return cudaGetLastError();
   }
-  static cudaError_t k7(const KArgs &a, int reduce, int renorm, cudaStream_t st) {
-    const size_t sm = smem_cn(a.nx, a.cn[0].lchunk);
-    if (a.imag) k_cn<R, R, 0><<<grid_cn(a, 0), T::kCnThreads, sm, st>>>(a, reduce, renorm);
-    else k_cn<R, C, 0><<<grid_cn(a, 0), T::kCnThreads, sm, st>>>(a, reduce, renorm);
-    return cudaGetLastError();
-  }
+  static cudaError_t k6(const KArgs &a, cudaStream_t st) { return cn<1>(a, 0, 0, st); }
+  static cudaError_t k7(const KArgs &a, int reduce, int renorm, cudaStream_t st) { return cn<0>(a, reduce, renorm, st); }
   static cudaError_t materialize(const KArgs &a, cudaStream_t st) {
     const size_t count = (size_t)a.nx * a.ny * a.nz;
     size_t blocks = (count + 255) / 256;

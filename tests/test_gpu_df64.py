@@ -83,6 +83,18 @@ def test_full_steps_match_oracle(orc, shape, h, mode):
     gpu.close()
 
 
+@pytest.mark.parametrize("shape", [(512, 6, 8), (6, 512, 8), (8, 6, 512)])
+def test_longest_lines(orc, shape):
+    """Lines of 512 points: the x and y sweeps fall back to the FP64 tile shape (the wide
+    one does not fit in shared memory)."""
+    psi = state(shape, 0.05)
+    gpu, p = make(orc, shape, 0.05, 0.001, abi.DGPE_REAL_TIME)
+    gpu.set_psi(psi)
+    gpu.step(2)
+    assert rel(gpu.get_psi(), orc.step(p, psi, 2)) < DF_STEP_TOL
+    gpu.close()
+
+
 @pytest.mark.parametrize("shape,h", SHAPES)
 def test_observables_match_oracle(orc, shape, h):
     psi = state(shape, h)
