@@ -51,6 +51,18 @@ template <typename R>
 __device__ __forceinline__ cplx<R> mul_conj(cplx<R> a, cplx<R> b) {
   return {a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im};
 }
+// double-float: one product and one fused product-sum per component (the builtin types get
+// the same from the compiler's contraction)
+__device__ __forceinline__ cplx<df> operator*(cplx<df> a, cplx<df> b) {
+  return {fma(a.re, b.re, -(a.im * b.im)), fma(a.re, b.im, a.im * b.re)};
+}
+__device__ __forceinline__ cplx<df> mul_conj(cplx<df> a, cplx<df> b) {
+  return {fma(a.re, b.re, a.im * b.im), fma(a.im, b.re, -(a.re * b.im))};
+}
+// 2 a - b (doubling is exact; for a pair it scales both parts)
+template <typename R>
+__device__ __forceinline__ R twice_minus(R a, R b) { return fma(R(2), a, -b); }
+__device__ __forceinline__ df twice_minus(df a, df b) { return df{2.0f * a.hi, 2.0f * a.lo} - b; }
 template <typename R>
 __device__ __forceinline__ cplx<R> scale(cplx<R> a, R s) { return {a.re * s, a.im * s}; }
 template <typename R>
@@ -676,7 +688,7 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
       const cplx<R> chi = cfma(T(H + e * kWarp), Y, cfma(T(G + e * kWarp), X, y[e]));
       const int q = (i + 1 + t) * es;
       const cplx<R> v = buf[q];
-      buf[q] = {fma(R(2), chi.re, -v.re), fma(R(2), chi.im, -v.im)};
+      buf[q] = {twice_minus(chi.re, v.re), twice_minus(chi.im, v.im)};
     }
   }
   if (t == 0) {
@@ -1761,8 +1773,8 @@ struct Impl {
   using C = cplx<R>;
   using T = Tiles<R>;
   static constexpr size_t E = sizeof(C);
-  // compile-time transforms of lengths 128-512 (not for double-float, whose kernels take
-  // many times longer to compile)
+  // compile-time transforms of lengths 128-512 (not for double-float: its kernels take many
+  // times longer to compile)
   static constexpr bool kCtSizes = !std::is_same<R, df>::value;
 
   static size_t smem_z_fft(const KArgs &a) { return 2 * (size_t)a.nz * (T::kZLines / 2 + 1) * E; }
