@@ -116,6 +116,21 @@ def test_longest_lines(orc, shape):
     gpu.close()
 
 
+@pytest.mark.parametrize("shape", [(150, 6, 8), (6, 300, 8), (8, 6, 384), (300, 10, 6)])
+@pytest.mark.parametrize("precision,tol", [(abi.DGPE_FP64, FP64_STEP_TOL), (abi.DGPE_MIXED, 2e-5)])
+def test_sweeps_on_lines_of_150_to_384(orc, shape, precision, tol):
+    """Lines of 150, 300 and 384 points (partly filled lanes: 8 and 16 unknowns per lane,
+    the last lanes idle)."""
+    psi = state(shape, 0.05)
+    cdt = np.complex128 if precision == abi.DGPE_FP64 else np.complex64
+    gpu, p = make(orc, shape, 0.05, 0.001, abi.DGPE_REAL_TIME, precision=precision)
+    gpu.set_psi(psi.astype(cdt))
+    gpu.step(2)
+    want = orc.step(p, psi.astype(cdt).astype(np.complex128), 2)
+    assert rel(gpu.get_psi().astype(np.complex128), want) < tol
+    gpu.close()
+
+
 def test_imaginary_time_64cubed_200_steps(orc):
     """The 64^3 imaginary-time workload (h = 0.2, dt = 0.004, nu = 1, g = 20, gdd = 10,
     Gaussian + 1e-3 noise with seed 1, 200 steps) against the oracle: psi, mu, E, rms."""
