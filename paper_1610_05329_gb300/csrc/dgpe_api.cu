@@ -385,16 +385,18 @@ int setup_tables(dgpe_ctx *c, bool cn_changed, bool ut_changed) {
   const double h[3] = {p->hx, p->hy, p->hz};
   const int n[3] = {p->nx, p->ny, p->nz};
   const double v[3] = {c->args.vx, c->args.vy, c->args.vz};
+  CnJobs jobs{};
+  jobs.imag = p->mode == DGPE_IMAG_TIME;
   for (int d = 0; d < 3; ++d) {
     int rc = map_cuda(c->ks->axis_potential(at(c, c->L.dtv[d]), n[d], h[d], v[d], p->dt, c->stream));
     if (rc) return rc;
     if (!cn_changed) continue;
-    rc = map_cuda(c->ks->cn_tables(at(c, c->L.cn[d]), c->args.cn[d].m, c->args.cn[d].chunk, c->args.cn_r[d],
-                                   p->mode == DGPE_IMAG_TIME, c->stream));
-    if (rc) return rc;
+    jobs.job[jobs.n++] = {at(c, c->L.cn[d]), c->args.cn[d].m, c->args.cn[d].chunk, c->args.cn_r[d]};
     if (p->mode == DGPE_REAL_TIME)   // the adjoint sweep is the sweep with dt -> -dt
-      rc = map_cuda(c->ks->cn_tables(at(c, c->L.cn_adj[d]), c->args.cn[d].m, c->args.cn[d].chunk,
-                                     -c->args.cn_r[d], 0, c->stream));
+      jobs.job[jobs.n++] = {at(c, c->L.cn_adj[d]), c->args.cn[d].m, c->args.cn[d].chunk, -c->args.cn_r[d]};
+  }
+  if (jobs.n) {
+    const int rc = map_cuda(c->ks->cn_tables(jobs, c->stream));
     if (rc) return rc;
   }
   if (ut_changed) return map_cuda(c->ks->dipolar_table(c->args, c->stream));

@@ -873,8 +873,12 @@ __device__ __forceinline__ void store_coef(Coef *tab, int k, Z64 v) {
 }
 
 template <typename R, typename Coef>
-__global__ void k_cn_tables(Coef *tab, int m, int chunk, double r, int imag) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+__global__ void k_cn_tables(CnJobs jobs) {
+  if (threadIdx.x != 0 || (int)blockIdx.x >= jobs.n) return;
+  const CnJob &jb = jobs.job[blockIdx.x];
+  Coef *tab = static_cast<Coef *>(jb.tab);
+  const int m = jb.m, chunk = jb.chunk, imag = jobs.imag;
+  const double r = jb.r;
   // lane-interleaved layout: interior point i = t*chunk + e of table q at q*mp + e*32 + t
   const int mp = kWarp * chunk;
   auto at = [&](int q, int i) { return q * mp + (i % chunk) * kWarp + i / chunk; };
@@ -1896,9 +1900,10 @@ struct Impl {
     return cudaGetLastError();
   }
 
-  static cudaError_t cn_tables(void *tab, int m, int chunk, double r, int imag, cudaStream_t st) {
-    if (imag) k_cn_tables<R, R><<<1, 1, 0, st>>>(reinterpret_cast<R *>(tab), m, chunk, r, imag);
-    else k_cn_tables<R, C><<<1, 1, 0, st>>>(reinterpret_cast<C *>(tab), m, chunk, r, imag);
+  static cudaError_t cn_tables(const CnJobs &jobs, cudaStream_t st) {
+    if (jobs.n <= 0) return cudaSuccess;
+    if (jobs.imag) k_cn_tables<R, R><<<jobs.n, 32, 0, st>>>(jobs);
+    else k_cn_tables<R, C><<<jobs.n, 32, 0, st>>>(jobs);
     return cudaGetLastError();
   }
 

@@ -26,6 +26,20 @@ struct FftPlan {
 // real in imaginary time, in the kernel precision), lane-interleaved: the entry of interior
 // point t*c + e sits at e*32 + t, so the 32 lanes of a warp read one contiguous segment;
 // then 10 x 32 scan factors of the lane carries (5 forward steps, 5 backward).
+// Factor tables to build in one launch (one block each): the three axes, forward and (real
+// time) the dt -> -dt tables of the adjoint sweeps.
+struct CnJob {
+  void *tab;
+  int m, chunk;
+  double r;   // dt / (4 h^2), negated for the adjoint tables
+};
+constexpr int kMaxCnJobs = 6;
+struct CnJobs {
+  CnJob job[kMaxCnJobs];
+  int n;
+  int imag;   // the same for every job of a call
+};
+
 struct CnTab {
   const void *tab;
   int m;
@@ -118,7 +132,7 @@ struct KernelSet {
   int elem_bytes;  // sizeof complex element
   cudaError_t (*init)();
   cudaError_t (*twiddles)(void *tw, const FftPlan &pl, cudaStream_t st);
-  cudaError_t (*cn_tables)(void *tab, int m, int chunk, double r, int imag, cudaStream_t st);
+  cudaError_t (*cn_tables)(const CnJobs &jobs, cudaStream_t st);
   cudaError_t (*axis_potential)(void *out, int n, double h, double v, double dt, cudaStream_t st);
   cudaError_t (*dipolar_table)(const KArgs &a, cudaStream_t st);   // fills utab
   // double-float only: complex128 -> the kernels' pairs (in place allowed), and back with the

@@ -22,9 +22,9 @@ MEMBERS = [((16, 16, 16), 0.6, abi.DGPE_IMAG_TIME, (1.0, 1.3, 0.7), 12.0, 6.0),
            ((12, 48, 24), 0.35, abi.DGPE_REAL_TIME, (2.0, 0.5, 1.1), 5.0, 4.0)]
 
 
-@pytest.mark.parametrize("precision", [abi.DGPE_FP64, abi.DGPE_MIXED])
+@pytest.mark.parametrize("precision", [abi.DGPE_FP64, abi.DGPE_MIXED, abi.DGPE_DF64])
 def test_batch_equals_individual_steps(precision):
-    cdt = np.complex128 if precision == abi.DGPE_FP64 else np.complex64
+    cdt = np.complex64 if precision == abi.DGPE_MIXED else np.complex128
     batched, alone = [], []
     for k, (shape, h, mode, nu, g, gdd) in enumerate(MEMBERS):
         psi = inputs.gaussian_psi(shape, h, seed=20 + k).astype(cdt)
@@ -72,4 +72,23 @@ def test_autotune_restores_state_and_keeps_parity(orc):
         assert np.linalg.norm(c.get_psi() - want) / np.linalg.norm(want) < 1e-10
     with pytest.raises(abi.DgpeError):
         c.set_tuning(dict(t, ylines=3))
+    c.close()
+
+
+def test_autotune_double_float(orc):
+    """The autotuner and every radix order on the double-float path, against the oracle."""
+    shape, h, dt = (32, 48, 24), 0.3, 0.005
+    psi = inputs.gaussian_psi(shape, h, seed=33)
+    c = abi.Condensate(shape, h, dt, mode=abi.DGPE_REAL_TIME, precision=abi.DGPE_DF64, nu=(1.0, 1.1, 0.9),
+                       g=25.0, gdd=15.0)
+    c.set_psi(psi)
+    t = c.autotune()
+    assert np.max(np.abs(c.get_psi() - psi)) < 2.0 ** -47 * np.max(np.abs(psi))
+    p = orc.make_params(shape, h, dt, orc.REAL_TIME, (1.0, 1.1, 0.9), 25.0, 15.0)
+    want = orc.step(p, psi, 6)
+    for style in (0, 1, 2):
+        c.set_tuning(dict(t, plan_style=(style, style, style)))
+        c.set_psi(psi)
+        c.step(6)
+        assert np.linalg.norm(c.get_psi() - want) / np.linalg.norm(want) < 1e-10
     c.close()
