@@ -87,7 +87,7 @@ struct KArgs {
   float kf[3];                 // 2 pi / (n_d h_d): wavenumber per frequency index (FP32 K3)
   DevState *state;
   double *partials;            // per-block reduction partials
-  const void *tw[3];           // twiddles e^{-2 pi i t / n_d}, t < n_d, for d = x, y, z
+  const void *tw[3];           // per-stage twiddle tables of plan[d] (layout in FftPlan), d = x, y, z
   FftPlan plan[3];
   CnTab cn[3];
   void *out;                   // optional output (Phi for get_phi)
