@@ -84,6 +84,10 @@ template <typename R>
 __device__ __forceinline__ cplx<R> cfma(cplx<R> a, cplx<R> b, cplx<R> d) {
   return {fma(a.re, b.re, fma(-a.im, b.im, d.re)), fma(a.re, b.im, fma(a.im, b.re, d.im))};
 }
+template <typename R>
+__device__ __forceinline__ R neg_coef(R a) { return -a; }
+template <typename R>
+__device__ __forceinline__ cplx<R> neg_coef(cplx<R> a) { return {-a.re, -a.im}; }
 // c v + d for the Crank-Nicolson coefficient c: real r (imaginary time) or i r (real time;
 // the complex Coef holds {0, r}, so only its imaginary part enters).
 template <typename R>
@@ -1419,6 +1423,21 @@ struct SumAcc<df> {
   __device__ __forceinline__ double value() const { return (double)v; }
 };
 
+// Block sums of n, x^2 n, y^2 n, z^2 n -> across blocks; the last block sets the norm and
+// the pending renormalisation factor s.
+__device__ __forceinline__ void finish_sweep_sums(const KArgs &a, double (&v)[4], int renorm) {
+  if (reduce_across_blocks<4>(v, a.partials, &a.state->ticket) && threadIdx.x == 0) {
+    DevState *st = a.state;
+    const double norm = a.hx * a.hy * a.hz * v[0];
+    for (int q = 0; q < 4; ++q) st->sums[q] = v[q];
+    st->norm = norm;
+    const bool ok = isfinite(norm) && norm > 0.0;
+    if (!ok) st->flags |= kFlagNonFinite;
+    set_scale(st, (renorm && ok) ? 1.0 / sqrt(norm) : 1.0);
+    st->steps += 1ull;
+  }
+}
+
 // Persistent, double-buffered: each CTA walks the tiles (fixed index, k-tile)
 // blockIdx.x, blockIdx.x + gridDim.x, ...; the cp.async copies of the next tile are in
 // flight while the current tile is solved and stored.
@@ -1524,16 +1543,123 @@ __global__ void __launch_bounds__(NT) k_cn(KArgs a, int reduce, int renorm) {
   }
   if (do_reduce) {
     double v[4] = {acc[0].value(), acc[1].value(), acc[2].value(), acc[3].value()};
-    if (reduce_across_blocks<4>(v, a.partials, &a.state->ticket) && threadIdx.x == 0) {
-      DevState *st = a.state;
-      const double norm = a.hx * a.hy * a.hz * v[0];
-      for (int q = 0; q < 4; ++q) st->sums[q] = v[q];
-      st->norm = norm;
-      const bool ok = isfinite(norm) && norm > 0.0;
-      if (!ok) st->flags |= kFlagNonFinite;
-      set_scale(st, (renorm && ok) ? 1.0 / sqrt(norm) : 1.0);
-      st->steps += 1ull;
+    finish_sweep_sums(a, v, renorm);
+  }
+}
+
+// K7 one-thread-per-line variant for the FP64-class types: one thread per x-line (K7) or
+// y-line (K6), consecutive threads on consecutive z (coalesced).  Thomas elimination with
+// the LU factors of k_cn_tables: the forward pass writes y_i over psi_i in place; the
+// backward pass reads y back, recovers psi_i = y_i - alpha_i y_{i-1} and writes
+// psi'_i = 2 chi_i - psi_i.  About 16 FP64-class instructions per point instead of the
+// chunked solver's 24 (no lane carries, no chunk fix-up), for twice its memory traffic,
+// which an FP64-bound step has to spare.
+template <typename R, typename Coef, int AXIS>
+__global__ void __launch_bounds__(128) k_cn_thread(KArgs a, int reduce, int renorm) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = AXIS == 0 ? a.nx : a.ny;
+  const int nfixed = AXIS == 0 ? a.ny : a.nx;
+  const long long nlines = (long long)nfixed * a.nz;
+  const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool do_reduce = AXIS == 0 && reduce;
+  R *x2tab = reinterpret_cast<R *>(smem_raw);
+  R *wxtab = x2tab + N;
+  if (do_reduce) {
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+      const double x = coordinate(n, a.nx, a.hx);
+      x2tab[n] = R(x * x);
+      wxtab[n] = R(quad_weight(n, a.nx, a.simpson));
     }
+    __syncthreads();
+  }
+  SumAcc<R> acc[4];
+  if (line < nlines) {
+    const int k = (int)(line % a.nz), fixed = (int)(line / a.nz);
+    const size_t stride = AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
+    C *p = reinterpret_cast<C *>(a.psi) + (AXIS == 1 ? (size_t)fixed * a.ny * a.nz : (size_t)fixed * a.nz) + k;
+    const Coef *tab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
+    const int chunk = a.cn[AXIS].chunk, mp = kWarp * chunk, m = a.cn[AXIS].m;
+    const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[AXIS], a.cn_rf[AXIS], a.cn_rl[AXIS]));
+    // interior point i (grid index i + 1) sits at e * 32 + t of each lane-interleaved table,
+    // i = t * chunk + e
+    // loads run kPf points ahead of the recurrences (registers as a ring)
+    constexpr int kPf = 8;
+    C ring[kPf];
+    C y = czero<R>();
+    {
+#pragma unroll
+      for (int j = 0; j < kPf; ++j) ring[j] = j < m ? p[(size_t)(j + 1) * stride] : czero<R>();
+      int e = 0, t = 0;
+      for (int i0 = 0; i0 < m; i0 += kPf) {
+#pragma unroll
+        for (int j = 0; j < kPf; ++j) {
+          const int i = i0 + j;
+          if (i < m) {
+            const C v = ring[j];
+            if (i + kPf < m) ring[j] = p[(size_t)(i + kPf + 1) * stride];
+            y = cfma(ldg(tab + e * kWarp + t), y, v);
+            p[(size_t)(i + 1) * stride] = y;
+            if (++e == chunk) {
+              e = 0;
+              ++t;
+            }
+          }
+        }
+      }
+    }
+    C chi = czero<R>(), yi = y;
+    R s0 = R(0), sx = R(0);
+    {
+      // y_{i-1}, i = m-1 .. 0, kPf ahead
+#pragma unroll
+      for (int j = 0; j < kPf; ++j) {
+        const int i = m - 1 - j;
+        ring[j] = i > 0 ? p[(size_t)i * stride] : czero<R>();
+      }
+      int e = (m - 1) % chunk, t = (m - 1) / chunk;
+      for (int j0 = 0; j0 < m; j0 += kPf) {
+#pragma unroll
+        for (int j = 0; j < kPf; ++j) {
+          const int i = m - 1 - (j0 + j);
+          if (i >= 0) {
+            const C ym = ring[j];
+            if (i - kPf >= 0) ring[j] = i - kPf > 0 ? p[(size_t)(i - kPf) * stride] : czero<R>();
+            const int q = e * kWarp + t;
+            chi = mul(ldg(tab + mp + q), cfma_c(c, chi, yi));
+            const C ps = cfma(neg_coef(ldg(tab + q)), ym, yi);
+            const C out = {twice_minus(chi.re, ps.re), twice_minus(chi.im, ps.im)};
+            p[(size_t)(i + 1) * stride] = out;
+            if (do_reduce) {
+              R d = out.re * out.re + out.im * out.im;
+              if (a.simpson) d *= wxtab[i + 1];
+              s0 += d;
+              sx = fma(x2tab[i + 1], d, sx);
+            }
+            yi = ym;
+            if (--e < 0) {
+              e = chunk - 1;
+              --t;
+            }
+          }
+        }
+      }
+    }
+    p[0] = czero<R>();
+    p[(size_t)(N - 1) * stride] = czero<R>();
+    if (do_reduce) {
+      const R wyz = quad_weight_r<R>(fixed, a.ny, a.simpson) * quad_weight_r<R>(k, a.nz, a.simpson);
+      const R yv = R(fixed - a.ny / 2) * R(a.hy), zv = R(k - a.nz / 2) * R(a.hz);
+      const R tt = wyz * s0;
+      acc[0].add(tt);
+      acc[1].add(wyz * sx);
+      acc[2].add(yv * yv * tt);
+      acc[3].add(zv * zv * tt);
+    }
+  }
+  if (do_reduce) {
+    double v[4] = {acc[0].value(), acc[1].value(), acc[2].value(), acc[3].value()};
+    finish_sweep_sums(a, v, renorm);
   }
 }
 
@@ -2044,9 +2170,19 @@ struct Impl {
     }
     return cudaGetLastError();
   }
+  // the FP64 sweeps run one thread per line (k_cn_thread)
+  static constexpr bool kCnThread = std::is_same<R, double>::value;
   template <int AXIS>
   static cudaError_t cn(const KArgs &a, int reduce, int renorm, cudaStream_t st) {
     const int n = AXIS == 0 ? a.nx : a.ny;
+    if constexpr (kCnThread) {
+      const long long lines = (long long)(AXIS == 0 ? a.ny : a.nx) * a.nz;
+      const unsigned blocks = (unsigned)((lines + 127) / 128);
+      const size_t sm = AXIS == 0 ? 2 * (size_t)n * sizeof(R) : 0;
+      if (a.imag) k_cn_thread<R, R, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
+      else k_cn_thread<R, C, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
+      return cudaGetLastError();
+    }
     if constexpr (std::is_same<R, df>::value) {
       if (cn_wide(a, AXIS)) {
         constexpr int B = T::kCnColsWide, NT = T::kCnThreadsWide;
@@ -2111,7 +2247,8 @@ struct Impl {
     const dim3 z = grid_z(a);
     const int bz = (int)(z.x * z.y);
     const int bx = ((a.nz + T::kCnCols - 1) / T::kCnCols) * a.ny;
-    return bz > bx ? bz : bx;
+    const int bt = (int)(((long long)a.ny * a.nz + 127) / 128);   // k_cn_thread along x
+    return std::max(bz, std::max(bx, bt));
   }
 
   static const KernelSet *set() {
