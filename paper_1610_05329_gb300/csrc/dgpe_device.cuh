@@ -247,14 +247,8 @@ struct Tiles<double> {
   static constexpr int kCnThreads = 128;  // 4 warps, two lines per warp
   static constexpr int kYBudget = 1024;   // K2/K4: lines per CTA ~ budget / ny
 };
-// double-float: the 16-byte values of FP64; its CN sweeps take the 16-warp CTAs of FP32
-// (the long FP32 dependency chains want the warps; the 128-register cap costs a few spills)
-// whenever the two 16-column tiles fit in shared memory, else the FP64 shape.
 template <>
-struct Tiles<df> : Tiles<double> {
-  static constexpr int kCnColsWide = 16;
-  static constexpr int kCnThreadsWide = 512;
-};
+struct Tiles<df> : Tiles<double> {};   // the 16-byte complex values of FP64
 template <>
 struct Tiles<float> {
   static constexpr int kZLines = 16;
@@ -1918,16 +1912,7 @@ struct Impl {
     return 2 * (size_t)cn_slots(n, lchunk) * (cols + 1) * E + (size_t)(4 * (kWarp << lchunk) + 10 * kWarp) * E +
            2 * (size_t)n * sizeof(R);
   }
-  // double-float sweeps in the wide shape when its tiles fit (static shared memory of the
-  // reduction included)
-  static bool cn_wide(const KArgs &a, int axis) {
-    if constexpr (!std::is_same<R, df>::value) {
-      return false;
-    } else {
-      const int n = a.cn[axis].m + 2;
-      return smem_cn(n, a.cn[axis].lchunk, T::kCnColsWide) + 4096 <= 227 * 1024;
-    }
-  }
+
 
   static dim3 grid_z(const KArgs &a) { return dim3((a.ny + T::kZLines - 1) / T::kZLines, a.nx); }
   // persistent grid of the CN kernels: all tiles, capped at the number of co-resident CTAs
@@ -2005,16 +1990,11 @@ struct Impl {
       chk(allow_smem(k5_zline<R, R, kZStep, 256>));
       chk(allow_smem(k5_zline<R, C, kZStep, 256>));
     }
-    chk(allow_smem(k_cn<R, R, 0>));
-    chk(allow_smem(k_cn<R, R, 1>));
-    chk(allow_smem(k_cn<R, C, 0>));
-    chk(allow_smem(k_cn<R, C, 1>));
-    if constexpr (std::is_same<R, df>::value) {
-      constexpr int B = T::kCnColsWide, NT = T::kCnThreadsWide;
-      chk(allow_smem(k_cn<R, R, 0, B, NT>));
-      chk(allow_smem(k_cn<R, R, 1, B, NT>));
-      chk(allow_smem(k_cn<R, C, 0, B, NT>));
-      chk(allow_smem(k_cn<R, C, 1, B, NT>));
+    if constexpr (!kCnThread) {
+      chk(allow_smem(k_cn<R, R, 0>));
+      chk(allow_smem(k_cn<R, R, 1>));
+      chk(allow_smem(k_cn<R, C, 0>));
+      chk(allow_smem(k_cn<R, C, 1>));
     }
     if constexpr (kAdjoint) chk(allow_smem(k5_adj_phase<R>));
     if constexpr (kAdjoint) chk(allow_smem(k5_adj_combine<R>));
@@ -2170,8 +2150,9 @@ struct Impl {
     }
     return cudaGetLastError();
   }
-  // the FP64 sweeps run one thread per line (k_cn_thread)
-  static constexpr bool kCnThread = std::is_same<R, double>::value;
+  // the FP64-class sweeps run one thread per line (k_cn_thread), the FP32 ones the chunked
+  // solver in persistent tiles (k_cn)
+  static constexpr bool kCnThread = Fp64Class<R>::value;
   template <int AXIS>
   static cudaError_t cn(const KArgs &a, int reduce, int renorm, cudaStream_t st) {
     const int n = AXIS == 0 ? a.nx : a.ny;
@@ -2181,20 +2162,11 @@ struct Impl {
       const size_t sm = AXIS == 0 ? 2 * (size_t)n * sizeof(R) : 0;
       if (a.imag) k_cn_thread<R, R, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
       else k_cn_thread<R, C, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
-      return cudaGetLastError();
+    } else {
+      const size_t sm = smem_cn(n, a.cn[AXIS].lchunk);
+      if (a.imag) k_cn<R, R, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, reduce, renorm);
+      else k_cn<R, C, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, reduce, renorm);
     }
-    if constexpr (std::is_same<R, df>::value) {
-      if (cn_wide(a, AXIS)) {
-        constexpr int B = T::kCnColsWide, NT = T::kCnThreadsWide;
-        const size_t sm = smem_cn(n, a.cn[AXIS].lchunk, B);
-        if (a.imag) k_cn<R, R, AXIS, B, NT><<<grid_cn(a, AXIS, B), NT, sm, st>>>(a, reduce, renorm);
-        else k_cn<R, C, AXIS, B, NT><<<grid_cn(a, AXIS, B), NT, sm, st>>>(a, reduce, renorm);
-        return cudaGetLastError();
-      }
-    }
-    const size_t sm = smem_cn(n, a.cn[AXIS].lchunk);
-    if (a.imag) k_cn<R, R, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, reduce, renorm);
-    else k_cn<R, C, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, reduce, renorm);
     return cudaGetLastError();
   }
   static cudaError_t k6(const KArgs &a, cudaStream_t st) { return cn<1>(a, 0, 0, st); }
