@@ -530,6 +530,7 @@ def main():
     ms = time_steps(c, args.steps, barrier)
     clk = clocks.stop()
     value, ms = aggregate_over_ranks(ms, npts * args.steps, dist, c.device)
+    launches_per_step = c.step_launches()
     roofline, kernels = kernel_profile(c, min(args.steps, 50), hbm_peak, peak_kind, name)
     e2e = e2e_run(abi, c, args.e2e_steps) if args.e2e_steps > 0 else None
     c.sync()
@@ -587,7 +588,7 @@ def main():
                        "prep": "%d imaginary-time steps at g=%g from the seeded Gaussian" % (PREP_STEPS, wl["g_prep"]),
                        "l2": "inputs larger than L2 (psi %d MB > 129 MB)" % (npts * (8 if wl["precision"] == "mixed" else 16) >> 20),
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
-            "gpu_launches": 7 * args.steps, "clocks": clk, "roofline": roofline, "kernels": kernels, "e2e": e2e}
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roofline, "kernels": kernels, "e2e": e2e}
     if mixed is not None:
         line["mixed_512x512x384"] = mixed
     if dfl is not None:

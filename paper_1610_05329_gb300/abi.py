@@ -120,6 +120,7 @@ _SIGNATURES = [
     ("dgpe_batch_destroy", None, [ctypes.c_void_p]),
     ("dgpe_autotune", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_tuning)]),
     ("dgpe_get_tuning", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_tuning)]),
+    ("dgpe_step_launches", ctypes.c_int, [ctypes.c_void_p, _P(ctypes.c_int)]),
     ("dgpe_set_tuning", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_tuning)]),
     ("dgpe_moments_noalloc", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_params), ctypes.c_void_p, ctypes.c_void_p]),
     ("dgpe_strerror", ctypes.c_char_p, [ctypes.c_int]),
@@ -269,6 +270,12 @@ def dgpe_autotune(ctx):
     t = dgpe_tuning()
     _check(load().dgpe_autotune(ctx, ctypes.byref(t)), "dgpe_autotune")
     return t.as_dict()
+
+
+def dgpe_step_launches(ctx):
+    n = ctypes.c_int()
+    _check(load().dgpe_step_launches(ctx, ctypes.byref(n)), "dgpe_step_launches")
+    return n.value
 
 
 def dgpe_get_tuning(ctx):
@@ -434,6 +441,9 @@ class Condensate:
 
     def tuning(self):
         return dgpe_get_tuning(self.ctx)
+
+    def step_launches(self):
+        return dgpe_step_launches(self.ctx)
 
     def adjoint_step(self, psi_k, gbar):
         """gbar (device tensor) <- cotangent of psi_k for one real-time step (in place)."""

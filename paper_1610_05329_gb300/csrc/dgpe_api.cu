@@ -895,6 +895,12 @@ int dgpe_set_tuning(dgpe_ctx *c, const dgpe_tuning *t) {
   return apply_tuning(c, *t);
 }
 
+int dgpe_step_launches(const dgpe_ctx *c, int *n) {
+  if (!c || !n) return DGPE_EINVAL;
+  *n = 6 + c->ks->k5_launches;   // K1 K2 K3 K4, K5 (1 or 2), K6 K7
+  return DGPE_OK;
+}
+
 int dgpe_get_tuning(const dgpe_ctx *c, dgpe_tuning *out) {
   if (!c || !out) return DGPE_EINVAL;
   *out = current_tuning(c);

@@ -1548,13 +1548,16 @@ __global__ void __launch_bounds__(NT) k_cn(KArgs a, int reduce, int renorm) {
 // psi'_i = 2 chi_i - psi_i.  About 16 FP64-class instructions per point instead of the
 // chunked solver's 24 (no lane carries, no chunk fix-up), for twice its memory traffic,
 // which an FP64-bound step has to spare.
+// AXIS 2 (the z sweep of the FP64-class step, after K5's phase-only pass): one thread per
+// z-line, consecutive threads on consecutive lines; a warp's accesses are 32 lines apart,
+// and the neighbouring points of the next iterations come from the same L1 sectors.
 template <typename R, typename Coef, int AXIS>
 __global__ void __launch_bounds__(128) k_cn_thread(KArgs a, int reduce, int renorm) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = AXIS == 0 ? a.nx : a.ny;
+  const int N = AXIS == 0 ? a.nx : AXIS == 1 ? a.ny : a.nz;
   const int nfixed = AXIS == 0 ? a.ny : a.nx;
-  const long long nlines = (long long)nfixed * a.nz;
+  const long long nlines = AXIS == 2 ? (long long)a.nx * a.ny : (long long)nfixed * a.nz;
   const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool do_reduce = AXIS == 0 && reduce;
   R *x2tab = reinterpret_cast<R *>(smem_raw);
@@ -1570,8 +1573,9 @@ __global__ void __launch_bounds__(128) k_cn_thread(KArgs a, int reduce, int reno
   SumAcc<R> acc[4];
   if (line < nlines) {
     const int k = (int)(line % a.nz), fixed = (int)(line / a.nz);
-    const size_t stride = AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
-    C *p = reinterpret_cast<C *>(a.psi) + (AXIS == 1 ? (size_t)fixed * a.ny * a.nz : (size_t)fixed * a.nz) + k;
+    const size_t stride = AXIS == 2 ? (size_t)1 : AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
+    C *p = reinterpret_cast<C *>(a.psi) +
+           (AXIS == 2 ? (size_t)line * a.nz : (AXIS == 1 ? (size_t)fixed * a.ny * a.nz : (size_t)fixed * a.nz) + k);
     const Coef *tab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
     const int chunk = a.cn[AXIS].chunk, mp = kWarp * chunk, m = a.cn[AXIS].m;
     const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[AXIS], a.cn_rf[AXIS], a.cn_rl[AXIS]));
@@ -1900,6 +1904,12 @@ struct Impl {
   // compile-time transforms of lengths 128-512 (not for double-float: its kernels take many
   // times longer to compile)
   static constexpr bool kCtSizes = !std::is_same<R, df>::value;
+  // the FP64-class sweeps run one thread per line (k_cn_thread), the FP32 ones the chunked
+  // solver in persistent tiles (k_cn)
+  static constexpr bool kCnThread = Fp64Class<R>::value;
+  // FP64: the z sweep too, after a phase-only K5 pass (the FP64 pipe bounds the step, so the
+  // fewer FP64 instructions win over the extra pass; for double-float they do not)
+  static constexpr bool kZSplit = std::is_same<R, double>::value;
 
   static size_t smem_z_fft(const KArgs &a) { return 2 * (size_t)a.nz * (T::kZLines / 2 + 1) * E; }
   static size_t smem_k5(const KArgs &a) {
@@ -1958,12 +1968,14 @@ struct Impl {
     chk(allow_smem(k_ffty<R, -1, 0>));
     chk(allow_smem(k_ffty<R, +1, 0>));
     chk(allow_smem(k3_fftx_dipolar<R, 0>));
-    chk(allow_smem(k5_zline<R, R, kZStep, 0>));
-    chk(allow_smem(k5_zline<R, C, kZStep, 0>));
-    chk(allow_smem(k5_zline<R, R, kZPhaseOnly, 0>));
-    chk(allow_smem(k5_zline<R, C, kZPhaseOnly, 0>));
-    chk(allow_smem(k5_zline<R, R, kZCnOnly, 0>));
-    chk(allow_smem(k5_zline<R, C, kZCnOnly, 0>));
+    chk(allow_smem(k5_zline<R, R, kZFast, 0>));
+    chk(allow_smem(k5_zline<R, C, kZFast, 0>));
+    if constexpr (!kZSplit) {
+      chk(allow_smem(k5_zline<R, R, kZPhaseOnly, 0>));
+      chk(allow_smem(k5_zline<R, C, kZPhaseOnly, 0>));
+      chk(allow_smem(k5_zline<R, R, kZCnOnly, 0>));
+      chk(allow_smem(k5_zline<R, C, kZCnOnly, 0>));
+    }
     chk(allow_smem(k5_zline<R, R, kZPhi, 0>));
     chk(allow_smem(k5_zline<R, R, kZObs, 0>));
     if constexpr (kCtSizes) {
@@ -1983,12 +1995,12 @@ struct Impl {
       chk(allow_smem(k3_fftx_dipolar<R, 384>));
       chk(allow_smem(k3_fftx_dipolar<R, 256>));
       chk(allow_smem(k3_fftx_dipolar<R, 128>));
-      chk(allow_smem(k5_zline<R, R, kZStep, 512>));
-      chk(allow_smem(k5_zline<R, C, kZStep, 512>));
-      chk(allow_smem(k5_zline<R, R, kZStep, 384>));
-      chk(allow_smem(k5_zline<R, C, kZStep, 384>));
-      chk(allow_smem(k5_zline<R, R, kZStep, 256>));
-      chk(allow_smem(k5_zline<R, C, kZStep, 256>));
+      chk(allow_smem(k5_zline<R, R, kZFast, 512>));
+      chk(allow_smem(k5_zline<R, C, kZFast, 512>));
+      chk(allow_smem(k5_zline<R, R, kZFast, 384>));
+      chk(allow_smem(k5_zline<R, C, kZFast, 384>));
+      chk(allow_smem(k5_zline<R, R, kZFast, 256>));
+      chk(allow_smem(k5_zline<R, C, kZFast, 256>));
     }
     if constexpr (!kCnThread) {
       chk(allow_smem(k_cn<R, R, 0>));
@@ -2114,35 +2126,50 @@ struct Impl {
     return cudaGetLastError();
   }
   static cudaError_t k4(const KArgs &a, cudaStream_t st) { return ffty<+1>(a, st); }
+  // K5 in mode ZM with coefficient type Co: the compile-time transform when the z plan is
+  // the default one of a supported length.
+  template <int ZM, typename Co>
+  static void k5_launch(const KArgs &a, dim3 g, size_t sm, cudaStream_t st) {
+    if constexpr (kCtSizes) {
+      if (plan_ct(a.plan[2], 512)) k5_zline<R, Co, ZM, 512><<<g, T::kZThreads, sm, st>>>(a);
+      else if (plan_ct(a.plan[2], 384)) k5_zline<R, Co, ZM, 384><<<g, T::kZThreads, sm, st>>>(a);
+      else if (plan_ct(a.plan[2], 256)) k5_zline<R, Co, ZM, 256><<<g, T::kZThreads, sm, st>>>(a);
+      else k5_zline<R, Co, ZM, 0><<<g, T::kZThreads, sm, st>>>(a);
+    } else {
+      k5_zline<R, Co, ZM, 0><<<g, T::kZThreads, sm, st>>>(a);
+    }
+  }
+  // the mode whose compile-time instances exist: the fused step (FP32), or the phase-only
+  // pass that precedes the per-line z sweep (FP64-class)
+  static constexpr int kZFast = kZSplit ? kZPhaseOnly : kZStep;
   static cudaError_t k5(const KArgs &a, int zmode, cudaStream_t st) {
+    if constexpr (kZSplit) {
+      // the z sweep runs one thread per line after the phase-only pass
+      if (zmode == kZCnOnly) return cn<2>(a, 0, 0, st);
+      if (zmode == kZStep) {
+        const cudaError_t e = k5(a, kZPhaseOnly, st);
+        return e != cudaSuccess ? e : cn<2>(a, 0, 0, st);
+      }
+    }
     const dim3 g = grid_z(a);
     const size_t sm = smem_k5(a);
+    if (zmode == kZFast) {
+      if (a.imag) k5_launch<kZFast, R>(a, g, sm, st);
+      else k5_launch<kZFast, C>(a, g, sm, st);
+      return cudaGetLastError();
+    }
     switch (zmode) {
-      case kZStep:
-        if constexpr (kCtSizes) {
-          if (a.imag) {
-            if (plan_ct(a.plan[2], 512)) k5_zline<R, R, kZStep, 512><<<g, T::kZThreads, sm, st>>>(a);
-            else if (plan_ct(a.plan[2], 384)) k5_zline<R, R, kZStep, 384><<<g, T::kZThreads, sm, st>>>(a);
-            else if (plan_ct(a.plan[2], 256)) k5_zline<R, R, kZStep, 256><<<g, T::kZThreads, sm, st>>>(a);
-            else k5_zline<R, R, kZStep, 0><<<g, T::kZThreads, sm, st>>>(a);
-          } else {
-            if (plan_ct(a.plan[2], 512)) k5_zline<R, C, kZStep, 512><<<g, T::kZThreads, sm, st>>>(a);
-            else if (plan_ct(a.plan[2], 384)) k5_zline<R, C, kZStep, 384><<<g, T::kZThreads, sm, st>>>(a);
-            else if (plan_ct(a.plan[2], 256)) k5_zline<R, C, kZStep, 256><<<g, T::kZThreads, sm, st>>>(a);
-            else k5_zline<R, C, kZStep, 0><<<g, T::kZThreads, sm, st>>>(a);
-          }
-        } else {
-          if (a.imag) k5_zline<R, R, kZStep, 0><<<g, T::kZThreads, sm, st>>>(a);
-          else k5_zline<R, C, kZStep, 0><<<g, T::kZThreads, sm, st>>>(a);
+      case kZPhaseOnly:
+        if constexpr (!kZSplit) {
+          if (a.imag) k5_zline<R, R, kZPhaseOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
+          else k5_zline<R, C, kZPhaseOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
         }
         break;
-      case kZPhaseOnly:
-        if (a.imag) k5_zline<R, R, kZPhaseOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
-        else k5_zline<R, C, kZPhaseOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
-        break;
       case kZCnOnly:
-        if (a.imag) k5_zline<R, R, kZCnOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
-        else k5_zline<R, C, kZCnOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
+        if constexpr (!kZSplit) {
+          if (a.imag) k5_zline<R, R, kZCnOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
+          else k5_zline<R, C, kZCnOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
+        }
         break;
       case kZPhi: k5_zline<R, R, kZPhi, 0><<<g, T::kZThreads, sm, st>>>(a); break;
       case kZObs: k5_zline<R, R, kZObs, 0><<<g, T::kZThreads, sm, st>>>(a); break;
@@ -2150,14 +2177,11 @@ struct Impl {
     }
     return cudaGetLastError();
   }
-  // the FP64-class sweeps run one thread per line (k_cn_thread), the FP32 ones the chunked
-  // solver in persistent tiles (k_cn)
-  static constexpr bool kCnThread = Fp64Class<R>::value;
   template <int AXIS>
   static cudaError_t cn(const KArgs &a, int reduce, int renorm, cudaStream_t st) {
-    const int n = AXIS == 0 ? a.nx : a.ny;
+    const int n = AXIS == 0 ? a.nx : AXIS == 1 ? a.ny : a.nz;
     if constexpr (kCnThread) {
-      const long long lines = (long long)(AXIS == 0 ? a.ny : a.nx) * a.nz;
+      const long long lines = AXIS == 2 ? (long long)a.nx * a.ny : (long long)(AXIS == 0 ? a.ny : a.nx) * a.nz;
       const unsigned blocks = (unsigned)((lines + 127) / 128);
       const size_t sm = AXIS == 0 ? 2 * (size_t)n * sizeof(R) : 0;
       if (a.imag) k_cn_thread<R, R, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
@@ -2227,7 +2251,7 @@ struct Impl {
     static const KernelSet ks = {(int)E, &init,          &twiddles,   &cn_tables, &axis_potential, &dipolar_table, &from_c128, &to_c128, &reset_state,
                                  &k1,        &k2,            &k3,         &k4,        &k5,             &k6,
                                  &k7,        &materialize,   &adj_phase,  &adj_combine, &loss_z2,
-                                 &max_blocks, &default_ylines, &y_smem};
+                                 &max_blocks, kZSplit ? 2 : 1, &default_ylines, &y_smem};
     return &ks;
   }
 };

@@ -152,6 +152,7 @@ struct KernelSet {
   cudaError_t (*adj_combine)(const KArgs &a, cudaStream_t st);   // gbar = u + 2 dt (g s + gdd Phi[s]) psi
   cudaError_t (*loss_z2)(const KArgs &a, cudaStream_t st);       // gbar = 2 h^3 z^2 psi
   int (*max_blocks)(const KArgs &a);   // upper bound on blocks of any reducing kernel
+  int k5_launches;                     // kernels behind one k5 step call (1 fused, or 2)
   int (*default_ylines)(int ny);
   size_t (*y_smem)(int ny, int ylines);
 };

@@ -78,6 +78,7 @@ def test_null_arguments(lib):
     assert lib.dgpe_step(None, 1) == abi.DGPE_EINVAL
     assert lib.dgpe_sync(None) == abi.DGPE_EINVAL
     assert lib.dgpe_get_tuning(None, None) == abi.DGPE_EINVAL
+    assert lib.dgpe_step_launches(None, None) == abi.DGPE_EINVAL
     lib.dgpe_destroy(None)
     n = ctypes.c_size_t()
     assert lib.dgpe_workspace_bytes(ctypes.byref(params(shape=(7, 8, 8))), ctypes.byref(n)) == abi.DGPE_EINVAL
