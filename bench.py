@@ -66,26 +66,32 @@ def kernel_source_sha1():
         return hashlib.sha1(f.read()).hexdigest()
 
 
-def fp64_flops_per_point(kernel, shape):
-    """Algorithmic FP64 flops per grid point of each real-time FP64 kernel (FMA = 2 flops);
-    the derivation is in the design notes.  FFT of length n: 5 n log2 n per complex line;
-    the half spectrum has (nz/2+1)/nz complex values per real point."""
+def fp64_flops_per_point(kernel, shape, precision="fp64"):
+    """Algorithmic FP64 flops per grid point of each real-time kernel (FMA = 2 flops) as the
+    kernels compute them; the derivation is in the design notes.  FFT of length n: 5 n log2 n
+    per complex line; the half spectrum has (nz/2+1)/nz complex values per real point.
+    Crank-Nicolson: the chunked warp solver (forward, backward, chunk fix-up, 2chi - psi,
+    lane scans) or the one-thread-per-line Thomas solver (forward, backward, psi recovered
+    from y, 2chi - psi)."""
     import math
     nx, ny, nz = shape
     half = (nz // 2 + 1) / nz
     chunk = 2
     while chunk * 32 < nz - 2:
         chunk *= 2
-    cn = 8 + 10 + 16 + 4 + 88.0 / chunk         # forward, backward, fix-up, 2chi - psi, lane scans
+    cn_chunked = 8 + 10 + 16 + 4 + 88.0 / chunk
+    cn_line = 8 + 10 + 8 + 4
+    # FP64: every sweep one thread per line; double-float: the x/y sweeps per line, z chunked
+    cn_z = cn_line if precision == "fp64" else cn_chunked
     return {
         "k1_density_r2c_z": 2.5 * math.log2(nz) + 5,
         "k2_fft_y": 5 * math.log2(ny) * half,
         "k3_fft_x_dipolar_ifft_x": (10 * math.log2(nx) + 2) * half,
         "k4_ifft_y": 5 * math.log2(ny) * half,
         # sine/cosine: 24 flops for |theta| <= 1/4 (every point of this workload), else 36 + reduction
-        "k5_c2r_z_phase_cn_z": 2.5 * math.log2(nz) + 2 + 9 + 24 + 6 + cn,
-        "k6_cn_y": cn,
-        "k7_cn_x_reduce": cn + 6,
+        "k5_c2r_z_phase_cn_z": 2.5 * math.log2(nz) + 2 + 9 + 24 + 6 + cn_z,
+        "k6_cn_y": cn_line,
+        "k7_cn_x_reduce": cn_line + 6,
     }.get(kernel, 0.0)
 
 
@@ -223,7 +229,7 @@ def kernel_profile(c, steps, hbm_peak, peak_kind, workload):
              "share": round(r["total_ms"] / total, 4), "bytes_per_launch": r["bytes_per_launch"],
              "achieved_gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4)}
         if wl["precision"] in ("fp64", "df64"):
-            fl = fp64_flops_per_point(r["name"], wl["shape"]) * npts
+            fl = fp64_flops_per_point(r["name"], wl["shape"], wl["precision"]) * npts
             d["fp64_flops_per_launch"] = fl
             d["fp64_tflops"] = round(fl / (avg * 1e-3) / 1e12, 4)
             d["frac_fp64"] = round(d["fp64_tflops"] / FP64_PEAK_TFLOPS, 4)
