@@ -251,7 +251,9 @@ int dgpe_step_launches(const dgpe_ctx *ctx, int *n);
 int dgpe_sync(dgpe_ctx *ctx);
 
 /* Per-kernel timing: when enabled, dgpe_step launches kernels one by one with CUDA events
- * around each (instead of replaying the graph) and accumulates their durations. */
+ * around each (instead of replaying the graph) and accumulates their durations.  A record
+ * covers one stage of the step: in FP64 the "k5" record times its two launches (the
+ * phase-only pass and the per-line z sweep) together. */
 int dgpe_set_timing(dgpe_ctx *ctx, int enable);
 /* Synchronises, then copies up to `max` records into out and sets *n to the number of
  * kernels timed. */
