@@ -1176,7 +1176,9 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
 // theta = dt (V + g s^2 |psi|^2 + gdd Phi), and the Crank-Nicolson solve along z.
 // ---------------------------------------------------------------------------------------
 template <typename R, typename Coef, int ZM, int N>
-__global__ void __launch_bounds__(Tiles<R>::kZThreads, ZM == kZObs ? 1 : Tiles<R>::kZMinBlocks)
+// (the FP64 phase-only pass runs three CTAs per SM: 80 registers and a few spills beat two)
+__global__ void __launch_bounds__(Tiles<R>::kZThreads,
+                                  ZM == kZObs ? 1 : (ZM == kZPhaseOnly && std::is_same<R, double>::value ? 3 : Tiles<R>::kZMinBlocks))
     k5_zline(KArgs a) {
   constexpr int zmode = ZM;   // one instance per mode: each gets its own register allocation
   using C = cplx<R>;
