@@ -1174,9 +1174,9 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
 // kz = nz/2 bins are dropped), Phi = result / (nx ny nz); then, per zmode, the potential
 // step psi <- s psi e^{-i theta} (real time) or s psi e^{-theta} (imaginary time) with
 // theta = dt (V + g s^2 |psi|^2 + gdd Phi), and the Crank-Nicolson solve along z.
+// The FP64 phase-only pass runs three CTAs per SM (80 registers and a few spills beat two).
 // ---------------------------------------------------------------------------------------
 template <typename R, typename Coef, int ZM, int N>
-// (the FP64 phase-only pass runs three CTAs per SM: 80 registers and a few spills beat two)
 __global__ void __launch_bounds__(Tiles<R>::kZThreads,
                                   ZM == kZObs ? 1 : (ZM == kZPhaseOnly && std::is_same<R, double>::value ? 3 : Tiles<R>::kZMinBlocks))
     k5_zline(KArgs a) {
