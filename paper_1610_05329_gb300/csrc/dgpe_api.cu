@@ -121,7 +121,7 @@ int check_physics(const dgpe_params *p) {
 }
 
 struct Layout {
-  size_t state, partials, tw[3], cn[3], cn_adj[3], dtv[3], psi, spec, utab, total;
+  size_t state, partials, tw[3], cn[3], cn_adj[3], dtv[3], psi, spec, utab, ybuf, total;
 };
 
 Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
@@ -153,6 +153,8 @@ Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
   off += align_up((size_t)(p->nz / 2 + 1) * p->nx * p->ny * e);
   L.utab = off;   // FP64 and double-float (8-byte entries); the FP32 kernels evaluate it in place
   if (p->precision != DGPE_MIXED) off += align_up((size_t)(p->nz / 2 + 1) * p->nx * p->ny * 8);
+  L.ybuf = off;   // the forward-elimination values of the FP64 per-line sweeps
+  if (p->precision == DGPE_FP64) off += align_up((size_t)p->nx * p->ny * p->nz * e);
   L.total = off;
   (void)ks;
   return L;
@@ -624,6 +626,7 @@ int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out) {
     a.dtv[d] = at(c, c->L.dtv[d]);
   }
   a.utab = at(c, c->L.utab);
+  a.ybuf = at(c, c->L.ybuf);
   const int n[3] = {p->nx, p->ny, p->nz};
   rc = map_cuda(cudaMemsetAsync(a.psi, 0, (size_t)p->nx * p->ny * p->nz * c->ks->elem_bytes, c->stream));
   if (!rc) rc = map_cuda(c->ks->reset_state(a.state, c->stream));

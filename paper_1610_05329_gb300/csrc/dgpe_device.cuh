@@ -452,6 +452,126 @@ __device__ __forceinline__ void butterfly(cplx<R> *v) {
   else bf8<R, DIR>(v);
 }
 
+// Tangent-form twiddles (FP64, radix 2, 4 and 8).  GB300 issues FP64 arithmetic at 1/64
+// of the FP32 rate, so the FP64 transforms count FP64 instructions, not memory traffic or
+// integer work.  A twiddle w = e^{-i phi} is stored as w = sigma i^q (1 + i t) with |t| <= 1
+// (q = 1 where |sin phi| > |cos phi|, so |sigma| >= 1/sqrt 2): v w = sigma u with
+// u = (1 + i t) i^q v, two FMAs, and sigma enters the butterfly's additions, which become
+// FMAs (the multiply-add FFT of Linzer & Feig 1993 and Goedecker 1997).  q follows from the
+// twiddle's index, so only (t, sigma) is stored.  A radix-8 butterfly with its seven
+// twiddles takes 67 FP64 instructions instead of 80, a radix-4 one 22 instead of 28, a
+// radix-2 one 6 instead of 8.  Entry r - 1 of index k holds {t_r, S_r}: S = sigma_1 for
+// radix 2; (sigma_1, sigma_2, sigma_3/sigma_1) for radix 4; (sigma_1, sigma_2,
+// sigma_3/sigma_1, sigma_4, sigma_5/sigma_1, sigma_6/sigma_2, sigma_7/sigma_3) for radix 8 --
+// the scales the butterflies below fold in (all between 1/sqrt 2 and sqrt 2 in magnitude).
+template <typename R, int P>
+struct TangentTw {
+  static constexpr bool value = std::is_same<R, double>::value && (P == 2 || P == 4 || P == 8);
+};
+// q of the twiddle e^{-2 pi i a / M}, 0 <= a < M: the angle lies within pi/4 of +-pi/2
+__host__ __device__ __forceinline__ bool tw_rot(int a, int M) {
+  int c = 8 * a;
+  if (c >= 4 * M) c -= 4 * M;
+  return c > M && c < 3 * M;
+}
+// u = (1 + i t) i^q v for the forward twiddle, (1 - i t) (-i)^q v for its conjugate; the
+// rotation and its sign are integer selects on the two FMA results
+template <int DIR>
+__device__ __forceinline__ cplx<double> tw_u(cplx<double> v, double t, bool q) {
+  constexpr unsigned long long kSign = 0x8000000000000000ULL;
+  const double tt = DIR < 0 ? t : -t;
+  const double x = fma(tt, v.re, v.im), y = fma(-tt, v.im, v.re);
+  const unsigned long long xb = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long yb = (unsigned long long)__double_as_longlong(y);
+  if (DIR < 0) return {q ? __longlong_as_double((long long)(xb ^ kSign)) : y, q ? y : x};
+  return {q ? x : y, q ? __longlong_as_double((long long)(yb ^ kSign)) : x};
+}
+// a + s b for real s
+__device__ __forceinline__ cplx<double> fma_s(double s, cplx<double> b, cplx<double> a) {
+  return {fma(s, b.re, a.re), fma(s, b.im, a.im)};
+}
+template <int DIR>
+__device__ __forceinline__ cplx<double> mul_dir_i(cplx<double> d) { return DIR < 0 ? mul_mi(d) : mul_i(d); }
+
+// twiddles of index k (table entries w[0..P-2], M = ns P) and the butterfly, in place
+template <int DIR, int P>
+__device__ __forceinline__ void butterfly_tangent(cplx<double> *v, const cplx<double> *__restrict__ w, int k, int M) {
+  cplx<double> u[P];
+  double sg[P];
+#pragma unroll
+  for (int r = 1; r < P; ++r) {
+    const cplx<double> e = ldg(w + r - 1);
+    u[r] = tw_u<DIR>(v[r], e.re, tw_rot(r * k, M));
+    sg[r] = e.im;
+  }
+  if constexpr (P == 2) {
+    const cplx<double> a = v[0];
+    v[0] = fma_s(sg[1], u[1], a);
+    v[1] = fma_s(-sg[1], u[1], a);
+  } else if constexpr (P == 4) {
+    const cplx<double> t0 = fma_s(sg[2], u[2], v[0]), t1 = fma_s(-sg[2], u[2], v[0]);
+    const cplx<double> p = fma_s(sg[3], u[3], u[1]);
+    const cplx<double> d = mul_dir_i<DIR>(fma_s(-sg[3], u[3], u[1]));
+    v[0] = fma_s(sg[1], p, t0);
+    v[2] = fma_s(-sg[1], p, t0);
+    v[1] = fma_s(sg[1], d, t1);
+    v[3] = fma_s(-sg[1], d, t1);
+  } else {
+    // even inputs (v0, sigma_2 u2, sigma_4 u4, sigma_6 u6): a radix-4 butterfly
+    const cplx<double> et0 = fma_s(sg[4], u[4], v[0]), et1 = fma_s(-sg[4], u[4], v[0]);
+    const cplx<double> ep = fma_s(sg[6], u[6], u[2]);
+    const cplx<double> ed = mul_dir_i<DIR>(fma_s(-sg[6], u[6], u[2]));
+    const cplx<double> e0 = fma_s(sg[2], ep, et0), e2 = fma_s(-sg[2], ep, et0);
+    const cplx<double> e1 = fma_s(sg[2], ed, et1), e3 = fma_s(-sg[2], ed, et1);
+    // odd inputs over sigma_1: (u1, rho_3 u3, rho_5 u5, rho_7 u7), rho_j = sigma_j / sigma_1
+    const cplx<double> ot0 = fma_s(sg[5], u[5], u[1]), ot1 = fma_s(-sg[5], u[5], u[1]);
+    const cplx<double> op = fma_s(sg[7], u[7], u[3]);
+    const cplx<double> od = mul_dir_i<DIR>(fma_s(-sg[7], u[7], u[3]));
+    const cplx<double> o0 = fma_s(sg[3], op, ot0), o2 = fma_s(-sg[3], op, ot0);
+    const cplx<double> o1 = fma_s(sg[3], od, ot1), o3 = fma_s(-sg[3], od, ot1);
+    // out_j = e_j + sigma_1 w8^j o_j, out_{j+4} = e_j - sigma_1 w8^j o_j, w8 = e^{DIR 2 pi i / 8}
+    const double h1 = sg[1] * 0.70710678118654752440084436210485;
+    cplx<double> z1, z3;
+    if (DIR < 0) {
+      z1 = {o1.re + o1.im, o1.im - o1.re};
+      z3 = {o3.im - o3.re, -(o3.re + o3.im)};
+    } else {
+      z1 = {o1.re - o1.im, o1.re + o1.im};
+      z3 = {-(o3.re + o3.im), o3.re - o3.im};
+    }
+    const cplx<double> r2 = mul_dir_i<DIR>(o2);
+    v[0] = fma_s(sg[1], o0, e0);
+    v[4] = fma_s(-sg[1], o0, e0);
+    v[1] = fma_s(h1, z1, e1);
+    v[5] = fma_s(-h1, z1, e1);
+    v[2] = fma_s(sg[1], r2, e2);
+    v[6] = fma_s(-sg[1], r2, e2);
+    v[3] = fma_s(h1, z3, e3);
+    v[7] = fma_s(-h1, z3, e3);
+  }
+}
+
+// The twiddles of index k of a stage (M = ns P) and the butterfly, for every precision; the
+// complex-twiddle form keeps one inlined butterfly per stage (twiddled or not), which the
+// double-float code, many instructions per operation, needs for its instruction cache.
+template <typename R, int DIR, int P>
+__device__ __forceinline__ void stage_butterfly(cplx<R> *v, bool twiddled, const cplx<R> *__restrict__ w, int k,
+                                                int M) {
+  if constexpr (TangentTw<R, P>::value) {
+    if (twiddled) butterfly_tangent<DIR, P>(v, w, k, M);
+    else butterfly<R, DIR, P>(v);
+  } else {
+    if (twiddled) {
+#pragma unroll
+      for (int r = 1; r < P; ++r) {
+        const cplx<R> t = ldg(w + r - 1);
+        v[r] = DIR < 0 ? v[r] * t : mul_conj(v[r], t);
+      }
+    }
+    butterfly<R, DIR, P>(v);
+  }
+}
+
 // One Stockham autosort stage of radix P over `nlines` lines held in shared memory,
 // element e of line l at [e * sb + l].  ns = product of the radices of earlier stages.
 // Butterfly j reads x[j + r n/P], twiddles by w_n^{r (j mod ns) n/(ns P)}, and writes the
@@ -475,15 +595,7 @@ __device__ __forceinline__ void fft_stage(const cplx<R> *__restrict__ src, cplx<
     cplx<R> v[P];
 #pragma unroll
     for (int r = 0; r < P; ++r) v[r] = in[r * in_stride];
-    if (ns > 1) {
-      const cplx<R> *w = tw + k * (P - 1);   // this stage's table: the P-1 twiddles of k
-#pragma unroll
-      for (int r = 1; r < P; ++r) {
-        const cplx<R> t = ldg(w + r - 1);
-        v[r] = DIR < 0 ? v[r] * t : mul_conj(v[r], t);
-      }
-    }
-    butterfly<R, DIR, P>(v);
+    stage_butterfly<R, DIR, P>(v, ns > 1, tw + k * (P - 1), k, ns * P);   // the P-1 twiddles of k
     cplx<R> *out = d0 + ((j - k) * P + k) * sb;
 #pragma unroll
     for (int s = 0; s < P; ++s) out[s * out_stride] = v[s];
@@ -568,15 +680,7 @@ __device__ __forceinline__ void fft_stage_ct(const cplx<R> *__restrict__ src, cp
     cplx<R> v[P];
 #pragma unroll
     for (int r = 0; r < P; ++r) v[r] = in[r * NBF * SB];
-    if constexpr (NS > 1) {
-      const cplx<R> *w = tw + k * (P - 1);
-#pragma unroll
-      for (int r = 1; r < P; ++r) {
-        const cplx<R> t = ldg(w + r - 1);
-        v[r] = DIR < 0 ? v[r] * t : mul_conj(v[r], t);
-      }
-    }
-    butterfly<R, DIR, P>(v);
+    stage_butterfly<R, DIR, P>(v, NS > 1, tw + k * (P - 1), k, NS * P);
     cplx<R> *out = dst + ((j - k) * P + k) * SB + line;
 #pragma unroll
     for (int s = 0; s < P; ++s) out[s * NS * SB] = v[s];
@@ -830,7 +934,20 @@ __device__ __forceinline__ R quad_weight_r(int i, int n, int simpson) {
 // Set-up kernels
 // ---------------------------------------------------------------------------------------
 // Per-stage twiddle tables of a plan (layout in FftPlan): entry twoff[s] + k (P-1) + r - 1
-// = e^{-2 pi i r k / (ns P)}.
+// = e^{-2 pi i r k / (ns P)}, or its tangent form {t_r, S_r} (see TangentTw) for the FP64
+// radix-2/4/8 stages.
+// sigma and t of the tangent form of e^{-2 pi i a / M}
+__device__ inline void tangent_twiddle(int a, int M, double *sigma, double *t) {
+  double s, c;
+  sincospi(2.0 * (double)a / (double)M, &s, &c);
+  if (tw_rot(a, M)) {   // e^{-i phi} = -sin phi * i * (1 + i cot phi)
+    *sigma = -s;
+    *t = c / s;
+  } else {              // e^{-i phi} = cos phi * (1 - i tan phi)
+    *sigma = c;
+    *t = -s / c;
+  }
+}
 template <typename R>
 __global__ void k_twiddles(cplx<R> *tw, FftPlan pl) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -843,8 +960,21 @@ __global__ void k_twiddles(cplx<R> *tw, FftPlan pl) {
   const int p = pl.radix[st];
   const int q = t - pl.twoff[st];
   const int k = q / (p - 1), r = q - k * (p - 1) + 1;
+  const int M = ns * p;
+  if (std::is_same<R, double>::value && (p == 2 || p == 4 || p == 8)) {
+    // the scale stored with t_r: sigma_r, or sigma_r over the scale it is folded against
+    const int den = (p == 4 && r == 3) || (p == 8 && (r == 3 || r == 5)) ? 1
+                    : p == 8 && r == 6                                   ? 2
+                    : p == 8 && r == 7                                   ? 3
+                                                                         : 0;
+    double sg, tr, sd = 1.0, td;
+    tangent_twiddle(r * k, M, &sg, &tr);
+    if (den) tangent_twiddle(den * k, M, &sd, &td);
+    tw[t] = {R(tr), R(sg / sd)};
+    return;
+  }
   double s, c;
-  sincospi(2.0 * (double)(r * k) / (double)(ns * p), &s, &c);
+  sincospi(2.0 * (double)(r * k) / (double)M, &s, &c);
   tw[t] = {R(c), R(-s)};
 }
 
@@ -1547,11 +1677,13 @@ __global__ void __launch_bounds__(NT) k_cn(KArgs a, int reduce, int renorm) {
 
 // K7 one-thread-per-line variant for the FP64-class types: one thread per x-line (K7) or
 // y-line (K6), consecutive threads on consecutive z (coalesced).  Thomas elimination with
-// the LU factors of k_cn_tables: the forward pass writes y_i over psi_i in place; the
-// backward pass reads y back, recovers psi_i = y_i - alpha_i y_{i-1} and writes
-// psi'_i = 2 chi_i - psi_i.  About 16 FP64-class instructions per point instead of the
-// chunked solver's 24 (no lane carries, no chunk fix-up), for twice its memory traffic,
-// which an FP64-bound step has to spare.
+// the LU factors of k_cn_tables; the backward pass writes psi'_i = 2 chi_i - psi_i over
+// psi_i.  FP64: the forward pass writes y_i to the scratch buffer and the backward pass
+// reads y_i and psi_i back, about 12 FP64 instructions per point instead of the chunked
+// solver's 24 (no lane carries, no chunk fix-up), for 2.5 times its memory traffic, which
+// the FP64-bound step has to spare.  Double-float, whose step leans on HBM more: y_i is
+// written over psi_i and the backward pass recovers psi_i = y_i - alpha_i y_{i-1} (4 more
+// operations per point, half a line's traffic less).
 // AXIS 2 (the z sweep of the FP64-class step, after K5's phase-only pass): one thread per
 // z-line, consecutive threads on consecutive lines; a warp's accesses are 32 lines apart,
 // and the neighbouring points of the next iterations come from the same L1 sectors.
@@ -1580,6 +1712,10 @@ __global__ void __launch_bounds__(128) k_cn_thread(KArgs a, int reduce, int reno
     const size_t stride = AXIS == 2 ? (size_t)1 : AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
     C *p = reinterpret_cast<C *>(a.psi) +
            (AXIS == 2 ? (size_t)line * a.nz : (AXIS == 1 ? (size_t)fixed * a.ny * a.nz : (size_t)fixed * a.nz) + k);
+    // FP64: y_i of this line at yb[i * nlines], consecutive lines side by side, so every
+    // access of a warp is one contiguous segment, whatever the axis
+    constexpr bool kScratch = std::is_same<R, double>::value;
+    C *yb = kScratch ? reinterpret_cast<C *>(a.ybuf) + line : nullptr;
     const Coef *tab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
     const int chunk = a.cn[AXIS].chunk, mp = kWarp * chunk, m = a.cn[AXIS].m;
     const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[AXIS], a.cn_rf[AXIS], a.cn_rl[AXIS]));
@@ -1601,7 +1737,8 @@ __global__ void __launch_bounds__(128) k_cn_thread(KArgs a, int reduce, int reno
             const C v = ring[j];
             if (i + kPf < m) ring[j] = p[(size_t)(i + kPf + 1) * stride];
             y = cfma(ldg(tab + e * kWarp + t), y, v);
-            p[(size_t)(i + 1) * stride] = y;
+            if constexpr (kScratch) yb[(size_t)i * nlines] = y;
+            else p[(size_t)(i + 1) * stride] = y;
             if (++e == chunk) {
               e = 0;
               ++t;
@@ -1613,11 +1750,18 @@ __global__ void __launch_bounds__(128) k_cn_thread(KArgs a, int reduce, int reno
     C chi = czero<R>(), yi = y;
     R s0 = R(0), sx = R(0);
     {
-      // y_{i-1}, i = m-1 .. 0, kPf ahead
+      // FP64: y_i and psi_i, i = m-1 .. 0, kPf ahead (ring holds y, pring psi);
+      // double-float: y_{i-1} in ring
+      C pring[kScratch ? kPf : 1];
 #pragma unroll
       for (int j = 0; j < kPf; ++j) {
         const int i = m - 1 - j;
-        ring[j] = i > 0 ? p[(size_t)i * stride] : czero<R>();
+        if constexpr (kScratch) {
+          ring[j] = i >= 0 ? yb[(size_t)i * nlines] : czero<R>();
+          pring[j] = i >= 0 ? p[(size_t)(i + 1) * stride] : czero<R>();
+        } else {
+          ring[j] = i > 0 ? p[(size_t)i * stride] : czero<R>();
+        }
       }
       int e = (m - 1) % chunk, t = (m - 1) / chunk;
       for (int j0 = 0; j0 < m; j0 += kPf) {
@@ -1625,11 +1769,23 @@ __global__ void __launch_bounds__(128) k_cn_thread(KArgs a, int reduce, int reno
         for (int j = 0; j < kPf; ++j) {
           const int i = m - 1 - (j0 + j);
           if (i >= 0) {
-            const C ym = ring[j];
-            if (i - kPf >= 0) ring[j] = i - kPf > 0 ? p[(size_t)(i - kPf) * stride] : czero<R>();
             const int q = e * kWarp + t;
-            chi = mul(ldg(tab + mp + q), cfma_c(c, chi, yi));
-            const C ps = cfma(neg_coef(ldg(tab + q)), ym, yi);
+            C ycur, ps;
+            if constexpr (kScratch) {
+              ycur = ring[j];
+              ps = pring[j];
+              if (i - kPf >= 0) {
+                ring[j] = yb[(size_t)(i - kPf) * nlines];
+                pring[j] = p[(size_t)(i - kPf + 1) * stride];
+              }
+            } else {
+              const C ym = ring[j];
+              if (i - kPf >= 0) ring[j] = i - kPf > 0 ? p[(size_t)(i - kPf) * stride] : czero<R>();
+              ycur = yi;
+              ps = cfma(neg_coef(ldg(tab + q)), ym, yi);
+              yi = ym;
+            }
+            chi = mul(ldg(tab + mp + q), cfma_c(c, chi, ycur));
             const C out = {twice_minus(chi.re, ps.re), twice_minus(chi.im, ps.im)};
             p[(size_t)(i + 1) * stride] = out;
             if (do_reduce) {
@@ -1638,7 +1794,6 @@ __global__ void __launch_bounds__(128) k_cn_thread(KArgs a, int reduce, int reno
               s0 += d;
               sx = fma(x2tab[i + 1], d, sx);
             }
-            yi = ym;
             if (--e < 0) {
               e = chunk - 1;
               --t;

@@ -84,6 +84,8 @@ struct KArgs {
   void *psi;                   // [nx][ny][nz] complex
   void *spec;                  // [nzh][nx][ny] complex, the z-half-spectrum-major layout
   const void *utab;            // Ut(k) (times the cutoff factor) on [nzh][nx][ny], FP64 only
+  void *ybuf;                  // [point][line] forward-elimination scratch of the FP64
+                               // one-thread-per-line sweeps (nx ny nz complex values)
   float kf[3];                 // 2 pi / (n_d h_d): wavenumber per frequency index (FP32 K3)
   DevState *state;
   double *partials;            // per-block reduction partials
