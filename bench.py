@@ -72,8 +72,8 @@ def fp64_flops_per_point(kernel, shape, precision="fp64"):
     kernels compute them; the derivation is in the design notes.  FFT of length n: 5 n log2 n
     per complex line; the half spectrum has (nz/2+1)/nz complex values per real point.
     Crank-Nicolson: the chunked warp solver (forward, backward, chunk fix-up, 2chi - psi,
-    lane scans) or the one-thread-per-line Thomas solver (forward, backward, psi recovered
-    from y, 2chi - psi)."""
+    lane scans) or the one-thread-per-line Thomas solver (forward, backward, 2chi - psi; in
+    double-float also psi recovered from y, which FP64 reads back instead)."""
     import math
     nx, ny, nz = shape
     half = (nz // 2 + 1) / nz
@@ -81,7 +81,7 @@ def fp64_flops_per_point(kernel, shape, precision="fp64"):
     while chunk * 32 < nz - 2:
         chunk *= 2
     cn_chunked = 8 + 10 + 16 + 4 + 88.0 / chunk
-    cn_line = 8 + 10 + 8 + 4
+    cn_line = 8 + 10 + 4 + (8 if precision == "df64" else 0)
     # FP64: every sweep one thread per line; double-float: the x/y sweeps per line, z chunked
     cn_z = cn_line if precision == "fp64" else cn_chunked
     return {

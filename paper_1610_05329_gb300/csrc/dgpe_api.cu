@@ -139,9 +139,10 @@ Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
   }
   for (int d = 0; d < 3; ++d) {
     L.cn[d] = off;
-    off += align_up((size_t)(4 * cn_chunk(n[d]) + 10) * kWarp * e);   // lane-interleaved tables + scan factors
-    L.cn_adj[d] = off;                                                 // the same for dt -> -dt (adjoint)
-    off += align_up((size_t)(4 * cn_chunk(n[d]) + 10) * kWarp * e);
+    // lane-interleaved tables, scan factors, then the twist pivot of the two-thread sweeps
+    off += align_up((size_t)(4 * cn_chunk(n[d]) + 11) * kWarp * e);
+    L.cn_adj[d] = off;   // the same for dt -> -dt (adjoint)
+    off += align_up((size_t)(4 * cn_chunk(n[d]) + 11) * kWarp * e);
   }
   for (int d = 0; d < 3; ++d) {
     L.dtv[d] = off;

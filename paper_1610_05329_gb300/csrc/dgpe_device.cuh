@@ -1019,6 +1019,8 @@ __global__ void k_cn_tables(CnJobs jobs) {
   Z64 fa[kWarp], ba[kWarp];   // per lane: P at the chunk end, G at the chunk start
   for (int t = 0; t < kWarp; ++t) fa[t] = ba[t] = one;
   Z64 e_prev = diag;
+  const int h = m / 2;   // the twist point of the two-thread (twisted) sweeps
+  Z64 e_h = diag, e_hm = diag;
   for (int s0 = 0; s0 < m; s0 += chunk) {
     const int end = min(s0 + chunk, m) - 1;
     for (int i = s0; i <= end; ++i) {
@@ -1028,6 +1030,8 @@ __global__ void k_cn_tables(CnJobs jobs) {
         const Z64 ca = zmul(c, a);
         e = Z64{diag.re - ca.re, diag.im - ca.im};
       }
+      if (i == h) e_h = e;
+      if (i == m - 1 - h) e_hm = e;
       al[i - s0] = a;
       be[i - s0] = zdiv(one, e);
       e_prev = e;
@@ -1063,6 +1067,8 @@ __global__ void k_cn_tables(CnJobs jobs) {
     for (int t = kWarp - 1; t >= d; --t) fa[t] = zmul(fa[t], fa[t - d]);
     for (int t = 0; t + d < kWarp; ++t) ba[t] = zmul(ba[t], ba[t + d]);
   }
+  // 1/gamma, gamma = e_h + e_{m-1-h} - (1 + 2c): the pivot of the twist point
+  store_coef<R>(tab, 4 * mp + 10 * kWarp, zdiv(one, Z64{e_h.re + e_hm.re - diag.re, e_h.im + e_hm.im - diag.im}));
 }
 
 // dt v_d x_i^2 on one axis, x_i = (i - n/2) h (the potential-step angle, per axis).
@@ -1820,6 +1826,154 @@ __global__ void __launch_bounds__(128) k_cn_thread(KArgs a, int reduce, int reno
   }
 }
 
+// FP64 sweeps: two threads per line, the twisted ("burn at both ends") factorization.  The
+// matrix tridiag(-c, 1 + 2c, -c) reads the same from either end, so its UL factors are its
+// LU factors mirrored: the top thread eliminates points 0 .. h-1 downwards
+// (y_i = psi_i + alpha_i y_{i-1}), the bottom thread points m-1 .. h+1 upwards
+// (z_i = psi_i + alpha_{m-1-i} z_{i+1}), both with table entry s at their s-th step.  They
+// meet at the twist point h = m/2:
+//   gamma x_h = psi_h + alpha_h y_{h-1} + alpha_{m-1-h} z_{h+1},
+//   gamma = e_h + e_{m-1-h} - (1 + 2c)   (e_i = 1/beta_i, the LU pivots; 1/gamma is stored
+// after the scan factors), then substitute back away from h: chi_i = beta_i (y_i + c chi_{i+1})
+// above, chi_i = beta_{m-1-i} (z_i + c chi_{i-1}) below, psi'_i = 2 chi_i - psi_i.  The same
+// 12 FP64 instructions per point as one thread per line, on twice the threads: at 256^3 a
+// sweep is 4096 warps, 6.7 per SM sub-partition instead of 3.4, so the last partial round of
+// warps idles a sub-partition's FP64 unit for 1/28 of the sweep instead of 1/6.  A warp holds
+// 16 lines: lanes 0-15 their top halves, lanes 16-31 their bottom halves.
+template <typename Coef, int AXIS>
+__global__ void __launch_bounds__(128, 7) k_cn_twisted(KArgs a, int reduce, int renorm) {
+  using R = double;
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = AXIS == 0 ? a.nx : AXIS == 1 ? a.ny : a.nz;
+  const int nfixed = AXIS == 0 ? a.ny : a.nx;
+  const long long nlines = AXIS == 2 ? (long long)a.nx * a.ny : (long long)nfixed * a.nz;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const bool bottom = lane >= kWarp / 2;
+  const long long line = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kWarp * (kWarp / 2) + (lane & 15);
+  const bool active = line < nlines;
+  const bool do_reduce = AXIS == 0 && reduce;
+  R *x2tab = reinterpret_cast<R *>(smem_raw);
+  R *wxtab = x2tab + N;
+  if (do_reduce) {
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+      const double x = coordinate(n, a.nx, a.hx);
+      x2tab[n] = x * x;
+      wxtab[n] = quad_weight(n, a.nx, a.simpson);
+    }
+    __syncthreads();
+  }
+  SumAcc<R> acc[4];
+  const long long ln = active ? line : 0;
+  const int k = (int)(ln % a.nz), fixed = (int)(ln / a.nz);
+  const size_t stride = AXIS == 2 ? (size_t)1 : AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
+  // grid index i + 1 of interior point i
+  C *p = reinterpret_cast<C *>(a.psi) +
+         (AXIS == 2 ? (size_t)ln * a.nz : (AXIS == 1 ? (size_t)fixed * a.ny * a.nz : (size_t)fixed * a.nz) + k) + stride;
+  // y_i (z_i) of this line at yb[i * nlines]: consecutive lines side by side
+  C *yb = reinterpret_cast<C *>(a.ybuf) + ln;
+  const Coef *tab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
+  const int lc = a.cn[AXIS].lchunk, chunk = 1 << lc, mp = kWarp << lc, m = a.cn[AXIS].m, h = m / 2;
+  const Coef c = CnCoef<R, Coef>::make(a.cn_r[AXIS]);
+  // table slot of interior point s (lane-interleaved layout)
+  auto slot = [&](int s) { return ((s & (chunk - 1)) << 5) + (s >> lc); };
+  const int dir = bottom ? -1 : 1;
+  const int nf = active ? (bottom ? m - 1 - h : h) : 0;   // elimination steps
+  const int i0 = bottom ? m - 1 : 0;                       // first point eliminated
+  constexpr int kPf = 4;
+  C ring[kPf];
+  C y = czero<R>();
+#pragma unroll
+  for (int j = 0; j < kPf; ++j) ring[j] = j < nf ? p[(ptrdiff_t)(i0 + dir * j) * (ptrdiff_t)stride] : czero<R>();
+  for (int s0 = 0; s0 < nf; s0 += kPf) {
+#pragma unroll
+    for (int j = 0; j < kPf; ++j) {
+      const int s = s0 + j;
+      if (s < nf) {
+        const C v = ring[j];
+        if (s + kPf < nf) ring[j] = p[(ptrdiff_t)(i0 + dir * (s + kPf)) * (ptrdiff_t)stride];
+        y = cfma(ldg(tab + slot(s)), y, v);
+        yb[(size_t)(i0 + dir * s) * (size_t)nlines] = y;
+      }
+    }
+  }
+  // the twist point: the bottom thread takes y_{h-1} from its partner and solves for x_h
+  C yt;
+  yt.re = __shfl_xor_sync(0xffffffffu, y.re, kWarp / 2);
+  yt.im = __shfl_xor_sync(0xffffffffu, y.im, kWarp / 2);
+  C xh = czero<R>(), ph = czero<R>();
+  if (bottom && active) {
+    ph = p[(size_t)h * stride];
+    const Coef ginv = ldg(tab + 4 * mp + 10 * kWarp);
+    // alpha_{m-1-h} multiplies z_{h+1} (zero when the bottom half eliminated nothing)
+    const C rhs = cfma(ldg(tab + slot(m - 1 - h)), y, cfma(ldg(tab + slot(h)), yt, ph));
+    xh = mul(ginv, rhs);
+  }
+  C xt;
+  xt.re = __shfl_xor_sync(0xffffffffu, xh.re, kWarp / 2);
+  xt.im = __shfl_xor_sync(0xffffffffu, xh.im, kWarp / 2);
+  if (!bottom) xh = xt;
+  R s0 = R(0), sx = R(0);
+  auto emit = [&](int i, C out) {
+    p[(size_t)i * stride] = out;
+    if (do_reduce) {
+      R d = out.re * out.re + out.im * out.im;
+      if (a.simpson) d *= wxtab[i + 1];
+      s0 += d;
+      sx = fma(x2tab[i + 1], d, sx);
+    }
+  };
+  if (bottom && active) emit(h, C{twice_minus(xh.re, ph.re), twice_minus(xh.im, ph.im)});
+  // back-substitution away from h: point ib0 - dir j, table entry tb0 - j
+  {
+    const int ib0 = bottom ? h + 1 : h - 1;
+    const int tb0 = bottom ? m - 2 - h : h - 1;
+    C yr[kPf], pr[kPf];
+#pragma unroll
+    for (int j = 0; j < kPf; ++j) {
+      const int i = ib0 - dir * j;
+      yr[j] = j < nf ? yb[(size_t)i * (size_t)nlines] : czero<R>();
+      pr[j] = j < nf ? p[(ptrdiff_t)i * (ptrdiff_t)stride] : czero<R>();
+    }
+    C chi = xh;
+    for (int j0 = 0; j0 < nf; j0 += kPf) {
+#pragma unroll
+      for (int jj = 0; jj < kPf; ++jj) {
+        const int j = j0 + jj;
+        if (j < nf) {
+          const int i = ib0 - dir * j;
+          const C yi = yr[jj], ps = pr[jj];
+          if (j + kPf < nf) {
+            const int in = ib0 - dir * (j + kPf);
+            yr[jj] = yb[(size_t)in * (size_t)nlines];
+            pr[jj] = p[(ptrdiff_t)in * (ptrdiff_t)stride];
+          }
+          chi = mul(ldg(tab + mp + slot(tb0 - j)), cfma_c(c, chi, yi));
+          emit(i, C{twice_minus(chi.re, ps.re), twice_minus(chi.im, ps.im)});
+        }
+      }
+    }
+  }
+  if (active) {
+    // the walls (grid points 0 and N-1)
+    if (!bottom) p[-(ptrdiff_t)stride] = czero<R>();
+    else p[(size_t)m * stride] = czero<R>();
+    if (do_reduce) {
+      const R wyz = quad_weight_r<R>(fixed, a.ny, a.simpson) * quad_weight_r<R>(k, a.nz, a.simpson);
+      const R yv = R(fixed - a.ny / 2) * R(a.hy), zv = R(k - a.nz / 2) * R(a.hz);
+      const R tt = wyz * s0;
+      acc[0].add(tt);
+      acc[1].add(wyz * sx);
+      acc[2].add(yv * yv * tt);
+      acc[3].add(zv * zv * tt);
+    }
+  }
+  if (do_reduce) {
+    double v[4] = {acc[0].value(), acc[1].value(), acc[2].value(), acc[3].value()};
+    finish_sweep_sums(a, v, renorm);
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Adjoint of the real-time potential step (the paper has no adjoint; this differentiates
 // the step above by hand).  With P(psi) = e^{-i theta} psi, theta = dt (V + g n + gdd Phi[n])
@@ -2341,10 +2495,16 @@ struct Impl {
     const int n = AXIS == 0 ? a.nx : AXIS == 1 ? a.ny : a.nz;
     if constexpr (kCnThread) {
       const long long lines = AXIS == 2 ? (long long)a.nx * a.ny : (long long)(AXIS == 0 ? a.ny : a.nx) * a.nz;
-      const unsigned blocks = (unsigned)((lines + 127) / 128);
       const size_t sm = AXIS == 0 ? 2 * (size_t)n * sizeof(R) : 0;
-      if (a.imag) k_cn_thread<R, R, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
-      else k_cn_thread<R, C, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
+      if constexpr (std::is_same<R, double>::value) {
+        const unsigned blocks = (unsigned)((lines + 63) / 64);   // 64 lines, two threads each
+        if (a.imag) k_cn_twisted<R, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
+        else k_cn_twisted<C, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
+      } else {
+        const unsigned blocks = (unsigned)((lines + 127) / 128);
+        if (a.imag) k_cn_thread<R, R, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
+        else k_cn_thread<R, C, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
+      }
     } else {
       const size_t sm = smem_cn(n, a.cn[AXIS].lchunk);
       if (a.imag) k_cn<R, R, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, reduce, renorm);
@@ -2402,7 +2562,9 @@ struct Impl {
     const dim3 z = grid_z(a);
     const int bz = (int)(z.x * z.y);
     const int bx = ((a.nz + T::kCnCols - 1) / T::kCnCols) * a.ny;
-    const int bt = (int)(((long long)a.ny * a.nz + 127) / 128);   // k_cn_thread along x
+    // the per-line sweep along x: 128 lines per block, 64 for the FP64 two-thread form
+    const int lpb = std::is_same<R, double>::value ? 64 : 128;
+    const int bt = (int)(((long long)a.ny * a.nz + lpb - 1) / lpb);
     return std::max(bz, std::max(bx, bt));
   }
 

@@ -25,7 +25,8 @@ struct FftPlan {
 // four arrays [alpha | beta | H | G] of 32*c coefficients each (complex in real time,
 // real in imaginary time, in the kernel precision), lane-interleaved: the entry of interior
 // point t*c + e sits at e*32 + t, so the 32 lanes of a warp read one contiguous segment;
-// then 10 x 32 scan factors of the lane carries (5 forward steps, 5 backward).
+// then 10 x 32 scan factors of the lane carries (5 forward steps, 5 backward), then
+// 1/gamma, the pivot of the twist point m/2 of the FP64 two-thread sweeps.
 // Factor tables to build in one launch (one block each): the three axes, forward and (real
 // time) the dt -> -dt tables of the adjoint sweeps.
 struct CnJob {
