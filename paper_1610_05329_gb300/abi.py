@@ -102,6 +102,7 @@ _SIGNATURES = [
     ("dgpe_set_psi", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("dgpe_get_psi", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("dgpe_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("dgpe_step_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("dgpe_substep", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("dgpe_observables", ctypes.c_int, [ctypes.c_void_p, _P(dgpe_obs)]),
     ("dgpe_get_phi", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -207,6 +208,11 @@ def dgpe_get_psi(ctx, ptr, where):
 
 def dgpe_step(ctx, nsteps):
     _check(load().dgpe_step(ctx, int(nsteps)), "dgpe_step")
+
+
+def dgpe_step_host(ctx, in_ptr, out_ptr, nsteps):
+    _check(load().dgpe_step_host(ctx, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), int(nsteps)),
+           "dgpe_step_host")
 
 
 def dgpe_substep(ctx, which):
@@ -417,6 +423,22 @@ class Condensate:
 
     def step(self, nsteps=1):
         dgpe_step(self.ctx, nsteps)
+
+    def step_host(self, psi_in, psi_out, nsteps=1):
+        """dgpe_step_host on CPU tensors or arrays of psi's shape and boundary dtype
+        (pinned tensors make the copies asynchronous).  Both must stay alive and unchanged,
+        and psi_out unread, until sync()."""
+        ptrs = []
+        for t in (psi_in, psi_out):
+            if isinstance(t, np.ndarray):
+                assert t.shape == self.shape and t.dtype == self.np_cdtype and t.flags.c_contiguous
+                ptrs.append(t.ctypes.data)
+            else:
+                assert tuple(t.shape) == self.shape and t.dtype == self.cdtype and t.is_contiguous()
+                assert t.device.type == "cpu"
+                ptrs.append(t.data_ptr())
+        self._keep_host = (psi_in, psi_out)
+        dgpe_step_host(self.ctx, ptrs[0], ptrs[1], nsteps)
 
     def substep(self, which):
         dgpe_substep(self.ctx, which)

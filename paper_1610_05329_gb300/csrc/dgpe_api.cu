@@ -259,6 +259,11 @@ struct dgpe_ctx {
   int latched;
   int plan_style[3];
   unsigned generation;   // bumped whenever the captured step would change (batches rebuild)
+  // dgpe_step_host: device staging of the host input and output, one copy stream each
+  void *stage_in, *stage_out;
+  cudaStream_t cs_in, cs_out;
+  cudaEvent_t ev_in_ready, ev_in_free, ev_out_ready, ev_out_free;
+  bool host_io;
 };
 
 struct dgpe_batch {
@@ -1108,9 +1113,67 @@ void dgpe_batch_destroy(dgpe_batch *b) {
 
 int dgpe_sync(dgpe_ctx *c) {
   if (!c) return DGPE_EINVAL;
-  const int rc = map_cuda(cudaStreamSynchronize(c->stream));
+  int rc = map_cuda(cudaStreamSynchronize(c->stream));
+  if (!rc && c->host_io) rc = map_cuda(cudaStreamSynchronize(c->cs_in));
+  if (!rc && c->host_io) rc = map_cuda(cudaStreamSynchronize(c->cs_out));
   if (rc) return rc;
   return check_device_flags(c);
+}
+
+namespace {
+// The staging buffers, streams and events of dgpe_step_host, created at its first call.
+int host_io_setup(dgpe_ctx *c) {
+  if (c->host_io) return DGPE_OK;
+  const size_t bytes = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;
+  int rc = map_cuda(cudaMalloc(&c->stage_in, bytes));
+  if (!rc) rc = map_cuda(cudaMalloc(&c->stage_out, bytes));
+  if (!rc) rc = map_cuda(cudaStreamCreateWithFlags(&c->cs_in, cudaStreamNonBlocking));
+  if (!rc) rc = map_cuda(cudaStreamCreateWithFlags(&c->cs_out, cudaStreamNonBlocking));
+  cudaEvent_t *ev[4] = {&c->ev_in_ready, &c->ev_in_free, &c->ev_out_ready, &c->ev_out_free};
+  for (int q = 0; q < 4 && !rc; ++q) rc = map_cuda(cudaEventCreateWithFlags(ev[q], cudaEventDisableTiming));
+  if (rc) return rc;   // dgpe_destroy frees whatever was created
+  c->host_io = true;
+  return DGPE_OK;
+}
+}  // namespace
+
+int dgpe_step_host(dgpe_ctx *c, const void *in, void *out, int nsteps) {
+  if (!c || !in || !out || nsteps < 0) return DGPE_EINVAL;
+  int rc = host_io_setup(c);
+  if (rc) return rc;
+  const size_t n = (size_t)c->p.nx * c->p.ny * c->p.nz;
+  const size_t bytes = n * c->ks->elem_bytes;
+  // host -> input staging on its copy stream, once the previous call has consumed the staging
+  rc = map_cuda(cudaStreamWaitEvent(c->cs_in, c->ev_in_free, 0));
+  if (!rc) rc = map_cuda(cudaMemcpyAsync(c->stage_in, in, bytes, cudaMemcpyHostToDevice, c->cs_in));
+  if (!rc) rc = map_cuda(cudaEventRecord(c->ev_in_ready, c->cs_in));
+  // staging -> psi on the context's stream (double-float: split into pairs on the way)
+  if (!rc) rc = map_cuda(cudaStreamWaitEvent(c->stream, c->ev_in_ready, 0));
+  if (!rc) {
+    if (c->p.precision == DGPE_DF64) rc = map_cuda(c->ks->from_c128(c->stage_in, c->args.psi, n, c->stream));
+    else rc = map_cuda(cudaMemcpyAsync(c->args.psi, c->stage_in, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  if (!rc) rc = map_cuda(c->ks->reset_state(c->args.state, c->stream));
+  if (!rc) rc = map_cuda(cudaEventRecord(c->ev_in_free, c->stream));
+  if (rc) return rc;
+  c->latched = DGPE_OK;
+  rc = dgpe_step(c, nsteps);
+  if (rc) return rc;
+  // psi (pending renormalisation applied: imaginary time only, real-time steps leave s = 1)
+  // -> output staging, once the previous call's output copy has left it
+  rc = map_cuda(cudaStreamWaitEvent(c->stream, c->ev_out_free, 0));
+  if (!rc && c->p.mode == DGPE_IMAG_TIME)
+    rc = launch(c, c->stream, kKMaterialize, [&] { return c->ks->materialize(c->args, c->stream); });
+  if (!rc) {
+    if (c->p.precision == DGPE_DF64) rc = map_cuda(c->ks->to_c128(c->args.psi, c->stage_out, n, c->stream));
+    else rc = map_cuda(cudaMemcpyAsync(c->stage_out, c->args.psi, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  if (!rc) rc = map_cuda(cudaEventRecord(c->ev_out_ready, c->stream));
+  // output staging -> host on the other copy stream
+  if (!rc) rc = map_cuda(cudaStreamWaitEvent(c->cs_out, c->ev_out_ready, 0));
+  if (!rc) rc = map_cuda(cudaMemcpyAsync(out, c->stage_out, bytes, cudaMemcpyDeviceToHost, c->cs_out));
+  if (!rc) rc = map_cuda(cudaEventRecord(c->ev_out_free, c->cs_out));
+  return rc;
 }
 
 int dgpe_set_timing(dgpe_ctx *c, int enable) {
@@ -1154,6 +1217,14 @@ int dgpe_kernel_times(dgpe_ctx *c, dgpe_kernel_time *out, int max, int *n) {
 void dgpe_destroy(dgpe_ctx *c) {
   if (!c) return;
   if (c->ws) cudaStreamSynchronize(c->stream);
+  if (c->cs_in) cudaStreamSynchronize(c->cs_in);
+  if (c->cs_out) cudaStreamSynchronize(c->cs_out);
+  for (cudaEvent_t e : {c->ev_in_ready, c->ev_in_free, c->ev_out_ready, c->ev_out_free})
+    if (e) cudaEventDestroy(e);
+  if (c->cs_in) cudaStreamDestroy(c->cs_in);
+  if (c->cs_out) cudaStreamDestroy(c->cs_out);
+  if (c->stage_in) cudaFree(c->stage_in);
+  if (c->stage_out) cudaFree(c->stage_out);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (const auto &pd : c->pending) {
     cudaEventDestroy(pd.a);

@@ -77,6 +77,7 @@ def test_create_rejects_invalid_parameters_without_touching_the_gpu(lib, bad):
 def test_null_arguments(lib):
     assert lib.dgpe_create(None, None, None) == abi.DGPE_EINVAL
     assert lib.dgpe_step(None, 1) == abi.DGPE_EINVAL
+    assert lib.dgpe_step_host(None, None, None, 1) == abi.DGPE_EINVAL
     assert lib.dgpe_sync(None) == abi.DGPE_EINVAL
     assert lib.dgpe_get_tuning(None, None) == abi.DGPE_EINVAL
     assert lib.dgpe_step_launches(None, None) == abi.DGPE_EINVAL
