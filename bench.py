@@ -51,11 +51,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch from ncu captures (profiles/), valid while the kernel
 # source is byte-identical to the one captured (sha1 of dgpe_device.cuh).
 NCU_TRAFFIC = {
-    # FP64: the K5 record times two launches (the phase-only pass and the per-line z sweep)
-    "a4ee63ede1b3a7a8b1a5564ecb136f3a6a7ad0d6": {
-        ("real256_fp64", "k5_c2r_z_phase_cn_z"): 1499.12e6,
-        ("real512x512x384_mixed", "k5_c2r_z_phase_cn_z"): 1959.07e6,
-        ("real256_df64", "k5_c2r_z_phase_cn_z"): 620.68e6,
+    # FP64: the K5 record times two launches (the phase-only pass and the two-thread z sweep)
+    "46be18559eabfd12b03d4a2b08c28d510f31f344": {
+        ("real256_fp64", "k5_c2r_z_phase_cn_z"): 1872.67e6,
+        ("real512x512x384_mixed", "k5_c2r_z_phase_cn_z"): 1958.98e6,
+        ("real256_df64", "k5_c2r_z_phase_cn_z"): 620.45e6,
     },
 }
 
