@@ -89,8 +89,9 @@ def fp64_flops_per_point(kernel, shape, precision="fp64"):
         "k2_fft_y": 5 * math.log2(ny) * half,
         "k3_fft_x_dipolar_ifft_x": (10 * math.log2(nx) + 2) * half,
         "k4_ifft_y": 5 * math.log2(ny) * half,
-        # sine/cosine: 22 flops for |theta| <= 1/4 (every point of this workload), else 36 + reduction
-        "k5_c2r_z_phase_cn_z": 2.5 * math.log2(nz) + 2 + 9 + 22 + 6 + cn_z,
+        # sine/cosine: 18 flops for |theta| <= 1/8 (99.5 % of this workload's points; the
+        # rest up to 0.15), 22 up to 1/4, else 36 + reduction
+        "k5_c2r_z_phase_cn_z": 2.5 * math.log2(nz) + 2 + 9 + 18 + 6 + cn_z,
         "k6_cn_y": cn_line,
         "k7_cn_x_reduce": cn_line + 6,
     }.get(kernel, 0.0)
