@@ -504,7 +504,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 512x512x384 mixed-precision line item")
     ap.add_argument("--no-df64", action="store_true", help="skip the 256^3 double-float line item")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 128^3 differentiation line item")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-condensate batching line item")
     ap.add_argument("--no-paper-grids", action="store_true", help="skip the paper-grid context line item")
