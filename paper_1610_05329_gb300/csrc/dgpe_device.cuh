@@ -103,6 +103,11 @@ __device__ __forceinline__ double shfl_down(double v, int d) { return __shfl_dow
 __device__ __forceinline__ float shfl_down(float v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
 __device__ __forceinline__ df shfl_up(df v, int d) { return {shfl_up(v.hi, d), shfl_up(v.lo, d)}; }
 __device__ __forceinline__ df shfl_down(df v, int d) { return {shfl_down(v.hi, d), shfl_down(v.lo, d)}; }
+__device__ __forceinline__ double shfl_xor(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ float shfl_xor(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ df shfl_xor(df v, int m) { return {shfl_xor(v.hi, m), shfl_xor(v.lo, m)}; }
+template <typename R>
+__device__ __forceinline__ cplx<R> shfl_xor(cplx<R> v, int m) { return {shfl_xor(v.re, m), shfl_xor(v.im, m)}; }
 template <typename R>
 __device__ __forceinline__ cplx<R> shfl_up(cplx<R> v, int d) { return {shfl_up(v.re, d), shfl_up(v.im, d)}; }
 template <typename R>
@@ -1701,169 +1706,27 @@ __global__ void __launch_bounds__(NT) k_cn(KArgs a, int reduce, int renorm) {
   }
 }
 
-// K7 one-thread-per-line variant for the FP64-class types: one thread per x-line (K7) or
-// y-line (K6), consecutive threads on consecutive z (coalesced).  Thomas elimination with
-// the LU factors of k_cn_tables; the backward pass writes psi'_i = 2 chi_i - psi_i over
-// psi_i.  FP64: the forward pass writes y_i to the scratch buffer and the backward pass
-// reads y_i and psi_i back, about 12 FP64 instructions per point instead of the chunked
-// solver's 24 (no lane carries, no chunk fix-up), for 2.5 times its memory traffic, which
-// the FP64-bound step has to spare.  Double-float, whose step leans on HBM more: y_i is
-// written over psi_i and the backward pass recovers psi_i = y_i - alpha_i y_{i-1} (4 more
-// operations per point, half a line's traffic less).
-// AXIS 2 (the z sweep of the FP64-class step, after K5's phase-only pass): one thread per
-// z-line, consecutive threads on consecutive lines; a warp's accesses are 32 lines apart,
-// and the neighbouring points of the next iterations come from the same L1 sectors.
-template <typename R, typename Coef, int AXIS>
-__global__ void __launch_bounds__(128) k_cn_thread(KArgs a, int reduce, int renorm) {
-  using C = cplx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = AXIS == 0 ? a.nx : AXIS == 1 ? a.ny : a.nz;
-  const int nfixed = AXIS == 0 ? a.ny : a.nx;
-  const long long nlines = AXIS == 2 ? (long long)a.nx * a.ny : (long long)nfixed * a.nz;
-  const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool do_reduce = AXIS == 0 && reduce;
-  R *x2tab = reinterpret_cast<R *>(smem_raw);
-  R *wxtab = x2tab + N;
-  if (do_reduce) {
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-      const double x = coordinate(n, a.nx, a.hx);
-      x2tab[n] = R(x * x);
-      wxtab[n] = R(quad_weight(n, a.nx, a.simpson));
-    }
-    __syncthreads();
-  }
-  SumAcc<R> acc[4];
-  if (line < nlines) {
-    const int k = (int)(line % a.nz), fixed = (int)(line / a.nz);
-    const size_t stride = AXIS == 2 ? (size_t)1 : AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
-    C *p = reinterpret_cast<C *>(a.psi) +
-           (AXIS == 2 ? (size_t)line * a.nz : (AXIS == 1 ? (size_t)fixed * a.ny * a.nz : (size_t)fixed * a.nz) + k);
-    // FP64: y_i of this line at yb[i * nlines], consecutive lines side by side, so every
-    // access of a warp is one contiguous segment, whatever the axis
-    constexpr bool kScratch = std::is_same<R, double>::value;
-    C *yb = kScratch ? reinterpret_cast<C *>(a.ybuf) + line : nullptr;
-    const Coef *tab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
-    const int chunk = a.cn[AXIS].chunk, mp = kWarp * chunk, m = a.cn[AXIS].m;
-    const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[AXIS], a.cn_rf[AXIS], a.cn_rl[AXIS]));
-    // interior point i (grid index i + 1) sits at e * 32 + t of each lane-interleaved table,
-    // i = t * chunk + e
-    // loads run kPf points ahead of the recurrences (registers as a ring)
-    constexpr int kPf = 8;
-    C ring[kPf];
-    C y = czero<R>();
-    {
-#pragma unroll
-      for (int j = 0; j < kPf; ++j) ring[j] = j < m ? p[(size_t)(j + 1) * stride] : czero<R>();
-      int e = 0, t = 0;
-      for (int i0 = 0; i0 < m; i0 += kPf) {
-#pragma unroll
-        for (int j = 0; j < kPf; ++j) {
-          const int i = i0 + j;
-          if (i < m) {
-            const C v = ring[j];
-            if (i + kPf < m) ring[j] = p[(size_t)(i + kPf + 1) * stride];
-            y = cfma(ldg(tab + e * kWarp + t), y, v);
-            if constexpr (kScratch) yb[(size_t)i * nlines] = y;
-            else p[(size_t)(i + 1) * stride] = y;
-            if (++e == chunk) {
-              e = 0;
-              ++t;
-            }
-          }
-        }
-      }
-    }
-    C chi = czero<R>(), yi = y;
-    R s0 = R(0), sx = R(0);
-    {
-      // FP64: y_i and psi_i, i = m-1 .. 0, kPf ahead (ring holds y, pring psi);
-      // double-float: y_{i-1} in ring
-      C pring[kScratch ? kPf : 1];
-#pragma unroll
-      for (int j = 0; j < kPf; ++j) {
-        const int i = m - 1 - j;
-        if constexpr (kScratch) {
-          ring[j] = i >= 0 ? yb[(size_t)i * nlines] : czero<R>();
-          pring[j] = i >= 0 ? p[(size_t)(i + 1) * stride] : czero<R>();
-        } else {
-          ring[j] = i > 0 ? p[(size_t)i * stride] : czero<R>();
-        }
-      }
-      int e = (m - 1) % chunk, t = (m - 1) / chunk;
-      for (int j0 = 0; j0 < m; j0 += kPf) {
-#pragma unroll
-        for (int j = 0; j < kPf; ++j) {
-          const int i = m - 1 - (j0 + j);
-          if (i >= 0) {
-            const int q = e * kWarp + t;
-            C ycur, ps;
-            if constexpr (kScratch) {
-              ycur = ring[j];
-              ps = pring[j];
-              if (i - kPf >= 0) {
-                ring[j] = yb[(size_t)(i - kPf) * nlines];
-                pring[j] = p[(size_t)(i - kPf + 1) * stride];
-              }
-            } else {
-              const C ym = ring[j];
-              if (i - kPf >= 0) ring[j] = i - kPf > 0 ? p[(size_t)(i - kPf) * stride] : czero<R>();
-              ycur = yi;
-              ps = cfma(neg_coef(ldg(tab + q)), ym, yi);
-              yi = ym;
-            }
-            chi = mul(ldg(tab + mp + q), cfma_c(c, chi, ycur));
-            const C out = {twice_minus(chi.re, ps.re), twice_minus(chi.im, ps.im)};
-            p[(size_t)(i + 1) * stride] = out;
-            if (do_reduce) {
-              R d = out.re * out.re + out.im * out.im;
-              if (a.simpson) d *= wxtab[i + 1];
-              s0 += d;
-              sx = fma(x2tab[i + 1], d, sx);
-            }
-            if (--e < 0) {
-              e = chunk - 1;
-              --t;
-            }
-          }
-        }
-      }
-    }
-    p[0] = czero<R>();
-    p[(size_t)(N - 1) * stride] = czero<R>();
-    if (do_reduce) {
-      const R wyz = quad_weight_r<R>(fixed, a.ny, a.simpson) * quad_weight_r<R>(k, a.nz, a.simpson);
-      const R yv = R(fixed - a.ny / 2) * R(a.hy), zv = R(k - a.nz / 2) * R(a.hz);
-      const R tt = wyz * s0;
-      acc[0].add(tt);
-      acc[1].add(wyz * sx);
-      acc[2].add(yv * yv * tt);
-      acc[3].add(zv * zv * tt);
-    }
-  }
-  if (do_reduce) {
-    double v[4] = {acc[0].value(), acc[1].value(), acc[2].value(), acc[3].value()};
-    finish_sweep_sums(a, v, renorm);
-  }
-}
-
-// FP64 sweeps: two threads per line, the twisted ("burn at both ends") factorization.  The
-// matrix tridiag(-c, 1 + 2c, -c) reads the same from either end, so its UL factors are its
-// LU factors mirrored: the top thread eliminates points 0 .. h-1 downwards
+// FP64-class sweeps: two threads per line, the twisted ("burn at both ends") factorization.
+// The matrix tridiag(-c, 1 + 2c, -c) reads the same from either end, so its UL factors are
+// its LU factors mirrored: the top thread eliminates points 0 .. h-1 downwards
 // (y_i = psi_i + alpha_i y_{i-1}), the bottom thread points m-1 .. h+1 upwards
 // (z_i = psi_i + alpha_{m-1-i} z_{i+1}), both with table entry s at their s-th step.  They
 // meet at the twist point h = m/2:
 //   gamma x_h = psi_h + alpha_h y_{h-1} + alpha_{m-1-h} z_{h+1},
 //   gamma = e_h + e_{m-1-h} - (1 + 2c)   (e_i = 1/beta_i, the LU pivots; 1/gamma is stored
 // after the scan factors), then substitute back away from h: chi_i = beta_i (y_i + c chi_{i+1})
-// above, chi_i = beta_{m-1-i} (z_i + c chi_{i-1}) below, psi'_i = 2 chi_i - psi_i.  The same
-// 12 FP64 instructions per point as one thread per line, on twice the threads: at 256^3 a
-// sweep is 4096 warps, 6.7 per SM sub-partition instead of 3.4, so the last partial round of
-// warps idles a sub-partition's FP64 unit for 1/28 of the sweep instead of 1/6.  A warp holds
-// 16 lines: lanes 0-15 their top halves, lanes 16-31 their bottom halves.
-template <typename Coef, int AXIS>
+// above, chi_i = beta_{m-1-i} (z_i + c chi_{i-1}) below, psi'_i = 2 chi_i - psi_i.  Twice the
+// threads of one thread per line: at 256^3 a sweep is 4096 warps, 6.7 per SM sub-partition
+// instead of 3.4, so the last partial round of warps idles a sub-partition for about 1/28 of
+// the sweep instead of 1/6.  A warp holds 16 lines: lanes 0-15 their top halves, lanes 16-31
+// their bottom halves.
+// FP64 (12 FP64 instructions per point) writes y and z to the scratch buffer and reads them
+// and psi back; double-float, whose step leans on HBM more, writes them over psi and
+// recovers psi_i = y_i - alpha_i y_{i-1} (z_i - alpha_{m-1-i} z_{i+1}) on the way back.
+template <typename R, typename Coef, int AXIS>
 __global__ void __launch_bounds__(128, 7) k_cn_twisted(KArgs a, int reduce, int renorm) {
-  using R = double;
   using C = cplx<R>;
+  constexpr bool kScratch = std::is_same<R, double>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = AXIS == 0 ? a.nx : AXIS == 1 ? a.ny : a.nz;
   const int nfixed = AXIS == 0 ? a.ny : a.nx;
@@ -1878,8 +1741,8 @@ __global__ void __launch_bounds__(128, 7) k_cn_twisted(KArgs a, int reduce, int 
   if (do_reduce) {
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
       const double x = coordinate(n, a.nx, a.hx);
-      x2tab[n] = x * x;
-      wxtab[n] = quad_weight(n, a.nx, a.simpson);
+      x2tab[n] = R(x * x);
+      wxtab[n] = R(quad_weight(n, a.nx, a.simpson));
     }
     __syncthreads();
   }
@@ -1890,11 +1753,12 @@ __global__ void __launch_bounds__(128, 7) k_cn_twisted(KArgs a, int reduce, int 
   // grid index i + 1 of interior point i
   C *p = reinterpret_cast<C *>(a.psi) +
          (AXIS == 2 ? (size_t)ln * a.nz : (AXIS == 1 ? (size_t)fixed * a.ny * a.nz : (size_t)fixed * a.nz) + k) + stride;
-  // y_i (z_i) of this line at yb[i * nlines]: consecutive lines side by side
-  C *yb = reinterpret_cast<C *>(a.ybuf) + ln;
+  // FP64: y_i (z_i) of this line at yb[i * nlines], consecutive lines side by side
+  C *yb = kScratch ? reinterpret_cast<C *>(a.ybuf) + ln : nullptr;
+  auto elim = [&](int i) -> C & { return kScratch ? yb[(size_t)i * (size_t)nlines] : p[(size_t)i * stride]; };
   const Coef *tab = reinterpret_cast<const Coef *>(a.cn[AXIS].tab);
   const int lc = a.cn[AXIS].lchunk, chunk = 1 << lc, mp = kWarp << lc, m = a.cn[AXIS].m, h = m / 2;
-  const Coef c = CnCoef<R, Coef>::make(a.cn_r[AXIS]);
+  const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[AXIS], a.cn_rf[AXIS], a.cn_rl[AXIS]));
   // table slot of interior point s (lane-interleaved layout)
   auto slot = [&](int s) { return ((s & (chunk - 1)) << 5) + (s >> lc); };
   const int dir = bottom ? -1 : 1;
@@ -1913,14 +1777,12 @@ __global__ void __launch_bounds__(128, 7) k_cn_twisted(KArgs a, int reduce, int 
         const C v = ring[j];
         if (s + kPf < nf) ring[j] = p[(ptrdiff_t)(i0 + dir * (s + kPf)) * (ptrdiff_t)stride];
         y = cfma(ldg(tab + slot(s)), y, v);
-        yb[(size_t)(i0 + dir * s) * (size_t)nlines] = y;
+        elim(i0 + dir * s) = y;
       }
     }
   }
   // the twist point: the bottom thread takes y_{h-1} from its partner and solves for x_h
-  C yt;
-  yt.re = __shfl_xor_sync(0xffffffffu, y.re, kWarp / 2);
-  yt.im = __shfl_xor_sync(0xffffffffu, y.im, kWarp / 2);
+  const C yt = shfl_xor(y, kWarp / 2);
   C xh = czero<R>(), ph = czero<R>();
   if (bottom && active) {
     ph = p[(size_t)h * stride];
@@ -1929,9 +1791,7 @@ __global__ void __launch_bounds__(128, 7) k_cn_twisted(KArgs a, int reduce, int 
     const C rhs = cfma(ldg(tab + slot(m - 1 - h)), y, cfma(ldg(tab + slot(h)), yt, ph));
     xh = mul(ginv, rhs);
   }
-  C xt;
-  xt.re = __shfl_xor_sync(0xffffffffu, xh.re, kWarp / 2);
-  xt.im = __shfl_xor_sync(0xffffffffu, xh.im, kWarp / 2);
+  const C xt = shfl_xor(xh, kWarp / 2);
   if (!bottom) xh = xt;
   R s0 = R(0), sx = R(0);
   auto emit = [&](int i, C out) {
@@ -1948,27 +1808,44 @@ __global__ void __launch_bounds__(128, 7) k_cn_twisted(KArgs a, int reduce, int 
   {
     const int ib0 = bottom ? h + 1 : h - 1;
     const int tb0 = bottom ? m - 2 - h : h - 1;
-    C yr[kPf], pr[kPf];
+    // FP64: y_i and psi_i of the coming points; double-float: the eliminated value one point
+    // further on (psi_i is recovered from it), the current one carried in `cur`
+    C yr[kPf], pr[kScratch ? kPf : 1];
 #pragma unroll
     for (int j = 0; j < kPf; ++j) {
-      const int i = ib0 - dir * j;
-      yr[j] = j < nf ? yb[(size_t)i * (size_t)nlines] : czero<R>();
-      pr[j] = j < nf ? p[(ptrdiff_t)i * (ptrdiff_t)stride] : czero<R>();
+      if constexpr (kScratch) {
+        const int i = ib0 - dir * j;
+        yr[j] = j < nf ? elim(i) : czero<R>();
+        pr[j] = j < nf ? p[(ptrdiff_t)i * (ptrdiff_t)stride] : czero<R>();
+      } else {
+        yr[j] = j + 1 < nf ? elim(ib0 - dir * (j + 1)) : czero<R>();
+      }
     }
-    C chi = xh;
+    C chi = xh, cur = y;
     for (int j0 = 0; j0 < nf; j0 += kPf) {
 #pragma unroll
       for (int jj = 0; jj < kPf; ++jj) {
         const int j = j0 + jj;
         if (j < nf) {
           const int i = ib0 - dir * j;
-          const C yi = yr[jj], ps = pr[jj];
-          if (j + kPf < nf) {
-            const int in = ib0 - dir * (j + kPf);
-            yr[jj] = yb[(size_t)in * (size_t)nlines];
-            pr[jj] = p[(ptrdiff_t)in * (ptrdiff_t)stride];
+          const int q = slot(tb0 - j);
+          C yi, ps;
+          if constexpr (kScratch) {
+            yi = yr[jj];
+            ps = pr[jj];
+            if (j + kPf < nf) {
+              const int in = ib0 - dir * (j + kPf);
+              yr[jj] = elim(in);
+              pr[jj] = p[(ptrdiff_t)in * (ptrdiff_t)stride];
+            }
+          } else {
+            const C nxt = yr[jj];
+            if (j + 1 + kPf < nf) yr[jj] = elim(ib0 - dir * (j + 1 + kPf));
+            yi = cur;
+            ps = cfma(neg_coef(ldg(tab + q)), nxt, cur);
+            cur = nxt;
           }
-          chi = mul(ldg(tab + mp + slot(tb0 - j)), cfma_c(c, chi, yi));
+          chi = mul(ldg(tab + mp + q), cfma_c(c, chi, yi));
           emit(i, C{twice_minus(chi.re, ps.re), twice_minus(chi.im, ps.im)});
         }
       }
@@ -2237,8 +2114,8 @@ struct Impl {
   // compile-time transforms of lengths 128-512 (not for double-float: its kernels take many
   // times longer to compile)
   static constexpr bool kCtSizes = !std::is_same<R, df>::value;
-  // the FP64-class sweeps run one thread per line (k_cn_thread), the FP32 ones the chunked
-  // solver in persistent tiles (k_cn)
+  // the FP64-class sweeps run a Thomas solve per line on two threads (k_cn_twisted), the
+  // FP32 ones the chunked solver in persistent tiles (k_cn)
   static constexpr bool kCnThread = Fp64Class<R>::value;
   // FP64: the z sweep too, after a phase-only K5 pass (the FP64 pipe bounds the step, so the
   // fewer FP64 instructions win over the extra pass; for double-float they do not)
@@ -2477,7 +2354,7 @@ struct Impl {
   static constexpr int kZFast = kZSplit ? kZPhaseOnly : kZStep;
   static cudaError_t k5(const KArgs &a, int zmode, cudaStream_t st) {
     if constexpr (kZSplit) {
-      // the z sweep runs one thread per line after the phase-only pass
+      // the z sweep runs per line (two threads each) after the phase-only pass
       if (zmode == kZCnOnly) return cn<2>(a, 0, 0, st);
       if (zmode == kZStep) {
         const cudaError_t e = k5(a, kZPhaseOnly, st);
@@ -2516,15 +2393,9 @@ struct Impl {
     if constexpr (kCnThread) {
       const long long lines = AXIS == 2 ? (long long)a.nx * a.ny : (long long)(AXIS == 0 ? a.ny : a.nx) * a.nz;
       const size_t sm = AXIS == 0 ? 2 * (size_t)n * sizeof(R) : 0;
-      if constexpr (std::is_same<R, double>::value) {
-        const unsigned blocks = (unsigned)((lines + 63) / 64);   // 64 lines, two threads each
-        if (a.imag) k_cn_twisted<R, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
-        else k_cn_twisted<C, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
-      } else {
-        const unsigned blocks = (unsigned)((lines + 127) / 128);
-        if (a.imag) k_cn_thread<R, R, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
-        else k_cn_thread<R, C, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
-      }
+      const unsigned blocks = (unsigned)((lines + 63) / 64);   // 64 lines, two threads each
+      if (a.imag) k_cn_twisted<R, R, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
+      else k_cn_twisted<R, C, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
     } else {
       const size_t sm = smem_cn(n, a.cn[AXIS].lchunk);
       if (a.imag) k_cn<R, R, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, reduce, renorm);
@@ -2582,9 +2453,7 @@ struct Impl {
     const dim3 z = grid_z(a);
     const int bz = (int)(z.x * z.y);
     const int bx = ((a.nz + T::kCnCols - 1) / T::kCnCols) * a.ny;
-    // the per-line sweep along x: 128 lines per block, 64 for the FP64 two-thread form
-    const int lpb = std::is_same<R, double>::value ? 64 : 128;
-    const int bt = (int)(((long long)a.ny * a.nz + lpb - 1) / lpb);
+    const int bt = (int)(((long long)a.ny * a.nz + 63) / 64);   // the two-thread sweep along x
     return std::max(bz, std::max(bx, bt));
   }
 
