@@ -82,8 +82,8 @@ def fp64_flops_per_point(kernel, shape, precision="fp64"):
         chunk *= 2
     cn_chunked = 8 + 10 + 16 + 4 + 88.0 / chunk
     cn_line = 8 + 10 + 4 + (8 if precision == "df64" else 0)
-    # FP64: every sweep one thread per line; double-float: the x/y sweeps per line, z chunked
-    cn_z = cn_line if precision == "fp64" else cn_chunked
+    # FP64 and double-float: every sweep per line (two threads each); FP32: chunked
+    cn_z = cn_line if precision in ("fp64", "df64") else cn_chunked
     return {
         "k1_density_r2c_z": 2.5 * math.log2(nz) + 5,
         "k2_fft_y": 5 * math.log2(ny) * half,

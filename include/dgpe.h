@@ -255,7 +255,7 @@ int dgpe_set_tuning(dgpe_ctx *ctx, const dgpe_tuning *t);
  * dgpe_set_tuning changes it); step_ms_default and step_ms_tuned are 0.  No CUDA call. */
 int dgpe_get_tuning(const dgpe_ctx *ctx, dgpe_tuning *out);
 /* Kernel launches of one dgpe_step step (7, or 8 where the z sweep is a pass of its own:
- * FP64).  No CUDA call. */
+ * FP64 and double-float).  No CUDA call. */
 int dgpe_step_launches(const dgpe_ctx *ctx, int *n);
 
 /* Wait for the stream; returns a latched device error if any. */

@@ -2117,9 +2117,9 @@ struct Impl {
   // the FP64-class sweeps run a Thomas solve per line on two threads (k_cn_twisted), the
   // FP32 ones the chunked solver in persistent tiles (k_cn)
   static constexpr bool kCnThread = Fp64Class<R>::value;
-  // FP64: the z sweep too, after a phase-only K5 pass (the FP64 pipe bounds the step, so the
-  // fewer FP64 instructions win over the extra pass; for double-float they do not)
-  static constexpr bool kZSplit = std::is_same<R, double>::value;
+  // and the z sweep too, after a phase-only K5 pass: the per-line solve's fewer arithmetic
+  // instructions win over the extra pass through HBM
+  static constexpr bool kZSplit = Fp64Class<R>::value;
 
   static size_t smem_z_fft(const KArgs &a) { return 2 * (size_t)a.nz * (T::kZLines / 2 + 1) * E; }
   static size_t smem_k5(const KArgs &a) {
