@@ -359,9 +359,10 @@ class Condensate:
 
     def close(self):
         if getattr(self, "ctx", None):
-            dgpe_destroy(self.ctx)
+            dgpe_destroy(self.ctx)   # waits for the copies of dgpe_step_host
             self.ctx = None
             self._ws = None
+            self._host_refs = []
 
     def __del__(self):
         try:
@@ -437,7 +438,8 @@ class Condensate:
                 assert tuple(t.shape) == self.shape and t.dtype == self.cdtype and t.is_contiguous()
                 assert t.device.type == "cpu"
                 ptrs.append(t.data_ptr())
-        self._keep_host = (psi_in, psi_out)
+        # the copies are asynchronous: hold the buffers of every call until sync()
+        self._host_refs = getattr(self, "_host_refs", []) + [(psi_in, psi_out)]
         dgpe_step_host(self.ctx, ptrs[0], ptrs[1], nsteps)
 
     def substep(self, which):
@@ -448,6 +450,7 @@ class Condensate:
 
     def sync(self):
         dgpe_sync(self.ctx)
+        self._host_refs = []
 
     def set_timing(self, enable):
         dgpe_set_timing(self.ctx, enable)
