@@ -1125,13 +1125,16 @@ namespace {
 int host_io_setup(dgpe_ctx *c) {
   if (c->host_io) return DGPE_OK;
   const size_t bytes = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;
-  int rc = map_cuda(cudaMalloc(&c->stage_in, bytes));
-  if (!rc) rc = map_cuda(cudaMalloc(&c->stage_out, bytes));
-  if (!rc) rc = map_cuda(cudaStreamCreateWithFlags(&c->cs_in, cudaStreamNonBlocking));
-  if (!rc) rc = map_cuda(cudaStreamCreateWithFlags(&c->cs_out, cudaStreamNonBlocking));
+  // a failed earlier attempt keeps what it created (dgpe_destroy frees it); create the rest
+  int rc = DGPE_OK;
+  if (!c->stage_in) rc = map_cuda(cudaMalloc(&c->stage_in, bytes));
+  if (!rc && !c->stage_out) rc = map_cuda(cudaMalloc(&c->stage_out, bytes));
+  if (!rc && !c->cs_in) rc = map_cuda(cudaStreamCreateWithFlags(&c->cs_in, cudaStreamNonBlocking));
+  if (!rc && !c->cs_out) rc = map_cuda(cudaStreamCreateWithFlags(&c->cs_out, cudaStreamNonBlocking));
   cudaEvent_t *ev[4] = {&c->ev_in_ready, &c->ev_in_free, &c->ev_out_ready, &c->ev_out_free};
-  for (int q = 0; q < 4 && !rc; ++q) rc = map_cuda(cudaEventCreateWithFlags(ev[q], cudaEventDisableTiming));
-  if (rc) return rc;   // dgpe_destroy frees whatever was created
+  for (int q = 0; q < 4 && !rc; ++q)
+    if (!*ev[q]) rc = map_cuda(cudaEventCreateWithFlags(ev[q], cudaEventDisableTiming));
+  if (rc) return rc;
   c->host_io = true;
   return DGPE_OK;
 }
