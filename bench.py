@@ -51,11 +51,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch from ncu captures (profiles/), valid while the kernel
 # source is byte-identical to the one captured (sha1 of dgpe_device.cuh).
 NCU_TRAFFIC = {
-    # FP64: the K5 record times two launches (the phase-only pass and the two-thread z sweep)
-    "46be18559eabfd12b03d4a2b08c28d510f31f344": {
-        ("real256_fp64", "k5_c2r_z_phase_cn_z"): 1872.67e6,
-        ("real512x512x384_mixed", "k5_c2r_z_phase_cn_z"): 1958.98e6,
-        ("real256_df64", "k5_c2r_z_phase_cn_z"): 620.45e6,
+    # FP64 and double-float: the K5 record times two launches (the phase-only pass and the
+    # two-thread z sweep)
+    "06fc2cb5fb7ffe412886e0d843e588392011e661": {
+        ("real256_fp64", "k5_c2r_z_phase_cn_z"): 1873.13e6,
+        ("real512x512x384_mixed", "k5_c2r_z_phase_cn_z"): 1958.92e6,
+        ("real256_df64", "k5_c2r_z_phase_cn_z"): 1495.66e6,
     },
 }
 
