@@ -160,13 +160,15 @@ int dgpe_step(dgpe_ctx *ctx, int nsteps);
 
 /* Host-resident states through the solver: copy psi in from host memory `in` (as
  * dgpe_set_psi), run nsteps steps, copy the result (as dgpe_get_psi) to host memory `out`.
- * Asynchronous: the copies run on two internal streams through two device staging buffers
- * of psi's size (allocated at the first call with cudaMalloc, outside the workspace, freed by
- * dgpe_destroy), so the input copy of one call overlaps the previous call's steps and its
- * output copy the next call's.  `in` must stay unchanged and `out` unread until dgpe_sync
- * (which waits for the copies too); pinned host memory lets the copies run asynchronously.
- * Device errors surface at dgpe_sync, as for dgpe_step.  NULL in/out or nsteps < 0:
- * DGPE_EINVAL. */
+ * Asynchronous: the copies run on two internal streams, and successive calls alternate the
+ * state between the workspace's psi buffer and a second one of the same size (allocated at
+ * the first call with cudaMalloc, outside the workspace, freed by dgpe_destroy; double-float
+ * also stages its converted output), so the input copy of one call overlaps the previous
+ * call's steps and its output copy the next call's, with no device-side copy.  `in` must stay
+ * unchanged and `out` unread until dgpe_sync (which waits for the copies too); later calls
+ * that change psi on this context wait for the output copy by themselves.  Pinned host
+ * memory lets the copies run asynchronously.  Device errors surface at dgpe_sync, as for
+ * dgpe_step.  NULL in/out or nsteps < 0: DGPE_EINVAL. */
 int dgpe_step_host(dgpe_ctx *ctx, const void *in, void *out, int nsteps);
 
 /* Apply one factor of the split step (DGPE_SUB_*) once, without renormalisation. */

@@ -259,10 +259,14 @@ struct dgpe_ctx {
   int latched;
   int plan_style[3];
   unsigned generation;   // bumped whenever the captured step would change (batches rebuild)
-  // dgpe_step_host: device staging of the host input and output, one copy stream each
-  void *stage_in, *stage_out;
+  // dgpe_step_host: a second psi buffer (successive states alternate between the two, each
+  // with its own captured step), the output staging of double-float, one copy stream each
+  // way, and their events
+  void *psi_main, *psi_alt, *stage_out;
+  cudaGraphExec_t graph_alt;
+  bool graph_alt_valid;
   cudaStream_t cs_in, cs_out;
-  cudaEvent_t ev_in_ready, ev_in_free, ev_out_ready, ev_out_free;
+  cudaEvent_t ev_in_ready, ev_out_ready, ev_stage_free, ev_main_done[2], ev_d2h_done[2];
   bool host_io;
 };
 
@@ -353,11 +357,25 @@ int enqueue_step(dgpe_ctx *c, cudaStream_t st) {
   return DGPE_OK;
 }
 
+// The captured step of the psi buffer the context currently holds (the workspace's, or the
+// second buffer of dgpe_step_host).
+bool on_alt_psi(const dgpe_ctx *c) { return c->psi_alt && c->args.psi == c->psi_alt; }
+
+// Work that changes psi first waits for the output copy of the last dgpe_step_host call,
+// which reads the state buffer itself.
+int wait_host_output(dgpe_ctx *c, cudaStream_t st) {
+  if (!c->host_io) return DGPE_OK;
+  return map_cuda(cudaStreamWaitEvent(st, c->ev_d2h_done[on_alt_psi(c) ? 1 : 0], 0));
+}
+
 int build_graph(dgpe_ctx *c) {
-  if (c->graph_valid) return DGPE_OK;
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
+  const bool alt = on_alt_psi(c);
+  cudaGraphExec_t &graph = alt ? c->graph_alt : c->graph;
+  bool &valid = alt ? c->graph_alt_valid : c->graph_valid;
+  if (valid) return DGPE_OK;
+  if (graph) {
+    cudaGraphExecDestroy(graph);
+    graph = nullptr;
   }
   const bool timing = c->timing;
   c->timing = false;
@@ -375,13 +393,13 @@ int build_graph(dgpe_ctx *c) {
     return rc;
   }
   if (e != cudaSuccess) return map_cuda(e);
-  e = cudaGraphInstantiate(&c->graph, g, 0);
+  e = cudaGraphInstantiate(&graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    c->graph = nullptr;
+    graph = nullptr;
     return map_cuda(e);
   }
-  c->graph_valid = true;
+  valid = true;
   return DGPE_OK;
 }
 
@@ -530,7 +548,7 @@ int apply_tuning(dgpe_ctx *c, const dgpe_tuning &t) {
   c->args.ylines = t.ylines;
   c->args.fft_threads = t.fft_threads;
   c->args.cn_per_sm = t.cn_per_sm;
-  c->graph_valid = false;
+  c->graph_valid = c->graph_alt_valid = false;
   ++c->generation;
   return rc;
 }
@@ -625,6 +643,7 @@ int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out) {
   a.state = static_cast<DevState *>(at(c, c->L.state));
   a.partials = static_cast<double *>(at(c, c->L.partials));
   a.psi = at(c, c->L.psi);
+  c->psi_main = a.psi;
   a.spec = at(c, c->L.spec);
   for (int d = 0; d < 3; ++d) {
     a.tw[d] = at(c, c->L.tw[d]);
@@ -667,7 +686,7 @@ int dgpe_set_params(dgpe_ctx *c, const dgpe_params *p) {
   // the step kernels read the trap only through the per-axis tables rebuilt below, so a
   // change of nu alone keeps the captured graph valid
   if (step_args_changed) {
-    c->graph_valid = false;
+    c->graph_valid = c->graph_alt_valid = false;
     ++c->generation;
   }
   return setup_tables(c, cn_changed, ut_changed);
@@ -675,6 +694,7 @@ int dgpe_set_params(dgpe_ctx *c, const dgpe_params *p) {
 
 int dgpe_set_psi(dgpe_ctx *c, const void *psi, int where) {
   if (!c || !psi || (where != DGPE_HOST && where != DGPE_DEVICE)) return DGPE_EINVAL;
+  if (const int w = wait_host_output(c, c->stream)) return w;
   const size_t n = (size_t)c->p.nx * c->p.ny * c->p.nz;
   const size_t bytes = n * c->ks->elem_bytes;
   int rc;
@@ -696,6 +716,7 @@ int dgpe_set_psi(dgpe_ctx *c, const void *psi, int where) {
 
 int dgpe_get_psi(dgpe_ctx *c, void *out, int where) {
   if (!c || !out || (where != DGPE_HOST && where != DGPE_DEVICE)) return DGPE_EINVAL;
+  if (const int w = wait_host_output(c, c->stream)) return w;
   const size_t bytes = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;
   int rc = launch(c, c->stream, kKMaterialize, [&] { return c->ks->materialize(c->args, c->stream); });
   if (rc) return rc;
@@ -727,6 +748,7 @@ int dgpe_get_psi(dgpe_ctx *c, void *out, int where) {
 int dgpe_step(dgpe_ctx *c, int nsteps) {
   if (!c || nsteps < 0) return DGPE_EINVAL;
   if (nsteps == 0) return DGPE_OK;
+  if (const int w = wait_host_output(c, c->stream)) return w;
   if (c->timing) {
     for (int s = 0; s < nsteps; ++s) {
       const int rc = enqueue_step(c, c->stream);
@@ -736,8 +758,9 @@ int dgpe_step(dgpe_ctx *c, int nsteps) {
   }
   int rc = build_graph(c);
   if (rc) return rc;
+  cudaGraphExec_t graph = on_alt_psi(c) ? c->graph_alt : c->graph;
   for (int s = 0; s < nsteps; ++s) {
-    rc = map_cuda(cudaGraphLaunch(c->graph, c->stream));
+    rc = map_cuda(cudaGraphLaunch(graph, c->stream));
     if (rc) return rc;
   }
   return DGPE_OK;
@@ -745,6 +768,7 @@ int dgpe_step(dgpe_ctx *c, int nsteps) {
 
 int dgpe_substep(dgpe_ctx *c, int which) {
   if (!c) return DGPE_EINVAL;
+  if (const int w = wait_host_output(c, c->stream)) return w;
   const KArgs &a = c->args;
   const KernelSet *ks = c->ks;
   cudaStream_t st = c->stream;
@@ -837,6 +861,7 @@ int dgpe_grad_z2(dgpe_ctx *c, int nseg, int steps_per_seg, const double *nu_z, v
   const GradLayout g = grad_layout(c, nseg, steps_per_seg);
   if (work_bytes < g.total) return DGPE_ENOMEM;
   if (reinterpret_cast<uintptr_t>(work) % kAlign) return DGPE_EINVAL;
+  if (const int w = wait_host_output(c, c->stream)) return w;
   char *w = static_cast<char *>(work);
   const int n = nseg * steps_per_seg;
   const size_t sb = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;
@@ -918,6 +943,7 @@ int dgpe_get_tuning(const dgpe_ctx *c, dgpe_tuning *out) {
 
 int dgpe_autotune(dgpe_ctx *c, dgpe_tuning *out) {
   if (!c || !out) return DGPE_EINVAL;
+  if (const int w = wait_host_output(c, c->stream)) return w;
   const size_t sb = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;
   void *saved = nullptr;
   DevState st_saved;
@@ -1088,6 +1114,7 @@ int dgpe_batch_step(dgpe_batch *b, int nsteps) {
   if (!b || nsteps < 0) return DGPE_EINVAL;
   if (nsteps == 0) return DGPE_OK;
   int rc = batch_build(b);
+  for (size_t i = 0; i < b->ctxs.size() && !rc; ++i) rc = wait_host_output(b->ctxs[i], b->stream);
   for (int s = 0; s < nsteps && !rc; ++s) rc = map_cuda(cudaGraphLaunch(b->graph, b->stream));
   return rc;
 }
@@ -1121,18 +1148,20 @@ int dgpe_sync(dgpe_ctx *c) {
 }
 
 namespace {
-// The staging buffers, streams and events of dgpe_step_host, created at its first call.
+// The second psi buffer, staging, streams and events of dgpe_step_host, created at its
+// first call.
 int host_io_setup(dgpe_ctx *c) {
   if (c->host_io) return DGPE_OK;
   const size_t bytes = (size_t)c->p.nx * c->p.ny * c->p.nz * c->ks->elem_bytes;
   // a failed earlier attempt keeps what it created (dgpe_destroy frees it); create the rest
   int rc = DGPE_OK;
-  if (!c->stage_in) rc = map_cuda(cudaMalloc(&c->stage_in, bytes));
-  if (!rc && !c->stage_out) rc = map_cuda(cudaMalloc(&c->stage_out, bytes));
+  if (!c->psi_alt) rc = map_cuda(cudaMalloc(&c->psi_alt, bytes));
+  if (!rc && c->p.precision == DGPE_DF64 && !c->stage_out) rc = map_cuda(cudaMalloc(&c->stage_out, bytes));
   if (!rc && !c->cs_in) rc = map_cuda(cudaStreamCreateWithFlags(&c->cs_in, cudaStreamNonBlocking));
   if (!rc && !c->cs_out) rc = map_cuda(cudaStreamCreateWithFlags(&c->cs_out, cudaStreamNonBlocking));
-  cudaEvent_t *ev[4] = {&c->ev_in_ready, &c->ev_in_free, &c->ev_out_ready, &c->ev_out_free};
-  for (int q = 0; q < 4 && !rc; ++q)
+  cudaEvent_t *ev[7] = {&c->ev_in_ready,    &c->ev_out_ready,   &c->ev_stage_free, &c->ev_main_done[0],
+                        &c->ev_main_done[1], &c->ev_d2h_done[0], &c->ev_d2h_done[1]};
+  for (int q = 0; q < 7 && !rc; ++q)
     if (!*ev[q]) rc = map_cuda(cudaEventCreateWithFlags(ev[q], cudaEventDisableTiming));
   if (rc) return rc;
   c->host_io = true;
@@ -1140,42 +1169,54 @@ int host_io_setup(dgpe_ctx *c) {
 }
 }  // namespace
 
+// Successive calls alternate between the workspace's psi buffer and a second one: the input
+// of a call is copied into the buffer that does not hold the current state while the steps
+// of the previous call still run, and its result is copied out of it while the next call's
+// steps run, with no device-side copy.  A buffer is written again once the main stream has
+// left it (ev_main_done, recorded where the state moves to the other buffer) and its
+// previous output copy has finished (ev_d2h_done).  Double-float converts its input in place
+// and its output through a staging buffer (the state itself stays in pairs).
 int dgpe_step_host(dgpe_ctx *c, const void *in, void *out, int nsteps) {
   if (!c || !in || !out || nsteps < 0) return DGPE_EINVAL;
   int rc = host_io_setup(c);
   if (rc) return rc;
   const size_t n = (size_t)c->p.nx * c->p.ny * c->p.nz;
   const size_t bytes = n * c->ks->elem_bytes;
-  // host -> input staging on its copy stream, once the previous call has consumed the staging
-  rc = map_cuda(cudaStreamWaitEvent(c->cs_in, c->ev_in_free, 0));
-  if (!rc) rc = map_cuda(cudaMemcpyAsync(c->stage_in, in, bytes, cudaMemcpyHostToDevice, c->cs_in));
+  const int cur = on_alt_psi(c) ? 1 : 0, tgt = 1 - cur;
+  void *const buf[2] = {c->psi_main, c->psi_alt};
+  // host -> the free buffer on the input copy stream
+  rc = map_cuda(cudaStreamWaitEvent(c->cs_in, c->ev_main_done[tgt], 0));
+  if (!rc) rc = map_cuda(cudaStreamWaitEvent(c->cs_in, c->ev_d2h_done[tgt], 0));
+  if (!rc) rc = map_cuda(cudaMemcpyAsync(buf[tgt], in, bytes, cudaMemcpyHostToDevice, c->cs_in));
   if (!rc) rc = map_cuda(cudaEventRecord(c->ev_in_ready, c->cs_in));
-  // staging -> psi on the context's stream (double-float: split into pairs on the way)
+  // the state moves to that buffer: from here on the main stream leaves the other one alone
   if (!rc) rc = map_cuda(cudaStreamWaitEvent(c->stream, c->ev_in_ready, 0));
-  if (!rc) {
-    if (c->p.precision == DGPE_DF64) rc = map_cuda(c->ks->from_c128(c->stage_in, c->args.psi, n, c->stream));
-    else rc = map_cuda(cudaMemcpyAsync(c->args.psi, c->stage_in, bytes, cudaMemcpyDeviceToDevice, c->stream));
-  }
+  if (!rc) rc = map_cuda(cudaEventRecord(c->ev_main_done[cur], c->stream));
+  if (rc) return rc;
+  c->args.psi = buf[tgt];
+  ++c->generation;   // batches holding this context capture its new buffer
+  if (c->p.precision == DGPE_DF64) rc = map_cuda(c->ks->from_c128(buf[tgt], buf[tgt], n, c->stream));
   if (!rc) rc = map_cuda(c->ks->reset_state(c->args.state, c->stream));
-  if (!rc) rc = map_cuda(cudaEventRecord(c->ev_in_free, c->stream));
   if (rc) return rc;
   c->latched = DGPE_OK;
   rc = dgpe_step(c, nsteps);
   if (rc) return rc;
-  // psi (pending renormalisation applied: imaginary time only, real-time steps leave s = 1)
-  // -> output staging, once the previous call's output copy has left it
-  rc = map_cuda(cudaStreamWaitEvent(c->stream, c->ev_out_free, 0));
-  if (!rc && c->p.mode == DGPE_IMAG_TIME)
+  // the pending renormalisation (imaginary time only: real-time steps leave s = 1)
+  if (c->p.mode == DGPE_IMAG_TIME)
     rc = launch(c, c->stream, kKMaterialize, [&] { return c->ks->materialize(c->args, c->stream); });
-  if (!rc) {
-    if (c->p.precision == DGPE_DF64) rc = map_cuda(c->ks->to_c128(c->args.psi, c->stage_out, n, c->stream));
-    else rc = map_cuda(cudaMemcpyAsync(c->stage_out, c->args.psi, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  const void *src = buf[tgt];
+  if (!rc && c->p.precision == DGPE_DF64) {
+    // pairs -> complex128 into the staging, once the previous output copy has left it
+    rc = map_cuda(cudaStreamWaitEvent(c->stream, c->ev_stage_free, 0));
+    if (!rc) rc = map_cuda(c->ks->to_c128(buf[tgt], c->stage_out, n, c->stream));
+    src = c->stage_out;
   }
   if (!rc) rc = map_cuda(cudaEventRecord(c->ev_out_ready, c->stream));
-  // output staging -> host on the other copy stream
+  // the result -> host on the output copy stream
   if (!rc) rc = map_cuda(cudaStreamWaitEvent(c->cs_out, c->ev_out_ready, 0));
-  if (!rc) rc = map_cuda(cudaMemcpyAsync(out, c->stage_out, bytes, cudaMemcpyDeviceToHost, c->cs_out));
-  if (!rc) rc = map_cuda(cudaEventRecord(c->ev_out_free, c->cs_out));
+  if (!rc) rc = map_cuda(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, c->cs_out));
+  if (!rc) rc = map_cuda(cudaEventRecord(c->ev_d2h_done[tgt], c->cs_out));
+  if (!rc && c->p.precision == DGPE_DF64) rc = map_cuda(cudaEventRecord(c->ev_stage_free, c->cs_out));
   return rc;
 }
 
@@ -1222,12 +1263,14 @@ void dgpe_destroy(dgpe_ctx *c) {
   if (c->ws) cudaStreamSynchronize(c->stream);
   if (c->cs_in) cudaStreamSynchronize(c->cs_in);
   if (c->cs_out) cudaStreamSynchronize(c->cs_out);
-  for (cudaEvent_t e : {c->ev_in_ready, c->ev_in_free, c->ev_out_ready, c->ev_out_free})
+  for (cudaEvent_t e : {c->ev_in_ready, c->ev_out_ready, c->ev_stage_free, c->ev_main_done[0], c->ev_main_done[1],
+                        c->ev_d2h_done[0], c->ev_d2h_done[1]})
     if (e) cudaEventDestroy(e);
   if (c->cs_in) cudaStreamDestroy(c->cs_in);
   if (c->cs_out) cudaStreamDestroy(c->cs_out);
-  if (c->stage_in) cudaFree(c->stage_in);
+  if (c->psi_alt) cudaFree(c->psi_alt);
   if (c->stage_out) cudaFree(c->stage_out);
+  if (c->graph_alt) cudaGraphExecDestroy(c->graph_alt);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (const auto &pd : c->pending) {
     cudaEventDestroy(pd.a);

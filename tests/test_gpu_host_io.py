@@ -37,6 +37,7 @@ def test_pipelined_calls_match_synchronous_calls(precision, mode):
     io = abi.Condensate(shape, h, 0.005, **kw)
     dtype = np.complex64 if precision == abi.DGPE_MIXED else np.complex128
     tdtype = torch.complex64 if precision == abi.DGPE_MIXED else torch.complex128
+    tol = 1e-5 if precision == abi.DGPE_MIXED else 1e-12
     ins = states(shape, h, dtype, 4)
     want = []
     for a in ins:
@@ -56,6 +57,26 @@ def test_pipelined_calls_match_synchronous_calls(precision, mode):
         io.step_host(a, same, 3)
     io.sync()
     assert np.array_equal(same.numpy(), want[-1])
+    # the state stays on the context: plain steps continue from it (whichever of the two
+    # buffers holds it), and a parameter change rebuilds the captured step of both buffers
+    for extra in range(2):
+        io.step_host(pin_in[extra], pin_out[extra], 3)
+        io.step(2)            # waits for the output copy, which reads the state buffer
+        ref.set_psi(ins[extra])
+        ref.step(5)
+        # imaginary time: the output applies the pending renormalisation to the state after
+        # 3 steps, which rounds differently from applying it after 5
+        got, exp = io.get_psi(), ref.get_psi()
+        assert np.linalg.norm(got - exp) <= tol * np.linalg.norm(exp), extra
+        io.sync()
+        assert np.array_equal(pin_out[extra].numpy(), want[extra]), extra
+    for c in (io, ref):
+        c.set_params(g=20.0)
+    io.step_host(pin_in[0], pin_out[0], 3)
+    io.sync()
+    ref.set_psi(ins[0])
+    ref.step(3)
+    assert np.array_equal(pin_out[0].numpy(), ref.get_psi())
     ref.close()
     io.close()
 
