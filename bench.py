@@ -194,6 +194,32 @@ def aggregate_over_ranks(ms_local, units_per_rank, dist=None, device=None):
     return ws * units_per_rank / (ms * 1e-3), ms
 
 
+def track_physics(obs0, obs1, steps):
+    """Norm drift, energy and rms sizes over the timed real-time steps (the quantities the
+    workload tracks)."""
+    return {"steps": steps, "norm_start": obs0["norm"], "norm_end": obs1["norm"],
+            "norm_drift": (obs1["norm"] - obs0["norm"]) / obs0["norm"],
+            "energy_start": obs0["energy"], "energy_end": obs1["energy"], "mu_end": obs1["mu"],
+            "rms_start": list(obs0["rms"]), "rms_end": list(obs1["rms"])}
+
+
+def mixed_vs_fp64(abi, wl, local, steps=20):
+    """The FP32-mixed path against the FP64 GPU path on the same prepared state: both run
+    the imaginary-time preparation and `steps` real-time steps; rel-L2 of psi and the relative
+    differences of mu and E."""
+    import torch
+    out = {}
+    for prec in ("mixed", "fp64"):
+        c = make_condensate(abi, dict(wl, precision=prec), local)
+        c.step(steps)
+        out[prec] = (c.get_psi(host=False).to(torch.complex128), c.observables())
+        c.close()
+    (pm, om), (pd, od) = out["mixed"], out["fp64"]
+    return {"steps_after_prep": steps, "psi_rel_l2": float(torch.linalg.norm(pm - pd) / torch.linalg.norm(pd)),
+            "mu_rel": abs(om["mu"] - od["mu"]) / abs(od["mu"]),
+            "energy_rel": abs(om["energy"] - od["energy"]) / abs(od["energy"])}
+
+
 def time_steps(c, steps, barrier):
     import torch
     st = c.stream
@@ -544,10 +570,12 @@ def main():
     c = make_condensate(abi, wl, local)
     npts = wl["shape"][0] * wl["shape"][1] * wl["shape"][2]
     c.step(args.warmup)
+    obs0 = c.observables()   # outside the timed region (it synchronises)
     clocks = ClockSampler(local)
     clocks.start()
     ms = time_steps(c, args.steps, barrier)
     clk = clocks.stop()
+    physics = track_physics(obs0, c.observables(), args.steps)
     value, ms = aggregate_over_ranks(ms, npts * args.steps, dist, c.device)
     launches_per_step = c.step_launches()
     roofline, kernels = kernel_profile(c, min(args.steps, 50), hbm_peak, peak_kind, name)
@@ -569,7 +597,8 @@ def main():
         mixed = {"value": value_m, "unit": UNIT, "ms_per_step": round(msm / args.steps, 4),
                  "dtype": "f32 (FP64 reductions)", "grid": list(wlm["shape"]), "roofline": rl_m, "kernels": kernels_m,
                  "algorithmic_bytes_per_step": sum(k["bytes_per_launch"] * k["launches"] for k in kernels_m)
-                 / min(args.steps, 50)}
+                 / min(args.steps, 50),
+                 "vs_fp64_gpu": mixed_vs_fp64(abi, wlm, local)}
 
     dfl = None
     if not args.no_df64:
@@ -607,7 +636,8 @@ def main():
                        "prep": "%d imaginary-time steps at g=%g from the seeded Gaussian" % (PREP_STEPS, wl["g_prep"]),
                        "l2": "inputs larger than L2 (psi %d MB > 129 MB)" % (npts * (8 if wl["precision"] == "mixed" else 16) >> 20),
                        "parallelism": "replicas" if ws > 1 else "1 GPU"},
-            "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roofline, "kernels": kernels, "e2e": e2e}
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roofline, "kernels": kernels, "e2e": e2e,
+            "physics": physics}
     if mixed is not None:
         line["mixed_512x512x384"] = mixed
     if dfl is not None:
