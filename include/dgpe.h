@@ -28,7 +28,8 @@
  * DGPE_MIXED.  All
  * device memory the solver uses is one workspace of dgpe_workspace_bytes() bytes: the
  * caller may own it (params.workspace, e.g. a PyTorch tensor) or let dgpe_create allocate
- * it with cudaMalloc.  Nothing is kept in global variables: one context per stream.
+ * it with cudaMalloc.  The one exception is dgpe_step_host, which allocates its second psi
+ * buffer at its first call.  Nothing is kept in global variables: one context per stream.
  *
  * Errors.  Every int-returning call returns DGPE_OK (0) or a negative DGPE_E* code; no C++
  * exception crosses the ABI.  Parameter checks happen before any CUDA call, so invalid
