@@ -290,7 +290,8 @@ def kernel_profile(c, steps, hbm_peak, peak_kind, workload):
 def e2e_run(abi, c, steps):
     """Same metric through the C ABI with pinned HOST buffers: every step copies psi in from
     host memory, steps once, and copies psi out to host memory, with dgpe_step_host (the
-    copies of successive steps overlapped with the steps through device staging buffers).
+    copies of successive steps overlapped with the steps; the state alternates between two
+    device buffers, each with its captured step).
     Timed on the host clock from the first call to dgpe_sync, which waits for the last
     output copy.  `serial_ms_per_step` is the same loop with the synchronous dgpe_set_psi /
     dgpe_step / dgpe_get_psi calls, for comparison."""
@@ -301,7 +302,8 @@ def e2e_run(abi, c, steps):
     host_in = torch.empty(c.shape, dtype=c.cdtype, pin_memory=True)
     host_out = torch.empty(c.shape, dtype=c.cdtype, pin_memory=True)
     abi.dgpe_get_psi(c.ctx, host_in.data_ptr(), abi.DGPE_HOST)
-    # one untimed call: it allocates the staging buffers and streams
+    # one untimed call: it allocates the second buffer and the copy streams and captures
+    # the step on that buffer
     abi.dgpe_step_host(c.ctx, host_in.data_ptr(), host_out.data_ptr(), 1)
     abi.dgpe_sync(c.ctx)
     torch.cuda.synchronize(c.device)
