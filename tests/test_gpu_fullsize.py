@@ -76,6 +76,28 @@ def test_mixed_512x512x384(orc):
     assert rel(got, ref64) < 2e-6
 
 
+def test_maximum_size_512cubed_fp64(orc):
+    """Every axis at the largest supported length (512), FP64 real time, one step against
+    the oracle; then double-float on the same input against the FP64 GPU result."""
+    import torch
+    shape, h, nu, g, gdd, dt = (512, 512, 512), 0.05, (1.0, 1.0, 2.0), 100.0, 60.0, 5e-4
+    psi0 = inputs.gaussian_psi(shape, h, noise=1e-3, seed=2)
+    gpu = abi.Condensate(shape, h, dt, mode=abi.DGPE_REAL_TIME, nu=nu, g=g, gdd=gdd)
+    gpu.set_psi(psi0)
+    gpu.step(1)
+    got = gpu.get_psi(host=False)
+    gpu.close()
+    want = orc.step(orc.make_params(shape, h, dt, orc.REAL_TIME, nu, g, gdd), psi0, 1)
+    assert rel(got.cpu().numpy(), want) < 1e-10
+    del want
+    dfc = abi.Condensate(shape, h, dt, mode=abi.DGPE_REAL_TIME, precision=abi.DGPE_DF64, nu=nu, g=g, gdd=gdd)
+    dfc.set_psi(psi0)
+    dfc.step(1)
+    got_df = dfc.get_psi(host=False)
+    dfc.close()
+    assert float(torch.linalg.norm(got_df - got) / torch.linalg.norm(got)) < 1e-11
+
+
 def test_adjoint_step_128cubed(orc):
     import torch
     shape, h, dt = (128, 128, 128), 0.2, 0.001
