@@ -1590,7 +1590,9 @@ __device__ __forceinline__ void finish_sweep_sums(const KArgs &a, double (&v)[4]
     const double norm = a.hx * a.hy * a.hz * v[0];
     for (int q = 0; q < 4; ++q) st->sums[q] = v[q];
     st->norm = norm;
-    const bool ok = isfinite(norm) && norm > 0.0;
+    // a zero state is a state (real time keeps it zero); only the renormalisation of
+    // imaginary time needs a positive norm
+    const bool ok = isfinite(norm) && (norm > 0.0 || !renorm);
     if (!ok) st->flags |= kFlagNonFinite;
     set_scale(st, (renorm && ok) ? 1.0 / sqrt(norm) : 1.0);
     st->steps += 1ull;

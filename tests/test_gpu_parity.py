@@ -199,6 +199,32 @@ def test_nonfinite_state_is_reported():
     gpu.close()
 
 
+@pytest.mark.parametrize("precision", [abi.DGPE_FP64, abi.DGPE_DF64, abi.DGPE_MIXED])
+def test_zero_state(precision):
+    """The degenerate state psi = 0: real time keeps it exactly zero with no error;
+    imaginary time cannot renormalise it and reports DGPE_ENONFINITE, as do the observables
+    (mu = E / norm is undefined)."""
+    shape, h = (12, 10, 8), 0.5
+    dtype = np.complex64 if precision == abi.DGPE_MIXED else np.complex128
+    zero = np.zeros(shape, dtype)
+    gpu = abi.Condensate(shape, h, 0.01, mode=abi.DGPE_REAL_TIME, precision=precision, g=10, gdd=5)
+    gpu.set_psi(zero)
+    gpu.step(3)
+    gpu.sync()
+    assert not np.any(gpu.get_psi())
+    with pytest.raises(abi.DgpeError) as e:
+        gpu.observables()
+    assert e.value.code == abi.DGPE_ENONFINITE
+    gpu.close()
+    gpu = abi.Condensate(shape, h, 0.01, mode=abi.DGPE_IMAG_TIME, precision=precision, g=10, gdd=5)
+    gpu.set_psi(zero)
+    gpu.step(1)
+    with pytest.raises(abi.DgpeError) as e:
+        gpu.sync()
+    assert e.value.code == abi.DGPE_ENONFINITE
+    gpu.close()
+
+
 @pytest.mark.parametrize("mode", [abi.DGPE_REAL_TIME, abi.DGPE_IMAG_TIME])
 def test_mixed_precision_error_vs_oracle(orc, mode):
     """FP32 path (complex64 psi, FP32 FFT/phase/CN, FP64 reductions): errors against the
