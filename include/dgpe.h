@@ -34,7 +34,8 @@
  * Errors.  Every int-returning call returns DGPE_OK (0) or a negative DGPE_E* code; no C++
  * exception crosses the ABI.  Parameter checks happen before any CUDA call, so invalid
  * parameters are reported even on a machine without a GPU.  Errors found on the device
- * (non-finite norm) are latched and returned by the next synchronising call
+ * (a non-finite norm, or a zero norm in imaginary time, which cannot be renormalised) are
+ * latched and returned by the next synchronising call
  * (dgpe_sync, dgpe_observables, dgpe_get_psi with a host buffer, dgpe_get_phi).
  * A context is not thread-safe: calls on one context must not overlap.
  */
@@ -51,7 +52,7 @@ extern "C" {
 #define DGPE_EINVAL (-1)        /* bad argument or parameter */
 #define DGPE_ENOMEM (-2)        /* device allocation failed or workspace too small */
 #define DGPE_ECUDA (-3)         /* a CUDA runtime call or kernel launch failed */
-#define DGPE_ENONFINITE (-4)    /* NaN/Inf met in a reduction (norm) on the device */
+#define DGPE_ENONFINITE (-4)    /* NaN/Inf in a reduction (norm, observables), or a zero norm to renormalise */
 #define DGPE_ETIMEOUT (-5)      /* a bounded device-side wait gave up */
 #define DGPE_EUNSUPPORTED (-6)  /* valid request this build does not support */
 
