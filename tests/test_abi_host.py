@@ -92,3 +92,16 @@ def test_too_small_workspace_is_rejected(lib):
     p.workspace_bytes = 16
     ctx = ctypes.c_void_p()
     assert lib.dgpe_create(ctypes.byref(p), None, ctypes.byref(ctx)) == abi.DGPE_ENOMEM
+
+
+def test_binding_constants_match_the_header():
+    """Every #define value of include/dgpe.h is the binding's constant of the same name, and
+    every error code has its own message."""
+    text = open(os.path.join(ROOT, "include", "dgpe.h")).read()
+    defines = dict(re.findall(r"#define (DGPE_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", text))
+    assert len(defines) >= 20
+    for name, value in defines.items():
+        assert getattr(abi, name) == int(value), name
+    codes = [int(v) for k, v in defines.items() if k == "DGPE_OK" or k.startswith("DGPE_E")]
+    messages = [abi.strerror(code) for code in codes]
+    assert len(set(messages)) == len(codes) and "unknown error code" not in messages
