@@ -53,10 +53,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 NCU_TRAFFIC = {
     # FP64 and double-float: the K5 record times two launches (the phase-only pass and the
     # two-thread z sweep)
-    "6e74978edcf1a77f9244da5384ac26bde487f79e": {
-        ("real256_fp64", "k5_c2r_z_phase_cn_z"): 1873.46e6,
-        ("real512x512x384_mixed", "k5_c2r_z_phase_cn_z"): 1959.30e6,
-        ("real256_df64", "k5_c2r_z_phase_cn_z"): 1495.71e6,
+    "259b70b7e04829fa9073a5fe7761fd4a47b9e057": {
+        ("real256_fp64", "k5_c2r_z_phase_cn_z"): 1872.43e6,
+        ("real512x512x384_mixed", "k5_c2r_z_phase_cn_z"): 1958.87e6,
+        ("real256_df64", "k5_c2r_z_phase_cn_z"): 1496.01e6,
     },
 }
 

@@ -1179,6 +1179,18 @@ __global__ void k_reset_state(DevState *st) {
   }
 }
 
+// d / 2 for a density d >= 0, exactly and off the FP64 pipe: the exponent field minus one
+// for 2^-1021 <= d < inf; 0 below (the half would be subnormal, under 2.3e-308: flushed);
+// inf and NaN unchanged.  Other types multiply.
+template <typename R>
+__device__ __forceinline__ R half_density(R d) { return R(0.5) * d; }
+template <>
+__device__ __forceinline__ double half_density(double d) {
+  const long long b = __double_as_longlong(d);
+  const long long h = b < (2LL << 52) ? 0LL : (b >= 0x7ff0000000000000LL ? b : b - (1LL << 52));
+  return __longlong_as_double(h);
+}
+
 // ---------------------------------------------------------------------------------------
 // K1: n = s^2 |psi|^2 of kZLines consecutive z-lines (i, j0..), packed in pairs as the
 // real and imaginary parts of one complex line, forward FFT along z, then the two real
@@ -1201,24 +1213,33 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) 
   const R s2 = R(0.5) * (a.unit_scale ? R(1) : scale_sq_of<R>(a.state));
   const C *psi = reinterpret_cast<const C *>(a.psi) + ((size_t)i * a.ny + j0) * nz;
   const int total = nl * nz;
-  LinePos pos(threadIdx.x, nz, blockDim.x);
-  for (int e0 = threadIdx.x; e0 < total; e0 += kUnroll * blockDim.x) {
-    C v[kUnroll];
+  // kHalve: s = 1 (real time), so the factor is the 1/2 alone, applied to FP64 densities by
+  // the exponent (half_density) instead of a multiply on the FP64 pipe
+  auto fill = [&](auto halve) {
+    constexpr bool kHalve = decltype(halve)::value;
+    LinePos pos(threadIdx.x, nz, blockDim.x);
+    for (int e0 = threadIdx.x; e0 < total; e0 += kUnroll * blockDim.x) {
+      C v[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e < total) v[u] = psi[e];
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e < total) {
-        R *z = reinterpret_cast<R *>(za + pos.k * SB + (pos.b >> 1));
-        z[pos.b & 1] = s2 * (v[u].re * v[u].re + v[u].im * v[u].im);
+      for (int u = 0; u < kUnroll; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < total) v[u] = psi[e];
       }
-      pos.next();
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < total) {
+          R *z = reinterpret_cast<R *>(za + pos.k * SB + (pos.b >> 1));
+          const R d = v[u].re * v[u].re + v[u].im * v[u].im;
+          if constexpr (kHalve) z[pos.b & 1] = half_density(d);
+          else z[pos.b & 1] = s2 * d;
+        }
+        pos.next();
+      }
     }
-  }
+  };
+  if (std::is_same<R, double>::value && s2 == R(0.5)) fill(std::true_type{});
+  else fill(std::false_type{});
   __syncthreads();
   const C *res = fft_lines_n<R, -1, N, PZ, SB, Tiles<R>::kZThreads>(za, zb, a.plan[2], np,
                                                                    reinterpret_cast<const C *>(a.tw[2]));
