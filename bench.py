@@ -504,22 +504,25 @@ def run_reference(args):
     psi = inputs.gaussian_psi(wl["shape"], wl["h"], noise=1e-3, seed=1)
     n = psi.size
     t0 = time.perf_counter()
-    psi = oracle.step(p, psi, 1)        # one untimed warm-up step (bounded)
+    psi = oracle.step(p, psi, 1)        # the first untimed warm-up step sizes the run
     t_step = time.perf_counter() - t0
     cap = max(1, int(150.0 / max(t_step, 1e-3)))
+    warmup = max(1, min(args.warmup, cap))
+    if warmup > 1:
+        psi = oracle.step(p, psi, warmup - 1)
     steps = min(args.steps, cap)
     t0 = time.perf_counter()
     psi = oracle.step(p, psi, steps)
     t = time.perf_counter() - t0
     value = n * steps / t
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
+            "warmup": warmup, "ms_per_step": t / steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": "real256_fp64", "grid": list(wl["shape"]), "mode": "real", "h": wl["h"],
                        "dt": wl["dt"], "g": wl["g"], "gdd": wl["gdd"], "nu": list(wl["nu"])},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": "%d of %d requested full 256^3 FP64 steps (1 warm-up step; capped to "
-                                       "~150 s)" % (steps, args.steps)},
+                             "sample": "%d of %d requested full 256^3 FP64 steps after %d warm-up steps "
+                                       "(each phase capped to ~150 s)" % (steps, args.steps, warmup)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
