@@ -237,6 +237,8 @@ int dgpe_batch_create(dgpe_ctx *const *ctxs, int n, void *cuda_stream, dgpe_batc
 int dgpe_batch_step(dgpe_batch *b, int nsteps);
 /* Wait for the batch stream; the first latched device error of any context. */
 int dgpe_batch_sync(dgpe_batch *b);
+/* Free the batch (its graph, capture streams and events) after waiting for its stream.  The
+ * contexts stay owned by the caller and usable.  NULL is safe. */
 void dgpe_batch_destroy(dgpe_batch *b);
 
 /* Launch shape of a context's step. */
