@@ -8,7 +8,10 @@ convolution theorem" (Solution method).  Pins:
     -f(kappa) / (2 (2 pi)^{3/2} s_rho^2 s_z) (Lahaye et al., Rep. Prog. Phys. 72, 126401
     (2009)), f the anisotropy function, for both kappa < 1 and kappa > 1; the closed form is
     itself checked against an independent 1D quadrature of the k-space integral;
-  * symmetry: an isotropic density has zero dipolar energy on a cubic grid.
+  * symmetry: an isotropic density has zero dipolar energy on a cubic grid;
+  * anisotropic grids: the kernel's values at hand-derived wavenumbers on a grid whose three
+    axes differ in both N and h (box lengths 4, 6 and 3, so no two axes share a wavenumber
+    spacing), and the closed-form energy on a grid with unequal N and h per axis.
 """
 import numpy as np
 import pytest
@@ -38,16 +41,19 @@ def e_dd_quadrature(sr, sz):
     return 0.5 * 2 * np.pi * val / (2 * np.pi) ** 3
 
 
-def gaussian_density(n, h, sr, sz):
-    x = (np.arange(n) - n // 2) * h
-    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+def gaussian_density(shape, h, sr, sz):
+    axes = [(np.arange(n) - n // 2) * hd for n, hd in zip(shape, h)]
+    X, Y, Z = np.meshgrid(*axes, indexing="ij")
     return np.exp(-(X ** 2 + Y ** 2) / sr ** 2 - Z ** 2 / sz ** 2) / (np.pi ** 1.5 * sr * sr * sz)
 
 
 def grid_e_dd(orc, n, h, sr, sz):
-    p = orc.make_params((n, n, n), h, 1e-3, orc.REAL_TIME, (1, 1, 1), 0.0, 1.0)
-    dens = gaussian_density(n, h, sr, sz)
-    return 0.5 * np.sum(orc.dipolar_phi(p, dens) * dens) * h ** 3
+    """1/2 h^3 sum Phi n of the cylindrical Gaussian; n and h per axis (or one for all)."""
+    shape = (n, n, n) if np.isscalar(n) else tuple(n)
+    hs = (h, h, h) if np.isscalar(h) else tuple(h)
+    p = orc.make_params(shape, hs, 1e-3, orc.REAL_TIME, (1, 1, 1), 0.0, 1.0)
+    dens = gaussian_density(shape, hs, sr, sz)
+    return 0.5 * np.sum(orc.dipolar_phi(p, dens) * dens) * np.prod(hs)
 
 
 def test_kernel_geometry(orc):
@@ -59,6 +65,64 @@ def test_kernel_geometry(orc):
     assert ut[1, 0, 0] == pytest.approx(-1.0) and ut[0, 3, 0] == pytest.approx(-1.0)
     assert ut[1, 0, 1] == pytest.approx(0.5)          # 45 degrees: 3/2 - 1
     assert np.array_equal(ut, ut[::-1, ::-1, ::-1][np.ix_(*[np.roll(np.arange(8), 1)] * 3)])  # even
+
+
+# Anisotropic grid: nx = 8, hx = 0.5 (box 4), ny = 12, hy = 0.5 (box 6), nz = 12, hz = 0.25
+# (box 3), so k_x = pi m/2, k_y = pi m/3, k_z = 2 pi m/3 for the signed index m.  Values of
+# Ut = 3 kz^2/|k|^2 - 1 worked out by hand at these indices:
+#   (4, 0, 3): kx = 2 pi (the Nyquist index, m = +4), kz = 2 pi       -> 45 degrees: 1/2
+#   (0, 2, 1): ky = 2 pi/3, kz = 2 pi/3                               -> 1/2
+#   (0, 0, 5): along z                                                -> 2
+#   (3, 0, 0), (0, 5, 0): in the xy plane                             -> -1
+#   (1, 1, 1): |k|^2 = pi^2 (1/4 + 1/9 + 4/9) = 29 pi^2/36, kz^2 = 16 pi^2/36 -> 48/29 - 1 = 19/29
+#   (7, 11, 11): the signed indices (-1, -1, -1)                      -> 19/29
+#   (2, 3, 1): |k|^2 = pi^2 (1 + 1 + 4/9) = 22 pi^2/9, kz^2 = 4 pi^2/9  -> 12/22 - 1 = -5/11
+ANISO_GRID = ((8, 12, 12), (0.5, 0.5, 0.25))
+ANISO_PINS = {(4, 0, 3): 0.5, (0, 2, 1): 0.5, (0, 0, 5): 2.0, (3, 0, 0): -1.0, (0, 5, 0): -1.0,
+              (1, 1, 1): 19 / 29, (7, 11, 11): 19 / 29, (2, 3, 1): -5 / 11}
+
+
+def test_kernel_geometry_anisotropic(orc):
+    shape, h = ANISO_GRID
+    ut = orc.dipolar_kernel(orc.make_params(shape, h, 1e-3, orc.REAL_TIME, (1, 1, 1), 0, 1))
+    assert ut.shape == shape
+    assert ut[0, 0, 0] == 0.0
+    for idx, want in ANISO_PINS.items():
+        assert ut[idx] == pytest.approx(want, rel=1e-14, abs=1e-15), idx
+
+
+def test_anisotropic_pins_detect_axis_mixups():
+    """The pins above fail if any axis's N or h is taken from another axis: every other
+    assignment of the (N, h) pairs to the axes, and every swap of one axis's h with another
+    axis's, changes at least one pinned value (the values evaluated here by hand formula,
+    not by the oracle; this shows the pins discriminate, it pins nothing itself)."""
+    import itertools
+    shape, h = ANISO_GRID
+
+    def ut_at(idx, ns, hs):
+        k = []
+        for m, n, hd in zip(idx, ns, hs):
+            ms = m if m <= n // 2 else m - n
+            k.append(2 * np.pi * ms / (n * hd))
+        k2 = sum(v * v for v in k)
+        return 3 * k[2] ** 2 / k2 - 1 if k2 > 0 else 0.0
+
+    def pins_hold(ns, hs):
+        return all(abs(ut_at(idx, ns, hs) - want) < 1e-9 for idx, want in ANISO_PINS.items())
+
+    assert pins_hold(shape, h)
+    for perm in itertools.permutations(range(3)):
+        if perm != (0, 1, 2):
+            assert not pins_hold([shape[a] for a in perm], [h[a] for a in perm]), perm
+    for a, b in itertools.combinations(range(3), 2):
+        hs = list(h)
+        hs[a], hs[b] = hs[b], hs[a]
+        ns = list(shape)
+        ns[a], ns[b] = ns[b], ns[a]
+        if hs != list(h):
+            assert not pins_hold(shape, hs), ("h", a, b)
+        if ns != list(shape):
+            assert not pins_hold(ns, h), ("n", a, b)
 
 
 @pytest.mark.parametrize("shape,h", [((4, 6, 8), (0.5, 0.4, 0.3)), ((6, 6, 6), 0.7), ((8, 4, 6), (0.3, 0.9, 0.5))])
@@ -84,6 +148,18 @@ def test_gaussian_dipolar_energy(orc, sr, sz):
     assert np.sign(large) == np.sign(exact)
     assert abs(large - exact) < 2e-4 * abs(exact)
     # the remaining error is the periodic-box error: it shrinks as the box grows
+    assert abs(large - exact) < 0.2 * abs(small - exact)
+
+
+@pytest.mark.parametrize("sr,sz", [(1.0, 0.6), (0.6, 1.0)])
+def test_gaussian_dipolar_energy_anisotropic_grid(orc, sr, sz):
+    """The closed form on a grid with unequal N and h per axis: 64 x 80 x 48 points at
+    h = (0.3, 0.25, 0.4) (box 19.2 x 20 x 19.2), and the half-size grid (box halved)."""
+    exact = e_dd_closed(sr, sz)
+    h = (0.3, 0.25, 0.4)
+    small = grid_e_dd(orc, (32, 40, 24), h, sr, sz)
+    large = grid_e_dd(orc, (64, 80, 48), h, sr, sz)
+    assert abs(large - exact) < 2e-4 * abs(exact)
     assert abs(large - exact) < 0.2 * abs(small - exact)
 
 
