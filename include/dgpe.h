@@ -53,7 +53,8 @@ extern "C" {
 #define DGPE_ENOMEM (-2)        /* device allocation failed or workspace too small */
 #define DGPE_ECUDA (-3)         /* a CUDA runtime call or kernel launch failed */
 #define DGPE_ENONFINITE (-4)    /* NaN/Inf in a reduction (norm, observables), or a zero norm to renormalise */
-#define DGPE_ETIMEOUT (-5)      /* a bounded device-side wait gave up */
+#define DGPE_ETIMEOUT (-5)      /* reserved: a bounded device-side wait gave up.  No kernel of this
+                                   build waits on a flag or on another block, so no call returns it */
 #define DGPE_EUNSUPPORTED (-6)  /* valid request this build does not support */
 
 #define DGPE_REAL_TIME 0
@@ -85,8 +86,9 @@ extern "C" {
 #define DGPE_SUB_CN_Z 3
 
 /*
- * Problem description.  Sizes: 4 <= n <= 512, n even, n = 2^a 3^b 5^c 7^d (the paper's
- * "FFT-friendly" sizes, except factors 11 and 13; radix-2/3/4/5/7/8 transforms), e.g.
+ * Problem description.  Sizes: 4 <= n <= 512, n even, n = 2^a 3^b 5^c 7^d (the sizes the
+ * paper recommends for its transforms, except factors 11 and 13; radix-2/3/4/5/7/8
+ * transforms), e.g.
  * the paper's own 480 x 480 x 500 and 480 x 480 x 250 grids.
  * h, dt > 0 and finite; nu, g, gdd finite.  workspace: NULL, or device memory of at least
  * workspace_bytes >= dgpe_workspace_bytes(p) bytes, 256-byte aligned, owned by the caller
@@ -135,29 +137,41 @@ typedef struct dgpe_kernel_time {
 
 typedef struct dgpe_ctx dgpe_ctx;
 
-/* Device bytes the solver needs for p (only shape and precision matter).  Host-only. */
+/* Device bytes the solver needs for p (only shape and precision matter).  Host-only.
+ * Paper: Summary of revisions, DBEC-GP-OMP (the memory of the dipolar transform is set by
+ * the half spectrum of the real-to-complex FFT). */
 int dgpe_workspace_bytes(const dgpe_params *p, size_t *bytes);
 
 /* Validate p, set up the workspace, FFT twiddles and Crank-Nicolson factor tables on
  * `cuda_stream` (a cudaStream_t; NULL = legacy default stream).  psi starts at zero.
- * On success *out owns the context; free it with dgpe_destroy. */
+ * On success *out owns the context; free it with dgpe_destroy.
+ * Paper: Nature of problem (the GP equation with contact and dipolar interaction in a
+ * harmonic anisotropic trap: nu, g, gdd); Solution method (discretised in space and time:
+ * the grid and dt); Additional comments (grid sizes are checked and an error is reported). */
 int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out);
 
 /* Change dt, mode, nu, g, gdd or h (e.g. the quench or a trap schedule) without
  * reallocation; shape and precision must stay the same (else DGPE_EINVAL).
- * Stream-ordered: takes effect for work enqueued afterwards. */
+ * Stream-ordered: takes effect for work enqueued afterwards.
+ * Paper: Nature of problem (the trap and interaction strengths); Solution method (imaginary
+ * or real time: stationary then non-stationary problems on one state). */
 int dgpe_set_params(dgpe_ctx *ctx, const dgpe_params *p);
 
 /* Copy psi in from `where` = DGPE_HOST or DGPE_DEVICE memory (layout above; complex128 for
- * FP64, complex64 for MIXED).  The caller keeps ownership.  Clears latched device errors. */
+ * FP64 and DF64, complex64 for MIXED).  The caller keeps ownership.  Clears latched device
+ * errors.  Paper: Solution method (the state the propagation starts from). */
 int dgpe_set_psi(dgpe_ctx *ctx, const void *psi, int where);
 
 /* Copy the current psi (pending renormalisation applied) to `out` in host or device memory.
- * Host copies synchronise the stream; device copies are stream-ordered. */
+ * Host copies synchronise the stream; device copies are stream-ordered.
+ * Paper: Solution method (the stationary or non-stationary solution the propagation yields). */
 int dgpe_get_psi(dgpe_ctx *ctx, void *out, int where);
 
 /* Enqueue nsteps >= 0 SSCN steps (stream-ordered, asynchronous; replayed from a CUDA graph).
- * In imaginary time every step renormalises (applied lazily: see dgpe_get_psi). */
+ * In imaginary time every step renormalises (applied lazily: see dgpe_get_psi).
+ * Paper: Solution method (split-step Crank-Nicolson, propagation in imaginary or real time
+ * over small time steps, the dipolar term in momentum space by the convolution theorem);
+ * Summary of revisions, DBEC-GP-OMP (the transform of the density is real-to-complex). */
 int dgpe_step(dgpe_ctx *ctx, int nsteps);
 
 /* Host-resident states through the solver: copy psi in from host memory `in` (as
@@ -170,18 +184,25 @@ int dgpe_step(dgpe_ctx *ctx, int nsteps);
  * unchanged and `out` unread until dgpe_sync (which waits for the copies too); later calls
  * that change psi on this context wait for the output copy by themselves.  Pinned host
  * memory lets the copies run asynchronously.  Device errors surface at dgpe_sync, as for
- * dgpe_step.  NULL in/out or nsteps < 0: DGPE_EINVAL. */
+ * dgpe_step.  NULL in/out or nsteps < 0: DGPE_EINVAL.
+ * Paper: Solution method (propagation); states that live in host memory between steps. */
 int dgpe_step_host(dgpe_ctx *ctx, const void *in, void *out, int nsteps);
 
-/* Apply one factor of the split step (DGPE_SUB_*) once, without renormalisation. */
+/* Apply one factor of the split step (DGPE_SUB_*) once, without renormalisation.
+ * Paper: Solution method (the factors of the split step). */
 int dgpe_substep(dgpe_ctx *ctx, int which);
 
 /* Compute the observables of the current state; synchronises the stream.
- * Returns DGPE_ENONFINITE if a sum is NaN/Inf. */
+ * Returns DGPE_ENONFINITE if a sum is NaN/Inf.
+ * Paper: Nature of problem (the properties of the condensate the GP equation describes);
+ * the paper prints no formula for them, so the forms are the readings stated at dgpe_obs
+ * (the step's own discrete Hamiltonian; the rectangle or Simpson quadrature). */
 int dgpe_observables(dgpe_ctx *ctx, dgpe_obs *o);
 
 /* Dipolar potential Phi = IDFT[Ut DFT(|psi|^2)] of the current state (real, [nx][ny][nz],
- * double for FP64, float for MIXED) into host or device memory.  Synchronises for host. */
+ * double for FP64 and DF64, float for MIXED) into host or device memory.  Synchronises for
+ * host.  Paper: Solution method (the dipolar contribution evaluated in momentum space by
+ * the convolution theorem). */
 int dgpe_get_phi(dgpe_ctx *ctx, void *out, int where);
 
 /* ---- Differentiation (real time only) ----------------------------------------------
@@ -202,12 +223,13 @@ int dgpe_get_phi(dgpe_ctx *ctx, void *out, int where);
 int dgpe_adjoint_step(dgpe_ctx *ctx, const void *psi_k, void *gbar);
 
 /* Synchronises and copies the accumulated {dL/dg, dL/dgdd, dL/dnu_z} into out[3]; reset != 0
- * zeroes the accumulators afterwards. */
+ * zeroes the accumulators afterwards.  (No paper counterpart: the paper has no adjoint.) */
 int dgpe_adjoint_grads(dgpe_ctx *ctx, double *out, int reset);
 
 /* Device bytes of the work buffer of dgpe_grad_z2 for nseg segments of steps_per_seg
  * steps: sqrt(N) checkpointing keeps ceil(N/k) checkpoints plus the k states of one
- * segment (k = ceil(sqrt(N)), N = nseg * steps_per_seg), the cotangent and nseg sums. */
+ * segment (k = ceil(sqrt(N)), N = nseg * steps_per_seg), the cotangent and nseg sums.
+ * (No paper counterpart: the paper has no adjoint.) */
 int dgpe_grad_z2_workspace_bytes(const dgpe_ctx *ctx, int nseg, int steps_per_seg, size_t *bytes);
 
 /* Gradient of L = hx hy hz sum z^2 |psi_N|^2 (= <z^2> of a unit-norm state) after
@@ -217,7 +239,8 @@ int dgpe_grad_z2_workspace_bytes(const dgpe_ctx *ctx, int nseg, int steps_per_se
  * work: device memory of dgpe_grad_z2_workspace_bytes(), 256-byte aligned, caller-owned.
  * Cost: one forward pass storing a checkpoint every k steps, then per segment (backwards)
  * a recomputation from its checkpoint and the adjoint steps through it.  On return the
- * context holds the initial psi and the initial nu_z again.  Synchronises. */
+ * context holds the initial psi and the initial nu_z again.  Synchronises.  (No paper
+ * counterpart: the paper has no adjoint; the forward steps are its Solution method.) */
 int dgpe_grad_z2(dgpe_ctx *ctx, int nseg, int steps_per_seg, const double *nu_z, void *work, size_t work_bytes,
                  double *loss, double *dnu, double *dg, double *dgdd);
 
@@ -230,18 +253,21 @@ typedef struct dgpe_batch dgpe_batch;
 
 /* n >= 1 distinct contexts on the current device; they must outlive the batch.  The batch
  * launches on cuda_stream; do not enqueue work on a context's own stream while a batch step
- * may still run (synchronise first). */
+ * may still run (synchronise first).  (No paper counterpart: see above.) */
 int dgpe_batch_create(dgpe_ctx *const *ctxs, int n, void *cuda_stream, dgpe_batch **out);
 /* nsteps SSCN steps of every context (one graph launch per step; the graph is rebuilt
- * when a context's step changed through dgpe_set_params or tuning).  Asynchronous. */
+ * when a context's step changed through dgpe_set_params or tuning).  Asynchronous.
+ * (No paper counterpart: the paper runs one condensate per program.) */
 int dgpe_batch_step(dgpe_batch *b, int nsteps);
-/* Wait for the batch stream; the first latched device error of any context. */
+/* Wait for the batch stream; the first latched device error of any context.  (No paper
+ * counterpart.) */
 int dgpe_batch_sync(dgpe_batch *b);
 /* Free the batch (its graph, capture streams and events) after waiting for its stream.  The
- * contexts stay owned by the caller and usable.  NULL is safe. */
+ * contexts stay owned by the caller and usable.  NULL is safe.  (No paper counterpart.) */
 void dgpe_batch_destroy(dgpe_batch *b);
 
-/* Launch shape of a context's step. */
+/* Launch shape of a context's step.  Paper: Summary of revisions, DBEC-GP-MPI (performance
+ * depends on the grid sizes and the machine, and configurations should be tried). */
 typedef struct dgpe_tuning {
   int plan_style[3];     /* FFT radix order per axis: 0 radix-8 first, 1 radix-4, 2 radix-3 first */
   int ylines;            /* lines per CTA of the y transforms: 2, 4, 8, 16 or 32 */
@@ -253,27 +279,31 @@ typedef struct dgpe_tuning {
 /* Time candidate launch shapes on this context's own shape (a few steps each, with CUDA
  * events per kernel), choose the fastest per kernel class, apply it and report it in *out.
  * psi and the device state are restored afterwards.  Synchronises; allocates one
- * psi-sized temporary with cudaMallocAsync. */
+ * psi-sized temporary with cudaMallocAsync.  Paper: as dgpe_tuning. */
 int dgpe_autotune(dgpe_ctx *ctx, dgpe_tuning *out);
-/* Apply a tuning (e.g. one found earlier for the same shape). DGPE_EINVAL if invalid. */
+/* Apply a tuning (e.g. one found earlier for the same shape). DGPE_EINVAL if invalid.
+ * Paper: as dgpe_tuning. */
 int dgpe_set_tuning(dgpe_ctx *ctx, const dgpe_tuning *t);
 /* The launch shape in use (the defaults of dgpe_create until dgpe_autotune or
- * dgpe_set_tuning changes it); step_ms_default and step_ms_tuned are 0.  No CUDA call. */
+ * dgpe_set_tuning changes it); step_ms_default and step_ms_tuned are 0.  No CUDA call.
+ * Paper: as dgpe_tuning. */
 int dgpe_get_tuning(const dgpe_ctx *ctx, dgpe_tuning *out);
 /* Kernel launches of one dgpe_step step (7, or 8 where the z sweep is a pass of its own:
- * FP64 and double-float).  No CUDA call. */
+ * FP64 and double-float).  No CUDA call.  (No paper counterpart; the paper times whole
+ * runs of the step loop, Tables 1-3.) */
 int dgpe_step_launches(const dgpe_ctx *ctx, int *n);
 
-/* Wait for the stream; returns a latched device error if any. */
+/* Wait for the stream; returns a latched device error if any.  (No paper counterpart.) */
 int dgpe_sync(dgpe_ctx *ctx);
 
 /* Per-kernel timing: when enabled, dgpe_step launches kernels one by one with CUDA events
  * around each (instead of replaying the graph) and accumulates their durations.  A record
  * covers one stage of the step: in FP64 the "k5" record times its two launches (the
- * phase-only pass and the per-line z sweep) together. */
+ * phase-only pass and the per-line z sweep) together.  (No paper counterpart; the paper
+ * times whole runs of the step loop, Tables 1-3.) */
 int dgpe_set_timing(dgpe_ctx *ctx, int enable);
 /* Synchronises, then copies up to `max` records into out and sets *n to the number of
- * kernels timed. */
+ * kernels timed.  (No paper counterpart.) */
 int dgpe_kernel_times(dgpe_ctx *ctx, dgpe_kernel_time *out, int max, int *n);
 
 /* Norm and rms sizes of a caller's psi without allocating any device memory.
@@ -301,14 +331,16 @@ int dgpe_kernel_times(dgpe_ctx *ctx, dgpe_kernel_time *out, int max, int *n);
  * enqueueing a memset and one kernel on cuda_stream (NULL = legacy default stream). */
 int dgpe_moments_noalloc(const void *psi, const dgpe_params *p, double *out, void *cuda_stream);
 
-/* Static text for an error code. */
+/* Static text for an error code.  Paper: Additional comments (invalid grid sizes are
+ * reported to the user as an error). */
 const char *dgpe_strerror(int code);
 
 /* Name and text of the last CUDA runtime error this thread's calls met (empty if none);
- * valid until the next call on the same thread. */
+ * valid until the next call on the same thread.  (No paper counterpart.) */
 const char *dgpe_last_cuda_error(void);
 
-/* Free the context and whatever it allocated (not a caller-owned workspace). NULL is ok. */
+/* Free the context and whatever it allocated (not a caller-owned workspace). NULL is ok.
+ * (No paper counterpart.) */
 void dgpe_destroy(dgpe_ctx *ctx);
 
 #ifdef __cplusplus

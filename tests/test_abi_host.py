@@ -105,3 +105,20 @@ def test_binding_constants_match_the_header():
     codes = [int(v) for k, v in defines.items() if k == "DGPE_OK" or k.startswith("DGPE_E")]
     messages = [abi.strerror(code) for code in codes]
     assert len(set(messages)) == len(codes) and "unknown error code" not in messages
+
+
+def test_every_declaration_cites_the_paper():
+    """Each entry point's comment names the passage of the paper it implements (section
+    names of the program summary: Nature of problem, Solution method, Summary of revisions,
+    Additional comments) or says that the paper has no counterpart."""
+    text = open(os.path.join(ROOT, "include", "dgpe.h")).read()
+    body = text[text.index("typedef struct dgpe_params"):]
+    missing = []
+    prev = 0
+    for m in re.finditer(r"^(?:int|void|const char \*)\s*(dgpe_\w+)\s*\(", body, flags=re.M):
+        chunk = body[prev:m.start()]
+        comments = " ".join(re.findall(r"/\*(.*?)\*/", chunk, flags=re.S))
+        if "paper" not in comments.lower():
+            missing.append(m.group(1))
+        prev = body.index(";", m.end()) + 1
+    assert not missing, missing

@@ -1,7 +1,7 @@
 """Pins of the oracle's dipolar mean field Phi = IDFT[Ut(k) DFT(n)], Ut = 3 kz^2/k^2 - 1.
 
-The paper evaluates the dipolar term "by a Fourier transformation to momentum space using a
-convolution theorem" (Solution method).  Pins:
+The paper evaluates the dipolar term in momentum space, where the convolution with the
+dipolar interaction becomes a product (Solution method).  Pins:
   * brute force: the FFT path equals the direct circular convolution with the real-space
     kernel K = naive IDFT(Ut) on tiny grids;
   * closed form: for a cylindrical Gaussian density the dipolar energy 1/2 int Phi n equals

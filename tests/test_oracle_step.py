@@ -1,7 +1,7 @@
 """Physics pins of the oracle's full SSCN step (potential, CN x/y/z, renormalisation).
 
-The paper's programs compute "stationary and non-stationary solutions by propagation in
-imaginary or real time" (Abstract; Solution method).  What the mathematics fixes:
+The paper's programs find stationary states by propagating in imaginary time and follow
+the dynamics by propagating in real time (Abstract; Solution method).  What the mathematics fixes:
   * non-interacting imaginary time converges to the harmonic ground state,
     mu = (nu_x + nu_y + nu_z)/2 and rms_d = 1/sqrt(2 nu_d), with O(h^2) grid error;
   * real time conserves the norm and is exactly reversible (dt -> -dt, reversed order);
