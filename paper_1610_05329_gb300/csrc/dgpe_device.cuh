@@ -125,17 +125,18 @@ __device__ __forceinline__ void sin_cos(double x, double *s, double *c) {
   // their bits), which keeps them off the FP64 pipe; NaN fails both
   const unsigned long long ab = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
   if (ab <= 0x3fc0000000000000ULL) {   // |x| <= 1/8
-    // Chebyshev least-squares fits of (sin x / x - 1)/x^2 and (cos x - 1)/x^2 as cubics in
-    // u = x^2 on [0, 1/64] (computed offline in 40-digit arithmetic; errors below 2e-19
-    // relative and 2e-18 absolute on |x| <= 1/8): two FMAs fewer than the |x| <= 1/4 branch
+    // least-squares fits of (sin x / x - 1)/x^2 and (cos x - 1)/x^2 as cubics in u = x^2
+    // at 64 Chebyshev nodes of [0, 1/64] (40-digit arithmetic, coefficients rounded to
+    // double: fit_sincos.py; errors below 2e-19 relative for the sine and 2e-18 absolute for
+    // the cosine on |x| <= 1/8): two FMAs fewer than the |x| <= 1/4 branch
     const double u = x * x;
-    double ps = 2.754949151820351e-06;
-    ps = fma(ps, u, -0.0001984126907687799);
+    double ps = 2.75494915427022e-06;
+    ps = fma(ps, u, -0.0001984126907688373);
     ps = fma(ps, u, 0.008333333333309446);
     ps = fma(ps, u, -0.16666666666666666);
     *s = fma(x * u, ps, x);
-    double pc = 2.4792977040825343e-05;
-    pc = fma(pc, u, -0.0013888888048085412);
+    double pc = 2.4792977072672542e-05;
+    pc = fma(pc, u, -0.0013888888048092878);
     pc = fma(pc, u, 0.04166666666640392);
     pc = fma(pc, u, -0.4999999999999999);
     *c = fma(u, pc, 1.0);
@@ -149,12 +150,12 @@ __device__ __forceinline__ void sin_cos(double x, double *s, double *c) {
     ps = fma(ps, u, 0.008333333333333333);
     ps = fma(ps, u, -0.16666666666666666);
     *s = fma(x * u, ps, x);
-    // cosine: a Chebyshev least-squares fit of (cos x - 1)/x^2 as a quartic in u = x^2 on
-    // [0, 1/16] (computed offline in 40-digit arithmetic; error below 5e-19 on |x| <= 1/4),
-    // one term fewer than the Taylor series for the same accuracy
-    double pc = -2.7524717487900135e-07;
-    pc = fma(pc, u, 2.4801569475683656e-05);
-    pc = fma(pc, u, -0.001388888888491021);
+    // cosine: the same least-squares fit of (cos x - 1)/x^2 as a quartic in u = x^2 on
+    // [0, 1/16] (fit_sincos.py; error below 5.2e-19 on |x| <= 1/4), one term fewer than the
+    // Taylor series for the same accuracy
+    double pc = -2.7524717767692497e-07;
+    pc = fma(pc, u, 2.48015694760334e-05);
+    pc = fma(pc, u, -0.0013888888884910347);
     pc = fma(pc, u, 0.041666666666663556);
     pc = fma(pc, u, -0.5);
     *c = fma(u, pc, 1.0);
