@@ -15,22 +15,25 @@ from paper_1610_05329_gb300 import abi, inputs
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", [abi.DGPE_FP64, abi.DGPE_MIXED])
-def test_moments_noalloc_matches_observables(precision):
+@pytest.mark.parametrize("integration", [abi.DGPE_RECTANGLE, abi.DGPE_SIMPSON])
+@pytest.mark.parametrize("precision", [abi.DGPE_FP64, abi.DGPE_MIXED, abi.DGPE_DF64])
+def test_moments_noalloc_matches_observables(precision, integration):
+    """Same norm and rms sizes as dgpe_observables of a context in the same precision and
+    quadrature (the double-float mode hands complex128 states to its callers)."""
     import torch
     from paper_1610_05329_gb300 import build
     build.build()
     shape, h = (24, 36, 48), (0.3, 0.25, 0.2)
     gpu = abi.Condensate(shape, h, 0.01, mode=abi.DGPE_IMAG_TIME, precision=precision, nu=(1.0, 1.3, 0.8),
-                         g=20.0, gdd=10.0)
+                         g=20.0, gdd=10.0, integration=integration)
     psi = inputs.gaussian_psi(shape, h, width=1.1, noise=1e-3, seed=17, center=(0.3, -0.2, 0.1))
     gpu.set_psi(psi)
     gpu.step(3)                       # a state with a pending renormalisation
     want = gpu.observables()
     dev_psi = gpu.get_psi(host=False)  # the normalised state, in device memory
     out = torch.zeros(4, dtype=torch.float64, device=dev_psi.device)
-    params = abi.make_params(shape, h, 0.01, precision=precision)
-    tol = 1e-11 if precision == abi.DGPE_FP64 else 1e-6
+    params = abi.make_params(shape, h, 0.01, precision=precision, integration=integration)
+    tol = 1e-6 if precision == abi.DGPE_MIXED else 1e-11
     stream = torch.cuda.current_stream().cuda_stream
     for _ in range(2):
         out.zero_()
