@@ -203,21 +203,114 @@ def track_physics(obs0, obs1, steps):
             "rms_start": list(obs0["rms"]), "rms_end": list(obs1["rms"])}
 
 
-def mixed_vs_fp64(abi, wl, local, steps=20):
-    """The FP32-mixed path against the FP64 GPU path on the same prepared state: both run
-    the imaginary-time preparation and `steps` real-time steps; rel-L2 of psi and the relative
-    differences of mu and E."""
+# The mixed-precision workload as defined: 512x512x384, h = 0.05, trap (1, 1, 2), g = 100,
+# gdd = 60; imaginary time at dt = 0.001, then real time at dt = 5e-4 (the unstated steps).
+PRECISION_WL = dict(shape=(512, 512, 384), h=0.05, nu=(1.0, 1.0, 2.0), g=100.0, gdd=60.0, dt_imag=0.001,
+                    dt_real=5e-4)
+MIXED_DTYPE = "f32 (reductions: FP32 terms, exact weights, double-float sums per point, FP64 across blocks)"
+
+
+def rel_errors(psi, obs, psi_ref, obs_ref):
+    """Errors of (psi, obs) against a reference: rel-L2 of psi and the relative errors of
+    mu, E, the rms sizes and the norm."""
     import torch
-    out = {}
-    for prec in ("mixed", "fp64"):
-        c = make_condensate(abi, dict(wl, precision=prec), local)
-        c.step(steps)
-        out[prec] = (c.get_psi(host=False).to(torch.complex128), c.observables())
-        c.close()
-    (pm, om), (pd, od) = out["mixed"], out["fp64"]
-    return {"steps_after_prep": steps, "psi_rel_l2": float(torch.linalg.norm(pm - pd) / torch.linalg.norm(pd)),
-            "mu_rel": abs(om["mu"] - od["mu"]) / abs(od["mu"]),
-            "energy_rel": abs(om["energy"] - od["energy"]) / abs(od["energy"])}
+    return {"psi_rel_l2": float(torch.linalg.norm(psi - psi_ref) / torch.linalg.norm(psi_ref)),
+            "mu_rel": abs(obs["mu"] - obs_ref["mu"]) / abs(obs_ref["mu"]),
+            "energy_rel": abs(obs["energy"] - obs_ref["energy"]) / abs(obs_ref["energy"]),
+            "rms_rel": [abs(a - b) / abs(b) for a, b in zip(obs["rms"], obs_ref["rms"])],
+            "norm_rel": abs(obs["norm"] - obs_ref["norm"]) / abs(obs_ref["norm"])}
+
+
+def run_phases(abi, local, precision, imag_steps, real_steps):
+    """The mixed-precision workload from the seeded Gaussian (width 1, 1e-3 noise, seed 1):
+    `imag_steps` imaginary-time steps, then `real_steps` real-time steps; the observables and
+    psi (complex128, on the device) after each phase."""
+    import torch
+    from paper_1610_05329_gb300 import inputs
+    wl = PRECISION_WL
+    c = abi.Condensate(wl["shape"], wl["h"], wl["dt_imag"], mode=abi.DGPE_IMAG_TIME, precision=PRECISIONS[precision],
+                       nu=wl["nu"], g=wl["g"], gdd=wl["gdd"], device=torch.device("cuda", local))
+    psi0 = inputs.gaussian_psi(wl["shape"], wl["h"], noise=1e-3, seed=1)
+    c.set_psi(torch.from_numpy(psi0).to(device=c.device, dtype=c.cdtype))
+    c.step(imag_steps)
+    out = [(c.observables(), c.get_psi(host=False).to(torch.complex128))]
+    c.set_params(mode=abi.DGPE_REAL_TIME, dt=wl["dt_real"])
+    c.step(real_steps)
+    out.append((c.observables(), c.get_psi(host=False).to(torch.complex128)))
+    c.close()
+    return out
+
+
+def precision_table(abi, local, imag_steps=500, real_steps=500):
+    """Error table of the FP32-mixed path on its workload against the FP64 GPU path, after
+    `imag_steps` imaginary-time and then `real_steps` real-time steps, each path from the same
+    seeded state.  (The comparison of both paths with the FP64 oracle at this size, over the
+    few steps the host cores finish in seconds, is a GPU test.)"""
+    import torch
+    wl = PRECISION_WL
+    t0 = time.perf_counter()
+    mixed = run_phases(abi, local, "mixed", imag_steps, real_steps)
+    fp64 = run_phases(abi, local, "fp64", imag_steps, real_steps)
+    table = {"grid": list(wl["shape"]), "h": wl["h"], "nu": list(wl["nu"]), "g": wl["g"], "gdd": wl["gdd"],
+             "dt_imag": wl["dt_imag"], "dt_real": wl["dt_real"], "start": "seeded Gaussian (width 1, 1e-3 noise, seed 1)",
+             "vs_fp64_gpu": {"after_imag": dict(steps=imag_steps, **rel_errors(*mixed[0][::-1], *fp64[0][::-1])),
+                             "after_real": dict(steps=real_steps, **rel_errors(*mixed[1][::-1], *fp64[1][::-1])),
+                             "fp64_after_imag": {k: fp64[0][0][k] for k in ("mu", "energy", "rms", "norm")},
+                             "fp64_after_real": {k: fp64[1][0][k] for k in ("mu", "energy", "rms", "norm")}},
+             "wall_s": None}
+    del mixed, fp64
+    torch.cuda.empty_cache()
+    table["wall_s"] = round(time.perf_counter() - t0, 2)
+    return table
+
+
+def ground_state_run(abi, local, tol=1e-10, check_every=100, max_steps=20000, real_steps=1000, record_every=100):
+    """The 256^3 real-time workload as defined: the imaginary-time ground state (FP64,
+    dt = 0.004, g = 50) from the seeded Gaussian, run until mu changes by less than `tol`
+    between checks `check_every` steps apart (at most `max_steps`); then the quench g -> 40
+    and `real_steps` real-time steps at dt = 5e-4, with the norm, energy and rms sizes every
+    `record_every` steps."""
+    import torch
+    from paper_1610_05329_gb300 import inputs
+    wl = WORKLOADS["real256_fp64"]
+    c = abi.Condensate(wl["shape"], wl["h"], wl["dt_prep"], mode=abi.DGPE_IMAG_TIME, precision=abi.DGPE_FP64,
+                       nu=wl["nu"], g=wl["g_prep"], gdd=wl["gdd"], device=torch.device("cuda", local))
+    c.set_psi(torch.from_numpy(inputs.gaussian_psi(wl["shape"], wl["h"], noise=1e-3, seed=1)).to(
+        device=c.device, dtype=c.cdtype))
+    t0 = time.perf_counter()
+    steps, mu_prev, dmu = 0, None, None
+    while steps < max_steps:
+        c.step(check_every)
+        steps += check_every
+        mu = c.observables()["mu"]
+        if mu_prev is not None:
+            dmu = abs(mu - mu_prev)
+            if dmu < tol:
+                break
+        mu_prev = mu
+    gs = c.observables()
+    imag_s = time.perf_counter() - t0
+    c.set_params(mode=abi.DGPE_REAL_TIME, dt=wl["dt"], g=wl["g"])
+    o0 = c.observables()
+    series = [{"step": 0, "norm": o0["norm"], "energy": o0["energy"], "rms": list(o0["rms"])}]
+    t1 = time.perf_counter()
+    for k in range(real_steps // record_every):
+        c.step(record_every)
+        o = c.observables()
+        series.append({"step": (k + 1) * record_every, "norm": o["norm"], "energy": o["energy"], "rms": list(o["rms"])})
+    real_s = time.perf_counter() - t1
+    c.close()
+    n0 = series[0]["norm"]
+    return {"grid": list(wl["shape"]), "imag": {"dt": wl["dt_prep"], "g": wl["g_prep"], "steps": steps,
+                                                "converged": dmu is not None and dmu < tol,
+                                                "criterion": "|delta mu| < %g between checks %d steps apart" % (tol, check_every),
+                                                "final_delta_mu": dmu, "mu": gs["mu"], "energy": gs["energy"],
+                                                "rms": list(gs["rms"]), "wall_s": round(imag_s, 2)},
+            "real": {"dt": wl["dt"], "g": wl["g"], "steps": real_steps,
+                     "norm_drift": (series[-1]["norm"] - n0) / n0,
+                     "max_norm_deviation": max(abs(r["norm"] - n0) for r in series) / n0,
+                     "energy_drift": (series[-1]["energy"] - series[0]["energy"]) / abs(series[0]["energy"]),
+                     "series": series, "wall_s": round(real_s, 2)}}
 
 
 def time_steps(c, steps, barrier):
@@ -374,7 +467,7 @@ def differentiation_run(abi, local, precision, steps, full=True):
     e1.record(c.stream)
     torch.cuda.synchronize(c.device)
     adj = e0.elapsed_time(e1)
-    out = {"grid": list(shape), "dtype": "f64" if precision == "fp64" else "f32 (FP64 reductions)",
+    out = {"grid": list(shape), "dtype": "f64" if precision == "fp64" else MIXED_DTYPE,
            "forward_ms_per_step": round(fwd / steps, 4), "adjoint_ms_per_step": round(adj / steps, 4),
            "adjoint_over_forward": round(adj / fwd, 3)}
     if full:
@@ -393,8 +486,9 @@ def batching_run(abi, local, steps=300, count=64):
     """The batching workload: 64 independent imaginary-time FP32-mixed condensates, cube
     sizes drawn from {32, 48, 64, 96, 128} (SplitMix64 seed 5), h = 12.8/N, g ~ U[5, 80],
     gdd ~ U[0, 0.9 g], nu_d ~ U[0.5, 2], dt = 0.001, `steps` steps each.  Sequential
-    per-condensate graph launches vs one batched graph (parallel branches) per step, after
-    autotuning one member per distinct size."""
+    per-condensate graph launches vs one batched graph launch for all `steps` steps (one
+    chain of steps per member, joined once), after autotuning one member per distinct size;
+    the first batched call (graph capture and instantiation, then the run) is untimed."""
     import torch
     from paper_1610_05329_gb300 import inputs
     sizes = [32, 48, 64, 96, 128]
@@ -440,7 +534,10 @@ def batching_run(abi, local, steps=300, count=64):
         c.set_psi(psi)
     seq_ms = timed(lambda: [c.step(steps) for c in conds])
     b = abi.Batch(conds)
-    b.step(1)
+    t0 = time.perf_counter()
+    b.step(steps)                        # builds the graph of `steps` steps per member, and runs it
+    b.sync()
+    first_call_s = time.perf_counter() - t0
     for c, psi in zip(conds, psis):
         c.set_psi(psi)
     bat_ms = timed(lambda: b.step(steps))
@@ -449,11 +546,13 @@ def batching_run(abi, local, steps=300, count=64):
     for c in conds:
         c.close()
     return {"condensates": count, "sizes": {str(n): sum(1 for m in members if m["n"] == n) for n in sizes},
-            "steps": steps, "points": npts, "dtype": "f32 (FP64 reductions)",
+            "steps": steps, "points": npts, "dtype": MIXED_DTYPE,
             "sequential_ms": round(seq_ms, 3), "batched_ms": round(bat_ms, 3),
             "sequential_updates_per_s": npts * steps / (seq_ms * 1e-3),
             "batched_updates_per_s": npts * steps / (bat_ms * 1e-3),
             "batched_speedup": round(seq_ms / bat_ms, 3),
+            "batched_graph_launches": 1,
+            "batched_first_call_s": round(first_call_s, 3),
             "autotune": {str(n): {k: (list(v) if isinstance(v, tuple) else v) for k, v in t.items()}
                          for n, t in tunings.items()}}
 
@@ -540,6 +639,10 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 128^3 differentiation line item")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-condensate batching line item")
     ap.add_argument("--no-paper-grids", action="store_true", help="skip the paper-grid context line item")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the 512x512x384 mixed-vs-FP64 error table (500 + 500 steps, and the oracle)")
+    ap.add_argument("--no-ground-state", action="store_true",
+                    help="skip the converged 256^3 ground state, quench and 1000 real-time steps")
     ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
                     help="time only this workload (profiling); the default line times both")
     args = ap.parse_args()
@@ -600,10 +703,9 @@ def main():
         cm.sync()
         cm.close()
         mixed = {"value": value_m, "unit": UNIT, "ms_per_step": round(msm / args.steps, 4),
-                 "dtype": "f32 (FP64 reductions)", "grid": list(wlm["shape"]), "roofline": rl_m, "kernels": kernels_m,
+                 "dtype": MIXED_DTYPE, "grid": list(wlm["shape"]), "roofline": rl_m, "kernels": kernels_m,
                  "algorithmic_bytes_per_step": sum(k["bytes_per_launch"] * k["launches"] for k in kernels_m)
-                 / min(args.steps, 50),
-                 "vs_fp64_gpu": mixed_vs_fp64(abi, wlm, local)}
+                 / min(args.steps, 50)}
 
     dfl = None
     if not args.no_df64:
@@ -630,6 +732,12 @@ def main():
     paper = None
     if not args.no_paper_grids and args.workload is None:
         paper = paper_grid_run(abi, local)
+    prec_table = None
+    if not args.no_precision and args.workload is None and rank == 0:
+        prec_table = precision_table(abi, local)
+    ground = None
+    if not args.no_ground_state and args.workload is None and rank == 0:
+        ground = ground_state_run(abi, local)
 
     if rank != 0:
         return
@@ -653,6 +761,10 @@ def main():
         line["batching_64"] = batch
     if paper is not None:
         line["paper_grids_fp64"] = paper
+    if prec_table is not None:
+        line["precision_512x512x384"] = prec_table
+    if ground is not None:
+        line["ground_state_256"] = ground
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)

@@ -61,7 +61,13 @@ extern "C" {
 #define DGPE_IMAG_TIME 1
 
 #define DGPE_FP64 0   /* complex128 psi; FFT, phase and CN in FP64 */
-#define DGPE_MIXED 1  /* complex64 psi; FFT, phase and CN in FP32; norm/mu/E sums in FP64 */
+/* complex64 psi; FFT, phase and CN in FP32; the norm sums FP64-class (FP32 terms, exact weights,
+ * double-float sums per point, FP64 across blocks), mu/E sums in FP64.  In real time every
+ * step restores the norm the real-time run began with (the norm of the state its first step
+ * started from), undoing the drift of the FP32-rounded Crank-Nicolson factors (about 3e-7
+ * of the norm per step, systematic); the exact scheme conserves the norm, so this corrects
+ * rounding only.  dgpe_grad_z2 runs its trajectory without it. */
+#define DGPE_MIXED 1
 /* Double-float: every value is a pair of FP32 numbers hi + lo (about 48 significant bits)
  * and every operation runs on the FP32 pipe, which GB300 issues 64 times as fast as FP64.
  * The caller sees complex128 (dgpe_set_psi/dgpe_get_psi convert at the boundary) and FP64
@@ -246,17 +252,22 @@ int dgpe_grad_z2(dgpe_ctx *ctx, int nseg, int steps_per_seg, const double *nu_z,
 
 /* ---- Batching and launch-shape tuning -----------------------------------------------
  * Many independent condensates (different shapes and parameters) advanced together: one
- * CUDA graph holds every context's step kernels as parallel branches, so small grids that
- * cannot fill the GPU alone run concurrently.  The paper runs one condensate per program;
- * this serves many small independent ones (parameter scans). */
+ * CUDA graph holds every context's steps as parallel branches, so small grids that cannot
+ * fill the GPU alone run concurrently.  The paper runs one condensate per program; this
+ * serves many small independent ones (parameter scans). */
 typedef struct dgpe_batch dgpe_batch;
 
 /* n >= 1 distinct contexts on the current device; they must outlive the batch.  The batch
  * launches on cuda_stream; do not enqueue work on a context's own stream while a batch step
  * may still run (synchronise first).  (No paper counterpart: see above.) */
 int dgpe_batch_create(dgpe_ctx *const *ctxs, int n, void *cuda_stream, dgpe_batch **out);
-/* nsteps SSCN steps of every context (one graph launch per step; the graph is rebuilt
- * when a context's step changed through dgpe_set_params or tuning).  Asynchronous.
+/* nsteps SSCN steps of every context, as one graph launch: each context's nsteps steps form
+ * one chain of kernels (a branch of the graph), and the branches are joined once, at the
+ * end, so no context waits for another between steps.  A graph holds at most 2^18 kernel
+ * nodes; a longer run launches several graphs of equal length (and one shorter).  Graphs
+ * are built at the first call with a given nsteps (capture and instantiation, host time
+ * that grows with nsteps x contexts), cached for up to four step counts, and rebuilt when a
+ * context's step changed through dgpe_set_params or tuning.  Asynchronous.
  * (No paper counterpart: the paper runs one condensate per program.) */
 int dgpe_batch_step(dgpe_batch *b, int nsteps);
 /* Wait for the batch stream; the first latched device error of any context.  (No paper
@@ -317,13 +328,17 @@ int dgpe_kernel_times(dgpe_ctx *ctx, dgpe_kernel_time *out, int max, int *n);
  * counter, 256 KiB) is one fixed array inside the library, of which every GPU that loads
  * the library keeps one copy until the process exits.
  *
- * psi: device memory, [nx][ny][nz] complex128 (p->precision = DGPE_FP64) or complex64
- * (DGPE_MIXED), owned by the caller.  Only p->nx, ny, nz, hx, hy, hz and precision are
- * read; the grid is x_i = (i - nx/2) hx as everywhere in this library.
- * out: device memory for 4 doubles, owned by the caller: norm = hx hy hz sum |psi|^2,
- * rms_x, rms_y, rms_z (sqrt(sum d^2 |psi|^2 / sum |psi|^2)), written in stream order.
- * Sizes: at most 2^27 = 512^3 points (the fixed scratch holds the partial sums of that
- * many); larger grids return DGPE_EUNSUPPORTED.  Bad pointers or sizes: DGPE_EINVAL.
+ * psi: device memory, [nx][ny][nz], owned by the caller: complex128 for p->precision =
+ * DGPE_FP64 or DGPE_DF64 (the double-float mode's caller format, as at dgpe_set_psi), complex64
+ * for DGPE_MIXED.  Only p->nx, ny, nz, hx, hy, hz, precision and integration are read; the
+ * grid is x_i = (i - nx/2) hx as everywhere in this library, and with DGPE_SIMPSON every sum
+ * carries the composite Simpson weights, as in dgpe_observables.
+ * out: device memory for 4 doubles, owned by the caller: norm = hx hy hz sum w |psi|^2,
+ * rms_x, rms_y, rms_z (sqrt(sum w d^2 |psi|^2 / sum w |psi|^2)), written in stream order.
+ * Sizes: each axis at most 512 (the library's grid limit; the kernel keeps the z weights
+ * in a fixed table of 512 entries and its partial sums in the fixed scratch, whatever the
+ * size); larger axes return DGPE_EUNSUPPORTED.  Bad pointers, sizes, spacings, precision
+ * or integration: DGPE_EINVAL.
  * The first call on each GPU looks up that GPU's copy of the scratch array; make that
  * first call before any stream capture.  Every call on a GPU shares the same scratch, so
  * calls whose GPU work may overlap (e.g. on unordered streams) race and give wrong

@@ -9,6 +9,8 @@
 #include <string.h>
 
 #include <new>
+#include <algorithm>
+#include <map>
 #include <vector>
 
 #include "dgpe.h"
@@ -259,6 +261,9 @@ struct dgpe_ctx {
   int latched;
   int plan_style[3];
   unsigned generation;   // bumped whenever the captured step would change (batches rebuild)
+  // real time, FP32-mixed: every step restores the norm the real-time run began with (off
+  // during dgpe_grad_z2, whose adjoint differentiates the plain step)
+  bool restore_norm;
   // dgpe_step_host: a second psi buffer (successive states alternate between the two, each
   // with its own captured step), the output staging of double-float, one copy stream each
   // way, and their events
@@ -277,7 +282,7 @@ struct dgpe_batch {
   cudaStream_t cap = nullptr;
   std::vector<cudaStream_t> branches;
   std::vector<cudaEvent_t> events;
-  cudaGraphExec_t graph = nullptr;
+  std::map<int, cudaGraphExec_t> graphs;   // steps per branch -> instantiated graph
 };
 
 namespace {
@@ -353,7 +358,8 @@ int enqueue_step(dgpe_ctx *c, cudaStream_t st) {
   if ((rc = enqueue_potential_transforms(c, st))) return rc;
   if ((rc = launch(c, st, kK5C2RzPhaseCnz, [&] { return ks->k5(a, kZStep, st); }))) return rc;
   if ((rc = launch(c, st, kK6CnY, [&] { return ks->k6(a, st); }))) return rc;
-  if ((rc = launch(c, st, kK7CnXReduce, [&] { return ks->k7(a, 1, a.imag, st); }))) return rc;
+  const int renorm = a.imag ? kRenormUnit : (c->restore_norm ? kRenormRestore : kRenormNone);
+  if ((rc = launch(c, st, kK7CnXReduce, [&] { return ks->k7(a, 1, renorm, st); }))) return rc;
   return DGPE_OK;
 }
 
@@ -616,6 +622,7 @@ int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out) {
   dgpe_ctx *c = new (std::nothrow) dgpe_ctx();
   if (!c) return DGPE_ENOMEM;
   c->p = *p;
+  c->restore_norm = p->precision == DGPE_MIXED;
   c->ks = kernel_set(p->precision);
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->args = base_args(p);
@@ -875,6 +882,16 @@ int dgpe_grad_z2(dgpe_ctx *c, int nseg, int steps_per_seg, const double *nu_z, v
     if (rc == DGPE_OK) rc = r;
     return rc == DGPE_OK;
   };
+  // the adjoint differentiates the plain step: no norm restoration (FP32-mixed) while the
+  // trajectory runs, so that every checkpoint and recomputed state is the state itself
+  const bool restore = c->restore_norm;
+  auto set_restore = [&](bool on) {
+    if (c->restore_norm == on) return;
+    c->restore_norm = on;
+    c->graph_valid = c->graph_alt_valid = false;
+    ++c->generation;
+  };
+  set_restore(false);
   // absorb a pending renormalisation so that every checkpoint is the state itself
   chk(launch(c, st, kKMaterialize, [&] { return c->ks->materialize(c->args, st); }));
   chk(map_cuda(cudaMemsetAsync(c->args.state->grads, 0, 4 * sizeof(double), st)));
@@ -918,6 +935,7 @@ int dgpe_grad_z2(dgpe_ctx *c, int nseg, int steps_per_seg, const double *nu_z, v
   chk(map_cuda(cudaMemcpyAsync(gr, c->args.state->grads, sizeof(gr), cudaMemcpyDeviceToHost, st)));
   chk(map_cuda(cudaMemcpyAsync(dnu, dnu_dev, (size_t)nseg * sizeof(double), cudaMemcpyDeviceToHost, st)));
   chk(map_cuda(cudaStreamSynchronize(st)));
+  set_restore(restore);
   if (rc) return rc;
   *dg = gr[0];
   *dgdd = gr[1];
@@ -1072,15 +1090,27 @@ int dgpe_batch_create(dgpe_ctx *const *ctxs, int n, void *cuda_stream, dgpe_batc
   return DGPE_OK;
 }
 
-// One graph: a fork from the capture stream to one branch per context, each branch the
-// context's seven step kernels, then a join.  Independent branches run concurrently.
-static int batch_build(dgpe_batch *b) {
-  bool stale = b->graph == nullptr;
+// Kernel nodes of one batch graph at most; a longer run launches several graphs.
+constexpr long long kBatchMaxNodes = 1LL << 18;
+constexpr size_t kBatchMaxGraphs = 4;   // cached step counts per batch
+
+static void batch_drop_graphs(dgpe_batch *b) {
+  for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+// The graph of `steps` steps of every context: a fork from the capture stream to one
+// branch per context, each branch that context's step kernels `steps` times in a row, then
+// one join.  The branches are independent chains, so a small grid's steps never wait for a
+// large grid's; the GPU interleaves the chains' kernels.
+static int batch_graph(dgpe_batch *b, int steps, cudaGraphExec_t *out) {
+  bool stale = false;
   for (size_t i = 0; i < b->ctxs.size(); ++i) stale = stale || b->gens[i] != b->ctxs[i]->generation;
-  if (!stale) return DGPE_OK;
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
+  if (stale || b->graphs.size() >= kBatchMaxGraphs) batch_drop_graphs(b);
+  const auto it = b->graphs.find(steps);
+  if (it != b->graphs.end()) {
+    *out = it->second;
+    return DGPE_OK;
   }
   const int n = (int)b->ctxs.size();
   std::vector<char> timing(n);
@@ -1092,7 +1122,7 @@ static int batch_build(dgpe_batch *b) {
   if (!rc) rc = map_cuda(cudaEventRecord(b->events[n], b->cap));
   for (int i = 0; i < n && !rc; ++i) {
     rc = map_cuda(cudaStreamWaitEvent(b->branches[i], b->events[n], 0));
-    if (!rc) rc = enqueue_step(b->ctxs[i], b->branches[i]);
+    for (int s = 0; s < steps && !rc; ++s) rc = enqueue_step(b->ctxs[i], b->branches[i]);
     if (!rc) rc = map_cuda(cudaEventRecord(b->events[i], b->branches[i]));
     if (!rc) rc = map_cuda(cudaStreamWaitEvent(b->cap, b->events[i], 0));
   }
@@ -1100,22 +1130,31 @@ static int batch_build(dgpe_batch *b) {
   const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
   for (int i = 0; i < n; ++i) b->ctxs[i]->timing = timing[i];
   if (!rc) rc = map_cuda(e);
-  if (!rc) rc = map_cuda(cudaGraphInstantiate(&b->graph, g, 0));
+  cudaGraphExec_t exec = nullptr;
+  if (!rc) rc = map_cuda(cudaGraphInstantiate(&exec, g, 0));
   if (g) cudaGraphDestroy(g);
-  if (rc) {
-    b->graph = nullptr;
-    return rc;
-  }
+  if (rc) return rc;
+  b->graphs[steps] = exec;
   for (int i = 0; i < n; ++i) b->gens[i] = b->ctxs[i]->generation;
+  *out = exec;
   return DGPE_OK;
 }
 
 int dgpe_batch_step(dgpe_batch *b, int nsteps) {
   if (!b || nsteps < 0) return DGPE_EINVAL;
   if (nsteps == 0) return DGPE_OK;
-  int rc = batch_build(b);
+  long long per_step = 0;   // kernel nodes of one step of every context
+  for (dgpe_ctx *c : b->ctxs) per_step += 6 + c->ks->k5_launches;
+  const int per_graph = (int)std::max<long long>(1, std::min<long long>(nsteps, kBatchMaxNodes / per_step));
+  int rc = DGPE_OK;
   for (size_t i = 0; i < b->ctxs.size() && !rc; ++i) rc = wait_host_output(b->ctxs[i], b->stream);
-  for (int s = 0; s < nsteps && !rc; ++s) rc = map_cuda(cudaGraphLaunch(b->graph, b->stream));
+  for (int done = 0; done < nsteps && !rc;) {
+    const int k = std::min(per_graph, nsteps - done);
+    cudaGraphExec_t exec = nullptr;
+    rc = batch_graph(b, k, &exec);
+    if (!rc) rc = map_cuda(cudaGraphLaunch(exec, b->stream));
+    done += k;
+  }
   return rc;
 }
 
@@ -1129,7 +1168,7 @@ int dgpe_batch_sync(dgpe_batch *b) {
 void dgpe_batch_destroy(dgpe_batch *b) {
   if (!b) return;
   if (b->stream || b->cap) cudaStreamSynchronize(b->stream);
-  if (b->graph) cudaGraphExecDestroy(b->graph);
+  batch_drop_graphs(b);
   for (cudaEvent_t e : b->events)
     if (e) cudaEventDestroy(e);
   for (cudaStream_t st : b->branches)
@@ -1201,8 +1240,9 @@ int dgpe_step_host(dgpe_ctx *c, const void *in, void *out, int nsteps) {
   c->latched = DGPE_OK;
   rc = dgpe_step(c, nsteps);
   if (rc) return rc;
-  // the pending renormalisation (imaginary time only: real-time steps leave s = 1)
-  if (c->p.mode == DGPE_IMAG_TIME)
+  // the pending scale (imaginary time; real time where the mixed path restores the norm:
+  // FP64 and double-float real-time steps leave s = 1)
+  if (c->p.mode == DGPE_IMAG_TIME || c->restore_norm)
     rc = launch(c, c->stream, kKMaterialize, [&] { return c->ks->materialize(c->args, c->stream); });
   const void *src = buf[tgt];
   if (!rc && c->p.precision == DGPE_DF64) {

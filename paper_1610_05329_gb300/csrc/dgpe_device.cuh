@@ -201,12 +201,27 @@ __device__ __forceinline__ void sin_cos(double x, double *s, double *c) {
     default: *s = -cr; *c = sr; break;
   }
 }
-// FP32 sine and cosine by the same method: r = x - k pi/2 with k = rint(2x/pi) taken from
+// FP32 sine and cosine by the same method (a short Taylor branch for |x| <= 1/4, then):
+// r = x - k pi/2 with k = rint(2x/pi) taken from
 // the low bits of the FP32 sum 2x/pi + 1.5 * 2^23 (no conversion instruction), pi/2 split
 // into three floats and subtracted by FMAs; Taylor series through r^9 (sine) and r^10
 // (cosine) on |r| <= pi/4, first omitted terms below 2e-9.  |x| >= 2^16 and non-finite x
 // go to the general routine.
 __device__ __forceinline__ void sin_cos(float x, float *s, float *c) {
+  if (fabsf(x) <= 0.25f) {
+    // short angles (nearly every point of the phase step): Taylor series through x^7 and
+    // x^6, first omitted terms below 1.1e-11 and 3.8e-10 at |x| = 1/4, no reduction
+    const float u = x * x;
+    float ps = -1.9841269841269841e-4f;
+    ps = fmaf(ps, u, 8.3333333333333333e-3f);
+    ps = fmaf(ps, u, -0.16666666666666666f);
+    *s = fmaf(x * u, ps, x);
+    float pc = -1.3888888888888889e-3f;
+    pc = fmaf(pc, u, 4.1666666666666667e-2f);
+    pc = fmaf(pc, u, -0.5f);
+    *c = fmaf(u, pc, 1.0f);
+    return;
+  }
   if (!(fabsf(x) < 65536.0f)) {
     sincosf(x, s, c);
     return;
@@ -346,6 +361,17 @@ struct DFAcc {
     const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(v, bp));
     hi = t;
     lo = __fadd_rn(lo, err);
+  }
+  // a v for an FP32 a, exactly: the product p = fl(a v) and its error fma(a, v, -p)
+  __device__ __forceinline__ void add_prod(float a, float v) {
+    const float p = __fmul_rn(a, v);
+    add(p);
+    lo = __fadd_rn(lo, fmaf(a, v, -p));
+  }
+  // a (x.hi + x.lo) for an FP32 a
+  __device__ __forceinline__ void add_scaled(float a, const DFAcc &x) {
+    add_prod(a, x.hi);
+    lo = fmaf(a, x.lo, lo);
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
@@ -948,6 +974,15 @@ __device__ __forceinline__ double quad_weight(int i, int n, int simpson) {
   return (i & 1) ? 4.0 / 3.0 : 2.0 / 3.0;
 }
 
+// 3 x the quadrature weight: 1 (rectangle rule: the factor 3 is not applied), or Simpson's
+// 1, 4, 2, ..., 4, 1 and 0 on the last point, all exact small integers.
+__device__ __forceinline__ int quad_weight3(int i, int n, int simpson) {
+  if (!simpson) return 1;
+  if (i > n - 2) return 0;
+  if (i == 0 || i == n - 2) return 1;
+  return (i & 1) ? 4 : 2;
+}
+
 template <typename R>
 __device__ __forceinline__ R quad_weight_r(int i, int n, int simpson) {
   if (!simpson) return R(1);
@@ -1174,6 +1209,8 @@ __global__ void k_reset_state(DevState *st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     set_scale(st, 1.0);
     st->norm = 0.0;
+    st->norm_in = 0.0;
+    st->norm_ref = 0.0;
     st->flags = 0u;
     st->ticket = 0u;
     st->steps = 0ull;
@@ -1352,6 +1389,152 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Register-resident transforms (FP32) of lines of N = 64 Q points (Q = 2, 4 or 8) with
+// T = N/8 threads per line: thread t holds elements t + T r (r = 0..7) of its line before
+// and after the transform.  Three Stockham stages of the default plan (radix 8, 8, Q): the
+// first and the last in registers, two exchanges through shared memory between them.  The
+// callers load the registers straight from global memory and store them straight back
+// (consecutive t on consecutive lanes: coalesced), so a transform costs two shared-memory
+// round trips instead of a staging copy and one round trip per stage; and a forward
+// transform leaves its output in the layout the inverse transform's input needs.
+// Stage 1 (ns = 1):  butterfly t on x[t + T r]             -> y[8 t + s]
+// Stage 2 (ns = 8):  butterfly t on y[t + T r], k = t mod 8 -> z[8 (t - k) + k + 8 s]
+// Stage 3 (ns = 64): butterflies j = t + T u (u < 8/Q) on z[j + 64 r], k = j -> o[j + 64 s]
+//                    = o[t + T (u + (8/Q) s)]
+// Shared memory: element i of a line at pad(i) * LS (+ the caller's column offset),
+// pad(i) = i + i/8.  With LS = 1 (one line per buffer) or LS = 8 (eight columns
+// interleaved, lanes spanning the columns), every access above is free of bank conflicts
+// within a half-warp.
+// ---------------------------------------------------------------------------------------
+template <int N>
+struct RegFft {
+  static_assert(N == 128 || N == 256 || N == 512, "N = 64 Q, Q = 2, 4 or 8");
+  static constexpr int Q = N / 64;
+  static constexpr int T = N / 8;
+  static constexpr int SLOTS = N + N / 8;
+  __device__ static __forceinline__ int pad(int i) { return i + (i >> 3); }
+};
+
+template <int DIR>
+__device__ __forceinline__ cplx<float> twiddle(cplx<float> v, cplx<float> w) {
+  return DIR < 0 ? v * w : mul_conj(v, w);
+}
+
+// One transform of the registers v (see RegFft).  sa, sb: this line's two shared buffers
+// (element i at pad(i) * LS); tw: the per-stage twiddle table of the default plan of length
+// N (stage 2 at offset 7, stage 3 at offset 63); sync: the barrier that spans the threads
+// of the line (and of every line that shares them).
+template <int DIR, int N, int LS, typename Sync>
+__device__ __forceinline__ void reg_fft(cplx<float> (&v)[8], cplx<float> *__restrict__ sa, cplx<float> *__restrict__ sb,
+                                        int t, const cplx<float> *__restrict__ tw, Sync sync) {
+  using F = RegFft<N>;
+  using C = cplx<float>;
+  constexpr int T = F::T, Q = F::Q, U = 8 / Q;
+  butterfly<float, DIR, 8>(v);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) sa[F::pad(8 * t + s) * LS] = v[s];
+  sync();
+  {
+    const int k = t & 7;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = sa[F::pad(t + T * r) * LS];
+#pragma unroll
+    for (int r = 1; r < 8; ++r) v[r] = twiddle<DIR>(v[r], ldg(tw + 7 + k * 7 + r - 1));
+    butterfly<float, DIR, 8>(v);
+    const int base = 8 * (t - k) + k;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) sb[F::pad(base + 8 * s) * LS] = v[s];
+  }
+  sync();
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int j = t + T * u;
+    C w[Q];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) w[r] = sb[F::pad(j + 64 * r) * LS];
+#pragma unroll
+    for (int r = 1; r < Q; ++r) w[r] = twiddle<DIR>(w[r], ldg(tw + 63 + j * (Q - 1) + r - 1));
+    butterfly<float, DIR, Q>(w);
+#pragma unroll
+    for (int s = 0; s < Q; ++s) v[u + U * s] = w[s];
+  }
+}
+
+// K2 / K4 in FP32 for ny = 128, 256 or 512 with the default plan: 256 / T lines per CTA,
+// each line's registers loaded from and stored to global memory directly.
+template <int DIR, int N>
+__global__ void __launch_bounds__(256, 4) k_ffty_reg(KArgs a) {
+  using C = cplx<float>;
+  using F = RegFft<N>;
+  constexpr int T = F::T, LPC = 256 / T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int l = threadIdx.x / T, t = threadIdx.x % T;
+  const size_t line = (size_t)blockIdx.x * LPC + l;
+  const bool active = line < (size_t)a.nzh * a.nx;
+  C *sa = reinterpret_cast<C *>(smem_raw) + (size_t)l * 2 * F::SLOTS;
+  C *g = reinterpret_cast<C *>(a.spec) + (active ? line : 0) * N;
+  C v[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r] = active ? g[t + T * r] : czero<float>();
+  auto sync = [] {
+    if constexpr (T > kWarp) __syncthreads();
+    else __syncwarp();
+  };
+  reg_fft<DIR, N, 1>(v, sa, sa + F::SLOTS, t, reinterpret_cast<const C *>(a.tw[1]), sync);
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) g[t + T * r] = v[r];
+  }
+}
+
+// K3 in FP32 for nx = 128, 256 or 512 with the default plan: the forward transform along x,
+// the product with Ut(k) in registers (each thread's outputs are exactly its inputs of the
+// inverse transform), the inverse transform; 8 consecutive ky columns per CTA, the lanes of
+// a warp spanning them (64-byte rows), the columns interleaved in shared memory.
+template <int N>
+__global__ void __launch_bounds__(8 * RegFft<N>::T, 1024 / (8 * RegFft<N>::T)) k3_reg(KArgs a) {
+  using C = cplx<float>;
+  using F = RegFft<N>;
+  constexpr int T = F::T, B = 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = threadIdx.x % B, t = threadIdx.x / B;
+  const int m = blockIdx.y, j0 = blockIdx.x * B;
+  const int jy = j0 + b;
+  const bool active = jy < a.ny;
+  C *sa = reinterpret_cast<C *>(smem_raw) + b;
+  C *sb = sa + (size_t)B * F::SLOTS;
+  C *g = reinterpret_cast<C *>(a.spec) + (size_t)m * a.nx * a.ny + (active ? jy : 0);
+  const size_t sx = (size_t)a.ny;
+  C v[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r] = active ? g[(size_t)(t + T * r) * sx] : czero<float>();
+  const C *tw = reinterpret_cast<const C *>(a.tw[0]);
+  auto sync = [] { __syncthreads(); };
+  reg_fft<-1, N, B>(v, sa, sb, t, tw, sync);
+  // Ut(k) = 3 kz^2 / |k|^2 - 1 (Ut(0) = 0) at kx index t + T q, k_d = q_d 2 pi / (n_d h_d)
+  {
+    const float fx = a.kf[0], fy = a.kf[1], fz = a.kf[2];
+    const float ky = (float)(jy <= a.ny / 2 ? jy : jy - a.ny) * fy, kz = (float)m * fz;
+    const float kz2 = kz * kz, kyz2 = fmaf(ky, ky, kz2);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = t + T * q;
+      const float kx = (float)(i <= N / 2 ? i : i - N) * fx;
+      const float k2 = fmaf(kx, kx, kyz2);
+      float u = k2 > 0.0f ? __fdividef(3.0f * kz2, k2) - 1.0f : 0.0f;
+      if (a.has_cutoff && k2 > 0.0f) u *= cutoff_factor<float>(sqrtf(k2) * a.cutoff_f);
+      v[q] = scale(v[q], u);
+    }
+  }
+  __syncthreads();   // the inverse transform's first exchange reuses sa
+  reg_fft<+1, N, B>(v, sa, sb, t, tw, sync);
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) g[(size_t)(t + T * r) * sx] = v[r];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // K5: the z-line kernel.  For kZLines lines (i, j0..): inverse half-spectrum transform
 // along z (C2R, two real lines per complex FFT; the imaginary parts of the kz = 0 and
 // kz = nz/2 bins are dropped), Phi = result / (nx ny nz); then, per zmode, the potential
@@ -1395,6 +1578,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads,
     for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next())
       cp_async(tile + pos.b * LS + cn_slot(pos.k, lc), psi + e);
   }
+  cp_async_commit();
 
   if (zmode != kZCnOnly) {
     const C *spec = reinterpret_cast<const C *>(a.spec) + line0;
@@ -1432,6 +1616,26 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads,
                                                              reinterpret_cast<const C *>(a.tw[2]));
   }
 
+  // the CN-z factor tables (alpha, beta, H, G; 4 * 32 * chunk values), staged into the
+  // transform buffer that does not hold the result: they arrive during the phase loop, and
+  // the solve reads them from shared memory.  They take 128 chunk sizeof(Coef) bytes, the
+  // buffer nz PZ sizeof(C): with chunk the least power of two >= max(2, (nz - 2)/32) they fit
+  // for the compile-time lengths (256 to 512); the runtime-length instance reads them from
+  // global memory.
+  const Coef *ztab = reinterpret_cast<const Coef *>(a.cn[2].tab);
+  if constexpr (N > 0) {
+    static_assert(N >= 64, "the staged tables fit the spare transform buffer");
+    if (zmode == kZStep || zmode == kZCnOnly) {
+      C *spare = (zmode == kZCnOnly || res != za) ? za : zb;
+      const int bytes = 4 * (kWarp << lc) * (int)sizeof(Coef);
+      const uint4 *src = reinterpret_cast<const uint4 *>(a.cn[2].tab);
+      uint4 *dst = reinterpret_cast<uint4 *>(spare);
+      for (int q = threadIdx.x; q < bytes / 16; q += blockDim.x) cp_async(dst + q, src + q);
+      ztab = reinterpret_cast<const Coef *>(spare);
+    }
+  }
+  cp_async_commit();
+
   if (zmode == kZPhi) {
     // Phi in the kernel precision; double for double-float
     using O = typename std::conditional<std::is_same<R, df>::value, double, R>::type;
@@ -1443,12 +1647,15 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads,
     }
     return;
   }
-  cp_async_wait_all();
+  cp_async_wait_group<1>();   // the psi tile (the tables may still be in flight)
   __syncthreads();
 
   if (zmode == kZObs) {
+    // the sums are taken over the stored values; the pending scale enters in FP64 at the end
+    // (s^2 for the quadratic sums, s^4 for the contact term; Phi already carries s^2 through
+    // K1's density), so FP32 data are not rounded again by the scaling
     double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const R sr = R(s);
+    const R sr = R(1);
     const double x = coordinate(i, a.nx, a.hx);
     const double wxi = quad_weight(i, a.nx, a.simpson);
     const R ihx2 = R(1.0 / (a.hx * a.hx)), ihy2 = R(1.0 / (a.hy * a.hy)), ihz2 = R(1.0 / (a.hz * a.hz));
@@ -1507,6 +1714,8 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads,
     if (reduce_across_blocks<8>(v, a.partials, &a.state->ticket) && threadIdx.x == 0) {
       const double dv = a.hx * a.hy * a.hz;
       DevState *st = a.state;
+      const double s2 = st->s * st->s;
+      for (int q = 0; q < 8; ++q) v[q] *= q == 3 ? s2 * s2 : s2;
       for (int q = 0; q < 8; ++q) st->sums[q] = v[q];
       const double norm = dv * v[0];
       const double ekin = dv * v[1], etrap = dv * v[2], econ = 0.5 * dv * v[3], edd = 0.5 * dv * v[4];
@@ -1565,10 +1774,11 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads,
   }
 
   if (zmode == kZStep || zmode == kZCnOnly) {
+    cp_async_wait_group<0>();
+    __syncthreads();
     const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[2], a.cn_rf[2], a.cn_rl[2]));
-    const Coef *tab = reinterpret_cast<const Coef *>(a.cn[2].tab);
     for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp)
-      cn_line_any<R, Coef, false>(tile + b * LS, 1, a.cn[2].m, lc, tab, scan_s, c);
+      cn_line_any<R, Coef, (N > 0)>(tile + b * LS, 1, a.cn[2].m, lc, ztab, scan_s, c);
     __syncthreads();
   }
 
@@ -1580,13 +1790,18 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads,
 // ---------------------------------------------------------------------------------------
 // K6 / K7: Crank-Nicolson along y (AXIS = 1, lines psi[i][:][k]) or x (AXIS = 0, lines
 // psi[:][j][k]) for kCnCols consecutive k per CTA (one warp per line).  K7 (x) also sums
-// n, x^2 n, y^2 n, z^2 n (FP64 totals; per-thread sums in FP64 for FP64 data; for FP32
-// data, FP32 sums over the points of one tile column, accumulated across tiles in
-// double-float) and, in the last block, sets the norm and the pending
-// renormalisation factor s = 1/sqrt(norm) (imaginary time) or 1 (real time).
+// n, x^2 n, y^2 n, z^2 n (FP64 totals) and, in the last block, sets the norm and the pending
+// renormalisation factor s = 1/sqrt(norm) (imaginary time) or 1 (real time).  The x^2 n
+// sum is not taken (nothing reads it: the observables take their own FP64 sums).  FP64
+// data: FP64 sums per thread.  FP32 data (k_cn): the terms n = |psi|^2 in FP32 (the state's
+// own precision), and from there every product exact and every sum in double-float, point
+// by point (error about 2^-44 of the total): the weights are exact small integers (3 x the
+// Simpson weights per axis, the squared signed index instead of the squared coordinate),
+// the products by them exact (FMA exact product), the sums Knuth's TwoSum; the factors
+// h_d^2 and (1/3)^3 (Simpson) are applied in FP64 at the end.
 // ---------------------------------------------------------------------------------------
-// Running sums of the reduction: FP64 for FP64 data; for FP32 data, double-float (FP32
-// instructions only), fed once per tile column with that column's FP32 partial sums.
+// Running sums of the reduction of the FP64-class per-line sweeps: FP64 for FP64 data,
+// double-float pairs for double-float data.
 template <typename R>
 struct SumAcc;
 template <>
@@ -1596,8 +1811,6 @@ struct SumAcc<double> {
   __device__ __forceinline__ double value() const { return v; }
 };
 template <>
-struct SumAcc<float> : DFAcc {};
-template <>
 struct SumAcc<df> {
   df v{0.0f, 0.0f};
   __device__ __forceinline__ void add(df t) { v = v + t; }
@@ -1605,7 +1818,13 @@ struct SumAcc<df> {
 };
 
 // Block sums of n, x^2 n, y^2 n, z^2 n -> across blocks; the last block sets the norm and
-// the pending renormalisation factor s.
+// the pending scale s of the state.  renorm: kRenormNone (real time: s = 1), kRenormUnit
+// (imaginary time: s = 1/sqrt(norm)), kRenormRestore (real time, FP32-mixed: s restores the
+// norm the state had when the real-time run began, the true norm of the state the first
+// real-time step started from, or its own output's norm if that is unknown).  The exact
+// real-time step conserves the norm; the FP32-rounded Crank-Nicolson factor tables make
+// each sweep non-unitary by about 1e-7 (the same rounding at every point of a line, so it
+// adds up instead of averaging out), and this undoes that drift from the FP64-class sum.
 __device__ __forceinline__ void finish_sweep_sums(const KArgs &a, double (&v)[4], int renorm) {
   if (reduce_across_blocks<4>(v, a.partials, &a.state->ticket) && threadIdx.x == 0) {
     DevState *st = a.state;
@@ -1614,9 +1833,18 @@ __device__ __forceinline__ void finish_sweep_sums(const KArgs &a, double (&v)[4]
     st->norm = norm;
     // a zero state is a state (real time keeps it zero); only the renormalisation of
     // imaginary time needs a positive norm
-    const bool ok = isfinite(norm) && (norm > 0.0 || !renorm);
+    const bool ok = isfinite(norm) && (norm > 0.0 || renorm != kRenormUnit);
     if (!ok) st->flags |= kFlagNonFinite;
-    set_scale(st, (renorm && ok) ? 1.0 / sqrt(norm) : 1.0);
+    double s = 1.0;
+    if (renorm == kRenormUnit) {
+      if (ok) s = 1.0 / sqrt(norm);
+      st->norm_ref = 0.0;   // a later real-time run takes its own reference
+    } else if (renorm == kRenormRestore && ok && norm > 0.0) {
+      if (!(st->norm_ref > 0.0)) st->norm_ref = st->norm_in > 0.0 ? st->norm_in : norm;
+      s = sqrt(st->norm_ref / norm);
+    }
+    set_scale(st, s);
+    st->norm_in = norm * s * s;
     st->steps += 1ull;
   }
 }
@@ -1626,7 +1854,8 @@ __device__ __forceinline__ void finish_sweep_sums(const KArgs &a, double (&v)[4]
 // flight while the current tile is solved and stored.
 // B columns (z) per tile, NT threads (B divides NT; one or two lines per warp).
 template <typename R, typename Coef, int AXIS, int B = Tiles<R>::kCnCols, int NT = Tiles<R>::kCnThreads>
-__global__ void __launch_bounds__(NT) k_cn(KArgs a, int reduce, int renorm) {
+__global__ void __launch_bounds__(NT, 512 / NT) k_cn(KArgs a, int reduce, int renorm) {
+  static_assert(std::is_same<R, float>::value, "the chunked sweeps serve FP32 data");
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int SB = B + 1;
@@ -1640,8 +1869,7 @@ __global__ void __launch_bounds__(NT) k_cn(KArgs a, int reduce, int renorm) {
   C *nxt = cur + slots * SB;
   Coef *stab = reinterpret_cast<Coef *>(nxt + slots * SB);     // factor tables, staged once
   const int ntab = 4 * (kWarp << lc) + 10 * kWarp;
-  R *x2tab = reinterpret_cast<R *>(stab + ntab);
-  R *wxtab = x2tab + N;                                         // quadrature weights along x
+  float *wxtab = reinterpret_cast<float *>(stab + ntab);        // W_x(i) = 3 x the weight (or 1)
   const size_t stride = AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
   C *gpsi = reinterpret_cast<C *>(a.psi);
   const int b = threadIdx.x % B;   // B divides the block size: the column is fixed per thread
@@ -1665,9 +1893,7 @@ __global__ void __launch_bounds__(NT) k_cn(KArgs a, int reduce, int renorm) {
 
   if (do_reduce)
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
-      const double x = coordinate(n, a.nx, a.hx);
-      x2tab[n] = R(x * x);
-      wxtab[n] = R(quad_weight(n, a.nx, a.simpson));
+      wxtab[n] = (float)quad_weight3(n, a.nx, a.simpson);
     }
   const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[AXIS], a.cn_rf[AXIS], a.cn_rl[AXIS]));
   {
@@ -1675,8 +1901,7 @@ __global__ void __launch_bounds__(NT) k_cn(KArgs a, int reduce, int renorm) {
     for (int q = threadIdx.x; q < ntab; q += blockDim.x) stab[q] = gtab[q];
   }
   const Coef *tab = stab;
-  SumAcc<R> acc[4];
-  const R hy = R(a.hy), hz = R(a.hz);
+  DFAcc acc[4];
 
   int tile = blockIdx.x;
   if (tile < ntiles) issue(tile, cur);
@@ -1696,27 +1921,24 @@ __global__ void __launch_bounds__(NT) k_cn(KArgs a, int reduce, int renorm) {
       cn_line_any<R, Coef, true>(cur + l, SB, a.cn[AXIS].m, lc, tab, tab + 4 * (kWarp << lc), c);
     __syncthreads();
     if (b < nb) {
-      R s0 = R(0), sx = R(0);   // this column's partial sums of n and x^2 n
+      DFAcc s0;   // this thread's share of the column: sum W_x n
       C *dst = gpsi + base + b + (size_t)n0 * stride;
 #pragma unroll 4
       for (int n = n0; n < N; n += nstep, dst += nstep * stride) {
         const C w = cur[cn_slot(n, lc) * SB + b];
         *dst = w;
         if (do_reduce) {
-          R d = w.re * w.re + w.im * w.im;
-          if (a.simpson) d *= wxtab[n];
-          s0 += d;
-          sx = fma(x2tab[n], d, sx);
+          const float d = fmaf(w.re, w.re, w.im * w.im);
+          s0.add(wxtab[n] * d);       // exact: W_x is 0, 1, 2 or 4
         }
       }
       if (do_reduce) {
-        const R wyz = quad_weight_r<R>(fixed, a.ny, a.simpson) * quad_weight_r<R>(k0 + b, a.nz, a.simpson);
-        const R y = R(fixed - a.ny / 2) * hy, z = R(k0 + b - a.nz / 2) * hz;
-        const R t = wyz * s0;
-        acc[0].add(t);
-        acc[1].add(wyz * sx);
-        acc[2].add(y * y * t);
-        acc[3].add(z * z * t);
+        // W_y W_z is 0 or a power of two up to 16; j'^2 W_y W_z <= 2^20: exact floats
+        const int jj = fixed - a.ny / 2, kk = k0 + b - a.nz / 2;
+        const int wyz = quad_weight3(fixed, a.ny, a.simpson) * quad_weight3(k0 + b, a.nz, a.simpson);
+        acc[0].add_scaled((float)wyz, s0);
+        acc[2].add_scaled((float)(jj * jj * wyz), s0);
+        acc[3].add_scaled((float)(kk * kk * wyz), s0);
       }
     }
     __syncthreads();   // `cur` is refilled by the prefetch two tiles ahead
@@ -1725,7 +1947,8 @@ __global__ void __launch_bounds__(NT) k_cn(KArgs a, int reduce, int renorm) {
     nxt = t;
   }
   if (do_reduce) {
-    double v[4] = {acc[0].value(), acc[1].value(), acc[2].value(), acc[3].value()};
+    const double w = a.simpson ? 1.0 / 27.0 : 1.0;   // (1/3)^3 of the integer Simpson weights
+    double v[4] = {acc[0].value() * w, 0.0, acc[2].value() * (w * a.hy * a.hy), acc[3].value() * (w * a.hz * a.hz)};
     finish_sweep_sums(a, v, renorm);
   }
 }
@@ -1760,14 +1983,9 @@ __global__ void __launch_bounds__(128, 7) k_cn_twisted(KArgs a, int reduce, int 
   const long long line = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kWarp * (kWarp / 2) + (lane & 15);
   const bool active = line < nlines;
   const bool do_reduce = AXIS == 0 && reduce;
-  R *x2tab = reinterpret_cast<R *>(smem_raw);
-  R *wxtab = x2tab + N;
+  R *wxtab = reinterpret_cast<R *>(smem_raw);   // quadrature weights along x
   if (do_reduce) {
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-      const double x = coordinate(n, a.nx, a.hx);
-      x2tab[n] = R(x * x);
-      wxtab[n] = R(quad_weight(n, a.nx, a.simpson));
-    }
+    for (int n = threadIdx.x; n < N; n += blockDim.x) wxtab[n] = R(quad_weight(n, a.nx, a.simpson));
     __syncthreads();
   }
   SumAcc<R> acc[4];
@@ -1817,14 +2035,13 @@ __global__ void __launch_bounds__(128, 7) k_cn_twisted(KArgs a, int reduce, int 
   }
   const C xt = shfl_xor(xh, kWarp / 2);
   if (!bottom) xh = xt;
-  R s0 = R(0), sx = R(0);
+  R s0 = R(0);
   auto emit = [&](int i, C out) {
     p[(size_t)i * stride] = out;
     if (do_reduce) {
       R d = out.re * out.re + out.im * out.im;
       if (a.simpson) d *= wxtab[i + 1];
       s0 += d;
-      sx = fma(x2tab[i + 1], d, sx);
     }
   };
   if (bottom && active) emit(h, C{twice_minus(xh.re, ph.re), twice_minus(xh.im, ph.im)});
@@ -1884,7 +2101,6 @@ __global__ void __launch_bounds__(128, 7) k_cn_twisted(KArgs a, int reduce, int 
       const R yv = R(fixed - a.ny / 2) * R(a.hy), zv = R(k - a.nz / 2) * R(a.hz);
       const R tt = wyz * s0;
       acc[0].add(tt);
-      acc[1].add(wyz * sx);
       acc[2].add(yv * yv * tt);
       acc[3].add(zv * zv * tt);
     }
@@ -2193,6 +2409,25 @@ struct Impl {
     return e;
   }
 
+  // (a member of the class template: instantiated only where it is called, FP32)
+  static cudaError_t init_reg() {
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) {
+      if (e == cudaSuccess) e = r;
+    };
+    using K = void (*)(KArgs);
+    chk(allow_smem(static_cast<K>(k_ffty_reg<-1, 512>)));
+    chk(allow_smem(static_cast<K>(k_ffty_reg<+1, 512>)));
+    chk(allow_smem(static_cast<K>(k_ffty_reg<-1, 256>)));
+    chk(allow_smem(static_cast<K>(k_ffty_reg<+1, 256>)));
+    chk(allow_smem(static_cast<K>(k_ffty_reg<-1, 128>)));
+    chk(allow_smem(static_cast<K>(k_ffty_reg<+1, 128>)));
+    chk(allow_smem(static_cast<K>(k3_reg<512>)));
+    chk(allow_smem(static_cast<K>(k3_reg<256>)));
+    chk(allow_smem(static_cast<K>(k3_reg<128>)));
+    return e;
+  }
+
   static cudaError_t init() {
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t r) {
@@ -2242,6 +2477,7 @@ struct Impl {
       chk(allow_smem(k_cn<R, C, 0>));
       chk(allow_smem(k_cn<R, C, 1>));
     }
+    if constexpr (kRegFft) chk(init_reg());
     if constexpr (kAdjoint) chk(allow_smem(k5_adj_phase<R>));
     if constexpr (kAdjoint) chk(allow_smem(k5_adj_combine<R>));
     return e;
@@ -2326,8 +2562,28 @@ struct Impl {
   static bool y_fixed(const KArgs &a, int n) {
     return a.ylines == y_lines_per_cta<R>(n) && a.fft_threads == kFftThreads && plan_ct(a.plan[1], n);
   }
+  // the register-resident FP32 transforms (default plans of length 128, 256, 512)
+  static constexpr bool kRegFft = std::is_same<R, float>::value;
+  static constexpr size_t kRegYSmem = 2 * (256 / 64) * (size_t)RegFft<512>::SLOTS * sizeof(cplx<float>);
+  template <int N>
+  static constexpr size_t reg_x_smem() { return 2 * 8 * (size_t)RegFft<N>::SLOTS * sizeof(cplx<float>); }
+  template <int DIR, int N>
+  static void ffty_reg(const KArgs &a, cudaStream_t st) {
+    const size_t lines = (size_t)a.nzh * a.nx, lpc = 256 / RegFft<N>::T;
+    k_ffty_reg<DIR, N><<<(unsigned)((lines + lpc - 1) / lpc), 256, kRegYSmem, st>>>(a);
+  }
+  template <int N>
+  static void k3_reg_launch(const KArgs &a, cudaStream_t st) {
+    const dim3 grid((a.ny + 7) / 8, a.nzh);
+    k3_reg<N><<<grid, 8 * RegFft<N>::T, reg_x_smem<N>(), st>>>(a);
+  }
   template <int DIR>
   static cudaError_t ffty(const KArgs &a, cudaStream_t st) {
+    if constexpr (kRegFft) {
+      if (plan_ct(a.plan[1], 512)) return ffty_reg<DIR, 512>(a, st), cudaGetLastError();
+      if (plan_ct(a.plan[1], 256)) return ffty_reg<DIR, 256>(a, st), cudaGetLastError();
+      if (plan_ct(a.plan[1], 128)) return ffty_reg<DIR, 128>(a, st), cudaGetLastError();
+    }
     const size_t lines = (size_t)a.nzh * a.nx;
     const int L = a.ylines;
     const dim3 g((unsigned)((lines + L - 1) / L));
@@ -2345,6 +2601,11 @@ struct Impl {
   }
   static cudaError_t k2(const KArgs &a, cudaStream_t st) { return ffty<-1>(a, st); }
   static cudaError_t k3(const KArgs &a, cudaStream_t st) {
+    if constexpr (kRegFft) {
+      if (plan_ct(a.plan[0], 512)) return k3_reg_launch<512>(a, st), cudaGetLastError();
+      if (plan_ct(a.plan[0], 256)) return k3_reg_launch<256>(a, st), cudaGetLastError();
+      if (plan_ct(a.plan[0], 128)) return k3_reg_launch<128>(a, st), cudaGetLastError();
+    }
     dim3 grid((a.ny + T::kXCols - 1) / T::kXCols, a.nzh);
     const size_t sm = smem_x(a);
     const bool fixed = a.fft_threads == kFftThreads;
@@ -2416,7 +2677,7 @@ struct Impl {
     const int n = AXIS == 0 ? a.nx : AXIS == 1 ? a.ny : a.nz;
     if constexpr (kCnThread) {
       const long long lines = AXIS == 2 ? (long long)a.nx * a.ny : (long long)(AXIS == 0 ? a.ny : a.nx) * a.nz;
-      const size_t sm = AXIS == 0 ? 2 * (size_t)n * sizeof(R) : 0;
+      const size_t sm = AXIS == 0 ? (size_t)n * sizeof(R) : 0;
       const unsigned blocks = (unsigned)((lines + 63) / 64);   // 64 lines, two threads each
       if (a.imag) k_cn_twisted<R, R, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
       else k_cn_twisted<R, C, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);

@@ -54,7 +54,9 @@ struct DevState {
   float sf, s2f;     // s and s^2 rounded to FP32 (read by the FP32 kernels)
   float sl, s2l;     // the FP32 remainders: (sf, sl) and (s2f, s2l) are double-float pairs
   double norm;       // hx hy hz sum |psi_buf|^2 after the last full step
-  double sums[8];    // last reduction (step: n, x^2 n, y^2 n, z^2 n; obs: 8 terms)
+  double norm_in;    // the true norm (s^2 norm) of the state the next step starts from; 0: unknown
+  double norm_ref;   // the norm real-time steps restore (FP32-mixed); 0: not yet taken
+  double sums[8];    // last reduction (step: n, 0 (x^2 n is not summed), y^2 n, z^2 n; obs: 8 terms)
   double obs[12];    // observables of the last dgpe_observables call
   double grads[4];      // adjoint accumulators: dL/dg, dL/dgdd, dL/dnu_z
   unsigned int flags;   // bit 0: non-finite norm
@@ -106,6 +108,9 @@ struct KArgs {
 };
 
 // Modes of the z-line kernel (C2R along z + potential step + CN along z).
+// What the x sweep's last block does with the norm it sums (see finish_sweep_sums).
+enum RenormMode : int { kRenormNone = 0, kRenormUnit = 1, kRenormRestore = 2 };
+
 enum ZMode : int {
   kZStep = 0,        // phase, then CN-z
   kZPhaseOnly = 1,   // phase only

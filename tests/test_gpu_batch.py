@@ -92,3 +92,28 @@ def test_autotune_double_float(orc):
         c.step(6)
         assert np.linalg.norm(c.get_psi() - want) / np.linalg.norm(want) < 1e-10
     c.close()
+
+
+def test_batch_step_counts_and_graph_cache():
+    """dgpe_batch_step(b, n) runs each member's n steps as one chain in one graph launch;
+    graphs are cached per step count (at most four).  Any sequence of calls, with more
+    distinct counts than the cache holds, equals the members' own steps bitwise."""
+    batched, alone = [], []
+    for k, (shape, h, mode, nu, g, gdd) in enumerate(MEMBERS):
+        psi = inputs.gaussian_psi(shape, h, seed=40 + k).astype(np.complex64)
+        for group in (batched, alone):
+            c = abi.Condensate(shape, h, 0.004, mode=mode, precision=abi.DGPE_MIXED, nu=nu, g=g, gdd=gdd)
+            c.set_psi(psi)
+            group.append(c)
+    b = abi.Batch(batched)
+    counts = [2, 5, 2, 1, 4, 3, 6, 5]
+    for n in counts:
+        b.step(n)
+    b.sync()
+    for c in alone:
+        c.step(sum(counts))
+    for x, y in zip(batched, alone):
+        assert np.array_equal(x.get_psi(), y.get_psi())
+    b.close()
+    for c in batched + alone:
+        c.close()

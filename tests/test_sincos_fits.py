@@ -160,9 +160,14 @@ def test_fp64_cody_waite_pieces(fp64):
 
 def test_fp32_constants(fp32):
     f32 = lambda v: float(np.float32(v))
-    # FP32 routine: sine through r^9, cosine through r^10, every literal the float of 1/n!
-    assert [f32(v) for v in fp32["ps"][0]] == taylor(1, 4, odd=True, cast=f32)
-    assert [f32(v) for v in fp32["pc"][0]] == taylor(0, 4, odd=False, cast=f32)
+    # FP32 routine: |x| <= 1/4 sine through x^7 and cosine through x^6, then (reduced
+    # argument) sine through r^9 and cosine through r^10; every literal the float of 1/n!
+    assert [f32(v) for v in fp32["ps"][0]] == taylor(1, 3, odd=True, cast=f32)
+    assert [f32(v) for v in fp32["pc"][0]] == taylor(0, 2, odd=False, cast=f32)
+    assert [f32(v) for v in fp32["ps"][1]] == taylor(1, 4, odd=True, cast=f32)
+    assert [f32(v) for v in fp32["pc"][1]] == taylor(0, 4, odd=False, cast=f32)
+    # the short branch's truncation: first omitted terms x^9/9! and x^8/8! at x = 1/4
+    assert 0.25 ** 9 / math.factorial(9) < 1.1e-11 and 0.25 ** 8 / math.factorial(8) < 3.8e-10
     pieces = [f32(v) for v in re.findall(r"r = fmaf\(-k, %s, (?:x|r)\);" % NUM, fp32["body"])]
     assert len(pieces) == 3
     with mp.workdps(40):
