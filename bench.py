@@ -214,7 +214,11 @@ def rel_errors(psi, obs, psi_ref, obs_ref):
     """Errors of (psi, obs) against a reference: rel-L2 of psi and the relative errors of
     mu, E, the rms sizes and the norm."""
     import torch
+    # the same after removing the best global phase e^{i phi}, phi = arg <psi_ref, psi>
+    ov = torch.vdot(psi_ref.flatten(), psi.flatten())
+    aligned = psi * (ov.conj() / abs(ov)) if abs(ov) > 0 else psi
     return {"psi_rel_l2": float(torch.linalg.norm(psi - psi_ref) / torch.linalg.norm(psi_ref)),
+            "psi_rel_l2_phase_aligned": float(torch.linalg.norm(aligned - psi_ref) / torch.linalg.norm(psi_ref)),
             "mu_rel": abs(obs["mu"] - obs_ref["mu"]) / abs(obs_ref["mu"]),
             "energy_rel": abs(obs["energy"] - obs_ref["energy"]) / abs(obs_ref["energy"]),
             "rms_rel": [abs(a - b) / abs(b) for a, b in zip(obs["rms"], obs_ref["rms"])],

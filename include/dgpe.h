@@ -259,7 +259,11 @@ typedef struct dgpe_batch dgpe_batch;
 
 /* n >= 1 distinct contexts on the current device; they must outlive the batch.  The batch
  * launches on cuda_stream; do not enqueue work on a context's own stream while a batch step
- * may still run (synchronise first).  (No paper counterpart: see above.) */
+ * may still run (synchronise first).  FP32-mixed contexts of the same shape, mode and
+ * launch shape are stepped as a group: each kernel of the step is one launch for all of
+ * them (their arguments in a device array of n entries that dgpe_batch_create allocates with
+ * cudaMalloc); other contexts run their own kernels.  Results are bitwise those of each
+ * context's own steps.  (No paper counterpart: see above.) */
 int dgpe_batch_create(dgpe_ctx *const *ctxs, int n, void *cuda_stream, dgpe_batch **out);
 /* nsteps SSCN steps of every context, as one graph launch: each context's nsteps steps form
  * one chain of kernels (a branch of the graph), and the branches are joined once, at the

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdgpe.so")
-SOURCES = ["dgpe_api.cu", "kernels_f64.cu", "kernels_f32.cu", "kernels_df64.cu", "dgpe_noalloc.cu"]
+SOURCES = ["dgpe_api.cu", "kernels_f64.cu", "kernels_f32.cu", "kernels_f32_group.cu", "kernels_df64.cu",
+           "dgpe_noalloc.cu"]
 HEADERS = ["dgpe_device.cuh", "dgpe_internal.h", "dgpe_df64.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

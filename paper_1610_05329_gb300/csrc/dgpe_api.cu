@@ -283,6 +283,17 @@ struct dgpe_batch {
   std::vector<cudaStream_t> branches;
   std::vector<cudaEvent_t> events;
   std::map<int, cudaGraphExec_t> graphs;   // steps per branch -> instantiated graph
+  // same-shaped FP32 contexts stepped together (each kernel one launch for the group): the
+  // members, their arguments on the host and in device memory (args_dev: one array for all
+  // groups, allocated at dgpe_batch_create)
+  struct Group {
+    std::vector<int> members;
+    size_t offset;   // first entry of the group in args_dev
+  };
+  std::vector<Group> groups;
+  std::vector<int> singles;   // contexts stepped on their own
+  std::vector<KArgs> args_host;
+  KArgs *args_dev = nullptr;
 };
 
 namespace {
@@ -1082,12 +1093,65 @@ int dgpe_batch_create(dgpe_ctx *const *ctxs, int n, void *cuda_stream, dgpe_batc
   b->events.assign(n + 1, nullptr);
   for (int i = 0; i < n && !rc; ++i) rc = map_cuda(cudaStreamCreateWithFlags(&b->branches[i], cudaStreamNonBlocking));
   for (int i = 0; i <= n && !rc; ++i) rc = map_cuda(cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming));
+  // the argument array of the grouped launches (at most every context in one group)
+  if (!rc) rc = map_cuda(cudaMalloc(reinterpret_cast<void **>(&b->args_dev), (size_t)n * sizeof(KArgs)));
   if (rc) {
     dgpe_batch_destroy(b);
     return rc;
   }
   *out = b;
   return DGPE_OK;
+}
+
+// Contexts whose step kernels can run as one grouped launch: FP32, and the same shape,
+// mode, norm handling and launch shape (radix orders, y lines per CTA, transform threads,
+// sweep CTAs per SM).
+static bool same_group(const dgpe_ctx *x, const dgpe_ctx *y) {
+  const KArgs &a = x->args, &b = y->args;
+  if (x->ks != y->ks || !x->ks->step_group) return false;
+  if (a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.imag != b.imag || x->restore_norm != y->restore_norm)
+    return false;
+  if (a.ylines != b.ylines || a.fft_threads != b.fft_threads || a.cn_per_sm != b.cn_per_sm) return false;
+  for (int d = 0; d < 3; ++d)
+    if (x->plan_style[d] != y->plan_style[d]) return false;
+  return true;
+}
+
+// Sort the contexts into groups (two or more members) and singles, and copy every group's
+// arguments to the device array, stream-ordered on the batch stream (before any later
+// launch of the batch's graphs).
+static int batch_group(dgpe_batch *b) {
+  const int n = (int)b->ctxs.size();
+  b->groups.clear();
+  b->singles.clear();
+  b->args_host.clear();
+  std::vector<char> used(n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (used[i]) continue;
+    dgpe_batch::Group g;
+    g.members.push_back(i);
+    for (int j = i + 1; j < n; ++j)
+      if (!used[j] && same_group(b->ctxs[i], b->ctxs[j])) {
+        g.members.push_back(j);
+        used[j] = 1;
+      }
+    if (g.members.size() < 2) {
+      b->singles.push_back(i);
+      continue;
+    }
+    g.offset = b->args_host.size();
+    for (int m : g.members) b->args_host.push_back(b->ctxs[m]->args);
+    b->groups.push_back(g);
+  }
+  if (b->args_host.empty()) return DGPE_OK;
+  int rc = DGPE_OK;
+  for (const dgpe_batch::Group &g : b->groups)
+    if (!rc) rc = map_cuda(b->ctxs[g.members[0]]->ks->init_group());
+  if (!rc) rc = map_cuda(cudaMemcpyAsync(b->args_dev, b->args_host.data(), b->args_host.size() * sizeof(KArgs),
+                                         cudaMemcpyHostToDevice, b->stream));
+  // the host copy is read by the transfer: keep it unchanged until it has run
+  if (!rc) rc = map_cuda(cudaStreamSynchronize(b->stream));
+  return rc;
 }
 
 // Kernel nodes of one batch graph at most; a longer run launches several graphs.
@@ -1112,6 +1176,10 @@ static int batch_graph(dgpe_batch *b, int steps, cudaGraphExec_t *out) {
     *out = it->second;
     return DGPE_OK;
   }
+  if (b->graphs.empty()) {   // (re)building: the contexts' arguments may have changed
+    const int grc = batch_group(b);
+    if (grc) return grc;
+  }
   const int n = (int)b->ctxs.size();
   std::vector<char> timing(n);
   for (int i = 0; i < n; ++i) {
@@ -1120,12 +1188,22 @@ static int batch_graph(dgpe_batch *b, int steps, cudaGraphExec_t *out) {
   }
   int rc = map_cuda(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
   if (!rc) rc = map_cuda(cudaEventRecord(b->events[n], b->cap));
-  for (int i = 0; i < n && !rc; ++i) {
-    rc = map_cuda(cudaStreamWaitEvent(b->branches[i], b->events[n], 0));
-    for (int s = 0; s < steps && !rc; ++s) rc = enqueue_step(b->ctxs[i], b->branches[i]);
+  // a branch per group (its first member's stream and event) and per single context
+  auto branch = [&](int i, auto &&enqueue) {
+    if (!rc) rc = map_cuda(cudaStreamWaitEvent(b->branches[i], b->events[n], 0));
+    for (int s = 0; s < steps && !rc; ++s) rc = enqueue(b->branches[i]);
     if (!rc) rc = map_cuda(cudaEventRecord(b->events[i], b->branches[i]));
     if (!rc) rc = map_cuda(cudaStreamWaitEvent(b->cap, b->events[i], 0));
+  };
+  for (const dgpe_batch::Group &g : b->groups) {
+    const dgpe_ctx *c0 = b->ctxs[g.members[0]];
+    const KArgs &a0 = c0->args;
+    const int renorm = a0.imag ? kRenormUnit : (c0->restore_norm ? kRenormRestore : kRenormNone);
+    branch(g.members[0], [&](cudaStream_t st) {
+      return map_cuda(c0->ks->step_group(a0, b->args_dev + g.offset, (int)g.members.size(), renorm, st));
+    });
   }
+  for (int i : b->singles) branch(i, [&](cudaStream_t st) { return enqueue_step(b->ctxs[i], st); });
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
   for (int i = 0; i < n; ++i) b->ctxs[i]->timing = timing[i];
@@ -1169,6 +1247,7 @@ void dgpe_batch_destroy(dgpe_batch *b) {
   if (!b) return;
   if (b->stream || b->cap) cudaStreamSynchronize(b->stream);
   batch_drop_graphs(b);
+  if (b->args_dev) cudaFree(b->args_dev);
   for (cudaEvent_t e : b->events)
     if (e) cudaEventDestroy(e);
   for (cudaStream_t st : b->branches)

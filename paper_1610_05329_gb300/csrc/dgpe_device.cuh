@@ -1237,7 +1237,7 @@ __device__ __forceinline__ double half_density(double d) {
 // the half spectrum m = 0..nz/2 is stored to spec[m][i][j].
 // ---------------------------------------------------------------------------------------
 template <typename R, int N>
-__global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) {
+__device__ __forceinline__ void k1_density_r2cz_body(const KArgs &a) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int BZ = Tiles<R>::kZLines;
@@ -1296,12 +1296,19 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a) 
     }
   }
 }
+// one condensate (G = false, its arguments passed by value), or condensate blockIdx.z of
+// a group of same-shaped condensates (G = true, the arguments from the device array ga)
+template <typename R, int N, bool G = false>
+__global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a, const KArgs *ga) {
+  if constexpr (G) k1_density_r2cz_body<R, N>(ga[blockIdx.z]);
+  else k1_density_r2cz_body<R, N>(a);
+}
 
 // ---------------------------------------------------------------------------------------
 // K2 / K4: FFT along y of the contiguous lines spec[m][i][:].
 // ---------------------------------------------------------------------------------------
 template <typename R, int DIR, int N>
-__global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a) {
+__device__ __forceinline__ void k_ffty_body(const KArgs &a) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // N > 0: ny = N with the default lines per CTA and 256 threads, fixed at compile time
@@ -1330,6 +1337,13 @@ __global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a) {
 #pragma unroll 4
   for (int e = threadIdx.x; e < nl * n; e += blockDim.x, pos.next()) spec[e] = res[pos.k * SB + pos.b];
 }
+// one condensate (G = false, its arguments passed by value), or condensate blockIdx.z of
+// a group of same-shaped condensates (G = true, the arguments from the device array ga)
+template <typename R, int DIR, int N, bool G = false>
+__global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a, const KArgs *ga) {
+  if constexpr (G) k_ffty_body<R, DIR, N>(ga[blockIdx.z]);
+  else k_ffty_body<R, DIR, N>(a);
+}
 
 // ---------------------------------------------------------------------------------------
 // K3: for the plane kz = m, lines along x (stride ny), kXCols consecutive ky per CTA:
@@ -1337,7 +1351,7 @@ __global__ void __launch_bounds__(kFftThreads) k_ffty(KArgs a) {
 // inverse FFT along x.
 // ---------------------------------------------------------------------------------------
 template <typename R, int N>
-__global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
+__device__ __forceinline__ void k3_fftx_dipolar_body(const KArgs &a) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int BX = Tiles<R>::kXCols;
@@ -1386,6 +1400,13 @@ __global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a) {
     const int b = e % BX, k = e / BX;
     if (b < nb) spec[(size_t)k * a.ny + b] = out[k * SB + b];
   }
+}
+// one condensate (G = false, its arguments passed by value), or condensate blockIdx.z of
+// a group of same-shaped condensates (G = true, the arguments from the device array ga)
+template <typename R, int N, bool G = false>
+__global__ void __launch_bounds__(kFftThreads) k3_fftx_dipolar(KArgs a, const KArgs *ga) {
+  if constexpr (G) k3_fftx_dipolar_body<R, N>(ga[blockIdx.z]);
+  else k3_fftx_dipolar_body<R, N>(a);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1463,7 +1484,7 @@ __device__ __forceinline__ void reg_fft(cplx<float> (&v)[8], cplx<float> *__rest
 // K2 / K4 in FP32 for ny = 128, 256 or 512 with the default plan: 256 / T lines per CTA,
 // each line's registers loaded from and stored to global memory directly.
 template <int DIR, int N>
-__global__ void __launch_bounds__(256, 4) k_ffty_reg(KArgs a) {
+__device__ __forceinline__ void k_ffty_reg_body(const KArgs &a) {
   using C = cplx<float>;
   using F = RegFft<N>;
   constexpr int T = F::T, LPC = 256 / T;
@@ -1486,13 +1507,20 @@ __global__ void __launch_bounds__(256, 4) k_ffty_reg(KArgs a) {
     for (int r = 0; r < 8; ++r) g[t + T * r] = v[r];
   }
 }
+// one condensate (G = false, its arguments passed by value), or condensate blockIdx.z of
+// a group of same-shaped condensates (G = true, the arguments from the device array ga)
+template <int DIR, int N, bool G = false>
+__global__ void __launch_bounds__(256, 4) k_ffty_reg(KArgs a, const KArgs *ga) {
+  if constexpr (G) k_ffty_reg_body<DIR, N>(ga[blockIdx.z]);
+  else k_ffty_reg_body<DIR, N>(a);
+}
 
 // K3 in FP32 for nx = 128, 256 or 512 with the default plan: the forward transform along x,
 // the product with Ut(k) in registers (each thread's outputs are exactly its inputs of the
 // inverse transform), the inverse transform; 8 consecutive ky columns per CTA, the lanes of
 // a warp spanning them (64-byte rows), the columns interleaved in shared memory.
 template <int N>
-__global__ void __launch_bounds__(8 * RegFft<N>::T, 1024 / (8 * RegFft<N>::T)) k3_reg(KArgs a) {
+__device__ __forceinline__ void k3_reg_body(const KArgs &a) {
   using C = cplx<float>;
   using F = RegFft<N>;
   constexpr int T = F::T, B = 8;
@@ -1533,6 +1561,13 @@ __global__ void __launch_bounds__(8 * RegFft<N>::T, 1024 / (8 * RegFft<N>::T)) k
     for (int r = 0; r < 8; ++r) g[(size_t)(t + T * r) * sx] = v[r];
   }
 }
+// one condensate (G = false, its arguments passed by value), or condensate blockIdx.z of
+// a group of same-shaped condensates (G = true, the arguments from the device array ga)
+template <int N, bool G = false>
+__global__ void __launch_bounds__(8 * RegFft<N>::T, 1024 / (8 * RegFft<N>::T)) k3_reg(KArgs a, const KArgs *ga) {
+  if constexpr (G) k3_reg_body<N>(ga[blockIdx.z]);
+  else k3_reg_body<N>(a);
+}
 
 // ---------------------------------------------------------------------------------------
 // K5: the z-line kernel.  For kZLines lines (i, j0..): inverse half-spectrum transform
@@ -1543,9 +1578,7 @@ __global__ void __launch_bounds__(8 * RegFft<N>::T, 1024 / (8 * RegFft<N>::T)) k
 // The FP64 phase-only pass runs three CTAs per SM (80 registers and a few spills beat two).
 // ---------------------------------------------------------------------------------------
 template <typename R, typename Coef, int ZM, int N>
-__global__ void __launch_bounds__(Tiles<R>::kZThreads,
-                                  ZM == kZObs ? 1 : (ZM == kZPhaseOnly && std::is_same<R, double>::value ? 3 : Tiles<R>::kZMinBlocks))
-    k5_zline(KArgs a) {
+__device__ __forceinline__ void k5_zline_body(const KArgs &a) {
   constexpr int zmode = ZM;   // one instance per mode: each gets its own register allocation
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1620,7 +1653,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads,
   // transform buffer that does not hold the result: they arrive during the phase loop, and
   // the solve reads them from shared memory.  They take 128 chunk sizeof(Coef) bytes, the
   // buffer nz PZ sizeof(C): with chunk the least power of two >= max(2, (nz - 2)/32) they fit
-  // for the compile-time lengths (256 to 512); the runtime-length instance reads them from
+  // for the compile-time lengths (128 to 512); the runtime-length instance reads them from
   // global memory.
   const Coef *ztab = reinterpret_cast<const Coef *>(a.cn[2].tab);
   if constexpr (N > 0) {
@@ -1786,6 +1819,14 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads,
 #pragma unroll 4
   for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) psi[e] = tile[pos.b * LS + cn_slot(pos.k, lc)];
 }
+// one condensate (G = false, its arguments passed by value), or condensate blockIdx.z of
+// a group of same-shaped condensates (G = true, the arguments from the device array ga)
+template <typename R, typename Coef, int ZM, int N, bool G = false>
+__global__ void __launch_bounds__(Tiles<R>::kZThreads,
+                                  ZM == kZObs ? 1 : (ZM == kZPhaseOnly && std::is_same<R, double>::value ? 3 : Tiles<R>::kZMinBlocks)) k5_zline(KArgs a, const KArgs *ga) {
+  if constexpr (G) k5_zline_body<R, Coef, ZM, N>(ga[blockIdx.z]);
+  else k5_zline_body<R, Coef, ZM, N>(a);
+}
 
 // ---------------------------------------------------------------------------------------
 // K6 / K7: Crank-Nicolson along y (AXIS = 1, lines psi[i][:][k]) or x (AXIS = 0, lines
@@ -1854,7 +1895,7 @@ __device__ __forceinline__ void finish_sweep_sums(const KArgs &a, double (&v)[4]
 // flight while the current tile is solved and stored.
 // B columns (z) per tile, NT threads (B divides NT; one or two lines per warp).
 template <typename R, typename Coef, int AXIS, int B = Tiles<R>::kCnCols, int NT = Tiles<R>::kCnThreads>
-__global__ void __launch_bounds__(NT, 512 / NT) k_cn(KArgs a, int reduce, int renorm) {
+__device__ __forceinline__ void k_cn_body(const KArgs &a, int reduce, int renorm) {
   static_assert(std::is_same<R, float>::value, "the chunked sweeps serve FP32 data");
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1951,6 +1992,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_cn(KArgs a, int reduce, int re
     double v[4] = {acc[0].value() * w, 0.0, acc[2].value() * (w * a.hy * a.hy), acc[3].value() * (w * a.hz * a.hz)};
     finish_sweep_sums(a, v, renorm);
   }
+}
+// one condensate (G = false, its arguments passed by value), or condensate blockIdx.z of
+// a group of same-shaped condensates (G = true, the arguments from the device array ga)
+template <typename R, typename Coef, int AXIS, int B = Tiles<R>::kCnCols, int NT = Tiles<R>::kCnThreads, bool G = false>
+__global__ void __launch_bounds__(NT, 512 / NT) k_cn(KArgs a, const KArgs *ga, int reduce, int renorm) {
+  if constexpr (G) k_cn_body<R, Coef, AXIS, B, NT>(ga[blockIdx.z], reduce, renorm);
+  else k_cn_body<R, Coef, AXIS, B, NT>(a, reduce, renorm);
 }
 
 // FP64-class sweeps: two threads per line, the twisted ("burn at both ends") factorization.
@@ -2415,7 +2463,7 @@ struct Impl {
     auto chk = [&](cudaError_t r) {
       if (e == cudaSuccess) e = r;
     };
-    using K = void (*)(KArgs);
+    using K = void (*)(KArgs, const KArgs *);
     chk(allow_smem(static_cast<K>(k_ffty_reg<-1, 512>)));
     chk(allow_smem(static_cast<K>(k_ffty_reg<+1, 512>)));
     chk(allow_smem(static_cast<K>(k_ffty_reg<-1, 256>)));
@@ -2470,6 +2518,8 @@ struct Impl {
       chk(allow_smem(k5_zline<R, C, kZFast, 384>));
       chk(allow_smem(k5_zline<R, R, kZFast, 256>));
       chk(allow_smem(k5_zline<R, C, kZFast, 256>));
+      chk(allow_smem(k5_zline<R, R, kZFast, 128>));
+      chk(allow_smem(k5_zline<R, C, kZFast, 128>));
     }
     if constexpr (!kCnThread) {
       chk(allow_smem(k_cn<R, R, 0>));
@@ -2547,13 +2597,13 @@ struct Impl {
     const dim3 g = grid_z(a);
     const size_t sm = smem_z_fft(a);
     if constexpr (kCtSizes) {
-      if (plan_ct(a.plan[2], 512)) k1_density_r2cz<R, 512><<<g, T::kZThreads, sm, st>>>(a);
-      else if (plan_ct(a.plan[2], 384)) k1_density_r2cz<R, 384><<<g, T::kZThreads, sm, st>>>(a);
-      else if (plan_ct(a.plan[2], 256)) k1_density_r2cz<R, 256><<<g, T::kZThreads, sm, st>>>(a);
-      else if (plan_ct(a.plan[2], 128)) k1_density_r2cz<R, 128><<<g, T::kZThreads, sm, st>>>(a);
-      else k1_density_r2cz<R, 0><<<g, T::kZThreads, sm, st>>>(a);
+      if (plan_ct(a.plan[2], 512)) k1_density_r2cz<R, 512><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else if (plan_ct(a.plan[2], 384)) k1_density_r2cz<R, 384><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else if (plan_ct(a.plan[2], 256)) k1_density_r2cz<R, 256><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else if (plan_ct(a.plan[2], 128)) k1_density_r2cz<R, 128><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else k1_density_r2cz<R, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
     } else {
-      k1_density_r2cz<R, 0><<<g, T::kZThreads, sm, st>>>(a);
+      k1_density_r2cz<R, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
     }
     return cudaGetLastError();
   }
@@ -2570,12 +2620,12 @@ struct Impl {
   template <int DIR, int N>
   static void ffty_reg(const KArgs &a, cudaStream_t st) {
     const size_t lines = (size_t)a.nzh * a.nx, lpc = 256 / RegFft<N>::T;
-    k_ffty_reg<DIR, N><<<(unsigned)((lines + lpc - 1) / lpc), 256, kRegYSmem, st>>>(a);
+    k_ffty_reg<DIR, N><<<(unsigned)((lines + lpc - 1) / lpc), 256, kRegYSmem, st>>>(a, nullptr);
   }
   template <int N>
   static void k3_reg_launch(const KArgs &a, cudaStream_t st) {
     const dim3 grid((a.ny + 7) / 8, a.nzh);
-    k3_reg<N><<<grid, 8 * RegFft<N>::T, reg_x_smem<N>(), st>>>(a);
+    k3_reg<N><<<grid, 8 * RegFft<N>::T, reg_x_smem<N>(), st>>>(a, nullptr);
   }
   template <int DIR>
   static cudaError_t ffty(const KArgs &a, cudaStream_t st) {
@@ -2589,13 +2639,13 @@ struct Impl {
     const dim3 g((unsigned)((lines + L - 1) / L));
     const size_t sm = smem_y(a);
     if constexpr (kCtSizes) {
-      if (y_fixed(a, 512)) k_ffty<R, DIR, 512><<<g, kFftThreads, sm, st>>>(a);
-      else if (y_fixed(a, 384)) k_ffty<R, DIR, 384><<<g, kFftThreads, sm, st>>>(a);
-      else if (y_fixed(a, 256)) k_ffty<R, DIR, 256><<<g, kFftThreads, sm, st>>>(a);
-      else if (y_fixed(a, 128)) k_ffty<R, DIR, 128><<<g, kFftThreads, sm, st>>>(a);
-      else k_ffty<R, DIR, 0><<<g, a.fft_threads, sm, st>>>(a);
+      if (y_fixed(a, 512)) k_ffty<R, DIR, 512><<<g, kFftThreads, sm, st>>>(a, nullptr);
+      else if (y_fixed(a, 384)) k_ffty<R, DIR, 384><<<g, kFftThreads, sm, st>>>(a, nullptr);
+      else if (y_fixed(a, 256)) k_ffty<R, DIR, 256><<<g, kFftThreads, sm, st>>>(a, nullptr);
+      else if (y_fixed(a, 128)) k_ffty<R, DIR, 128><<<g, kFftThreads, sm, st>>>(a, nullptr);
+      else k_ffty<R, DIR, 0><<<g, a.fft_threads, sm, st>>>(a, nullptr);
     } else {
-      k_ffty<R, DIR, 0><<<g, a.fft_threads, sm, st>>>(a);
+      k_ffty<R, DIR, 0><<<g, a.fft_threads, sm, st>>>(a, nullptr);
     }
     return cudaGetLastError();
   }
@@ -2610,13 +2660,13 @@ struct Impl {
     const size_t sm = smem_x(a);
     const bool fixed = a.fft_threads == kFftThreads;
     if constexpr (kCtSizes) {
-      if (fixed && plan_ct(a.plan[0], 512)) k3_fftx_dipolar<R, 512><<<grid, kFftThreads, sm, st>>>(a);
-      else if (fixed && plan_ct(a.plan[0], 384)) k3_fftx_dipolar<R, 384><<<grid, kFftThreads, sm, st>>>(a);
-      else if (fixed && plan_ct(a.plan[0], 256)) k3_fftx_dipolar<R, 256><<<grid, kFftThreads, sm, st>>>(a);
-      else if (fixed && plan_ct(a.plan[0], 128)) k3_fftx_dipolar<R, 128><<<grid, kFftThreads, sm, st>>>(a);
-      else k3_fftx_dipolar<R, 0><<<grid, a.fft_threads, sm, st>>>(a);
+      if (fixed && plan_ct(a.plan[0], 512)) k3_fftx_dipolar<R, 512><<<grid, kFftThreads, sm, st>>>(a, nullptr);
+      else if (fixed && plan_ct(a.plan[0], 384)) k3_fftx_dipolar<R, 384><<<grid, kFftThreads, sm, st>>>(a, nullptr);
+      else if (fixed && plan_ct(a.plan[0], 256)) k3_fftx_dipolar<R, 256><<<grid, kFftThreads, sm, st>>>(a, nullptr);
+      else if (fixed && plan_ct(a.plan[0], 128)) k3_fftx_dipolar<R, 128><<<grid, kFftThreads, sm, st>>>(a, nullptr);
+      else k3_fftx_dipolar<R, 0><<<grid, a.fft_threads, sm, st>>>(a, nullptr);
     } else {
-      k3_fftx_dipolar<R, 0><<<grid, a.fft_threads, sm, st>>>(a);
+      k3_fftx_dipolar<R, 0><<<grid, a.fft_threads, sm, st>>>(a, nullptr);
     }
     return cudaGetLastError();
   }
@@ -2626,12 +2676,13 @@ struct Impl {
   template <int ZM, typename Co>
   static void k5_launch(const KArgs &a, dim3 g, size_t sm, cudaStream_t st) {
     if constexpr (kCtSizes) {
-      if (plan_ct(a.plan[2], 512)) k5_zline<R, Co, ZM, 512><<<g, T::kZThreads, sm, st>>>(a);
-      else if (plan_ct(a.plan[2], 384)) k5_zline<R, Co, ZM, 384><<<g, T::kZThreads, sm, st>>>(a);
-      else if (plan_ct(a.plan[2], 256)) k5_zline<R, Co, ZM, 256><<<g, T::kZThreads, sm, st>>>(a);
-      else k5_zline<R, Co, ZM, 0><<<g, T::kZThreads, sm, st>>>(a);
+      if (plan_ct(a.plan[2], 512)) k5_zline<R, Co, ZM, 512><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else if (plan_ct(a.plan[2], 384)) k5_zline<R, Co, ZM, 384><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else if (plan_ct(a.plan[2], 256)) k5_zline<R, Co, ZM, 256><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else if (plan_ct(a.plan[2], 128)) k5_zline<R, Co, ZM, 128><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else k5_zline<R, Co, ZM, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
     } else {
-      k5_zline<R, Co, ZM, 0><<<g, T::kZThreads, sm, st>>>(a);
+      k5_zline<R, Co, ZM, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
     }
   }
   // the mode whose compile-time instances exist: the fused step (FP32), or the phase-only
@@ -2656,18 +2707,18 @@ struct Impl {
     switch (zmode) {
       case kZPhaseOnly:
         if constexpr (!kZSplit) {
-          if (a.imag) k5_zline<R, R, kZPhaseOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
-          else k5_zline<R, C, kZPhaseOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
+          if (a.imag) k5_zline<R, R, kZPhaseOnly, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+          else k5_zline<R, C, kZPhaseOnly, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
         }
         break;
       case kZCnOnly:
         if constexpr (!kZSplit) {
-          if (a.imag) k5_zline<R, R, kZCnOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
-          else k5_zline<R, C, kZCnOnly, 0><<<g, T::kZThreads, sm, st>>>(a);
+          if (a.imag) k5_zline<R, R, kZCnOnly, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+          else k5_zline<R, C, kZCnOnly, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
         }
         break;
-      case kZPhi: k5_zline<R, R, kZPhi, 0><<<g, T::kZThreads, sm, st>>>(a); break;
-      case kZObs: k5_zline<R, R, kZObs, 0><<<g, T::kZThreads, sm, st>>>(a); break;
+      case kZPhi: k5_zline<R, R, kZPhi, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr); break;
+      case kZObs: k5_zline<R, R, kZObs, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr); break;
       default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -2683,8 +2734,8 @@ struct Impl {
       else k_cn_twisted<R, C, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
     } else {
       const size_t sm = smem_cn(n, a.cn[AXIS].lchunk);
-      if (a.imag) k_cn<R, R, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, reduce, renorm);
-      else k_cn<R, C, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, reduce, renorm);
+      if (a.imag) k_cn<R, R, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, nullptr, reduce, renorm);
+      else k_cn<R, C, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, nullptr, reduce, renorm);
     }
     return cudaGetLastError();
   }
@@ -2743,11 +2794,153 @@ struct Impl {
   }
 
   static const KernelSet *set() {
+    // groups of same-shaped condensates launched together: FP32 only (kernels_f32_group.cu)
+    constexpr bool kGroup = std::is_same<R, float>::value;
     static const KernelSet ks = {(int)E, &init,          &twiddles,   &cn_tables, &axis_potential, &dipolar_table, &from_c128, &to_c128, &reset_state,
                                  &k1,        &k2,            &k3,         &k4,        &k5,             &k6,
                                  &k7,        &materialize,   &adj_phase,  &adj_combine, &loss_z2,
-                                 &max_blocks, kZSplit ? 2 : 1, &default_ylines, &y_smem};
+                                 &max_blocks, kZSplit ? 2 : 1, &default_ylines, &y_smem,
+                                 kGroup ? &group_init_f32 : nullptr, kGroup ? &group_step_f32 : nullptr};
     return &ks;
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// One step of a group of same-shaped condensates (same shape, precision, mode and launch
+// shape; their own psi, physics and device state): every kernel of the step is launched
+// once for all of them, condensate z = blockIdx.z with its arguments ga[z] in device
+// memory.  a is one member's arguments, for the launch configuration.  A group of 16
+// condensates of 128^3 then runs each kernel as one grid of 16 times the blocks, instead of
+// 16 small grids whose launch latency and last partial waves dominate.  The arithmetic per
+// condensate is that of its own step, so the results are bitwise the same.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+struct GroupLaunch {
+  using I = Impl<R>;
+  using C = cplx<R>;
+  using T = Tiles<R>;
+  static_assert(std::is_same<R, float>::value, "grouped steps serve the FP32-mixed path");
+
+  template <typename K>
+  static void attr(K k, cudaError_t &e) {
+    if (e == cudaSuccess) e = I::allow_smem(k);
+  }
+  static cudaError_t init() {
+    cudaError_t e = cudaSuccess;
+    attr(k1_density_r2cz<R, 512, true>, e);
+    attr(k1_density_r2cz<R, 384, true>, e);
+    attr(k1_density_r2cz<R, 256, true>, e);
+    attr(k1_density_r2cz<R, 128, true>, e);
+    attr(k1_density_r2cz<R, 0, true>, e);
+    attr(k_ffty<R, -1, 0, true>, e);
+    attr(k_ffty<R, +1, 0, true>, e);
+    attr(k_ffty<R, -1, 384, true>, e);
+    attr(k_ffty<R, +1, 384, true>, e);
+    attr(k3_fftx_dipolar<R, 384, true>, e);
+    attr(k3_fftx_dipolar<R, 0, true>, e);
+    using K = void (*)(KArgs, const KArgs *);
+    attr(static_cast<K>(k_ffty_reg<-1, 512, true>), e);
+    attr(static_cast<K>(k_ffty_reg<+1, 512, true>), e);
+    attr(static_cast<K>(k_ffty_reg<-1, 256, true>), e);
+    attr(static_cast<K>(k_ffty_reg<+1, 256, true>), e);
+    attr(static_cast<K>(k_ffty_reg<-1, 128, true>), e);
+    attr(static_cast<K>(k_ffty_reg<+1, 128, true>), e);
+    attr(static_cast<K>(k3_reg<512, true>), e);
+    attr(static_cast<K>(k3_reg<256, true>), e);
+    attr(static_cast<K>(k3_reg<128, true>), e);
+    attr(k5_zline<R, R, kZStep, 512, true>, e);
+    attr(k5_zline<R, C, kZStep, 512, true>, e);
+    attr(k5_zline<R, R, kZStep, 384, true>, e);
+    attr(k5_zline<R, C, kZStep, 384, true>, e);
+    attr(k5_zline<R, R, kZStep, 256, true>, e);
+    attr(k5_zline<R, C, kZStep, 256, true>, e);
+    attr(k5_zline<R, R, kZStep, 128, true>, e);
+    attr(k5_zline<R, C, kZStep, 128, true>, e);
+    attr(k5_zline<R, R, kZStep, 0, true>, e);
+    attr(k5_zline<R, C, kZStep, 0, true>, e);
+    attr(k_cn<R, R, 0, T::kCnCols, T::kCnThreads, true>, e);
+    attr(k_cn<R, R, 1, T::kCnCols, T::kCnThreads, true>, e);
+    attr(k_cn<R, C, 0, T::kCnCols, T::kCnThreads, true>, e);
+    attr(k_cn<R, C, 1, T::kCnCols, T::kCnThreads, true>, e);
+    return e;
+  }
+
+  template <int DIR>
+  static void ffty(const KArgs &a, const KArgs *ga, unsigned n, cudaStream_t st) {
+    const size_t lines = (size_t)a.nzh * a.nx;
+    auto reg = [&](auto len) {
+      constexpr int N = decltype(len)::value;
+      const size_t lpc = 256 / RegFft<N>::T;
+      k_ffty_reg<DIR, N, true><<<dim3((unsigned)((lines + lpc - 1) / lpc), 1, n), 256, I::kRegYSmem, st>>>(a, ga);
+    };
+    if (I::plan_ct(a.plan[1], 512)) return reg(std::integral_constant<int, 512>{});
+    if (I::plan_ct(a.plan[1], 256)) return reg(std::integral_constant<int, 256>{});
+    if (I::plan_ct(a.plan[1], 128)) return reg(std::integral_constant<int, 128>{});
+    const int L = a.ylines;
+    const dim3 g((unsigned)((lines + L - 1) / L), 1, n);
+    const size_t sm = I::smem_y(a);
+    if (I::y_fixed(a, 384)) k_ffty<R, DIR, 384, true><<<g, kFftThreads, sm, st>>>(a, ga);
+    else k_ffty<R, DIR, 0, true><<<g, a.fft_threads, sm, st>>>(a, ga);
+  }
+  static void k3(const KArgs &a, const KArgs *ga, unsigned n, cudaStream_t st) {
+    auto reg = [&](auto len) {
+      constexpr int N = decltype(len)::value;
+      k3_reg<N, true><<<dim3((a.ny + 7) / 8, a.nzh, n), 8 * RegFft<N>::T, I::template reg_x_smem<N>(), st>>>(a, ga);
+    };
+    if (I::plan_ct(a.plan[0], 512)) return reg(std::integral_constant<int, 512>{});
+    if (I::plan_ct(a.plan[0], 256)) return reg(std::integral_constant<int, 256>{});
+    if (I::plan_ct(a.plan[0], 128)) return reg(std::integral_constant<int, 128>{});
+    const dim3 g((a.ny + T::kXCols - 1) / T::kXCols, a.nzh, n);
+    const size_t sm = I::smem_x(a);
+    if (a.fft_threads == kFftThreads && I::plan_ct(a.plan[0], 384))
+      k3_fftx_dipolar<R, 384, true><<<g, kFftThreads, sm, st>>>(a, ga);
+    else
+      k3_fftx_dipolar<R, 0, true><<<g, a.fft_threads, sm, st>>>(a, ga);
+  }
+  template <typename Co>
+  static void k5(const KArgs &a, const KArgs *ga, unsigned n, cudaStream_t st) {
+    dim3 g = I::grid_z(a);
+    g.z = n;
+    const size_t sm = I::smem_k5(a);
+    if (I::plan_ct(a.plan[2], 512)) k5_zline<R, Co, kZStep, 512, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+    else if (I::plan_ct(a.plan[2], 384)) k5_zline<R, Co, kZStep, 384, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+    else if (I::plan_ct(a.plan[2], 256)) k5_zline<R, Co, kZStep, 256, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+    else if (I::plan_ct(a.plan[2], 128)) k5_zline<R, Co, kZStep, 128, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+    else k5_zline<R, Co, kZStep, 0, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+  }
+  template <typename Co, int AXIS>
+  static void cn(const KArgs &a, const KArgs *ga, unsigned n, int reduce, int renorm, cudaStream_t st) {
+    dim3 g = I::grid_cn(a, AXIS);
+    g.z = n;
+    const size_t sm = I::smem_cn(AXIS == 0 ? a.nx : a.ny, a.cn[AXIS].lchunk);
+    k_cn<R, Co, AXIS, T::kCnCols, T::kCnThreads, true><<<g, T::kCnThreads, sm, st>>>(a, ga, reduce, renorm);
+  }
+  static cudaError_t step(const KArgs &a, const KArgs *ga, int count, int renorm, cudaStream_t st) {
+    if (count < 1 || count > 65535) return cudaErrorInvalidValue;
+    const unsigned n = (unsigned)count;
+    {
+      dim3 g = I::grid_z(a);
+      g.z = n;
+      const size_t sm = I::smem_z_fft(a);
+      if (I::plan_ct(a.plan[2], 512)) k1_density_r2cz<R, 512, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+      else if (I::plan_ct(a.plan[2], 384)) k1_density_r2cz<R, 384, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+      else if (I::plan_ct(a.plan[2], 256)) k1_density_r2cz<R, 256, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+      else if (I::plan_ct(a.plan[2], 128)) k1_density_r2cz<R, 128, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+      else k1_density_r2cz<R, 0, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+    }
+    ffty<-1>(a, ga, n, st);
+    k3(a, ga, n, st);
+    ffty<+1>(a, ga, n, st);
+    if (a.imag) {
+      k5<R>(a, ga, n, st);
+      cn<R, 1>(a, ga, n, 0, 0, st);
+      cn<R, 0>(a, ga, n, 1, renorm, st);
+    } else {
+      k5<C>(a, ga, n, st);
+      cn<C, 1>(a, ga, n, 0, 0, st);
+      cn<C, 0>(a, ga, n, 1, renorm, st);
+    }
+    return cudaGetLastError();
   }
 };
 

@@ -163,7 +163,15 @@ struct KernelSet {
   int k5_launches;                     // kernels behind one k5 step call (1 fused, or 2)
   int (*default_ylines)(int ny);
   size_t (*y_smem)(int ny, int ylines);
+  // one step of a group of same-shaped condensates, each kernel launched once for all of
+  // them (ga: their arguments in device memory; a: one member's); null where the precision
+  // has no grouped kernels (FP64, double-float)
+  cudaError_t (*init_group)();
+  cudaError_t (*step_group)(const KArgs &a, const KArgs *ga, int n, int renorm, cudaStream_t st);
 };
+
+cudaError_t group_init_f32();
+cudaError_t group_step_f32(const KArgs &a, const KArgs *ga, int n, int renorm, cudaStream_t st);
 
 const KernelSet *kernels_f64();
 const KernelSet *kernels_f32();
