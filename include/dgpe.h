@@ -267,7 +267,9 @@ typedef struct dgpe_batch dgpe_batch;
 int dgpe_batch_create(dgpe_ctx *const *ctxs, int n, void *cuda_stream, dgpe_batch **out);
 /* nsteps SSCN steps of every context, as one graph launch: each context's nsteps steps form
  * one chain of kernels (a branch of the graph), and the branches are joined once, at the
- * end, so no context waits for another between steps.  A graph holds at most 2^18 kernel
+ * end, so no context waits for another between steps; branches with less work (fewer points)
+ * run at a higher stream priority, so that short chains of small grids interleave with long
+ * ones instead of waiting behind them.  A graph holds at most 2^18 kernel
  * nodes; a longer run launches several graphs of equal length (and one shorter).  Graphs
  * are built at the first call with a given nsteps (capture and instantiation, host time
  * that grows with nsteps x contexts), cached for up to four step counts, and rebuilt when a

@@ -11,6 +11,7 @@
 #include <new>
 #include <algorithm>
 #include <map>
+#include <utility>
 #include <vector>
 
 #include "dgpe.h"
@@ -1143,6 +1144,34 @@ static int batch_group(dgpe_batch *b) {
     for (int m : g.members) b->args_host.push_back(b->ctxs[m]->args);
     b->groups.push_back(g);
   }
+  // branch priorities: the less work a branch (group or single) has, the higher its stream
+  // priority, so that the short, latency-bound chains of small grids get SMs as soon as the
+  // large grids' blocks free them instead of waiting behind whole launches (the graph keeps
+  // each kernel's priority from the stream it was captured on)
+  {
+    std::vector<std::pair<double, int>> work;   // (points x members, branch leader)
+    for (const dgpe_batch::Group &g : b->groups) {
+      const KArgs &a = b->ctxs[g.members[0]]->args;
+      work.push_back({(double)a.nx * a.ny * a.nz * g.members.size(), g.members[0]});
+    }
+    for (int i : b->singles) {
+      const KArgs &a = b->ctxs[i]->args;
+      work.push_back({(double)a.nx * a.ny * a.nz, i});
+    }
+    std::sort(work.begin(), work.end(), [](const std::pair<double, int> &x, const std::pair<double, int> &y) {
+      return x.first > y.first;
+    });
+    int least = 0, greatest = 0;
+    int rc0 = map_cuda(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    for (size_t k = 0; k < work.size() && !rc0; ++k) {
+      const int prio = least - (int)std::min<size_t>(k, (size_t)(least - greatest));
+      cudaStream_t &st = b->branches[work[k].second];
+      if (st) cudaStreamDestroy(st);
+      st = nullptr;
+      rc0 = map_cuda(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio));
+    }
+    if (rc0) return rc0;
+  }
   if (b->args_host.empty()) return DGPE_OK;
   int rc = DGPE_OK;
   for (const dgpe_batch::Group &g : b->groups)
@@ -1209,7 +1238,7 @@ static int batch_graph(dgpe_batch *b, int steps, cudaGraphExec_t *out) {
   for (int i = 0; i < n; ++i) b->ctxs[i]->timing = timing[i];
   if (!rc) rc = map_cuda(e);
   cudaGraphExec_t exec = nullptr;
-  if (!rc) rc = map_cuda(cudaGraphInstantiate(&exec, g, 0));
+  if (!rc) rc = map_cuda(cudaGraphInstantiate(&exec, g, cudaGraphInstantiateFlagUseNodePriority));
   if (g) cudaGraphDestroy(g);
   if (rc) return rc;
   b->graphs[steps] = exec;

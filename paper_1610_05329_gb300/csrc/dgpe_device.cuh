@@ -340,11 +340,13 @@ struct LinePos {
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 template <typename C>
 __device__ __forceinline__ void cp_async(C *dst, const C *src) {
-  static_assert(sizeof(C) == 8 || sizeof(C) == 16, "8- or 16-byte elements");
+  static_assert(sizeof(C) == 4 || sizeof(C) == 8 || sizeof(C) == 16, "4-, 8- or 16-byte elements");
   if constexpr (sizeof(C) == 16)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-  else
+  else if constexpr (sizeof(C) == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -381,6 +383,18 @@ struct DFAcc {
 // banks.  cn_slots = slots of a line of n points.
 __host__ __device__ inline int cn_slot(int n, int lchunk) { return n + (max(n - 1, 0) >> lchunk); }
 __host__ __device__ inline int cn_slots(int n, int lchunk) { return n + ((n - 2) >> lchunk); }
+
+// Points n = k0 + W j (j = 0, 1, ...) of a line in a Crank-Nicolson tile, for W a multiple of
+// the chunk: their slots cn_slot(n) = n + ((n - 1) >> lchunk) advance by the constant
+// W + (W >> lchunk), from k0 + ((k0 - 1) >> lchunk) (an arithmetic shift: -1 for k0 = 0,
+// where the wall n = 0 itself is slot 0).  The tile loops of the compile-time line lengths
+// walk their points this way instead of recomputing the slot and the line of every point.
+template <int W>
+struct SlotWalk {
+  int base, step;
+  __device__ __forceinline__ SlotWalk(int k0, int lchunk) : base(k0 + ((k0 - 1) >> lchunk)), step(W + (W >> lchunk)) {}
+  __device__ __forceinline__ int operator()(int j, int k0) const { return (k0 | j) == 0 ? 0 : base + j * step; }
+};
 
 // ---------------------------------------------------------------------------------------
 // FFT: radix-2/3/4/5/7/8 butterflies (DIR = -1 forward e^{-i..}, +1 inverse, unnormalised)
@@ -780,13 +794,15 @@ __device__ __forceinline__ cplx<R> *fft_lines_n(cplx<R> *a, cplx<R> *b, const Ff
 // + t for interior point t * chunk + e, then the scan factors: forward step k (offset
 // 2^k) at 4 mp + k * 32 + t, backward step k at 4 mp + (5 + k) * 32 + t.
 // ---------------------------------------------------------------------------------------
-template <typename R, typename Coef, int CH, bool SHARED_TAB>
+// FULL: the line is padded to 32 CH unknowns (m = 32 CH; the padded slots hold zeros and the
+// tables decouple them), so every lane has a whole chunk and no per-point guard.
+template <typename R, typename Coef, int CH, bool SHARED_TAB, bool FULL = false>
 __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m, int lchunk,
                                         const Coef *__restrict__ tab, const Coef *__restrict__ scan_s, Coef c) {
   const int t = threadIdx.x & (kWarp - 1);
   constexpr int chunk = CH;
   const int s0 = t * chunk;
-  const int len = max(0, min(chunk, m - s0));
+  const int len = FULL ? CH : max(0, min(chunk, m - s0));
   const int mp = kWarp << lchunk;
   const Coef *alpha = tab + t;
   const Coef *beta = tab + mp + t;
@@ -849,19 +865,19 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   }
   if (t == 0) {
     buf[0] = czero<R>();
-    buf[(m + 1 + (m >> lchunk)) * es] = czero<R>();
+    if (!FULL) buf[(m + 1 + (m >> lchunk)) * es] = czero<R>();   // (FULL: the padding already holds 0)
   }
 }
 
 // cn_line with the chunk length as a compile-time constant (every unrolled iteration live).
-template <typename R, typename Coef, bool SHARED_TAB>
+template <typename R, typename Coef, bool SHARED_TAB, bool FULL = false>
 __device__ __forceinline__ void cn_line_any(cplx<R> *__restrict__ buf, int es, int m, int lchunk,
                                             const Coef *__restrict__ tab, const Coef *__restrict__ scan_s, Coef c) {
   switch (lchunk) {
-    case 1: cn_line<R, Coef, 2, SHARED_TAB>(buf, es, m, lchunk, tab, scan_s, c); break;
-    case 2: cn_line<R, Coef, 4, SHARED_TAB>(buf, es, m, lchunk, tab, scan_s, c); break;
-    case 3: cn_line<R, Coef, 8, SHARED_TAB>(buf, es, m, lchunk, tab, scan_s, c); break;
-    default: cn_line<R, Coef, 16, SHARED_TAB>(buf, es, m, lchunk, tab, scan_s, c); break;
+    case 1: cn_line<R, Coef, 2, SHARED_TAB, FULL>(buf, es, m, lchunk, tab, scan_s, c); break;
+    case 2: cn_line<R, Coef, 4, SHARED_TAB, FULL>(buf, es, m, lchunk, tab, scan_s, c); break;
+    case 3: cn_line<R, Coef, 8, SHARED_TAB, FULL>(buf, es, m, lchunk, tab, scan_s, c); break;
+    default: cn_line<R, Coef, 16, SHARED_TAB, FULL>(buf, es, m, lchunk, tab, scan_s, c); break;
   }
 }
 
@@ -1082,11 +1098,16 @@ __global__ void k_cn_tables(CnJobs jobs) {
   Z64 e_prev = diag;
   const int h = m / 2;   // the twist point of the two-thread (twisted) sweeps
   Z64 e_h = diag, e_hm = diag;
-  for (int s0 = 0; s0 < m; s0 += chunk) {
-    const int end = min(s0 + chunk, m) - 1;
+  // all 32 chunks: positions i >= m are padding, decoupled (alpha = 0, e = 1), so a solve
+  // over the padded length with zero values there gives zero there and leaves the m real
+  // unknowns exactly as they are (the padding only ever multiplies zeros)
+  for (int s0 = 0; s0 < kWarp * chunk; s0 += chunk) {
+    const int end = s0 + chunk - 1;
     for (int i = s0; i <= end; ++i) {
       Z64 a = {0.0, 0.0}, e = diag;
-      if (i > 0) {
+      if (i >= m) {
+        e = one;
+      } else if (i > 0) {
         a = zdiv(c, e_prev);
         const Z64 ca = zmul(c, a);
         e = Z64{diag.re - ca.re, diag.im - ca.im};
@@ -1598,18 +1619,57 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
   C *psi = reinterpret_cast<C *>(a.psi) + line0 * nz;
   const C *res = nullptr;
 
-  // the CN-z scan factors, staged after the per-CTA potential tables
-  Coef *scan_s = reinterpret_cast<Coef *>(reinterpret_cast<R *>(tile + BZ * LS) + nz + BZ);
+  // the CN-z scan factors, staged after the per-CTA potential tables (dt V_z per point of a
+  // line, dt V_y per line; dt V_x of this CTA's x index is a register).  For the compile-time
+  // lengths (nz a multiple of 4: every piece 16-byte aligned) they are cp.async copies in the
+  // psi tile's group, so their latency hides behind the spectrum load and the transform.
+  R *tz = reinterpret_cast<R *>(tile + BZ * LS);
+  R *ty = tz + nz;
+  Coef *scan_s = reinterpret_cast<Coef *>(ty + BZ);
+  constexpr bool kAsyncTabs = N > 0 && !Fp64Class<R>::value;   // (FP64-class: pipe bound, unchanged)
+  static_assert(N % 4 == 0, "16-byte aligned pieces");
+  const bool phase = zmode == kZStep || zmode == kZPhaseOnly;
+  R dtvx = R(0);
+  if (phase) dtvx = reinterpret_cast<const R *>(a.dtv[0])[i];
   if (zmode == kZStep || zmode == kZCnOnly) {
     const Coef *gscan = reinterpret_cast<const Coef *>(a.cn[2].tab) + 4 * (kWarp << lc);
-    for (int q = threadIdx.x; q < 10 * kWarp; q += blockDim.x) scan_s[q] = gscan[q];
+    if constexpr (kAsyncTabs) {
+      constexpr int chunks = 10 * kWarp * (int)sizeof(Coef) / 16;
+      for (int q = threadIdx.x; q < chunks; q += blockDim.x)
+        cp_async(reinterpret_cast<uint4 *>(scan_s) + q, reinterpret_cast<const uint4 *>(gscan) + q);
+    } else {
+      for (int q = threadIdx.x; q < 10 * kWarp; q += blockDim.x) scan_s[q] = gscan[q];
+    }
+  }
+  if (kAsyncTabs && phase) {
+    const R *dtv_y = reinterpret_cast<const R *>(a.dtv[1]) + j0;
+    const R *dtv_z = reinterpret_cast<const R *>(a.dtv[2]);
+    for (int q = threadIdx.x; q < nz * (int)sizeof(R) / 16; q += blockDim.x)
+      cp_async(reinterpret_cast<uint4 *>(tz) + q, reinterpret_cast<const uint4 *>(dtv_z) + q);
+    if (threadIdx.x < nl) cp_async(ty + threadIdx.x, dtv_y + threadIdx.x);
   }
 
-  // psi tile: asynchronous copies, overlapped with the spectrum load and the C2R transform
+  // psi tile: asynchronous copies, overlapped with the spectrum load and the C2R transform.
+  // Compile-time lengths: thread (line b, offset k0 < W) copies the points k0 + W j of its
+  // line (W = threads / lines: 16 consecutive points of a line per half-warp, coalesced).
+  constexpr int W = Tiles<R>::kZThreads / BZ;
+  constexpr bool kWalk = N > 0 && !Fp64Class<R>::value;
+  static_assert(N % W == 0 && Tiles<R>::kZThreads % BZ == 0, "the walk covers whole lines");
   if (zmode != kZPhi) {
-    LinePos pos(threadIdx.x, nz, blockDim.x);
-    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next())
-      cp_async(tile + pos.b * LS + cn_slot(pos.k, lc), psi + e);
+    if constexpr (kWalk) {
+      const int b = threadIdx.x / W, k0 = threadIdx.x % W;
+      if (b < nl) {
+        const SlotWalk<W> w(k0, lc);
+        C *dst = tile + b * LS;
+        const C *src = psi + (size_t)b * nz + k0;
+#pragma unroll 8
+        for (int j = 0; j < N / W; ++j) cp_async(dst + w(j, k0), src + W * j);
+      }
+    } else {
+      LinePos pos(threadIdx.x, nz, blockDim.x);
+      for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next())
+        cp_async(tile + pos.b * LS + cn_slot(pos.k, lc), psi + e);
+    }
   }
   cp_async_commit();
 
@@ -1772,29 +1832,28 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
   if (zmode == kZStep || zmode == kZPhaseOnly) {
     // theta = dt (V + g n + gdd Phi): dt V_z per n and dt (V_x + V_y) per line come from
     // small per-CTA tables; the 1/(nx ny nz) of the inverse transform is folded into gdd.
-    R *tz = reinterpret_cast<R *>(tile + BZ * LS);
-    R *txy = tz + nz;
-    const R *dtv_x = reinterpret_cast<const R *>(a.dtv[0]);
-    const R *dtv_y = reinterpret_cast<const R *>(a.dtv[1]);
-    const R *dtv_z = reinterpret_cast<const R *>(a.dtv[2]);
-    for (int n = threadIdx.x; n < nz; n += blockDim.x) tz[n] = dtv_z[n];
-    if (threadIdx.x < nl) txy[threadIdx.x] = dtv_x[i] + dtv_y[j0 + threadIdx.x];
-    __syncthreads();
+    if constexpr (!kAsyncTabs) {
+      const R *dtv_y = reinterpret_cast<const R *>(a.dtv[1]);
+      const R *dtv_z = reinterpret_cast<const R *>(a.dtv[2]);
+      for (int n = threadIdx.x; n < nz; n += blockDim.x) tz[n] = dtv_z[n];
+      if (threadIdx.x < nl) ty[threadIdx.x] = dtvx + dtv_y[j0 + threadIdx.x];   // dt (V_x + V_y) per line
+      __syncthreads();
+    }
     const R sr = R(s);
     const bool scaled = s != R(1);
     const R dtg = pick<R>(a.dtg, a.dtg_f, a.dtg_l), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f, a.dtgdd_n_l);
     // lines fastest: the padded tile rows (odd stride LS) and the pair-interleaved Phi are
     // read without bank conflicts
-    LinePos pos(threadIdx.x, nl, blockDim.x);   // pos.b = z index n, pos.k = line b
-    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
-      const int n = pos.b, b = pos.k;
-      const int q = b * LS + cn_slot(n, lc);
+    auto phase_at = [&](int n, int b, int q) {
       C v = tile[q];
       if (scaled) v = scale(v, sr);
       const C z = res[n * SB + (b >> 1)];
       const R phi = (b & 1) ? z.im : z.re;
       const R dens = v.re * v.re + v.im * v.im;
-      const R theta = fma(dtg, dens, fma(dtgdd, phi, txy[b] + tz[n]));
+      // dt (V_x + V_y): the async path copied dt V_y and adds dt V_x here (one FP32 add); the
+      // other path summed them per line
+      const R vxy = kAsyncTabs ? ty[b] + dtvx : ty[b];
+      const R theta = fma(dtg, dens, fma(dtgdd, phi, vxy + tz[n]));
       if (a.imag) {
         tile[q] = scale(v, exp_r(-theta));
       } else {
@@ -1802,6 +1861,19 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
         sin_cos(theta, &sn, &cs);
         tile[q] = {v.re * cs + v.im * sn, v.im * cs - v.re * sn};
       }
+    };
+    if constexpr (kWalk) {
+      // thread (line b, offset n0 < W): the points n0 + W i of line b, lines fastest
+      const int b = threadIdx.x % BZ, n0 = threadIdx.x / BZ;
+      if (b < nl) {
+        const SlotWalk<W> w(n0, lc);
+#pragma unroll 4
+        for (int i = 0; i < N / W; ++i) phase_at(n0 + W * i, b, b * LS + w(i, n0));
+      }
+    } else {
+      LinePos pos(threadIdx.x, nl, blockDim.x);   // pos.b = z index n, pos.k = line b
+      for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next())
+        phase_at(pos.b, pos.k, pos.k * LS + cn_slot(pos.b, lc));
     }
     __syncthreads();
   }
@@ -1815,9 +1887,20 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
     __syncthreads();
   }
 
-  LinePos pos(threadIdx.x, nz, blockDim.x);
+  if constexpr (kWalk) {
+    const int b = threadIdx.x / W, k0 = threadIdx.x % W;
+    if (b < nl) {
+      const SlotWalk<W> w(k0, lc);
+      const C *src = tile + b * LS;
+      C *dst = psi + (size_t)b * nz + k0;
+#pragma unroll 8
+      for (int j = 0; j < N / W; ++j) dst[W * j] = src[w(j, k0)];
+    }
+  } else {
+    LinePos pos(threadIdx.x, nz, blockDim.x);
 #pragma unroll 4
-  for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) psi[e] = tile[pos.b * LS + cn_slot(pos.k, lc)];
+    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) psi[e] = tile[pos.b * LS + cn_slot(pos.k, lc)];
+  }
 }
 // one condensate (G = false, its arguments passed by value), or condensate blockIdx.z of
 // a group of same-shaped condensates (G = true, the arguments from the device array ga)
@@ -1894,7 +1977,8 @@ __device__ __forceinline__ void finish_sweep_sums(const KArgs &a, double (&v)[4]
 // blockIdx.x, blockIdx.x + gridDim.x, ...; the cp.async copies of the next tile are in
 // flight while the current tile is solved and stored.
 // B columns (z) per tile, NT threads (B divides NT; one or two lines per warp).
-template <typename R, typename Coef, int AXIS, int B = Tiles<R>::kCnCols, int NT = Tiles<R>::kCnThreads>
+template <typename R, typename Coef, int AXIS, int B = Tiles<R>::kCnCols, int NT = Tiles<R>::kCnThreads,
+          bool FULL = false>
 __device__ __forceinline__ void k_cn_body(const KArgs &a, int reduce, int renorm) {
   static_assert(std::is_same<R, float>::value, "the chunked sweeps serve FP32 data");
   using C = cplx<R>;
@@ -1905,7 +1989,9 @@ __device__ __forceinline__ void k_cn_body(const KArgs &a, int reduce, int renorm
   const int nkt = (a.nz + B - 1) / B;
   const int ntiles = nfixed * nkt;
   const int lc = a.cn[AXIS].lchunk;
-  const int slots = cn_slots(N, lc);
+  // FULL: the lines padded to 32 chunks of unknowns (grid indices up to m_pad + 1)
+  const int m_pad = kWarp << lc;
+  const int slots = FULL ? cn_slots(m_pad + 2, lc) : cn_slots(N, lc);
   C *cur = reinterpret_cast<C *>(smem_raw);
   C *nxt = cur + slots * SB;
   Coef *stab = reinterpret_cast<Coef *>(nxt + slots * SB);     // factor tables, staged once
@@ -1914,7 +2000,8 @@ __device__ __forceinline__ void k_cn_body(const KArgs &a, int reduce, int renorm
   const size_t stride = AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
   C *gpsi = reinterpret_cast<C *>(a.psi);
   const int b = threadIdx.x % B;   // B divides the block size: the column is fixed per thread
-  const int n0 = threadIdx.x / B, nstep = blockDim.x / B;
+  const int n0 = threadIdx.x / B;
+  constexpr int nstep = NT / B;   // the launch has NT threads
   const bool do_reduce = AXIS == 0 && reduce;
 
   auto tile_origin = [&](int tile, int &fixed, int &k0) -> size_t {
@@ -1927,7 +2014,11 @@ __device__ __forceinline__ void k_cn_body(const KArgs &a, int reduce, int renorm
     const size_t base = tile_origin(tile, fixed, k0);
     if (b < min(B, a.nz - k0)) {
       const C *src = gpsi + base + b + (size_t)n0 * stride;
-      for (int n = n0; n < N; n += nstep, src += nstep * stride) cp_async(buf + cn_slot(n, lc) * SB + b, src);
+      const SlotWalk<NT / B> w(n0, lc);
+#pragma unroll 4
+      // (FULL: not the far wall, whose slot stays zero, as the padding's do)
+      const int nload = FULL ? N - 1 : N;
+      for (int j = 0; n0 + (NT / B) * j < nload; ++j, src += (NT / B) * stride) cp_async(buf + w(j, n0) * SB + b, src);
     }
     cp_async_commit();
   };
@@ -1943,6 +2034,13 @@ __device__ __forceinline__ void k_cn_body(const KArgs &a, int reduce, int renorm
   }
   const Coef *tab = stab;
   DFAcc acc[4];
+  if constexpr (FULL) {   // the far wall and the padding: zero in both buffers, once
+    for (int q = threadIdx.x; q < (m_pad + 2 - N) * SB; q += blockDim.x) {
+      const int g = N - 1 + q / SB, col = q % SB;
+      cur[cn_slot(g, lc) * SB + col] = czero<R>();
+      nxt[cn_slot(g, lc) * SB + col] = czero<R>();
+    }
+  }
 
   int tile = blockIdx.x;
   if (tile < ntiles) issue(tile, cur);
@@ -1959,14 +2057,15 @@ __device__ __forceinline__ void k_cn_body(const KArgs &a, int reduce, int renorm
     const size_t base = tile_origin(tile, fixed, k0);
     const int nb = min(B, a.nz - k0);
     for (int l = threadIdx.x / kWarp; l < nb; l += blockDim.x / kWarp)
-      cn_line_any<R, Coef, true>(cur + l, SB, a.cn[AXIS].m, lc, tab, tab + 4 * (kWarp << lc), c);
+      cn_line_any<R, Coef, true, FULL>(cur + l, SB, FULL ? m_pad : a.cn[AXIS].m, lc, tab, tab + 4 * (kWarp << lc), c);
     __syncthreads();
     if (b < nb) {
       DFAcc s0;   // this thread's share of the column: sum W_x n
       C *dst = gpsi + base + b + (size_t)n0 * stride;
+      const SlotWalk<NT / B> walk(n0, lc);
 #pragma unroll 4
-      for (int n = n0; n < N; n += nstep, dst += nstep * stride) {
-        const C w = cur[cn_slot(n, lc) * SB + b];
+      for (int j = 0, n = n0; n < N; ++j, n += nstep, dst += nstep * stride) {
+        const C w = cur[walk(j, n0) * SB + b];
         *dst = w;
         if (do_reduce) {
           const float d = fmaf(w.re, w.re, w.im * w.im);
@@ -1995,10 +2094,11 @@ __device__ __forceinline__ void k_cn_body(const KArgs &a, int reduce, int renorm
 }
 // one condensate (G = false, its arguments passed by value), or condensate blockIdx.z of
 // a group of same-shaped condensates (G = true, the arguments from the device array ga)
-template <typename R, typename Coef, int AXIS, int B = Tiles<R>::kCnCols, int NT = Tiles<R>::kCnThreads, bool G = false>
+template <typename R, typename Coef, int AXIS, int B = Tiles<R>::kCnCols, int NT = Tiles<R>::kCnThreads, bool G = false,
+          bool FULL = false>
 __global__ void __launch_bounds__(NT, 512 / NT) k_cn(KArgs a, const KArgs *ga, int reduce, int renorm) {
-  if constexpr (G) k_cn_body<R, Coef, AXIS, B, NT>(ga[blockIdx.z], reduce, renorm);
-  else k_cn_body<R, Coef, AXIS, B, NT>(a, reduce, renorm);
+  if constexpr (G) k_cn_body<R, Coef, AXIS, B, NT, FULL>(ga[blockIdx.z], reduce, renorm);
+  else k_cn_body<R, Coef, AXIS, B, NT, FULL>(a, reduce, renorm);
 }
 
 // FP64-class sweeps: two threads per line, the twisted ("burn at both ends") factorization.
@@ -2434,9 +2534,15 @@ struct Impl {
     }
     return n;
   }
+  // the chunked sweeps pad a line to 32 whole chunks (no per-point guard) when that adds at
+  // most two unknowns (the power-of-two lengths); the tile line then has 32 chunk + 2 points
+  static bool cn_full(const KArgs &a, int axis) { return (kWarp << a.cn[axis].lchunk) <= a.cn[axis].m + 2; }
+  static int cn_len(const KArgs &a, int axis) {
+    return cn_full(a, axis) ? (kWarp << a.cn[axis].lchunk) + 2 : a.cn[axis].m + 2;
+  }
   static dim3 grid_cn(const KArgs &a, int axis, int cols = T::kCnCols) {
     const int tiles = ((a.nz + cols - 1) / cols) * (axis == 0 ? a.ny : a.nx);
-    const int n = a.cn[axis].m + 2;
+    const int n = cn_len(a, axis);
     const size_t sm = smem_cn(n, a.cn[axis].lchunk, cols);
     const int fit = sm * 2 + 4096 <= 227 * 1024 ? 2 : 1;
     const int per_sm = a.cn_per_sm < fit ? (a.cn_per_sm < 1 ? 1 : a.cn_per_sm) : fit;
@@ -2522,10 +2628,15 @@ struct Impl {
       chk(allow_smem(k5_zline<R, C, kZFast, 128>));
     }
     if constexpr (!kCnThread) {
+      constexpr int B = T::kCnCols, NT = T::kCnThreads;
       chk(allow_smem(k_cn<R, R, 0>));
       chk(allow_smem(k_cn<R, R, 1>));
       chk(allow_smem(k_cn<R, C, 0>));
       chk(allow_smem(k_cn<R, C, 1>));
+      chk(allow_smem(k_cn<R, R, 0, B, NT, false, true>));
+      chk(allow_smem(k_cn<R, R, 1, B, NT, false, true>));
+      chk(allow_smem(k_cn<R, C, 0, B, NT, false, true>));
+      chk(allow_smem(k_cn<R, C, 1, B, NT, false, true>));
     }
     if constexpr (kRegFft) chk(init_reg());
     if constexpr (kAdjoint) chk(allow_smem(k5_adj_phase<R>));
@@ -2733,9 +2844,16 @@ struct Impl {
       if (a.imag) k_cn_twisted<R, R, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
       else k_cn_twisted<R, C, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
     } else {
-      const size_t sm = smem_cn(n, a.cn[AXIS].lchunk);
-      if (a.imag) k_cn<R, R, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, nullptr, reduce, renorm);
-      else k_cn<R, C, AXIS><<<grid_cn(a, AXIS), T::kCnThreads, sm, st>>>(a, nullptr, reduce, renorm);
+      constexpr int B = T::kCnCols, NT = T::kCnThreads;
+      const size_t sm = smem_cn(cn_len(a, AXIS), a.cn[AXIS].lchunk);
+      const dim3 g = grid_cn(a, AXIS);
+      if (cn_full(a, AXIS)) {
+        if (a.imag) k_cn<R, R, AXIS, B, NT, false, true><<<g, NT, sm, st>>>(a, nullptr, reduce, renorm);
+        else k_cn<R, C, AXIS, B, NT, false, true><<<g, NT, sm, st>>>(a, nullptr, reduce, renorm);
+      } else {
+        if (a.imag) k_cn<R, R, AXIS><<<g, NT, sm, st>>>(a, nullptr, reduce, renorm);
+        else k_cn<R, C, AXIS><<<g, NT, sm, st>>>(a, nullptr, reduce, renorm);
+      }
     }
     return cudaGetLastError();
   }
@@ -2862,6 +2980,10 @@ struct GroupLaunch {
     attr(k_cn<R, R, 1, T::kCnCols, T::kCnThreads, true>, e);
     attr(k_cn<R, C, 0, T::kCnCols, T::kCnThreads, true>, e);
     attr(k_cn<R, C, 1, T::kCnCols, T::kCnThreads, true>, e);
+    attr(k_cn<R, R, 0, T::kCnCols, T::kCnThreads, true, true>, e);
+    attr(k_cn<R, R, 1, T::kCnCols, T::kCnThreads, true, true>, e);
+    attr(k_cn<R, C, 0, T::kCnCols, T::kCnThreads, true, true>, e);
+    attr(k_cn<R, C, 1, T::kCnCols, T::kCnThreads, true, true>, e);
     return e;
   }
 
@@ -2912,8 +3034,11 @@ struct GroupLaunch {
   static void cn(const KArgs &a, const KArgs *ga, unsigned n, int reduce, int renorm, cudaStream_t st) {
     dim3 g = I::grid_cn(a, AXIS);
     g.z = n;
-    const size_t sm = I::smem_cn(AXIS == 0 ? a.nx : a.ny, a.cn[AXIS].lchunk);
-    k_cn<R, Co, AXIS, T::kCnCols, T::kCnThreads, true><<<g, T::kCnThreads, sm, st>>>(a, ga, reduce, renorm);
+    const size_t sm = I::smem_cn(I::cn_len(a, AXIS), a.cn[AXIS].lchunk);
+    if (I::cn_full(a, AXIS))
+      k_cn<R, Co, AXIS, T::kCnCols, T::kCnThreads, true, true><<<g, T::kCnThreads, sm, st>>>(a, ga, reduce, renorm);
+    else
+      k_cn<R, Co, AXIS, T::kCnCols, T::kCnThreads, true><<<g, T::kCnThreads, sm, st>>>(a, ga, reduce, renorm);
   }
   static cudaError_t step(const KArgs &a, const KArgs *ga, int count, int renorm, cudaStream_t st) {
     if (count < 1 || count > 65535) return cudaErrorInvalidValue;
