@@ -1655,24 +1655,32 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
   constexpr int W = Tiles<R>::kZThreads / BZ;
   constexpr bool kWalk = N > 0 && !Fp64Class<R>::value;
   static_assert(N % W == 0 && Tiles<R>::kZThreads % BZ == 0, "the walk covers whole lines");
-  if (zmode != kZPhi) {
-    if constexpr (kWalk) {
-      const int b = threadIdx.x / W, k0 = threadIdx.x % W;
-      if (b < nl) {
-        const SlotWalk<W> w(k0, lc);
-        C *dst = tile + b * LS;
-        const C *src = psi + (size_t)b * nz + k0;
+  // issued after the first batch of spectrum loads: the transform needs those first, so they
+  // go out ahead of the tile's copies
+  bool psi_issued = false;
+  auto issue_psi = [&]() {
+    if (psi_issued) return;
+    psi_issued = true;
+    if (zmode != kZPhi) {
+      if constexpr (kWalk) {
+        const int b = threadIdx.x / W, k0 = threadIdx.x % W;
+        if (b < nl) {
+          const SlotWalk<W> w(k0, lc);
+          C *dst = tile + b * LS;
+          const C *src = psi + (size_t)b * nz + k0;
 #pragma unroll 8
-        for (int j = 0; j < N / W; ++j) cp_async(dst + w(j, k0), src + W * j);
+          for (int j = 0; j < N / W; ++j) cp_async(dst + w(j, k0), src + W * j);
+        }
+      } else {
+        LinePos pos(threadIdx.x, nz, blockDim.x);
+        for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next())
+          cp_async(tile + pos.b * LS + cn_slot(pos.k, lc), psi + e);
       }
-    } else {
-      LinePos pos(threadIdx.x, nz, blockDim.x);
-      for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next())
-        cp_async(tile + pos.b * LS + cn_slot(pos.k, lc), psi + e);
     }
-  }
-  cp_async_commit();
+    cp_async_commit();
+  };
 
+  if (zmode == kZCnOnly) issue_psi();
   if (zmode != kZCnOnly) {
     const C *spec = reinterpret_cast<const C *>(a.spec) + line0;
     const size_t plane = (size_t)a.nx * a.ny;
@@ -1686,10 +1694,18 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
         for (int u = 0; u < kUnroll; ++u) {
           const int m = m0 + u * mstep;
           if (m < a.nzh) {
-            x1[u] = spec[m * plane + 2 * p];
-            x2[u] = spec[m * plane + 2 * p + 1];
+            if constexpr (std::is_same<R, float>::value) {
+              // the pair's two values are adjacent and 16-byte aligned (ny even): one load
+              const float4 q = *reinterpret_cast<const float4 *>(spec + m * plane + 2 * p);
+              x1[u] = {q.x, q.y};
+              x2[u] = {q.z, q.w};
+            } else {
+              x1[u] = spec[m * plane + 2 * p];
+              x2[u] = spec[m * plane + 2 * p + 1];
+            }
           }
         }
+        issue_psi();
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
           const int m = m0 + u * mstep;
@@ -1704,6 +1720,7 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
         }
       }
     }
+    issue_psi();   // (threads without spectrum rows)
     __syncthreads();
     res = fft_lines_n<R, +1, N, PZ, SB, Tiles<R>::kZThreads>(za, zb, a.plan[2], np,
                                                              reinterpret_cast<const C *>(a.tw[2]));
@@ -2069,7 +2086,7 @@ __device__ __forceinline__ void k_cn_body(const KArgs &a, int reduce, int renorm
         *dst = w;
         if (do_reduce) {
           const float d = fmaf(w.re, w.re, w.im * w.im);
-          s0.add(wxtab[n] * d);       // exact: W_x is 0, 1, 2 or 4
+          s0.add(a.simpson ? wxtab[n] * d : d);   // exact: W_x is 0, 1, 2 or 4 (1 without Simpson)
         }
       }
       if (do_reduce) {
