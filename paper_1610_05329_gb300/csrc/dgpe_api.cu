@@ -124,8 +124,16 @@ int check_physics(const dgpe_params *p) {
 }
 
 struct Layout {
-  size_t state, partials, tw[3], cn[3], cn_adj[3], dtv[3], psi, spec, utab, ybuf, total;
+  size_t state, partials, tw[3], cn[3], cn_adj[3], cnz, dtv[3], psi, spec, utab, ybuf, total;
 };
+
+// FP32 contexts whose compile-time K5 (nz = 128, 256, 384, 512) solves along z at a chunk
+// other than the sweeps' power of two (nz = 384: 12 points per lane) get their own tables.
+bool needs_cnz(const dgpe_params *p) {
+  const int nz = p->nz;
+  return p->precision == DGPE_MIXED && (nz == 128 || nz == 256 || nz == 384 || nz == 512) &&
+         k5_chunk(nz) != cn_chunk(nz);
+}
 
 Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
   const size_t e = (size_t)(p->precision == DGPE_MIXED ? 8 : 16);
@@ -146,6 +154,11 @@ Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
     off += align_up((size_t)(4 * cn_chunk(n[d]) + 11) * kWarp * e);
     L.cn_adj[d] = off;   // the same for dt -> -dt (adjoint)
     off += align_up((size_t)(4 * cn_chunk(n[d]) + 11) * kWarp * e);
+  }
+  L.cnz = 0;   // K5's z tables at their own chunk (FP32 where the compile-time K5 needs them)
+  if (needs_cnz(p)) {
+    L.cnz = off;
+    off += align_up((size_t)(4 * k5_chunk(p->nz) + 11) * kWarp * e);
   }
   for (int d = 0; d < 3; ++d) {
     L.dtv[d] = off;
@@ -439,6 +452,8 @@ int setup_tables(dgpe_ctx *c, bool cn_changed, bool ut_changed) {
     if (p->mode == DGPE_REAL_TIME)   // the adjoint sweep is the sweep with dt -> -dt
       jobs.job[jobs.n++] = {at(c, c->L.cn_adj[d]), c->args.cn[d].m, c->args.cn[d].chunk, -c->args.cn_r[d]};
   }
+  if (cn_changed && c->L.cnz)
+    jobs.job[jobs.n++] = {at(c, c->L.cnz), c->args.cn[2].m, k5_chunk(p->nz), c->args.cn_r[2]};
   if (jobs.n) {
     const int rc = map_cuda(c->ks->cn_tables(jobs, c->stream));
     if (rc) return rc;
@@ -671,6 +686,7 @@ int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out) {
   }
   a.utab = at(c, c->L.utab);
   a.ybuf = at(c, c->L.ybuf);
+  a.cnz_tab = c->L.cnz ? at(c, c->L.cnz) : nullptr;
   const int n[3] = {p->nx, p->ny, p->nz};
   rc = map_cuda(cudaMemsetAsync(a.psi, 0, (size_t)p->nx * p->ny * p->nz * c->ks->elem_bytes, c->stream));
   if (!rc) rc = map_cuda(c->ks->reset_state(a.state, c->stream));

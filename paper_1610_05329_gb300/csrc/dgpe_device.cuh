@@ -384,11 +384,28 @@ struct DFAcc {
 __host__ __device__ inline int cn_slot(int n, int lchunk) { return n + (max(n - 1, 0) >> lchunk); }
 __host__ __device__ inline int cn_slots(int n, int lchunk) { return n + ((n - 2) >> lchunk); }
 
+// K5's tile stride (slots per line) at a compile-time length n (FP32): the padded line of
+// 32 k5_chunk(n) + 2 points with one pad slot per chunk, rounded up to an odd stride.
+__host__ __device__ constexpr int k5_tile_stride(int n) { return kWarp * k5_chunk(n) + 35; }
+
 // Points n = k0 + W j (j = 0, 1, ...) of a line in a Crank-Nicolson tile, for W a multiple of
 // the chunk: their slots cn_slot(n) = n + ((n - 1) >> lchunk) advance by the constant
 // W + (W >> lchunk), from k0 + ((k0 - 1) >> lchunk) (an arithmetic shift: -1 for k0 = 0,
 // where the wall n = 0 itself is slot 0).  The tile loops of the compile-time line lengths
 // walk their points this way instead of recomputing the slot and the line of every point.
+// The same for any chunk CH (K5's z solve at 12 points per lane): period P = lcm(W, CH);
+// a thread at offset o < P walks n = o + P j, slot n + (n - 1)/CH = base + j (P + P/CH),
+// base = o + (o - 1)/CH (-1 for o = 0, with the wall n = 0 at slot 0).
+template <int P, int CH>
+struct SlotWalkP {
+  static_assert(P % CH == 0, "whole chunks per period");
+  int base;
+  static constexpr int step = P + P / CH;
+  __device__ __forceinline__ explicit SlotWalkP(int o) : base(o == 0 ? -1 : o + (o - 1) / CH) {}
+  __device__ __forceinline__ int operator()(int j, int o) const { return (o | j) == 0 ? 0 : base + j * step; }
+};
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+
 template <int W>
 struct SlotWalk {
   int base, step;
@@ -803,7 +820,7 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   constexpr int chunk = CH;
   const int s0 = t * chunk;
   const int len = FULL ? CH : max(0, min(chunk, m - s0));
-  const int mp = kWarp << lchunk;
+  constexpr int mp = kWarp * CH;
   const Coef *alpha = tab + t;
   const Coef *beta = tab + mp + t;
   const Coef *H = tab + 2 * mp + t;
@@ -1276,6 +1293,23 @@ __device__ __forceinline__ void k1_density_r2cz_body(const KArgs &a) {
   // the exponent (half_density) instead of a multiply on the FP64 pipe
   auto fill = [&](auto halve) {
     constexpr bool kHalve = decltype(halve)::value;
+    if constexpr (N > 0 && !Fp64Class<R>::value) {
+      // FP32, compile-time length: thread (line b, offset k0 < W) takes the points k0 + W j of
+      // line b (a line per half-warp: coalesced loads, and the 4-byte stores into the
+      // pair-interleaved buffer (stride SB = 9 pairs) fall on 16 distinct banks per line)
+      constexpr int W = Tiles<R>::kZThreads / BZ;
+      const int b = threadIdx.x / W, k0 = threadIdx.x % W;
+      if (b < nl) {
+        const C *src = psi + (size_t)b * nz + k0;
+        R *z = reinterpret_cast<R *>(za + k0 * SB + (b >> 1)) + (b & 1);
+#pragma unroll 8
+        for (int j = 0; j < N / W; ++j) {
+          const C v = src[W * j];
+          z[2 * SB * W * j] = s2 * (v.re * v.re + v.im * v.im);
+        }
+      }
+      return;
+    }
     LinePos pos(threadIdx.x, nz, blockDim.x);
     for (int e0 = threadIdx.x; e0 < total; e0 += kUnroll * blockDim.x) {
       C v[kUnroll];
@@ -1609,7 +1643,17 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
   const int nz = N > 0 ? N : a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
   const int nl = min(BZ, a.ny - j0), np = nl >> 1;
   const int lc = a.cn[2].lchunk;
-  const int LS = cn_slots(nz, lc);
+  // Compile-time lengths (FP32, the fused step): the z solve takes CHZ = k5_chunk(N) points
+  // per lane on a line padded to 32 CHZ unknowns (every lane busy, no per-point guard), the
+  // tile one pad slot per CHZ points, lines kept at an odd stride (distinct banks across
+  // lines); the tile loops walk period PW = lcm(W, CHZ) (W = threads / lines).
+  constexpr int W = Tiles<R>::kZThreads / BZ;
+  constexpr bool kWalk = N > 0 && !Fp64Class<R>::value;
+  constexpr int CHZ = kWalk ? k5_chunk(N) : 1;
+  constexpr int PW = kWalk ? W / gcd_c(W, CHZ) * CHZ : W;
+  constexpr int SUBS = PW / W;
+  static_assert(!kWalk || (N % PW == 0 && zmode == kZStep), "compile-time FP32 instances: the fused step");
+  const int LS = kWalk ? k5_tile_stride(N) : cn_slots(nz, lc);
   C *za = reinterpret_cast<C *>(smem_raw);
   C *zb = za + nz * SB;
   C *tile = zb + nz * SB;
@@ -1631,8 +1675,11 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
   const bool phase = zmode == kZStep || zmode == kZPhaseOnly;
   R dtvx = R(0);
   if (phase) dtvx = reinterpret_cast<const R *>(a.dtv[0])[i];
+  // the z solve's tables: K5's own at CHZ points per lane where that is not the sweeps' chunk
+  const Coef *ztab_g = reinterpret_cast<const Coef *>(kWalk && a.cnz_tab ? a.cnz_tab : a.cn[2].tab);
+  const int zmp = kWalk ? kWarp * CHZ : (kWarp << lc);
   if (zmode == kZStep || zmode == kZCnOnly) {
-    const Coef *gscan = reinterpret_cast<const Coef *>(a.cn[2].tab) + 4 * (kWarp << lc);
+    const Coef *gscan = ztab_g + 4 * zmp;
     if constexpr (kAsyncTabs) {
       constexpr int chunks = 10 * kWarp * (int)sizeof(Coef) / 16;
       for (int q = threadIdx.x; q < chunks; q += blockDim.x)
@@ -1652,8 +1699,6 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
   // psi tile: asynchronous copies, overlapped with the spectrum load and the C2R transform.
   // Compile-time lengths: thread (line b, offset k0 < W) copies the points k0 + W j of its
   // line (W = threads / lines: 16 consecutive points of a line per half-warp, coalesced).
-  constexpr int W = Tiles<R>::kZThreads / BZ;
-  constexpr bool kWalk = N > 0 && !Fp64Class<R>::value;
   static_assert(N % W == 0 && Tiles<R>::kZThreads % BZ == 0, "the walk covers whole lines");
   // issued after the first batch of spectrum loads: the transform needs those first, so they
   // go out ahead of the tile's copies
@@ -1665,11 +1710,15 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
       if constexpr (kWalk) {
         const int b = threadIdx.x / W, k0 = threadIdx.x % W;
         if (b < nl) {
-          const SlotWalk<W> w(k0, lc);
           C *dst = tile + b * LS;
-          const C *src = psi + (size_t)b * nz + k0;
+#pragma unroll
+          for (int sub = 0; sub < SUBS; ++sub) {
+            const int o = k0 + W * sub;
+            const SlotWalkP<PW, CHZ> w(o);
+            const C *src = psi + (size_t)b * nz + o;
 #pragma unroll 8
-          for (int j = 0; j < N / W; ++j) cp_async(dst + w(j, k0), src + W * j);
+            for (int j = 0; j < N / PW; ++j) cp_async(dst + w(j, o), src + PW * j);
+          }
         }
       } else {
         LinePos pos(threadIdx.x, nz, blockDim.x);
@@ -1737,8 +1786,8 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
     static_assert(N >= 64, "the staged tables fit the spare transform buffer");
     if (zmode == kZStep || zmode == kZCnOnly) {
       C *spare = (zmode == kZCnOnly || res != za) ? za : zb;
-      const int bytes = 4 * (kWarp << lc) * (int)sizeof(Coef);
-      const uint4 *src = reinterpret_cast<const uint4 *>(a.cn[2].tab);
+      const int bytes = 4 * zmp * (int)sizeof(Coef);
+      const uint4 *src = reinterpret_cast<const uint4 *>(ztab_g);
       uint4 *dst = reinterpret_cast<uint4 *>(spare);
       for (int q = threadIdx.x; q < bytes / 16; q += blockDim.x) cp_async(dst + q, src + q);
       ztab = reinterpret_cast<const Coef *>(spare);
@@ -1880,12 +1929,16 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
       }
     };
     if constexpr (kWalk) {
-      // thread (line b, offset n0 < W): the points n0 + W i of line b, lines fastest
+      // thread (line b, offset n0 < W): the points n0 + W sub + PW i of line b, lines fastest
       const int b = threadIdx.x % BZ, n0 = threadIdx.x / BZ;
       if (b < nl) {
-        const SlotWalk<W> w(n0, lc);
+#pragma unroll
+        for (int sub = 0; sub < SUBS; ++sub) {
+          const int o = n0 + W * sub;
+          const SlotWalkP<PW, CHZ> w(o);
 #pragma unroll 4
-        for (int i = 0; i < N / W; ++i) phase_at(n0 + W * i, b, b * LS + w(i, n0));
+          for (int i = 0; i < N / PW; ++i) phase_at(o + PW * i, b, b * LS + w(i, o));
+        }
       }
     } else {
       LinePos pos(threadIdx.x, nl, blockDim.x);   // pos.b = z index n, pos.k = line b
@@ -1896,22 +1949,39 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
   }
 
   if (zmode == kZStep || zmode == kZCnOnly) {
+    if constexpr (kWalk) {
+      // the padded solve: the far wall (grid N - 1, which the phase loop has written) and the
+      // points beyond it, up to the padded length 32 CHZ, hold zero; after the phase loop's
+      // barrier, before the solve's
+      constexpr int kPad = kWarp * CHZ + 2 - N;
+      static_assert(kPad >= 1 && kPad * BZ <= Tiles<R>::kZThreads, "a thread per padded slot");
+      if (threadIdx.x < BZ * kPad) {
+        const int b = threadIdx.x / kPad, g = N - 1 + threadIdx.x % kPad;
+        tile[b * LS + g + (g - 1) / CHZ] = czero<R>();
+      }
+    }
     cp_async_wait_group<0>();
     __syncthreads();
     const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[2], a.cn_rf[2], a.cn_rl[2]));
-    for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp)
-      cn_line_any<R, Coef, (N > 0)>(tile + b * LS, 1, a.cn[2].m, lc, ztab, scan_s, c);
+    for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp) {
+      if constexpr (kWalk) cn_line<R, Coef, CHZ, true, true>(tile + b * LS, 1, kWarp * CHZ, lc, ztab, scan_s, c);
+      else cn_line_any<R, Coef, (N > 0)>(tile + b * LS, 1, a.cn[2].m, lc, ztab, scan_s, c);
+    }
     __syncthreads();
   }
 
   if constexpr (kWalk) {
     const int b = threadIdx.x / W, k0 = threadIdx.x % W;
     if (b < nl) {
-      const SlotWalk<W> w(k0, lc);
       const C *src = tile + b * LS;
-      C *dst = psi + (size_t)b * nz + k0;
+#pragma unroll
+      for (int sub = 0; sub < SUBS; ++sub) {
+        const int o = k0 + W * sub;
+        const SlotWalkP<PW, CHZ> w(o);
+        C *dst = psi + (size_t)b * nz + o;
 #pragma unroll 8
-      for (int j = 0; j < N / W; ++j) dst[W * j] = src[w(j, k0)];
+        for (int j = 0; j < N / PW; ++j) dst[PW * j] = src[w(j, o)];
+      }
     }
   } else {
     LinePos pos(threadIdx.x, nz, blockDim.x);
@@ -2032,9 +2102,9 @@ __device__ __forceinline__ void k_cn_body(const KArgs &a, int reduce, int renorm
     if (b < min(B, a.nz - k0)) {
       const C *src = gpsi + base + b + (size_t)n0 * stride;
       const SlotWalk<NT / B> w(n0, lc);
-#pragma unroll 4
       // (FULL: not the far wall, whose slot stays zero, as the padding's do)
       const int nload = FULL ? N - 1 : N;
+#pragma unroll 4
       for (int j = 0; n0 + (NT / B) * j < nload; ++j, src += (NT / B) * stride) cp_async(buf + w(j, n0) * SB + b, src);
     }
     cp_async_commit();
@@ -2528,7 +2598,11 @@ struct Impl {
 
   static size_t smem_z_fft(const KArgs &a) { return 2 * (size_t)a.nz * (T::kZLines / 2 + 1) * E; }
   static size_t smem_k5(const KArgs &a) {
-    return 2 * (size_t)a.nz * (T::kZLines / 2) * E + (size_t)T::kZLines * cn_slots(a.nz, a.cn[2].lchunk) * E +
+    // the tile: the sweeps' layout, or (FP32, compile-time lengths) K5's padded one
+    int ls = cn_slots(a.nz, a.cn[2].lchunk);
+    if (std::is_same<R, float>::value && (a.nz == 128 || a.nz == 256 || a.nz == 384 || a.nz == 512))
+      ls = std::max(ls, k5_tile_stride(a.nz));
+    return 2 * (size_t)a.nz * (T::kZLines / 2) * E + (size_t)T::kZLines * ls * E +
            (size_t)(a.nz + T::kZLines) * sizeof(R) + (size_t)10 * kWarp * E;
   }
   static size_t smem_y(const KArgs &a) { return 2 * (size_t)a.ny * (a.ylines + 1) * E; }

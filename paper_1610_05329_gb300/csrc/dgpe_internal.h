@@ -34,7 +34,12 @@ struct CnJob {
   int m, chunk;
   double r;   // dt / (4 h^2), negated for the adjoint tables
 };
-constexpr int kMaxCnJobs = 6;
+constexpr int kMaxCnJobs = 8;
+
+// Interior points per lane of K5's z solve at a compile-time length n: the least chunk with
+// 32 chunks covering the n - 2 unknowns (12 for n = 384; the sweeps' power of two for 128,
+// 256, 512), so that the line pads to 32 whole chunks with at most a few padded unknowns.
+__host__ __device__ constexpr int k5_chunk(int n) { return (n - 2 + 31) / 32; }
 struct CnJobs {
   CnJob job[kMaxCnJobs];
   int n;
@@ -95,6 +100,8 @@ struct KArgs {
   const void *tw[3];           // per-stage twiddle tables of plan[d] (layout in FftPlan), d = x, y, z
   FftPlan plan[3];
   CnTab cn[3];
+  const void *cnz_tab;         // K5's z tables at k5_chunk(nz) points per lane, where that is not
+                               // cn[2].chunk (FP32, compile-time nz); else null
   void *out;                   // optional output (Phi for get_phi)
   // adjoint step
   void *gbar;                  // cotangent field (same layout as psi)
