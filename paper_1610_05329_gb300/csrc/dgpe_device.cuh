@@ -1506,28 +1506,36 @@ __device__ __forceinline__ void reg_fft(cplx<float> (&v)[8], cplx<float> *__rest
   using F = RegFft<N>;
   using C = cplx<float>;
   constexpr int T = F::T, Q = F::Q, U = 8 / Q;
+  // the padded indices, pad(i) = i + i/8, are linear in the unrolled counters (T and 64 are
+  // multiples of 8): computed once per thread, the rest are immediate offsets
+  //   stage 1 writes pad(8 t + s)             = 9 t + s (s < 8)
+  //   stage 2 reads  pad(t + T r)             = (t + t/8) + r (9 T / 8)
+  //   stage 2 writes pad(8 (t - k) + k + 8 s) = 72 (t/8) + k + 9 s,  k = t mod 8
+  //   stage 3 reads  pad(j + 64 r)            = (j + j/8) + 72 r,    j = t + T u
+  const int rd = t + (t >> 3);
   butterfly<float, DIR, 8>(v);
 #pragma unroll
-  for (int s = 0; s < 8; ++s) sa[F::pad(8 * t + s) * LS] = v[s];
+  for (int s = 0; s < 8; ++s) sa[(9 * t + s) * LS] = v[s];
   sync();
   {
     const int k = t & 7;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) v[r] = sa[F::pad(t + T * r) * LS];
+    for (int r = 0; r < 8; ++r) v[r] = sa[(rd + r * (9 * T / 8)) * LS];
 #pragma unroll
     for (int r = 1; r < 8; ++r) v[r] = twiddle<DIR>(v[r], ldg(tw + 7 + k * 7 + r - 1));
     butterfly<float, DIR, 8>(v);
-    const int base = 8 * (t - k) + k;
+    const int wr = 72 * (t >> 3) + k;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) sb[F::pad(base + 8 * s) * LS] = v[s];
+    for (int s = 0; s < 8; ++s) sb[(wr + 9 * s) * LS] = v[s];
   }
   sync();
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int j = t + T * u;
+    const int rj = rd + T * u + (T / 8) * u;   // pad(j): T u is a multiple of 8
     C w[Q];
 #pragma unroll
-    for (int r = 0; r < Q; ++r) w[r] = sb[F::pad(j + 64 * r) * LS];
+    for (int r = 0; r < Q; ++r) w[r] = sb[(rj + 72 * r) * LS];
 #pragma unroll
     for (int r = 1; r < Q; ++r) w[r] = twiddle<DIR>(w[r], ldg(tw + 63 + j * (Q - 1) + r - 1));
     butterfly<float, DIR, Q>(w);
