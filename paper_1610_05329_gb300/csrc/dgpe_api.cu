@@ -658,6 +658,11 @@ int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out) {
   c->args.ylines = c->ks->default_ylines(p->ny);
   c->args.fft_threads = 256;
   c->args.cn_per_sm = 2;
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      c->args.nsm = nsm;
+  }
   rc = map_cuda(c->ks->init());
   if (!rc) rc = map_cuda(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   if (!rc) {

@@ -349,6 +349,12 @@ __device__ __forceinline__ void cp_async(C *dst, const C *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Bulk prefetch of bytes [p, p + n) into L2 (no destination, no completion to wait for):
+// p 16-byte aligned, n a multiple of 16.  The tile kernels that run in waves of CTAs use it
+// to fetch the rows of the tile that a CTA one resident wave later will load.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned n) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(__cvta_generic_to_global(p)), "r"(n) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -1308,6 +1314,14 @@ __device__ __forceinline__ void k1_density_r2cz_body(const KArgs &a) {
           z[2 * SB * W * j] = s2 * (v.re * v.re + v.im * v.im);
         }
       }
+      // the psi rows of the CTA one resident wave ahead into L2 (residency: the CTAs whose
+      // two transform buffers fit the SM's shared memory, at most 6 by registers)
+      constexpr int kRes = (228 * 1024) / (2 * N * SB * (int)sizeof(C) + 1024) < 6 ? (228 * 1024) / (2 * N * SB * (int)sizeof(C) + 1024) : 6;
+      const int nbx = gridDim.x, L = blockIdx.y * nbx + blockIdx.x + kRes * a.nsm;
+      if (threadIdx.x == 0 && a.nsm > 0 && L < nbx * (int)gridDim.y) {
+        const int i2 = L / nbx, j2 = (L - i2 * nbx) * BZ;
+        prefetch_l2(reinterpret_cast<const C *>(a.psi) + ((size_t)i2 * a.ny + j2) * nz, min(BZ, a.ny - j2) * nz * (unsigned)sizeof(C));
+      }
       return;
     }
     LinePos pos(threadIdx.x, nz, blockDim.x);
@@ -1778,6 +1792,21 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
       }
     }
     issue_psi();   // (threads without spectrum rows)
+    if constexpr (kWalk) {
+      // the rows of tile L + ahead (L the linear CTA index, ahead the CTAs resident at once):
+      // that CTA starts about when this one ends and finds its spectrum and psi rows in L2
+      const int ahead = Tiles<R>::kZMinBlocks * a.nsm;
+      const int nbx = gridDim.x, L = blockIdx.y * nbx + blockIdx.x + ahead;
+      if (ahead > 0 && L < nbx * (int)gridDim.y) {
+        const int i2 = L / nbx, j2 = (L - i2 * nbx) * BZ;
+        const int nl2 = min(BZ, a.ny - j2);   // even: 16-byte multiples
+        const size_t l2 = (size_t)i2 * a.ny + j2;
+        const C *sp2 = reinterpret_cast<const C *>(a.spec) + l2;
+        for (int m = threadIdx.x; m < a.nzh; m += blockDim.x) prefetch_l2(sp2 + m * plane, nl2 * (unsigned)sizeof(C));
+        if (threadIdx.x == blockDim.x - 1)
+          prefetch_l2(reinterpret_cast<const C *>(a.psi) + l2 * nz, nl2 * nz * (unsigned)sizeof(C));
+      }
+    }
     __syncthreads();
     res = fft_lines_n<R, +1, N, PZ, SB, Tiles<R>::kZThreads>(za, zb, a.plan[2], np,
                                                              reinterpret_cast<const C *>(a.tw[2]));

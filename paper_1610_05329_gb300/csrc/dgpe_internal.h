@@ -112,6 +112,8 @@ struct KArgs {
   int ylines;                  // K2/K4 lines per CTA (power of two, <= 32)
   int fft_threads;             // K2/K3/K4 threads per CTA (128 or 256)
   int cn_per_sm;               // K6/K7 persistent CTAs per SM (1 or 2; capped by shared memory)
+  int nsm;                     // SMs of the device: the FP32 tile kernels prefetch into L2 the tile of
+                               // the CTA one resident wave ahead (residency x nsm; 0: no prefetch)
 };
 
 // Modes of the z-line kernel (C2R along z + potential step + CN along z).
