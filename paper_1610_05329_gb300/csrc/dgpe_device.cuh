@@ -3160,7 +3160,10 @@ struct GroupLaunch {
   }
   template <typename Co, int AXIS>
   static void cn(const KArgs &a, const KArgs *ga, unsigned n, int reduce, int renorm, cudaStream_t st) {
+    // one resident wave for the whole group: each member's share of the persistent CTAs,
+    // so that every CTA stages the factor tables once for many tiles and prefetches
     dim3 g = I::grid_cn(a, AXIS);
+    g.x = (g.x + n - 1) / n;
     g.z = n;
     const size_t sm = I::smem_cn(I::cn_len(a, AXIS), a.cn[AXIS].lchunk);
     if (I::cn_full(a, AXIS))
