@@ -2672,7 +2672,9 @@ struct Impl {
     const int tiles = ((a.nz + cols - 1) / cols) * (axis == 0 ? a.ny : a.nx);
     const int n = cn_len(a, axis);
     const size_t sm = smem_cn(n, a.cn[axis].lchunk, cols);
-    const int fit = sm * 2 + 4096 <= 227 * 1024 ? 2 : 1;
+    // co-resident CTAs per SM: by shared memory, and by registers (NT threads of up to 128)
+    const int fit_regs = 65536 / (T::kCnThreads * 128) < 1 ? 1 : 65536 / (T::kCnThreads * 128);
+    const int fit = std::min(sm * 2 + 4096 <= 227 * 1024 ? 2 : 1, fit_regs);
     const int per_sm = a.cn_per_sm < fit ? (a.cn_per_sm < 1 ? 1 : a.cn_per_sm) : fit;
     const int cap = sm_count() * per_sm;
     return dim3(tiles < cap ? tiles : cap);
@@ -3163,7 +3165,7 @@ struct GroupLaunch {
     // one resident wave for the whole group: each member's share of the persistent CTAs,
     // so that every CTA stages the factor tables once for many tiles and prefetches
     dim3 g = I::grid_cn(a, AXIS);
-    g.x = (g.x + n - 1) / n;
+    g.x = g.x / n < 1 ? 1 : g.x / n;
     g.z = n;
     const size_t sm = I::smem_cn(I::cn_len(a, AXIS), a.cn[AXIS].lchunk);
     if (I::cn_full(a, AXIS))
