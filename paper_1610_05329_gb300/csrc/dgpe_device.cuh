@@ -819,14 +819,18 @@ __device__ __forceinline__ cplx<R> *fft_lines_n(cplx<R> *a, cplx<R> *b, const Ff
 // ---------------------------------------------------------------------------------------
 // FULL: the line is padded to 32 CH unknowns (m = 32 CH; the padded slots hold zeros and the
 // tables decouple them), so every lane has a whole chunk and no per-point guard.
-template <typename R, typename Coef, int CH, bool SHARED_TAB, bool FULL = false>
+// L: lanes per line (32, or 8 for the short lines: four lines per warp, lanes 8g .. 8g + 7,
+// log2(L) scan steps; the tables in the L-lane layout).
+template <typename R, typename Coef, int CH, bool SHARED_TAB, bool FULL = false, int L = kWarp>
 __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m, int lchunk,
                                         const Coef *__restrict__ tab, const Coef *__restrict__ scan_s, Coef c) {
-  const int t = threadIdx.x & (kWarp - 1);
+  static_assert(L == kWarp || L == 8, "32 or 8 lanes per line");
+  constexpr int LG = L == kWarp ? 5 : 3;
+  const int t = threadIdx.x & (L - 1);
   constexpr int chunk = CH;
   const int s0 = t * chunk;
   const int len = FULL ? CH : max(0, min(chunk, m - s0));
-  constexpr int mp = kWarp * CH;
+  constexpr int mp = L * CH;
   const Coef *alpha = tab + t;
   const Coef *beta = tab + mp + t;
   const Coef *H = tab + 2 * mp + t;
@@ -844,16 +848,17 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   for (int e = 0; e < CH; ++e) {
     if (e < len) {
       const int i = s0 + e;
-      acc = cfma(T(alpha + e * kWarp), acc, buf[(i + 1 + t) * es]);
+      acc = cfma(T(alpha + e * L), acc, buf[(i + 1 + t) * es]);
       y[e] = acc;
     }
   }
-  // forward carries: Y_{t+1} = A_t Y_t + B_t, Y_0 = 0
+  // forward carries: Y_{t+1} = A_t Y_t + B_t, Y_0 = 0 (the shuffles span the warp; a lane
+  // takes a neighbour's value only within its own line's L lanes)
   cplx<R> B = acc;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < LG; ++k) {
     const cplx<R> Bp = shfl_up(B, 1 << k);
-    if (t >= (1 << k)) B = cfma(scan[k * kWarp], Bp, B);
+    if (t >= (1 << k)) B = cfma(scan[k * L], Bp, B);
   }
   cplx<R> Y = shfl_up(B, 1);
   if (t == 0) Y = czero<R>();
@@ -862,25 +867,25 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
 #pragma unroll
   for (int e = CH - 1; e >= 0; --e) {
     if (e < len) {
-      acc = mul(T(beta + e * kWarp), cfma_c(c, acc, y[e]));
+      acc = mul(T(beta + e * L), cfma_c(c, acc, y[e]));
       y[e] = acc;
     }
   }
   // backward carries: X_t = G_{s0} X_{t+1} + (chi0_{s0} + H_{s0} Y_t), X_32 = 0
   cplx<R> B2 = len > 0 ? cfma(T(H), Y, acc) : czero<R>();
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < LG; ++k) {
     const cplx<R> Bn = shfl_down(B2, 1 << k);
-    if (t + (1 << k) < kWarp) B2 = cfma(scan[(5 + k) * kWarp], Bn, B2);
+    if (t + (1 << k) < L) B2 = cfma(scan[(LG + k) * L], Bn, B2);
   }
   cplx<R> X = shfl_down(B2, 1);
-  if (t == kWarp - 1) X = czero<R>();
+  if (t == L - 1) X = czero<R>();
 
 #pragma unroll
   for (int e = 0; e < CH; ++e) {
     if (e < len) {
       const int i = s0 + e;
-      const cplx<R> chi = cfma(T(H + e * kWarp), Y, cfma(T(G + e * kWarp), X, y[e]));
+      const cplx<R> chi = cfma(T(H + e * L), Y, cfma(T(G + e * L), X, y[e]));
       const int q = (i + 1 + t) * es;
       const cplx<R> v = buf[q];
       buf[q] = {twice_minus(chi.re, v.re), twice_minus(chi.im, v.im)};
@@ -1108,10 +1113,11 @@ __global__ void k_cn_tables(CnJobs jobs) {
   const CnJob &jb = jobs.job[blockIdx.x];
   Coef *tab = static_cast<Coef *>(jb.tab);
   const int m = jb.m, chunk = jb.chunk, imag = jobs.imag;
+  const int L = jb.lanes == 8 ? 8 : kWarp, lg = L == 8 ? 3 : 5;   // lanes per line, log2
   const double r = jb.r;
-  // lane-interleaved layout: interior point i = t*chunk + e of table q at q*mp + e*32 + t
-  const int mp = kWarp * chunk;
-  auto at = [&](int q, int i) { return q * mp + (i % chunk) * kWarp + i / chunk; };
+  // lane-interleaved layout: interior point i = t*chunk + e of table q at q*mp + e*L + t
+  const int mp = L * chunk;
+  auto at = [&](int q, int i) { return q * mp + (i % chunk) * L + i / chunk; };
   const Z64 c = imag ? Z64{r, 0.0} : Z64{0.0, r};
   const Z64 diag = {1.0 + 2.0 * c.re, 2.0 * c.im};
   const Z64 one = {1.0, 0.0};
@@ -1121,10 +1127,10 @@ __global__ void k_cn_tables(CnJobs jobs) {
   Z64 e_prev = diag;
   const int h = m / 2;   // the twist point of the two-thread (twisted) sweeps
   Z64 e_h = diag, e_hm = diag;
-  // all 32 chunks: positions i >= m are padding, decoupled (alpha = 0, e = 1), so a solve
+  // all L chunks: positions i >= m are padding, decoupled (alpha = 0, e = 1), so a solve
   // over the padded length with zero values there gives zero there and leaves the m real
   // unknowns exactly as they are (the padding only ever multiplies zeros)
-  for (int s0 = 0; s0 < kWarp * chunk; s0 += chunk) {
+  for (int s0 = 0; s0 < L * chunk; s0 += chunk) {
     const int end = s0 + chunk - 1;
     for (int i = s0; i <= end; ++i) {
       Z64 a = {0.0, 0.0}, e = diag;
@@ -1164,16 +1170,17 @@ __global__ void k_cn_tables(CnJobs jobs) {
   }
   // Kogge-Stone scan factors: before step k (offset d = 2^k) lane t holds the product of
   // the factors of lanes t - 2^k + 1 .. t (forward) or t .. t + 2^k - 1 (backward).
-  for (int k = 0, d = 1; d < kWarp; ++k, d <<= 1) {
-    for (int t = 0; t < kWarp; ++t) {
-      store_coef<R>(tab, 4 * mp + k * kWarp + t, fa[t]);
-      store_coef<R>(tab, 4 * mp + (5 + k) * kWarp + t, ba[t]);
+  // Layout: forward step k at 4 mp + k L + t, backward step k at 4 mp + (lg + k) L + t.
+  for (int k = 0, d = 1; d < L; ++k, d <<= 1) {
+    for (int t = 0; t < L; ++t) {
+      store_coef<R>(tab, 4 * mp + k * L + t, fa[t]);
+      store_coef<R>(tab, 4 * mp + (lg + k) * L + t, ba[t]);
     }
-    for (int t = kWarp - 1; t >= d; --t) fa[t] = zmul(fa[t], fa[t - d]);
-    for (int t = 0; t + d < kWarp; ++t) ba[t] = zmul(ba[t], ba[t + d]);
+    for (int t = L - 1; t >= d; --t) fa[t] = zmul(fa[t], fa[t - d]);
+    for (int t = 0; t + d < L; ++t) ba[t] = zmul(ba[t], ba[t + d]);
   }
   // 1/gamma, gamma = e_h + e_{m-1-h} - (1 + 2c): the pivot of the twist point
-  store_coef<R>(tab, 4 * mp + 10 * kWarp, zdiv(one, Z64{e_h.re + e_hm.re - diag.re, e_h.im + e_hm.im - diag.im}));
+  store_coef<R>(tab, 4 * mp + 2 * lg * L, zdiv(one, Z64{e_h.re + e_hm.re - diag.re, e_h.im + e_hm.im - diag.im}));
 }
 
 // dt v_d x_i^2 on one axis, x_i = (i - n/2) h (the potential-step angle, per axis).
@@ -2225,6 +2232,140 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_cn(KArgs a, const KArgs *ga, i
   else k_cn_body<R, Coef, AXIS, B, NT, FULL>(a, reduce, renorm);
 }
 
+// K6 / K7 for short FP32 lines of n = 8 CH points (CH = short_cn_chunk(n) = 4 .. 16): the
+// chunked solve on 8 lanes per line, CH points each (three scan steps instead of five, whose
+// cost per point on 32 lanes of 4 points outweighed the solve), four lines per warp, 4 warps
+// and 16 columns per tile, up to four CTAs per SM; persistent and double-buffered as k_cn.
+// The line is padded to the 8 CH unknowns of grid indices 1 .. n: the far wall n - 1 and the
+// slot n beyond it hold zero, and the tables (8-lane layout) decouple them.  Slot of grid
+// index g: g + (g - 1) / CH (slot 0 the wall g = 0).  The four lines of warp w are the columns
+// 2w, 2w + 8, 2w + 1 and 2w + 9: the two lines of a half-warp fall on distinct banks.
+template <typename Coef, int AXIS, int CH>
+__device__ __forceinline__ void k_cn_short_body(const KArgs &a, int reduce, int renorm) {
+  using R = float;
+  using C = cplx<float>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int L = 8, B = 16, NT = 128, SB = B + 1;
+  constexpr int N = L * CH;                     // the line length
+  constexpr int SLOTS = N + 2 + N / CH;         // grid indices 0 .. N + 1
+  constexpr int W = NT / B;                     // rows per pass of the tile loops
+  constexpr int P = W / gcd_c(W, CH) * CH;      // lcm(W, CH): the rows' slot walk period
+  constexpr int NTAB = 4 * L * CH + 6 * L;      // alpha, beta, H, G, then the scan factors
+  static_assert(N % P == 0 && P % W == 0, "whole periods per line");
+  const int nkt = (a.nz + B - 1) / B;
+  const int ntiles = (AXIS == 0 ? a.ny : a.nx) * nkt;
+  C *cur = reinterpret_cast<C *>(smem_raw);
+  C *nxt = cur + SLOTS * SB;
+  Coef *stab = reinterpret_cast<Coef *>(nxt + SLOTS * SB);
+  float *wxtab = reinterpret_cast<float *>(stab + NTAB);   // W_x(i) = 3 x the weight (or 1)
+  const size_t stride = AXIS == 1 ? (size_t)a.nz : (size_t)a.ny * a.nz;
+  C *gpsi = reinterpret_cast<C *>(a.psi);
+  const int b = threadIdx.x % B, n0 = threadIdx.x / B;
+  const bool do_reduce = AXIS == 0 && reduce;
+
+  auto tile_origin = [&](int tile, int &fixed, int &k0) -> size_t {
+    fixed = tile / nkt;
+    k0 = (tile - fixed * nkt) * B;
+    return AXIS == 1 ? (size_t)fixed * a.ny * a.nz + k0 : (size_t)fixed * a.nz + k0;
+  };
+  // rows 0 .. N - 2 (not the far wall, whose slot stays zero)
+  auto issue = [&](int tile, C *buf) {
+    int fixed, k0;
+    const size_t base = tile_origin(tile, fixed, k0);
+    if (b < min(B, a.nz - k0)) {
+      const C *src = gpsi + base + b;
+#pragma unroll
+      for (int sub = 0; sub < P / W; ++sub) {
+        const int o = n0 + W * sub;
+        const SlotWalkP<P, CH> w(o);
+#pragma unroll
+        for (int j = 0; j < N / P; ++j)
+          if (o + P * j < N - 1) cp_async(buf + w(j, o) * SB + b, src + (size_t)(o + P * j) * stride);
+      }
+    }
+    cp_async_commit();
+  };
+
+  for (int q = threadIdx.x; q < 3 * SB; q += NT) {   // grid indices N - 1 .. N + 1: zero, once
+    const int g = N - 1 + q / SB, col = q % SB;
+    cur[(g + (g - 1) / CH) * SB + col] = czero<R>();
+    nxt[(g + (g - 1) / CH) * SB + col] = czero<R>();
+  }
+  {
+    const Coef *gtab = reinterpret_cast<const Coef *>(a.cn8_tab[AXIS]);
+    for (int q = threadIdx.x; q < NTAB; q += NT) stab[q] = gtab[q];
+  }
+  if (do_reduce)
+    for (int n = threadIdx.x; n < N; n += NT) wxtab[n] = (float)quad_weight3(n, a.nx, a.simpson);
+  const Coef c = CnCoef<R, Coef>::make(a.cn_rf[AXIS]);
+  const int warp = threadIdx.x / kWarp, grp = (threadIdx.x & (kWarp - 1)) >> 3;
+  const int col = 2 * warp + (grp >> 1) + 8 * (grp & 1);
+  DFAcc acc[4];
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) issue(tile, cur);
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int next = tile + gridDim.x;
+    if (next < ntiles) {
+      issue(next, nxt);
+      cp_async_wait_group<1>();
+    } else {
+      cp_async_wait_group<0>();
+    }
+    __syncthreads();
+    int fixed, k0;
+    const size_t base = tile_origin(tile, fixed, k0);
+    const int nb = min(B, a.nz - k0);
+    // every column is solved (all lanes take part in the scans); those past nb are not stored
+    cn_line<R, Coef, CH, true, true, L>(cur + col, SB, N, 0, stab, stab + 4 * L * CH, c);
+    __syncthreads();
+    if (b < nb) {
+      DFAcc s0;   // this thread's share of the column: sum W_x n
+      C *dst = gpsi + base + b;
+#pragma unroll
+      for (int sub = 0; sub < P / W; ++sub) {
+        const int o = n0 + W * sub;
+        const SlotWalkP<P, CH> w(o);
+#pragma unroll
+        for (int j = 0; j < N / P; ++j) {
+          const int n = o + P * j;
+          const C v = cur[w(j, o) * SB + b];
+          dst[(size_t)n * stride] = v;
+          if (do_reduce) {
+            const float d = fmaf(v.re, v.re, v.im * v.im);
+            s0.add(a.simpson ? wxtab[n] * d : d);   // exact: W_x is 0, 1, 2 or 4 (1 without Simpson)
+          }
+        }
+      }
+      if (do_reduce) {
+        const int jj = fixed - a.ny / 2, kk = k0 + b - a.nz / 2;
+        const int wyz = quad_weight3(fixed, a.ny, a.simpson) * quad_weight3(k0 + b, a.nz, a.simpson);
+        acc[0].add_scaled((float)wyz, s0);
+        acc[2].add_scaled((float)(jj * jj * wyz), s0);
+        acc[3].add_scaled((float)(kk * kk * wyz), s0);
+      }
+    }
+    __syncthreads();   // `cur` is refilled by the prefetch two tiles ahead
+    C *t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  if (do_reduce) {
+    const double w = a.simpson ? 1.0 / 27.0 : 1.0;   // (1/3)^3 of the integer Simpson weights
+    double v[4] = {acc[0].value() * w, 0.0, acc[2].value() * (w * a.hy * a.hy), acc[3].value() * (w * a.hz * a.hz)};
+    finish_sweep_sums(a, v, renorm);
+  }
+}
+template <typename Coef, int AXIS, int CH, bool G = false>
+__global__ void __launch_bounds__(128, 4) k_cn_short(KArgs a, const KArgs *ga, int reduce, int renorm) {
+  if constexpr (G) k_cn_short_body<Coef, AXIS, CH>(ga[blockIdx.z], reduce, renorm);
+  else k_cn_short_body<Coef, AXIS, CH>(a, reduce, renorm);
+}
+// shared memory of k_cn_short at chunk CH: two tile buffers, the tables, the x weights
+__host__ __device__ constexpr size_t smem_cn_short(int ch) {
+  return 2 * (size_t)(8 * ch + 2 + 8) * 17 * 8 + (size_t)(4 * 8 * ch + 48) * 8 + (size_t)8 * ch * 4;
+}
+
 // FP64-class sweeps: two threads per line, the twisted ("burn at both ends") factorization.
 // The matrix tridiag(-c, 1 + 2c, -c) reads the same from either end, so its UL factors are
 // its LU factors mirrored: the top thread eliminates points 0 .. h-1 downwards
@@ -2964,6 +3105,36 @@ struct Impl {
     }
     return cudaGetLastError();
   }
+  // The short-line sweep (FP32, x or y lines of short_cn_chunk(n) != 0 with their 8-lane
+  // tables): launched for `members` condensates (blockIdx.z; ga their arguments when GRP) on
+  // one resident wave of persistent CTAs, four per SM.  False when the line takes k_cn.
+  template <int AXIS, bool GRP>
+  static bool cn_short(const KArgs &a, const KArgs *ga, unsigned members, int reduce, int renorm, cudaStream_t st) {
+    if constexpr (!std::is_same<R, float>::value) {
+      return false;
+    } else {
+      const int n = AXIS == 0 ? a.nx : a.ny;
+      const int ch = short_cn_chunk(n);
+      if (!ch || !a.cn8_tab[AXIS]) return false;
+      const int tiles = ((a.nz + 15) / 16) * (AXIS == 0 ? a.ny : a.nx);
+      const int per = std::max(1, sm_count() * 4 / (int)members);
+      const dim3 g(std::min(tiles, per), 1, members);
+      const size_t sm = smem_cn_short(ch);
+      auto go = [&](auto chc) {
+        constexpr int CH = decltype(chc)::value;
+        if (a.imag) k_cn_short<R, AXIS, CH, GRP><<<g, 128, sm, st>>>(a, ga, reduce, renorm);
+        else k_cn_short<C, AXIS, CH, GRP><<<g, 128, sm, st>>>(a, ga, reduce, renorm);
+      };
+      switch (ch) {
+        case 4: go(std::integral_constant<int, 4>{}); break;
+        case 6: go(std::integral_constant<int, 6>{}); break;
+        case 8: go(std::integral_constant<int, 8>{}); break;
+        case 12: go(std::integral_constant<int, 12>{}); break;
+        default: go(std::integral_constant<int, 16>{}); break;
+      }
+      return true;
+    }
+  }
   template <int AXIS>
   static cudaError_t cn(const KArgs &a, int reduce, int renorm, cudaStream_t st) {
     const int n = AXIS == 0 ? a.nx : AXIS == 1 ? a.ny : a.nz;
@@ -2974,6 +3145,9 @@ struct Impl {
       if (a.imag) k_cn_twisted<R, R, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
       else k_cn_twisted<R, C, AXIS><<<blocks, 128, sm, st>>>(a, reduce, renorm);
     } else {
+      if constexpr (AXIS < 2) {
+        if (cn_short<AXIS, false>(a, nullptr, 1, reduce, renorm, st)) return cudaGetLastError();
+      }
       constexpr int B = T::kCnCols, NT = T::kCnThreads;
       const size_t sm = smem_cn(cn_len(a, AXIS), a.cn[AXIS].lchunk);
       const dim3 g = grid_cn(a, AXIS);
@@ -3162,6 +3336,7 @@ struct GroupLaunch {
   }
   template <typename Co, int AXIS>
   static void cn(const KArgs &a, const KArgs *ga, unsigned n, int reduce, int renorm, cudaStream_t st) {
+    if (I::template cn_short<AXIS, true>(a, ga, n, reduce, renorm, st)) return;
     // one resident wave for the whole group: each member's share of the persistent CTAs,
     // so that every CTA stages the factor tables once for many tiles and prefetches
     dim3 g = I::grid_cn(a, AXIS);

@@ -32,9 +32,16 @@ struct FftPlan {
 struct CnJob {
   void *tab;
   int m, chunk;
-  double r;   // dt / (4 h^2), negated for the adjoint tables
+  double r;    // dt / (4 h^2), negated for the adjoint tables
+  int lanes;   // lanes per line of the layout: 32, or 8 (the short-line sweeps)
 };
-constexpr int kMaxCnJobs = 8;
+constexpr int kMaxCnJobs = 10;
+
+// FP32 sweeps of short lines: n = 8 CH points (CH = 4, 6, 8, 12 or 16) are solved on 8 lanes
+// per line, CH points each; 0 where the line takes the 32-lane solver.
+__host__ __device__ constexpr int short_cn_chunk(int n) {
+  return (n == 32 || n == 48 || n == 64 || n == 96 || n == 128) ? n / 8 : 0;
+}
 
 // Interior points per lane of K5's z solve at a compile-time length n: the least chunk with
 // 32 chunks covering the n - 2 unknowns (12 for n = 384; the sweeps' power of two for 128,
@@ -102,6 +109,8 @@ struct KArgs {
   CnTab cn[3];
   const void *cnz_tab;         // K5's z tables at k5_chunk(nz) points per lane, where that is not
                                // cn[2].chunk (FP32, compile-time nz); else null
+  const void *cn8_tab[2];      // x and y sweeps' tables in the 8-lane layout (FP32 lines of
+                               // short_cn_chunk(n) != 0); else null
   void *out;                   // optional output (Phi for get_phi)
   // adjoint step
   void *gbar;                  // cotangent field (same layout as psi)

@@ -120,12 +120,13 @@ def test_batch_step_counts_and_graph_cache():
 
 
 @pytest.mark.parametrize("mode", [abi.DGPE_IMAG_TIME, abi.DGPE_REAL_TIME])
-def test_grouped_members_equal_individual_steps(mode):
+@pytest.mark.parametrize("shape", [(24, 20, 32), (32, 48, 20)])   # (the second: short-line sweeps)
+def test_grouped_members_equal_individual_steps(mode, shape):
     """Same-shaped FP32 members (different physics and states) are stepped as one group, each
     kernel one launch for all of them; a member of another shape and an FP64 member run as
     branches of their own.  Every result equals the member's own steps bitwise, before and
     after a parameter change (which rebuilds the grouped launches' argument array)."""
-    shape, h = (24, 20, 32), 0.45
+    h = 0.45
     specs = [((1.0, 1.2, 0.8), 30.0, 10.0), ((0.7, 1.0, 1.5), 55.0, 40.0), ((1.3, 0.9, 1.1), 8.0, 2.0)]
     batched, alone = [], []
     for k, (nu, g, gdd) in enumerate(specs):

@@ -245,6 +245,26 @@ def test_mixed_precision_error_vs_oracle(orc, mode):
     gpu.close()
 
 
+@pytest.mark.parametrize("mode", [abi.DGPE_IMAG_TIME, abi.DGPE_REAL_TIME])
+@pytest.mark.parametrize("shape", [(48, 64, 20), (96, 128, 12), (128, 32, 36)])
+def test_mixed_short_line_sweeps_vs_oracle(orc, shape, mode):
+    """x and y lines of 32, 48, 64, 96 and 128 points take the 8-lane sweeps (4, 6, 8, 12 and
+    16 points per lane), with nz not a multiple of the 16-column tiles: FP32 errors against
+    the FP64 oracle after 10 steps, at the FP32-mixed bar of the 20-step test."""
+    h = 0.25
+    psi = state(shape, h)
+    gpu, p = make(orc, shape, h, 0.004, mode, precision=abi.DGPE_MIXED)
+    gpu.set_psi(psi.astype(np.complex64))
+    gpu.step(10)
+    got = gpu.get_psi().astype(np.complex128)
+    want = orc.step(p, psi.astype(np.complex64).astype(np.complex128), 10)
+    assert rel(got, want) < 2e-5
+    og, ow = gpu.observables(), orc.observables(p, want)
+    assert og["mu"] == pytest.approx(ow["mu"], rel=2e-5)
+    assert og["rms"][0] == pytest.approx(ow["rms"][0], rel=2e-5)
+    gpu.close()
+
+
 @pytest.mark.parametrize("dt", [3.0, -3.0, 0.37])
 def test_potential_step_large_phase_angles(orc, dt):
     """theta = dt (V + g n + gdd Phi) spanning many multiples of pi/2 (both signs), which
