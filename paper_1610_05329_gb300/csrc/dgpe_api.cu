@@ -124,7 +124,7 @@ int check_physics(const dgpe_params *p) {
 }
 
 struct Layout {
-  size_t state, partials, tw[3], cn[3], cn_adj[3], cnz, cn8[2], dtv[3], psi, spec, utab, ybuf, total;
+  size_t state, partials, tw[3], cn[3], cn_adj[3], cnz, cn8[3], dtv[3], psi, spec, utab, ybuf, total;
 };
 
 // FP32 contexts whose compile-time K5 (nz = 128, 256, 384, 512) solves along z at a chunk
@@ -160,9 +160,11 @@ Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
     L.cnz = off;
     off += align_up((size_t)(4 * k5_chunk(p->nz) + 11) * kWarp * e);
   }
-  for (int d = 0; d < 2; ++d) {   // the x and y sweeps' tables in the 8-lane layout (FP32 short lines)
+  // tables in the 8-lane layout: the x and y sweeps' (FP32 short lines), K5's z solve (FP32,
+  // nz = 128, the compile-time K5)
+  for (int d = 0; d < 3; ++d) {
     L.cn8[d] = 0;
-    if (p->precision == DGPE_MIXED && short_cn_chunk(n[d])) {
+    if (p->precision == DGPE_MIXED && (d < 2 ? short_cn_chunk(n[d]) != 0 : n[d] == 128)) {
       L.cn8[d] = off;
       off += align_up((size_t)(4 * 8 * short_cn_chunk(n[d]) + 49) * e);
     }
@@ -458,8 +460,7 @@ int setup_tables(dgpe_ctx *c, bool cn_changed, bool ut_changed) {
     jobs.job[jobs.n++] = {at(c, c->L.cn[d]), c->args.cn[d].m, c->args.cn[d].chunk, c->args.cn_r[d], kWarp};
     if (p->mode == DGPE_REAL_TIME)   // the adjoint sweep is the sweep with dt -> -dt
       jobs.job[jobs.n++] = {at(c, c->L.cn_adj[d]), c->args.cn[d].m, c->args.cn[d].chunk, -c->args.cn_r[d], kWarp};
-    if (d < 2 && c->L.cn8[d])
-      jobs.job[jobs.n++] = {at(c, c->L.cn8[d]), c->args.cn[d].m, short_cn_chunk(n[d]), c->args.cn_r[d], 8};
+    if (c->L.cn8[d]) jobs.job[jobs.n++] = {at(c, c->L.cn8[d]), c->args.cn[d].m, n[d] / 8, c->args.cn_r[d], 8};
   }
   if (cn_changed && c->L.cnz)
     jobs.job[jobs.n++] = {at(c, c->L.cnz), c->args.cn[2].m, k5_chunk(p->nz), c->args.cn_r[2], kWarp};
@@ -491,7 +492,7 @@ KArgs adjoint_sweep_args(dgpe_ctx *c, void *gbar) {
   a.psi = gbar;
   for (int d = 0; d < 3; ++d) {
     a.cn[d].tab = at(c, c->L.cn_adj[d]);
-    if (d < 2) a.cn8_tab[d] = nullptr;   // (the adjoint sweeps take the 32-lane solver)
+    a.cn8_tab[d] = nullptr;   // (the adjoint sweeps take the 32-lane solver)
     a.cn_r[d] = -a.cn_r[d];
     a.cn_rf[d] = -a.cn_rf[d];
     a.cn_rl[d] = -a.cn_rl[d];
@@ -702,7 +703,7 @@ int dgpe_create(const dgpe_params *p, void *cuda_stream, dgpe_ctx **out) {
   a.utab = at(c, c->L.utab);
   a.ybuf = at(c, c->L.ybuf);
   a.cnz_tab = c->L.cnz ? at(c, c->L.cnz) : nullptr;
-  for (int d = 0; d < 2; ++d) a.cn8_tab[d] = c->L.cn8[d] ? at(c, c->L.cn8[d]) : nullptr;
+  for (int d = 0; d < 3; ++d) a.cn8_tab[d] = c->L.cn8[d] ? at(c, c->L.cn8[d]) : nullptr;
   const int n[3] = {p->nx, p->ny, p->nz};
   rc = map_cuda(cudaMemsetAsync(a.psi, 0, (size_t)p->nx * p->ny * p->nz * c->ks->elem_bytes, c->stream));
   if (!rc) rc = map_cuda(c->ks->reset_state(a.state, c->stream));

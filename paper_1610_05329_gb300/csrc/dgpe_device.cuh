@@ -1678,7 +1678,10 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
   // lines); the tile loops walk period PW = lcm(W, CHZ) (W = threads / lines).
   constexpr int W = Tiles<R>::kZThreads / BZ;
   constexpr bool kWalk = N > 0 && !Fp64Class<R>::value;
-  constexpr int CHZ = kWalk ? k5_chunk(N) : 1;
+  // lines of 128: the z solve on 8 lanes per line (16 points each, three scan steps), the
+  // tables in the 8-lane layout; longer lines on 32 lanes
+  constexpr int LZ = kWalk && N == 128 ? 8 : kWarp;
+  constexpr int CHZ = kWalk ? (LZ == 8 ? N / 8 : k5_chunk(N)) : 1;
   constexpr int PW = kWalk ? W / gcd_c(W, CHZ) * CHZ : W;
   constexpr int SUBS = PW / W;
   static_assert(!kWalk || (N % PW == 0 && zmode == kZStep), "compile-time FP32 instances: the fused step");
@@ -1705,12 +1708,13 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
   R dtvx = R(0);
   if (phase) dtvx = reinterpret_cast<const R *>(a.dtv[0])[i];
   // the z solve's tables: K5's own at CHZ points per lane where that is not the sweeps' chunk
-  const Coef *ztab_g = reinterpret_cast<const Coef *>(kWalk && a.cnz_tab ? a.cnz_tab : a.cn[2].tab);
-  const int zmp = kWalk ? kWarp * CHZ : (kWarp << lc);
+  const Coef *ztab_g = reinterpret_cast<const Coef *>(
+      LZ == 8 ? a.cn8_tab[2] : (kWalk && a.cnz_tab ? a.cnz_tab : a.cn[2].tab));
+  const int zmp = kWalk ? LZ * CHZ : (kWarp << lc);
   if (zmode == kZStep || zmode == kZCnOnly) {
     const Coef *gscan = ztab_g + 4 * zmp;
     if constexpr (kAsyncTabs) {
-      constexpr int chunks = 10 * kWarp * (int)sizeof(Coef) / 16;
+      constexpr int chunks = (LZ == 8 ? 6 : 10) * LZ * (int)sizeof(Coef) / 16;   // the scan factors
       for (int q = threadIdx.x; q < chunks; q += blockDim.x)
         cp_async(reinterpret_cast<uint4 *>(scan_s) + q, reinterpret_cast<const uint4 *>(gscan) + q);
     } else {
@@ -1997,7 +2001,7 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
       // the padded solve: the far wall (grid N - 1, which the phase loop has written) and the
       // points beyond it, up to the padded length 32 CHZ, hold zero; after the phase loop's
       // barrier, before the solve's
-      constexpr int kPad = kWarp * CHZ + 2 - N;
+      constexpr int kPad = LZ * CHZ + 2 - N;
       static_assert(kPad >= 1 && kPad * BZ <= Tiles<R>::kZThreads, "a thread per padded slot");
       if (threadIdx.x < BZ * kPad) {
         const int b = threadIdx.x / kPad, g = N - 1 + threadIdx.x % kPad;
@@ -2007,9 +2011,18 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
     cp_async_wait_group<0>();
     __syncthreads();
     const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[2], a.cn_rf[2], a.cn_rl[2]));
-    for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp) {
-      if constexpr (kWalk) cn_line<R, Coef, CHZ, true, true>(tile + b * LS, 1, kWarp * CHZ, lc, ztab, scan_s, c);
-      else cn_line_any<R, Coef, (N > 0)>(tile + b * LS, 1, a.cn[2].m, lc, ztab, scan_s, c);
+    if constexpr (LZ == 8) {
+      // warps 0-3, four lines each: w, w + 8 (one half-warp), w + 4, w + 12 (the other);
+      // at the odd line stride two lines 8 apart fall on distinct banks.  Lines past nl are
+      // solved too (all lanes take part in the scans) and not stored.
+      static_assert(BZ == 16 && Tiles<R>::kZThreads >= 128, "16 lines on four warps");
+      const int w = threadIdx.x / kWarp, g = (threadIdx.x & (kWarp - 1)) >> 3;
+      if (w < 4) cn_line<R, Coef, CHZ, true, true, 8>(tile + (w + 8 * (g & 1) + 4 * (g >> 1)) * LS, 1, 8 * CHZ, lc, ztab, scan_s, c);
+    } else {
+      for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp) {
+        if constexpr (kWalk) cn_line<R, Coef, CHZ, true, true>(tile + b * LS, 1, kWarp * CHZ, lc, ztab, scan_s, c);
+        else cn_line_any<R, Coef, (N > 0)>(tile + b * LS, 1, a.cn[2].m, lc, ztab, scan_s, c);
+      }
     }
     __syncthreads();
   }
@@ -3061,7 +3074,7 @@ struct Impl {
       if (plan_ct(a.plan[2], 512)) k5_zline<R, Co, ZM, 512><<<g, T::kZThreads, sm, st>>>(a, nullptr);
       else if (plan_ct(a.plan[2], 384)) k5_zline<R, Co, ZM, 384><<<g, T::kZThreads, sm, st>>>(a, nullptr);
       else if (plan_ct(a.plan[2], 256)) k5_zline<R, Co, ZM, 256><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else if (plan_ct(a.plan[2], 128)) k5_zline<R, Co, ZM, 128><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else if (plan_ct(a.plan[2], 128) && a.cn8_tab[2]) k5_zline<R, Co, ZM, 128><<<g, T::kZThreads, sm, st>>>(a, nullptr);
       else k5_zline<R, Co, ZM, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
     } else {
       k5_zline<R, Co, ZM, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
@@ -3331,7 +3344,7 @@ struct GroupLaunch {
     if (I::plan_ct(a.plan[2], 512)) k5_zline<R, Co, kZStep, 512, true><<<g, T::kZThreads, sm, st>>>(a, ga);
     else if (I::plan_ct(a.plan[2], 384)) k5_zline<R, Co, kZStep, 384, true><<<g, T::kZThreads, sm, st>>>(a, ga);
     else if (I::plan_ct(a.plan[2], 256)) k5_zline<R, Co, kZStep, 256, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-    else if (I::plan_ct(a.plan[2], 128)) k5_zline<R, Co, kZStep, 128, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+    else if (I::plan_ct(a.plan[2], 128) && a.cn8_tab[2]) k5_zline<R, Co, kZStep, 128, true><<<g, T::kZThreads, sm, st>>>(a, ga);
     else k5_zline<R, Co, kZStep, 0, true><<<g, T::kZThreads, sm, st>>>(a, ga);
   }
   template <typename Co, int AXIS>

@@ -109,8 +109,8 @@ struct KArgs {
   CnTab cn[3];
   const void *cnz_tab;         // K5's z tables at k5_chunk(nz) points per lane, where that is not
                                // cn[2].chunk (FP32, compile-time nz); else null
-  const void *cn8_tab[2];      // x and y sweeps' tables in the 8-lane layout (FP32 lines of
-                               // short_cn_chunk(n) != 0); else null
+  const void *cn8_tab[3];      // tables in the 8-lane layout: the x and y sweeps' (FP32 lines of
+                               // short_cn_chunk(n) != 0) and K5's z solve (FP32, nz = 128); else null
   void *out;                   // optional output (Phi for get_phi)
   // adjoint step
   void *gbar;                  // cotangent field (same layout as psi)
