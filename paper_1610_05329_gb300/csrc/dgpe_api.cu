@@ -161,10 +161,10 @@ Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
     off += align_up((size_t)(4 * k5_chunk(p->nz) + 11) * kWarp * e);
   }
   // tables in the 8-lane layout: the x and y sweeps' (FP32 short lines), K5's z solve (FP32,
-  // nz = 128, the compile-time K5)
+  // the compile-time K5 of nz = 64, 96, 128)
   for (int d = 0; d < 3; ++d) {
     L.cn8[d] = 0;
-    if (p->precision == DGPE_MIXED && (d < 2 ? short_cn_chunk(n[d]) != 0 : n[d] == 128)) {
+    if (p->precision == DGPE_MIXED && (d < 2 ? short_cn_chunk(n[d]) != 0 : k5_short_z(n[d]))) {
       L.cn8[d] = off;
       off += align_up((size_t)(4 * 8 * short_cn_chunk(n[d]) + 49) * e);
     }

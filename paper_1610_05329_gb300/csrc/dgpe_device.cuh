@@ -1678,9 +1678,9 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
   // lines); the tile loops walk period PW = lcm(W, CHZ) (W = threads / lines).
   constexpr int W = Tiles<R>::kZThreads / BZ;
   constexpr bool kWalk = N > 0 && !Fp64Class<R>::value;
-  // lines of 128: the z solve on 8 lanes per line (16 points each, three scan steps), the
-  // tables in the 8-lane layout; longer lines on 32 lanes
-  constexpr int LZ = kWalk && N == 128 ? 8 : kWarp;
+  // lines of 64, 96, 128: the z solve on 8 lanes per line (8, 12, 16 points each, three scan
+  // steps), the tables in the 8-lane layout; longer lines on 32 lanes
+  constexpr int LZ = kWalk && k5_short_z(N) ? 8 : kWarp;
   constexpr int CHZ = kWalk ? (LZ == 8 ? N / 8 : k5_chunk(N)) : 1;
   constexpr int PW = kWalk ? W / gcd_c(W, CHZ) * CHZ : W;
   constexpr int SUBS = PW / W;
@@ -2780,6 +2780,8 @@ struct Impl {
   // compile-time transforms of lengths 128-512 (not for double-float: its kernels take many
   // times longer to compile)
   static constexpr bool kCtSizes = !std::is_same<R, df>::value;
+  // FP32 also at nz = 96 and 64 (K1, K5; the batched small grids)
+  static constexpr bool kShortCt = std::is_same<R, float>::value;
   // the FP64-class sweeps run a Thomas solve per line on two threads (k_cn_twisted), the
   // FP32 ones the chunked solver in persistent tiles (k_cn)
   static constexpr bool kCnThread = Fp64Class<R>::value;
@@ -2791,7 +2793,8 @@ struct Impl {
   static size_t smem_k5(const KArgs &a) {
     // the tile: the sweeps' layout, or (FP32, compile-time lengths) K5's padded one
     int ls = cn_slots(a.nz, a.cn[2].lchunk);
-    if (std::is_same<R, float>::value && (a.nz == 128 || a.nz == 256 || a.nz == 384 || a.nz == 512))
+    if (std::is_same<R, float>::value &&
+        (a.nz == 64 || a.nz == 96 || a.nz == 128 || a.nz == 256 || a.nz == 384 || a.nz == 512))
       ls = std::max(ls, k5_tile_stride(a.nz));
     return 2 * (size_t)a.nz * (T::kZLines / 2) * E + (size_t)T::kZLines * ls * E +
            (size_t)(a.nz + T::kZLines) * sizeof(R) + (size_t)10 * kWarp * E;
@@ -2910,6 +2913,14 @@ struct Impl {
       chk(allow_smem(k5_zline<R, C, kZFast, 256>));
       chk(allow_smem(k5_zline<R, R, kZFast, 128>));
       chk(allow_smem(k5_zline<R, C, kZFast, 128>));
+      if constexpr (kShortCt) {
+        chk(allow_smem(k1_density_r2cz<R, 96>));
+        chk(allow_smem(k1_density_r2cz<R, 64>));
+        chk(allow_smem(k5_zline<R, R, kZFast, 96>));
+        chk(allow_smem(k5_zline<R, C, kZFast, 96>));
+        chk(allow_smem(k5_zline<R, R, kZFast, 64>));
+        chk(allow_smem(k5_zline<R, C, kZFast, 64>));
+      }
     }
     if constexpr (!kCnThread) {
       constexpr int B = T::kCnCols, NT = T::kCnThreads;
@@ -2996,6 +3007,8 @@ struct Impl {
       else if (plan_ct(a.plan[2], 384)) k1_density_r2cz<R, 384><<<g, T::kZThreads, sm, st>>>(a, nullptr);
       else if (plan_ct(a.plan[2], 256)) k1_density_r2cz<R, 256><<<g, T::kZThreads, sm, st>>>(a, nullptr);
       else if (plan_ct(a.plan[2], 128)) k1_density_r2cz<R, 128><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else if (kShortCt && plan_ct(a.plan[2], 96)) k1_density_r2cz<R, kShortCt ? 96 : 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else if (kShortCt && plan_ct(a.plan[2], 64)) k1_density_r2cz<R, kShortCt ? 64 : 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
       else k1_density_r2cz<R, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
     } else {
       k1_density_r2cz<R, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
@@ -3074,7 +3087,9 @@ struct Impl {
       if (plan_ct(a.plan[2], 512)) k5_zline<R, Co, ZM, 512><<<g, T::kZThreads, sm, st>>>(a, nullptr);
       else if (plan_ct(a.plan[2], 384)) k5_zline<R, Co, ZM, 384><<<g, T::kZThreads, sm, st>>>(a, nullptr);
       else if (plan_ct(a.plan[2], 256)) k5_zline<R, Co, ZM, 256><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else if (plan_ct(a.plan[2], 128) && a.cn8_tab[2]) k5_zline<R, Co, ZM, 128><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else if (plan_ct(a.plan[2], 128) && (!kShortCt || a.cn8_tab[2])) k5_zline<R, Co, ZM, 128><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else if (kShortCt && plan_ct(a.plan[2], 96) && a.cn8_tab[2]) k5_zline<R, Co, ZM, kShortCt ? 96 : 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else if (kShortCt && plan_ct(a.plan[2], 64) && a.cn8_tab[2]) k5_zline<R, Co, ZM, kShortCt ? 64 : 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
       else k5_zline<R, Co, ZM, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
     } else {
       k5_zline<R, Co, ZM, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
@@ -3266,6 +3281,8 @@ struct GroupLaunch {
     attr(k1_density_r2cz<R, 384, true>, e);
     attr(k1_density_r2cz<R, 256, true>, e);
     attr(k1_density_r2cz<R, 128, true>, e);
+    attr(k1_density_r2cz<R, 96, true>, e);
+    attr(k1_density_r2cz<R, 64, true>, e);
     attr(k1_density_r2cz<R, 0, true>, e);
     attr(k_ffty<R, -1, 0, true>, e);
     attr(k_ffty<R, +1, 0, true>, e);
@@ -3289,6 +3306,10 @@ struct GroupLaunch {
     attr(k5_zline<R, C, kZStep, 384, true>, e);
     attr(k5_zline<R, R, kZStep, 256, true>, e);
     attr(k5_zline<R, C, kZStep, 256, true>, e);
+    attr(k5_zline<R, R, kZStep, 96, true>, e);
+    attr(k5_zline<R, C, kZStep, 96, true>, e);
+    attr(k5_zline<R, R, kZStep, 64, true>, e);
+    attr(k5_zline<R, C, kZStep, 64, true>, e);
     attr(k5_zline<R, R, kZStep, 128, true>, e);
     attr(k5_zline<R, C, kZStep, 128, true>, e);
     attr(k5_zline<R, R, kZStep, 0, true>, e);
@@ -3345,6 +3366,8 @@ struct GroupLaunch {
     else if (I::plan_ct(a.plan[2], 384)) k5_zline<R, Co, kZStep, 384, true><<<g, T::kZThreads, sm, st>>>(a, ga);
     else if (I::plan_ct(a.plan[2], 256)) k5_zline<R, Co, kZStep, 256, true><<<g, T::kZThreads, sm, st>>>(a, ga);
     else if (I::plan_ct(a.plan[2], 128) && a.cn8_tab[2]) k5_zline<R, Co, kZStep, 128, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+    else if (I::plan_ct(a.plan[2], 96) && a.cn8_tab[2]) k5_zline<R, Co, kZStep, 96, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+    else if (I::plan_ct(a.plan[2], 64) && a.cn8_tab[2]) k5_zline<R, Co, kZStep, 64, true><<<g, T::kZThreads, sm, st>>>(a, ga);
     else k5_zline<R, Co, kZStep, 0, true><<<g, T::kZThreads, sm, st>>>(a, ga);
   }
   template <typename Co, int AXIS>
@@ -3372,6 +3395,8 @@ struct GroupLaunch {
       else if (I::plan_ct(a.plan[2], 384)) k1_density_r2cz<R, 384, true><<<g, T::kZThreads, sm, st>>>(a, ga);
       else if (I::plan_ct(a.plan[2], 256)) k1_density_r2cz<R, 256, true><<<g, T::kZThreads, sm, st>>>(a, ga);
       else if (I::plan_ct(a.plan[2], 128)) k1_density_r2cz<R, 128, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+      else if (I::plan_ct(a.plan[2], 96)) k1_density_r2cz<R, 96, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+      else if (I::plan_ct(a.plan[2], 64)) k1_density_r2cz<R, 64, true><<<g, T::kZThreads, sm, st>>>(a, ga);
       else k1_density_r2cz<R, 0, true><<<g, T::kZThreads, sm, st>>>(a, ga);
     }
     ffty<-1>(a, ga, n, st);

@@ -42,6 +42,8 @@ constexpr int kMaxCnJobs = 10;
 __host__ __device__ constexpr int short_cn_chunk(int n) {
   return (n == 32 || n == 48 || n == 64 || n == 96 || n == 128) ? n / 8 : 0;
 }
+// FP32 compile-time K5 lengths whose z solve runs on 8 lanes per line (8-lane z tables)
+__host__ __device__ constexpr bool k5_short_z(int n) { return n == 64 || n == 96 || n == 128; }
 
 // Interior points per lane of K5's z solve at a compile-time length n: the least chunk with
 // 32 chunks covering the n - 2 unknowns (12 for n = 384; the sweeps' power of two for 128,
@@ -110,7 +112,7 @@ struct KArgs {
   const void *cnz_tab;         // K5's z tables at k5_chunk(nz) points per lane, where that is not
                                // cn[2].chunk (FP32, compile-time nz); else null
   const void *cn8_tab[3];      // tables in the 8-lane layout: the x and y sweeps' (FP32 lines of
-                               // short_cn_chunk(n) != 0) and K5's z solve (FP32, nz = 128); else null
+                               // short_cn_chunk(n) != 0) and K5's z solve (FP32, k5_short_z(nz)); else null
   void *out;                   // optional output (Phi for get_phi)
   // adjoint step
   void *gbar;                  // cotangent field (same layout as psi)

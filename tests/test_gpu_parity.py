@@ -246,12 +246,13 @@ def test_mixed_precision_error_vs_oracle(orc, mode):
 
 
 @pytest.mark.parametrize("mode", [abi.DGPE_IMAG_TIME, abi.DGPE_REAL_TIME])
-@pytest.mark.parametrize("shape", [(48, 64, 20), (96, 128, 12), (128, 32, 36), (32, 48, 128)])
+@pytest.mark.parametrize("shape", [(48, 64, 20), (96, 128, 12), (128, 32, 36), (32, 48, 128), (20, 24, 96),
+                                   (24, 20, 64)])
 def test_mixed_short_line_sweeps_vs_oracle(orc, shape, mode):
     """x and y lines of 32, 48, 64, 96 and 128 points take the 8-lane sweeps (4, 6, 8, 12 and
-    16 points per lane), with nz not a multiple of the 16-column tiles; z lines of 128 the
-    8-lane solve inside K5: FP32 errors against the FP64 oracle after 10 steps, at the
-    FP32-mixed bar of the 20-step test."""
+    16 points per lane), with nz not a multiple of the 16-column tiles; z lines of 64, 96 and
+    128 the 8-lane solve inside K5: FP32 errors against the FP64 oracle after 10 steps, at
+    the FP32-mixed bar of the 20-step test."""
     h = 0.25
     psi = state(shape, h)
     gpu, p = make(orc, shape, h, 0.004, mode, precision=abi.DGPE_MIXED)
