@@ -289,12 +289,15 @@ typedef struct dgpe_tuning {
   int plan_style[3];     /* FFT radix order per axis: 0 radix-8 first, 1 radix-4, 2 radix-3 first */
   int ylines;            /* lines per CTA of the y transforms: 2, 4, 8, 16 or 32 */
   int fft_threads;       /* threads per CTA of the y/x transforms: 128 or 256 */
-  int cn_per_sm;         /* CTAs per SM of the persistent Crank-Nicolson sweeps: 1 or 2 */
+  int cn_per_sm;         /* CTAs per SM of the persistent Crank-Nicolson sweeps: 1 or 2 (an upper
+                            bound: the FP32 sweeps of 512-thread CTAs fit one per SM by registers;
+                            those of short lines run four per SM regardless) */
   double step_ms_default, step_ms_tuned;  /* measured by dgpe_autotune (0 otherwise) */
 } dgpe_tuning;
 
 /* Time candidate launch shapes on this context's own shape (a few steps each, with CUDA
- * events per kernel), choose the fastest per kernel class, apply it and report it in *out.
+ * events per kernel), choose the fastest per kernel class (a radix order other than the
+ * default only when it is more than 3 % faster), apply it and report it in *out.
  * psi and the device state are restored afterwards.  Synchronises; allocates one
  * psi-sized temporary with cudaMallocAsync.  Paper: as dgpe_tuning. */
 int dgpe_autotune(dgpe_ctx *ctx, dgpe_tuning *out);
