@@ -1977,15 +1977,33 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
       }
     };
     if constexpr (kWalk) {
-      // thread (line b, offset n0 < W): the points n0 + W sub + PW i of line b, lines fastest
+      // thread (line b, offset n0 < W): the points n0 + W sub + PW i of line b, lines fastest;
+      // the line's dt (V_x + V_y) read once, its Phi (.re or .im of pair b/2) through its own
+      // float pointer
       const int b = threadIdx.x % BZ, n0 = threadIdx.x / BZ;
       if (b < nl) {
+        const R vxy = ty[b] + dtvx;
+        const R *phib = reinterpret_cast<const R *>(res + (b >> 1)) + (b & 1);
+        C *row = tile + b * LS;
 #pragma unroll
         for (int sub = 0; sub < SUBS; ++sub) {
           const int o = n0 + W * sub;
           const SlotWalkP<PW, CHZ> w(o);
 #pragma unroll 4
-          for (int i = 0; i < N / PW; ++i) phase_at(o + PW * i, b, b * LS + w(i, o));
+          for (int i = 0; i < N / PW; ++i) {
+            const int n = o + PW * i;
+            C v = row[w(i, o)];
+            if (scaled) v = scale(v, sr);
+            const R dens = v.re * v.re + v.im * v.im;
+            const R theta = fma(dtg, dens, fma(dtgdd, phib[2 * SB * n], vxy + tz[n]));
+            if (a.imag) {
+              row[w(i, o)] = scale(v, exp_r(-theta));
+            } else {
+              R sn, cs;
+              sin_cos(theta, &sn, &cs);
+              row[w(i, o)] = {v.re * cs + v.im * sn, v.im * cs - v.re * sn};
+            }
+          }
         }
       }
     } else {
