@@ -53,9 +53,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 NCU_TRAFFIC = {
     # FP64 and double-float: the K5 record times two launches (the phase-only pass and the
     # two-thread z sweep)
-    "a1cac022d9320c4413efd116f7507386b6519b11": {
-        ("real256_fp64", "k5_c2r_z_phase_cn_z"): 1851.67e6,
-        ("real512x512x384_mixed", "k5_c2r_z_phase_cn_z"): 1958.73e6,
+    "bc1402707517e1db295d8dcce984e30076cadd57": {
+        ("real256_fp64", "k5_c2r_z_phase_cn_z"): 1850.51e6,
+        ("real512x512x384_mixed", "k5_c2r_z_phase_cn_z"): 1960.35e6,
     },
 }
 
@@ -543,7 +543,9 @@ def batching_run(abi, local, steps=300, count=64):
     first_call_s = time.perf_counter() - t0
     for c, psi in zip(conds, psis):
         c.set_psi(psi)
+    torch.cuda.nvtx.range_push("batched")   # (profilers select the batched launch by this range)
     bat_ms = timed(lambda: b.step(steps))
+    torch.cuda.nvtx.range_pop()
     b.sync()
     b.close()
     for c in conds:
@@ -641,6 +643,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 128^3 differentiation line item")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-condensate batching line item")
+    ap.add_argument("--batch-steps", type=int, default=300, help="steps of the batching line item")
     ap.add_argument("--no-paper-grids", action="store_true", help="skip the paper-grid context line item")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the 512x512x384 mixed-vs-FP64 error table (500 + 500 steps, and the oracle)")
@@ -731,7 +734,7 @@ def main():
 
     batch = None
     if not args.no_batch and args.workload is None:
-        batch = batching_run(abi, local)
+        batch = batching_run(abi, local, steps=args.batch_steps)
     paper = None
     if not args.no_paper_grids and args.workload is None:
         paper = paper_grid_run(abi, local)
