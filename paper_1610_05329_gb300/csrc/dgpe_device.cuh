@@ -776,11 +776,65 @@ __device__ __forceinline__ void fft_stage_ct(const cplx<R> *__restrict__ src, cp
   }
 }
 
+// Two consecutive stages (radix P1 at ns = NS, then radix P2 at ns = NS P1) in one pass, the
+// intermediate values in registers: the P2 stage-1 butterflies j1 = (q2 + r Q) NS + k1
+// (r < P2, Q = N / (P1 P2 NS)) produce exactly the inputs of the P1 stage-2 butterflies
+// j2 = q2 NS P1 + s NS + k1 (s < P1), output s of the r-th feeding input r of the s-th.  The
+// same butterflies and twiddles as the two stages, in the same order per element: only the
+// round trip through shared memory and one barrier go.
+template <typename R, int DIR, int P1, int P2, int N, int NS, int LW, int SB, int NT>
+__device__ __forceinline__ void fft_stage_ct2(const cplx<R> *__restrict__ src, cplx<R> *__restrict__ dst, int nlines,
+                                              const cplx<R> *__restrict__ tw1, const cplx<R> *__restrict__ tw2) {
+  constexpr int NS2 = NS * P1, Q = N / (P1 * P2 * NS), NU = N / (P1 * P2), JSTEP = NT / LW;
+  static_assert(NT % LW == 0 && Q * P1 * P2 * NS == N, "whole fused units");
+  const int line = threadIdx.x % LW;
+  if (line >= nlines) return;
+  const int u0 = threadIdx.x / LW;
+#pragma unroll
+  for (int it = 0; it < (NU + JSTEP - 1) / JSTEP; ++it) {
+    const int u = u0 + it * JSTEP;
+    if (NU % JSTEP != 0 && u >= NU) break;
+    const int k1 = u % NS, q2 = u / NS;
+    cplx<R> w[P2][P1];
+#pragma unroll
+    for (int r = 0; r < P2; ++r) {
+      const int j1 = (q2 + r * Q) * NS + k1;
+      cplx<R> v[P1];
+#pragma unroll
+      for (int r1 = 0; r1 < P1; ++r1) v[r1] = src[(j1 + r1 * (N / P1)) * SB + line];
+      stage_butterfly<R, DIR, P1>(v, NS > 1, tw1 + k1 * (P1 - 1), k1, NS * P1);
+#pragma unroll
+      for (int q = 0; q < P1; ++q) w[r][q] = v[q];
+    }
+#pragma unroll
+    for (int q = 0; q < P1; ++q) {
+      const int k2 = q * NS + k1, j2 = q2 * NS2 + k2;
+      cplx<R> v[P2];
+#pragma unroll
+      for (int r = 0; r < P2; ++r) v[r] = w[r][q];
+      stage_butterfly<R, DIR, P2>(v, NS2 > 1, tw2 + k2 * (P2 - 1), k2, NS2 * P2);
+      cplx<R> *out = dst + ((j2 - k2) * P2 + k2) * SB + line;
+#pragma unroll
+      for (int s2 = 0; s2 < P2; ++s2) out[s2 * NS2 * SB] = v[s2];
+    }
+  }
+}
+
+// FP32: a radix-2 or radix-4 stage followed by a radix-3 stage runs as one fused pass
+template <typename R, int N, int ST>
+__host__ __device__ constexpr bool ct_fuse(int p) {
+  return std::is_same<R, float>::value && (p == 2 || p == 4) && ct_radix(N, ST + 1) == 3;
+}
+
 template <typename R, int DIR, int N, int LW, int SB, int NT, int ST = 0>
 __device__ __forceinline__ cplx<R> *fft_lines_ct(cplx<R> *a, cplx<R> *b, int nlines, const cplx<R> *tw) {
   constexpr int P = ct_radix(N, ST);
   if constexpr (P == 0) {
     return a;
+  } else if constexpr (ct_fuse<R, N, ST>(P)) {
+    fft_stage_ct2<R, DIR, P, 3, N, ct_ns(N, ST), LW, SB, NT>(a, b, nlines, tw + ct_twoff(N, ST), tw + ct_twoff(N, ST + 1));
+    __syncthreads();
+    return fft_lines_ct<R, DIR, N, LW, SB, NT, ST + 2>(b, a, nlines, tw);
   } else {
     fft_stage_ct<R, DIR, P, N, ct_ns(N, ST), LW, SB, NT>(a, b, nlines, tw + ct_twoff(N, ST));
     __syncthreads();
