@@ -1823,7 +1823,52 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
     const int half = nz / 2;
     const int p = threadIdx.x % PZ;
     const int mstep = blockDim.x / PZ;
-    if (p < np) {
+    if constexpr (kWalk) {
+      // the unpacking and the C2R's first stage (radix 8, untwiddled) in one pass: its
+      // butterfly j reads z[j + r J] (r < 8, J = N / 8), z[q] = x1 + i x2 of half-spectrum
+      // row q for q <= N / 2 (D) and the mirror of row N - q beyond (M); butterflies u and
+      // J - u read the same rows u + r J and (r + 1) J - u (r < 4), so one thread takes both
+      // (u = 0 and J / 2 alone; rows 0 and N / 2 with their imaginary parts dropped, where D and
+      // M agree).  The outputs go to zb at 8 j + s, as the stage writes them.
+      constexpr int J = N / 8;
+      static_assert(ct_radix(N, 0) == 8, "the first stage is radix 8");
+      auto D = [](float4 q) { return C{q.x - q.w, q.y + q.z}; };
+      auto M = [](float4 q) { return C{q.x + q.w, q.z - q.y}; };
+      if (p < np) {
+        for (int u = threadIdx.x / PZ; u <= J / 2; u += mstep) {
+          float4 ra[4], rb[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            ra[r] = *reinterpret_cast<const float4 *>(spec + (u + r * J) * plane + 2 * p);
+            rb[r] = *reinterpret_cast<const float4 *>(spec + ((r + 1) * J - u) * plane + 2 * p);
+          }
+          issue_psi();
+          if (u == 0) {   // rows 0 and N / 2: the kz = 0 and Nyquist bins are real
+            ra[0].y = ra[0].w = 0.0f;
+            rb[3].y = rb[3].w = 0.0f;
+          }
+          C v[8];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            v[r] = D(ra[r]);
+            v[r + 4] = M(rb[3 - r]);
+          }
+          butterfly<R, +1, 8>(v);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) zb[(8 * u + q) * SB + p] = v[q];
+          if (u > 0 && u < J / 2) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              v[r] = D(rb[r]);
+              v[r + 4] = M(ra[3 - r]);
+            }
+            butterfly<R, +1, 8>(v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) zb[(8 * (J - u) + q) * SB + p] = v[q];
+          }
+        }
+      }
+    } else if (p < np) {
       for (int m0 = threadIdx.x / PZ; m0 < a.nzh; m0 += kUnroll * mstep) {
         C x1[kUnroll], x2[kUnroll];
 #pragma unroll
@@ -1873,8 +1918,11 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
       }
     }
     __syncthreads();
-    res = fft_lines_n<R, +1, N, PZ, SB, Tiles<R>::kZThreads>(za, zb, a.plan[2], np,
-                                                             reinterpret_cast<const C *>(a.tw[2]));
+    if constexpr (kWalk)   // (the first stage done: from zb, at stage 1)
+      res = fft_lines_ct<R, +1, N, PZ, SB, Tiles<R>::kZThreads, 1>(zb, za, np, reinterpret_cast<const C *>(a.tw[2]));
+    else
+      res = fft_lines_n<R, +1, N, PZ, SB, Tiles<R>::kZThreads>(za, zb, a.plan[2], np,
+                                                               reinterpret_cast<const C *>(a.tw[2]));
   }
 
   // the CN-z factor tables (alpha, beta, H, G; 4 * 32 * chunk values), staged into the

@@ -120,7 +120,8 @@ def test_batch_step_counts_and_graph_cache():
 
 
 @pytest.mark.parametrize("mode", [abi.DGPE_IMAG_TIME, abi.DGPE_REAL_TIME])
-@pytest.mark.parametrize("shape", [(24, 20, 32), (32, 48, 20)])   # (the second: short-line sweeps)
+# (the second: short-line sweeps; the last three: K5's compile-time z lengths with the 8-lane z solve)
+@pytest.mark.parametrize("shape", [(24, 20, 32), (32, 48, 20), (20, 24, 64), (24, 20, 96), (16, 20, 128)])
 def test_grouped_members_equal_individual_steps(mode, shape):
     """Same-shaped FP32 members (different physics and states) are stepped as one group, each
     kernel one launch for all of them; a member of another shape and an FP64 member run as
