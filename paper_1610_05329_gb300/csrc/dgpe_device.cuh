@@ -1334,6 +1334,26 @@ __device__ __forceinline__ double half_density(double d) {
   return __longlong_as_double(h);
 }
 
+// The CTA `ahead` positions after this one in launch order (x fastest, then y, then the
+// member z of a grouped launch), for the L2 prefetch of the tile kernels: its tile (x-row
+// i2, j-tile bx2) and its member's arguments (ga + z2 for grouped launches, else a).  False
+// past the end of the grid.
+struct AheadTile {
+  int i2, bx2;
+  const KArgs *b;
+};
+__device__ __forceinline__ bool ahead_tile(const KArgs &a, const KArgs *ga, int ahead, AheadTile &t) {
+  // (32-bit: a grid of these kernels holds far fewer than 2^31 CTAs)
+  const unsigned gx = gridDim.x, gxy = gx * gridDim.y;
+  const unsigned L = (blockIdx.z * gridDim.y + blockIdx.y) * gx + blockIdx.x + (unsigned)ahead;
+  if (ahead <= 0 || L >= gxy * gridDim.z) return false;
+  const unsigned z2 = ga ? L / gxy : 0u, rem = L - z2 * gxy;
+  t.i2 = (int)(rem / gx);
+  t.bx2 = (int)(rem - (unsigned)t.i2 * gx);
+  t.b = ga ? ga + z2 : &a;
+  return true;
+}
+
 // ---------------------------------------------------------------------------------------
 // K1: n = s^2 |psi|^2 of kZLines consecutive z-lines (i, j0..), packed in pairs as the
 // real and imaginary parts of one complex line, forward FFT along z, then the two real
@@ -1342,7 +1362,7 @@ __device__ __forceinline__ double half_density(double d) {
 // the half spectrum m = 0..nz/2 is stored to spec[m][i][j].
 // ---------------------------------------------------------------------------------------
 template <typename R, int N>
-__device__ __forceinline__ void k1_density_r2cz_body(const KArgs &a) {
+__device__ __forceinline__ void k1_density_r2cz_body(const KArgs &a, const KArgs *ga) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int BZ = Tiles<R>::kZLines;
@@ -1378,10 +1398,10 @@ __device__ __forceinline__ void k1_density_r2cz_body(const KArgs &a) {
       // the psi rows of the CTA one resident wave ahead into L2 (residency: the CTAs whose
       // two transform buffers fit the SM's shared memory, at most 6 by registers)
       constexpr int kRes = (228 * 1024) / (2 * N * SB * (int)sizeof(C) + 1024) < 6 ? (228 * 1024) / (2 * N * SB * (int)sizeof(C) + 1024) : 6;
-      const int nbx = gridDim.x, L = blockIdx.y * nbx + blockIdx.x + kRes * a.nsm;
-      if (threadIdx.x == 0 && a.nsm > 0 && L < nbx * (int)gridDim.y) {
-        const int i2 = L / nbx, j2 = (L - i2 * nbx) * BZ;
-        prefetch_l2(reinterpret_cast<const C *>(a.psi) + ((size_t)i2 * a.ny + j2) * nz, min(BZ, a.ny - j2) * nz * (unsigned)sizeof(C));
+      AheadTile t;
+      if (threadIdx.x == 0 && ahead_tile(a, ga, kRes * a.nsm, t)) {
+        const int j2 = t.bx2 * BZ;
+        prefetch_l2(reinterpret_cast<const C *>(t.b->psi) + ((size_t)t.i2 * a.ny + j2) * nz, min(BZ, a.ny - j2) * nz * (unsigned)sizeof(C));
       }
       return;
     }
@@ -1430,8 +1450,8 @@ __device__ __forceinline__ void k1_density_r2cz_body(const KArgs &a) {
 // a group of same-shaped condensates (G = true, the arguments from the device array ga)
 template <typename R, int N, bool G = false>
 __global__ void __launch_bounds__(Tiles<R>::kZThreads) k1_density_r2cz(KArgs a, const KArgs *ga) {
-  if constexpr (G) k1_density_r2cz_body<R, N>(ga[blockIdx.z]);
-  else k1_density_r2cz_body<R, N>(a);
+  if constexpr (G) k1_density_r2cz_body<R, N>(ga[blockIdx.z], ga);
+  else k1_density_r2cz_body<R, N>(a, nullptr);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1716,7 +1736,7 @@ __global__ void __launch_bounds__(8 * RegFft<N>::T, 1024 / (8 * RegFft<N>::T)) k
 // The FP64 phase-only pass runs three CTAs per SM (80 registers and a few spills beat two).
 // ---------------------------------------------------------------------------------------
 template <typename R, typename Coef, int ZM, int N>
-__device__ __forceinline__ void k5_zline_body(const KArgs &a) {
+__device__ __forceinline__ void k5_zline_body(const KArgs &a, const KArgs *ga) {
   constexpr int zmode = ZM;   // one instance per mode: each gets its own register allocation
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1905,16 +1925,16 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
     if constexpr (kWalk) {
       // the rows of tile L + ahead (L the linear CTA index, ahead the CTAs resident at once):
       // that CTA starts about when this one ends and finds its spectrum and psi rows in L2
-      const int ahead = Tiles<R>::kZMinBlocks * a.nsm;
-      const int nbx = gridDim.x, L = blockIdx.y * nbx + blockIdx.x + ahead;
-      if (ahead > 0 && L < nbx * (int)gridDim.y) {
-        const int i2 = L / nbx, j2 = (L - i2 * nbx) * BZ;
+      // (grouped launches: across the members, each from its own buffers)
+      AheadTile t;
+      if (ahead_tile(a, ga, Tiles<R>::kZMinBlocks * a.nsm, t)) {
+        const int j2 = t.bx2 * BZ;
         const int nl2 = min(BZ, a.ny - j2);   // even: 16-byte multiples
-        const size_t l2 = (size_t)i2 * a.ny + j2;
-        const C *sp2 = reinterpret_cast<const C *>(a.spec) + l2;
+        const size_t l2 = (size_t)t.i2 * a.ny + j2;
+        const C *sp2 = reinterpret_cast<const C *>(t.b->spec) + l2;
         for (int m = threadIdx.x; m < a.nzh; m += blockDim.x) prefetch_l2(sp2 + m * plane, nl2 * (unsigned)sizeof(C));
         if (threadIdx.x == blockDim.x - 1)
-          prefetch_l2(reinterpret_cast<const C *>(a.psi) + l2 * nz, nl2 * nz * (unsigned)sizeof(C));
+          prefetch_l2(reinterpret_cast<const C *>(t.b->psi) + l2 * nz, nl2 * nz * (unsigned)sizeof(C));
       }
     }
     __syncthreads();
@@ -2171,8 +2191,8 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a) {
 template <typename R, typename Coef, int ZM, int N, bool G = false>
 __global__ void __launch_bounds__(Tiles<R>::kZThreads,
                                   ZM == kZObs ? 1 : (ZM == kZPhaseOnly && std::is_same<R, double>::value ? 3 : Tiles<R>::kZMinBlocks)) k5_zline(KArgs a, const KArgs *ga) {
-  if constexpr (G) k5_zline_body<R, Coef, ZM, N>(ga[blockIdx.z]);
-  else k5_zline_body<R, Coef, ZM, N>(a);
+  if constexpr (G) k5_zline_body<R, Coef, ZM, N>(ga[blockIdx.z], ga);
+  else k5_zline_body<R, Coef, ZM, N>(a, nullptr);
 }
 
 // ---------------------------------------------------------------------------------------
