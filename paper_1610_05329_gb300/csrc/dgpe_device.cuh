@@ -302,6 +302,12 @@ struct Tiles<float> {
   static constexpr int kCnThreads = 512;  // 16 warps, one line per warp
   static constexpr int kYBudget = 4096;
 };
+// z-lines per K5 tile: 32 for the FP32 compile-time lengths of at most 128 points (twice the
+// points per CTA over its fixed costs, and every warp busy in the 8-lane z solve), else kZLines
+template <typename R>
+__host__ __device__ constexpr int k5_lines(int n) {
+  return std::is_same<R, float>::value && (n == 64 || n == 96 || n == 128) ? 32 : Tiles<R>::kZLines;
+}
 constexpr int kFftThreads = 256;
 constexpr int kUnroll = 8;  // loads in flight per thread in the register-staged load loops
 
@@ -1740,7 +1746,7 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a, const KArgs *ga) {
   constexpr int zmode = ZM;   // one instance per mode: each gets its own register allocation
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int BZ = Tiles<R>::kZLines;
+  constexpr int BZ = k5_lines<R>(N);
   constexpr int PZ = BZ / 2;
   constexpr int SB = PZ;   // unpadded: the butterflies (pair fastest) and the line-fastest phase loop are conflict-free
   const int nz = N > 0 ? N : a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
@@ -2152,12 +2158,15 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a, const KArgs *ga) {
     __syncthreads();
     const Coef c = CnCoef<R, Coef>::make(pick<R>(a.cn_r[2], a.cn_rf[2], a.cn_rl[2]));
     if constexpr (LZ == 8) {
-      // warps 0-3, four lines each: w, w + 8 (one half-warp), w + 4, w + 12 (the other);
-      // at the odd line stride two lines 8 apart fall on distinct banks.  Lines past nl are
-      // solved too (all lanes take part in the scans) and not stored.
-      static_assert(BZ == 16 && Tiles<R>::kZThreads >= 128, "16 lines on four warps");
+      // four lines per warp, two per half-warp 8 apart (at the odd line stride they fall on
+      // distinct banks): 32 lines on the 8 warps (w + 8 g), or 16 on warps 0-3 (w, w + 8, w + 4,
+      // w + 12).  Lines past nl are solved too (all lanes take part in the scans), not stored.
+      static_assert((BZ == 32 || BZ == 16) && Tiles<R>::kZThreads == 256, "32 or 16 lines on 256 threads");
       const int w = threadIdx.x / kWarp, g = (threadIdx.x & (kWarp - 1)) >> 3;
-      if (w < 4) cn_line<R, Coef, CHZ, true, true, 8>(tile + (w + 8 * (g & 1) + 4 * (g >> 1)) * LS, 1, 8 * CHZ, lc, ztab, scan_s, c);
+      if constexpr (BZ == 32)
+        cn_line<R, Coef, CHZ, true, true, 8>(tile + (w + 8 * g) * LS, 1, 8 * CHZ, lc, ztab, scan_s, c);
+      else if (w < 4)
+        cn_line<R, Coef, CHZ, true, true, 8>(tile + (w + 8 * (g & 1) + 4 * (g >> 1)) * LS, 1, 8 * CHZ, lc, ztab, scan_s, c);
     } else {
       for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp) {
         if constexpr (kWalk) cn_line<R, Coef, CHZ, true, true>(tile + b * LS, 1, kWarp * CHZ, lc, ztab, scan_s, c);
@@ -2930,14 +2939,16 @@ struct Impl {
   static constexpr bool kZSplit = Fp64Class<R>::value;
 
   static size_t smem_z_fft(const KArgs &a) { return 2 * (size_t)a.nz * (T::kZLines / 2 + 1) * E; }
-  static size_t smem_k5(const KArgs &a) {
+  // K5's grid and shared memory for tiles of bz lines
+  static dim3 grid_z5(const KArgs &a, int bz) { return dim3((a.ny + bz - 1) / bz, a.nx); }
+  static size_t smem_k5(const KArgs &a, int bz = T::kZLines) {
     // the tile: the sweeps' layout, or (FP32, compile-time lengths) K5's padded one
     int ls = cn_slots(a.nz, a.cn[2].lchunk);
     if (std::is_same<R, float>::value &&
         (a.nz == 64 || a.nz == 96 || a.nz == 128 || a.nz == 256 || a.nz == 384 || a.nz == 512))
       ls = std::max(ls, k5_tile_stride(a.nz));
-    return 2 * (size_t)a.nz * (T::kZLines / 2) * E + (size_t)T::kZLines * ls * E +
-           (size_t)(a.nz + T::kZLines) * sizeof(R) + (size_t)10 * kWarp * E;
+    return 2 * (size_t)a.nz * (bz / 2) * E + (size_t)bz * ls * E + (size_t)(a.nz + bz) * sizeof(R) +
+           (size_t)10 * kWarp * E;
   }
   static size_t smem_y(const KArgs &a) { return 2 * (size_t)a.ny * (a.ylines + 1) * E; }
   static size_t smem_x(const KArgs &a) { return 2 * (size_t)a.nx * T::kXCols * E; }
@@ -3223,16 +3234,24 @@ struct Impl {
   // the default one of a supported length.
   template <int ZM, typename Co>
   static void k5_launch(const KArgs &a, dim3 g, size_t sm, cudaStream_t st) {
+    // (instances of other tile heights, k5_lines, get their own grid and shared memory)
+    auto go = [&](auto len) {
+      constexpr int N = decltype(len)::value;
+      constexpr int bz = k5_lines<R>(N);
+      if constexpr (bz == T::kZLines) k5_zline<R, Co, ZM, N><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      else k5_zline<R, Co, ZM, N><<<grid_z5(a, bz), T::kZThreads, smem_k5(a, bz), st>>>(a, nullptr);
+    };
+    using std::integral_constant;
     if constexpr (kCtSizes) {
-      if (plan_ct(a.plan[2], 512)) k5_zline<R, Co, ZM, 512><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else if (plan_ct(a.plan[2], 384)) k5_zline<R, Co, ZM, 384><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else if (plan_ct(a.plan[2], 256)) k5_zline<R, Co, ZM, 256><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else if (plan_ct(a.plan[2], 128) && (!kShortCt || a.cn8_tab[2])) k5_zline<R, Co, ZM, 128><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else if (kShortCt && plan_ct(a.plan[2], 96) && a.cn8_tab[2]) k5_zline<R, Co, ZM, kShortCt ? 96 : 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else if (kShortCt && plan_ct(a.plan[2], 64) && a.cn8_tab[2]) k5_zline<R, Co, ZM, kShortCt ? 64 : 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else k5_zline<R, Co, ZM, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      if (plan_ct(a.plan[2], 512)) go(integral_constant<int, 512>{});
+      else if (plan_ct(a.plan[2], 384)) go(integral_constant<int, 384>{});
+      else if (plan_ct(a.plan[2], 256)) go(integral_constant<int, 256>{});
+      else if (plan_ct(a.plan[2], 128) && (!kShortCt || a.cn8_tab[2])) go(integral_constant<int, 128>{});
+      else if (kShortCt && plan_ct(a.plan[2], 96) && a.cn8_tab[2]) go(integral_constant<int, kShortCt ? 96 : 0>{});
+      else if (kShortCt && plan_ct(a.plan[2], 64) && a.cn8_tab[2]) go(integral_constant<int, kShortCt ? 64 : 0>{});
+      else go(integral_constant<int, 0>{});
     } else {
-      k5_zline<R, Co, ZM, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      go(integral_constant<int, 0>{});
     }
   }
   // the mode whose compile-time instances exist: the fused step (FP32), or the phase-only
@@ -3499,16 +3518,21 @@ struct GroupLaunch {
   }
   template <typename Co>
   static void k5(const KArgs &a, const KArgs *ga, unsigned n, cudaStream_t st) {
-    dim3 g = I::grid_z(a);
-    g.z = n;
-    const size_t sm = I::smem_k5(a);
-    if (I::plan_ct(a.plan[2], 512)) k5_zline<R, Co, kZStep, 512, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-    else if (I::plan_ct(a.plan[2], 384)) k5_zline<R, Co, kZStep, 384, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-    else if (I::plan_ct(a.plan[2], 256)) k5_zline<R, Co, kZStep, 256, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-    else if (I::plan_ct(a.plan[2], 128) && a.cn8_tab[2]) k5_zline<R, Co, kZStep, 128, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-    else if (I::plan_ct(a.plan[2], 96) && a.cn8_tab[2]) k5_zline<R, Co, kZStep, 96, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-    else if (I::plan_ct(a.plan[2], 64) && a.cn8_tab[2]) k5_zline<R, Co, kZStep, 64, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-    else k5_zline<R, Co, kZStep, 0, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+    auto go = [&](auto len) {
+      constexpr int N = decltype(len)::value;
+      constexpr int bz = k5_lines<R>(N);
+      dim3 g = I::grid_z5(a, bz);
+      g.z = n;
+      k5_zline<R, Co, kZStep, N, true><<<g, T::kZThreads, I::smem_k5(a, bz), st>>>(a, ga);
+    };
+    using std::integral_constant;
+    if (I::plan_ct(a.plan[2], 512)) go(integral_constant<int, 512>{});
+    else if (I::plan_ct(a.plan[2], 384)) go(integral_constant<int, 384>{});
+    else if (I::plan_ct(a.plan[2], 256)) go(integral_constant<int, 256>{});
+    else if (I::plan_ct(a.plan[2], 128) && a.cn8_tab[2]) go(integral_constant<int, 128>{});
+    else if (I::plan_ct(a.plan[2], 96) && a.cn8_tab[2]) go(integral_constant<int, 96>{});
+    else if (I::plan_ct(a.plan[2], 64) && a.cn8_tab[2]) go(integral_constant<int, 64>{});
+    else go(integral_constant<int, 0>{});
   }
   template <typename Co, int AXIS>
   static void cn(const KArgs &a, const KArgs *ga, unsigned n, int reduce, int renorm, cudaStream_t st) {
