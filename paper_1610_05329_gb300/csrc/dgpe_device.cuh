@@ -302,10 +302,11 @@ struct Tiles<float> {
   static constexpr int kCnThreads = 512;  // 16 warps, one line per warp
   static constexpr int kYBudget = 4096;
 };
-// z-lines per K5 tile: 32 for the FP32 compile-time lengths of at most 128 points (twice the
-// points per CTA over its fixed costs, and every warp busy in the 8-lane z solve), else kZLines
+// z-lines per K1 and K5 tile: 32 for the FP32 compile-time lengths of at most 128 points
+// (twice the points per CTA over its fixed costs; in K5 every warp busy in the 8-lane z
+// solve), else kZLines
 template <typename R>
-__host__ __device__ constexpr int k5_lines(int n) {
+__host__ __device__ constexpr int ztile_lines(int n) {
   return std::is_same<R, float>::value && (n == 64 || n == 96 || n == 128) ? 32 : Tiles<R>::kZLines;
 }
 constexpr int kFftThreads = 256;
@@ -1371,7 +1372,7 @@ template <typename R, int N>
 __device__ __forceinline__ void k1_density_r2cz_body(const KArgs &a, const KArgs *ga) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int BZ = Tiles<R>::kZLines;
+  constexpr int BZ = ztile_lines<R>(N);
   constexpr int PZ = BZ / 2;
   constexpr int SB = PZ + 1;
   const int nz = N > 0 ? N : a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
@@ -1388,8 +1389,9 @@ __device__ __forceinline__ void k1_density_r2cz_body(const KArgs &a, const KArgs
     constexpr bool kHalve = decltype(halve)::value;
     if constexpr (N > 0 && !Fp64Class<R>::value) {
       // FP32, compile-time length: thread (line b, offset k0 < W) takes the points k0 + W j of
-      // line b (a line per half-warp: coalesced loads, and the 4-byte stores into the
-      // pair-interleaved buffer (stride SB = 9 pairs) fall on 16 distinct banks per line)
+      // line b (W consecutive points of a line per W lanes: coalesced loads; at W = 16 the
+      // 4-byte stores into the pair-interleaved buffer, stride SB = 9 pairs, fall on 16 distinct
+      // banks per line, at W = 8 (32-line tiles) on two-way shared banks)
       constexpr int W = Tiles<R>::kZThreads / BZ;
       const int b = threadIdx.x / W, k0 = threadIdx.x % W;
       if (b < nl) {
@@ -1746,7 +1748,7 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a, const KArgs *ga) {
   constexpr int zmode = ZM;   // one instance per mode: each gets its own register allocation
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int BZ = k5_lines<R>(N);
+  constexpr int BZ = ztile_lines<R>(N);
   constexpr int PZ = BZ / 2;
   constexpr int SB = PZ;   // unpadded: the butterflies (pair fastest) and the line-fastest phase loop are conflict-free
   const int nz = N > 0 ? N : a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
@@ -2938,7 +2940,7 @@ struct Impl {
   // instructions win over the extra pass through HBM
   static constexpr bool kZSplit = Fp64Class<R>::value;
 
-  static size_t smem_z_fft(const KArgs &a) { return 2 * (size_t)a.nz * (T::kZLines / 2 + 1) * E; }
+  static size_t smem_z_fft(const KArgs &a, int bz = T::kZLines) { return 2 * (size_t)a.nz * (bz / 2 + 1) * E; }
   // K5's grid and shared memory for tiles of bz lines
   static dim3 grid_z5(const KArgs &a, int bz) { return dim3((a.ny + bz - 1) / bz, a.nx); }
   static size_t smem_k5(const KArgs &a, int bz = T::kZLines) {
@@ -3151,18 +3153,23 @@ struct Impl {
     return true;
   }
   static cudaError_t k1(const KArgs &a, cudaStream_t st) {
-    const dim3 g = grid_z(a);
-    const size_t sm = smem_z_fft(a);
+    // (instances of other tile heights, ztile_lines, get their own grid and shared memory)
+    auto go = [&](auto len) {
+      constexpr int N = decltype(len)::value;
+      constexpr int bz = ztile_lines<R>(N);
+      k1_density_r2cz<R, N><<<grid_z5(a, bz), T::kZThreads, smem_z_fft(a, bz), st>>>(a, nullptr);
+    };
+    using std::integral_constant;
     if constexpr (kCtSizes) {
-      if (plan_ct(a.plan[2], 512)) k1_density_r2cz<R, 512><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else if (plan_ct(a.plan[2], 384)) k1_density_r2cz<R, 384><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else if (plan_ct(a.plan[2], 256)) k1_density_r2cz<R, 256><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else if (plan_ct(a.plan[2], 128)) k1_density_r2cz<R, 128><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else if (kShortCt && plan_ct(a.plan[2], 96)) k1_density_r2cz<R, kShortCt ? 96 : 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else if (kShortCt && plan_ct(a.plan[2], 64)) k1_density_r2cz<R, kShortCt ? 64 : 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
-      else k1_density_r2cz<R, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      if (plan_ct(a.plan[2], 512)) go(integral_constant<int, 512>{});
+      else if (plan_ct(a.plan[2], 384)) go(integral_constant<int, 384>{});
+      else if (plan_ct(a.plan[2], 256)) go(integral_constant<int, 256>{});
+      else if (plan_ct(a.plan[2], 128)) go(integral_constant<int, 128>{});
+      else if (kShortCt && plan_ct(a.plan[2], 96)) go(integral_constant<int, kShortCt ? 96 : 0>{});
+      else if (kShortCt && plan_ct(a.plan[2], 64)) go(integral_constant<int, kShortCt ? 64 : 0>{});
+      else go(integral_constant<int, 0>{});
     } else {
-      k1_density_r2cz<R, 0><<<g, T::kZThreads, sm, st>>>(a, nullptr);
+      go(integral_constant<int, 0>{});
     }
     return cudaGetLastError();
   }
@@ -3234,10 +3241,10 @@ struct Impl {
   // the default one of a supported length.
   template <int ZM, typename Co>
   static void k5_launch(const KArgs &a, dim3 g, size_t sm, cudaStream_t st) {
-    // (instances of other tile heights, k5_lines, get their own grid and shared memory)
+    // (instances of other tile heights, ztile_lines, get their own grid and shared memory)
     auto go = [&](auto len) {
       constexpr int N = decltype(len)::value;
-      constexpr int bz = k5_lines<R>(N);
+      constexpr int bz = ztile_lines<R>(N);
       if constexpr (bz == T::kZLines) k5_zline<R, Co, ZM, N><<<g, T::kZThreads, sm, st>>>(a, nullptr);
       else k5_zline<R, Co, ZM, N><<<grid_z5(a, bz), T::kZThreads, smem_k5(a, bz), st>>>(a, nullptr);
     };
@@ -3520,7 +3527,7 @@ struct GroupLaunch {
   static void k5(const KArgs &a, const KArgs *ga, unsigned n, cudaStream_t st) {
     auto go = [&](auto len) {
       constexpr int N = decltype(len)::value;
-      constexpr int bz = k5_lines<R>(N);
+      constexpr int bz = ztile_lines<R>(N);
       dim3 g = I::grid_z5(a, bz);
       g.z = n;
       k5_zline<R, Co, kZStep, N, true><<<g, T::kZThreads, I::smem_k5(a, bz), st>>>(a, ga);
@@ -3552,16 +3559,21 @@ struct GroupLaunch {
     if (count < 1 || count > 65535) return cudaErrorInvalidValue;
     const unsigned n = (unsigned)count;
     {
-      dim3 g = I::grid_z(a);
-      g.z = n;
-      const size_t sm = I::smem_z_fft(a);
-      if (I::plan_ct(a.plan[2], 512)) k1_density_r2cz<R, 512, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-      else if (I::plan_ct(a.plan[2], 384)) k1_density_r2cz<R, 384, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-      else if (I::plan_ct(a.plan[2], 256)) k1_density_r2cz<R, 256, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-      else if (I::plan_ct(a.plan[2], 128)) k1_density_r2cz<R, 128, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-      else if (I::plan_ct(a.plan[2], 96)) k1_density_r2cz<R, 96, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-      else if (I::plan_ct(a.plan[2], 64)) k1_density_r2cz<R, 64, true><<<g, T::kZThreads, sm, st>>>(a, ga);
-      else k1_density_r2cz<R, 0, true><<<g, T::kZThreads, sm, st>>>(a, ga);
+      auto go = [&](auto len) {
+        constexpr int N = decltype(len)::value;
+        constexpr int bz = ztile_lines<R>(N);
+        dim3 g = I::grid_z5(a, bz);
+        g.z = n;
+        k1_density_r2cz<R, N, true><<<g, T::kZThreads, I::smem_z_fft(a, bz), st>>>(a, ga);
+      };
+      using std::integral_constant;
+      if (I::plan_ct(a.plan[2], 512)) go(integral_constant<int, 512>{});
+      else if (I::plan_ct(a.plan[2], 384)) go(integral_constant<int, 384>{});
+      else if (I::plan_ct(a.plan[2], 256)) go(integral_constant<int, 256>{});
+      else if (I::plan_ct(a.plan[2], 128)) go(integral_constant<int, 128>{});
+      else if (I::plan_ct(a.plan[2], 96)) go(integral_constant<int, 96>{});
+      else if (I::plan_ct(a.plan[2], 64)) go(integral_constant<int, 64>{});
+      else go(integral_constant<int, 0>{});
     }
     ffty<-1>(a, ga, n, st);
     k3(a, ga, n, st);
