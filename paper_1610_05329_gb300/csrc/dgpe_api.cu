@@ -124,7 +124,7 @@ int check_physics(const dgpe_params *p) {
 }
 
 struct Layout {
-  size_t state, partials, tw[3], cn[3], cn_adj[3], cnz, cn8[3], dtv[3], psi, spec, utab, ybuf, total;
+  size_t state, partials, tw[3], cn[3], cn_adj[3], cnz, cn8[3], cn8_adj[2], dtv[3], psi, spec, utab, ybuf, total;
 };
 
 // FP32 contexts whose compile-time K5 (nz = 128, 256, 384, 512) solves along z at a chunk
@@ -166,6 +166,13 @@ Layout layout_of(const dgpe_params *p, const KernelSet *ks, int max_blocks) {
     L.cn8[d] = 0;
     if (p->precision == DGPE_MIXED && (d < 2 ? short_cn_chunk(n[d]) != 0 : k5_short_z(n[d]))) {
       L.cn8[d] = off;
+      off += align_up((size_t)(4 * 8 * short_cn_chunk(n[d]) + 49) * e);
+    }
+  }
+  for (int d = 0; d < 2; ++d) {   // the same for dt -> -dt (the adjoint x and y sweeps)
+    L.cn8_adj[d] = 0;
+    if (L.cn8[d]) {
+      L.cn8_adj[d] = off;
       off += align_up((size_t)(4 * 8 * short_cn_chunk(n[d]) + 49) * e);
     }
   }
@@ -461,6 +468,8 @@ int setup_tables(dgpe_ctx *c, bool cn_changed, bool ut_changed) {
     if (p->mode == DGPE_REAL_TIME)   // the adjoint sweep is the sweep with dt -> -dt
       jobs.job[jobs.n++] = {at(c, c->L.cn_adj[d]), c->args.cn[d].m, c->args.cn[d].chunk, -c->args.cn_r[d], kWarp};
     if (c->L.cn8[d]) jobs.job[jobs.n++] = {at(c, c->L.cn8[d]), c->args.cn[d].m, n[d] / 8, c->args.cn_r[d], 8};
+    if (d < 2 && c->L.cn8_adj[d] && p->mode == DGPE_REAL_TIME)
+      jobs.job[jobs.n++] = {at(c, c->L.cn8_adj[d]), c->args.cn[d].m, n[d] / 8, -c->args.cn_r[d], 8};
   }
   if (cn_changed && c->L.cnz)
     jobs.job[jobs.n++] = {at(c, c->L.cnz), c->args.cn[2].m, k5_chunk(p->nz), c->args.cn_r[2], kWarp};
@@ -492,7 +501,9 @@ KArgs adjoint_sweep_args(dgpe_ctx *c, void *gbar) {
   a.psi = gbar;
   for (int d = 0; d < 3; ++d) {
     a.cn[d].tab = at(c, c->L.cn_adj[d]);
-    a.cn8_tab[d] = nullptr;   // (the adjoint sweeps take the 32-lane solver)
+    // the adjoint x and y sweeps of short lines on their own 8-lane tables; K5's z solve does
+    // not run in the adjoint step
+    a.cn8_tab[d] = d < 2 && c->L.cn8_adj[d] ? at(c, c->L.cn8_adj[d]) : nullptr;
     a.cn_r[d] = -a.cn_r[d];
     a.cn_rf[d] = -a.cn_rf[d];
     a.cn_rl[d] = -a.cn_rl[d];

@@ -35,7 +35,7 @@ struct CnJob {
   double r;    // dt / (4 h^2), negated for the adjoint tables
   int lanes;   // lanes per line of the layout: 32, or 8 (the short-line sweeps)
 };
-constexpr int kMaxCnJobs = 10;
+constexpr int kMaxCnJobs = 12;
 
 // FP32 sweeps of short lines: n = 8 CH points (CH = 4, 6, 8, 12 or 16) are solved on 8 lanes
 // per line, CH points each; 0 where the line takes the 32-lane solver.
