@@ -958,6 +958,76 @@ __device__ __forceinline__ void cn_line(cplx<R> *__restrict__ buf, int es, int m
   }
 }
 
+// Two lines of the same factor tables (and the same padded length, FULL) solved by one warp
+// in lockstep: each table and scan-factor value is read from shared memory once for both
+// lines, and the two recurrences interleave.  The arithmetic of each line is cn_line's.
+template <typename R, typename Coef, int CH>
+__device__ __forceinline__ void cn_line2(cplx<R> *__restrict__ b1, cplx<R> *__restrict__ b2, int es,
+                                         const Coef *__restrict__ tab, const Coef *__restrict__ scan_s, Coef c) {
+  const int t = threadIdx.x & (kWarp - 1);
+  constexpr int mp = kWarp * CH;
+  const Coef *alpha = tab + t, *beta = tab + mp + t, *H = tab + 2 * mp + t, *G = tab + 3 * mp + t;
+  const Coef *scan = scan_s + t;
+  cplx<R> y1[CH], y2[CH];
+  cplx<R> a1 = czero<R>(), a2 = czero<R>();
+#pragma unroll
+  for (int e = 0; e < CH; ++e) {
+    const Coef al = alpha[e * kWarp];
+    const int q = (t * CH + e + 1 + t) * es;
+    a1 = cfma(al, a1, b1[q]);
+    a2 = cfma(al, a2, b2[q]);
+    y1[e] = a1;
+    y2[e] = a2;
+  }
+  cplx<R> B1 = a1, B2 = a2;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const Coef f = scan[k * kWarp];
+    const cplx<R> p1 = shfl_up(B1, 1 << k), p2 = shfl_up(B2, 1 << k);
+    if (t >= (1 << k)) {
+      B1 = cfma(f, p1, B1);
+      B2 = cfma(f, p2, B2);
+    }
+  }
+  cplx<R> Y1 = shfl_up(B1, 1), Y2 = shfl_up(B2, 1);
+  if (t == 0) Y1 = Y2 = czero<R>();
+  a1 = a2 = czero<R>();
+#pragma unroll
+  for (int e = CH - 1; e >= 0; --e) {
+    const Coef be = beta[e * kWarp];
+    a1 = mul(be, cfma_c(c, a1, y1[e]));
+    a2 = mul(be, cfma_c(c, a2, y2[e]));
+    y1[e] = a1;
+    y2[e] = a2;
+  }
+  const Coef h0 = H[0];
+  cplx<R> C1 = cfma(h0, Y1, a1), C2 = cfma(h0, Y2, a2);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const Coef f = scan[(5 + k) * kWarp];
+    const cplx<R> n1 = shfl_down(C1, 1 << k), n2 = shfl_down(C2, 1 << k);
+    if (t + (1 << k) < kWarp) {
+      C1 = cfma(f, n1, C1);
+      C2 = cfma(f, n2, C2);
+    }
+  }
+  cplx<R> X1 = shfl_down(C1, 1), X2 = shfl_down(C2, 1);
+  if (t == kWarp - 1) X1 = X2 = czero<R>();
+#pragma unroll
+  for (int e = 0; e < CH; ++e) {
+    const Coef h = H[e * kWarp], g = G[e * kWarp];
+    const int q = (t * CH + e + 1 + t) * es;
+    const cplx<R> chi1 = cfma(h, Y1, cfma(g, X1, y1[e])), chi2 = cfma(h, Y2, cfma(g, X2, y2[e]));
+    const cplx<R> v1 = b1[q], v2 = b2[q];
+    b1[q] = {twice_minus(chi1.re, v1.re), twice_minus(chi1.im, v1.im)};
+    b2[q] = {twice_minus(chi2.re, v2.re), twice_minus(chi2.im, v2.im)};
+  }
+  if (t == 0) {
+    b1[0] = czero<R>();
+    b2[0] = czero<R>();
+  }
+}
+
 // cn_line with the chunk length as a compile-time constant (every unrolled iteration live).
 template <typename R, typename Coef, bool SHARED_TAB, bool FULL = false>
 __device__ __forceinline__ void cn_line_any(cplx<R> *__restrict__ buf, int es, int m, int lchunk,
@@ -2169,6 +2239,12 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a, const KArgs *ga) {
         cn_line<R, Coef, CHZ, true, true, 8>(tile + (w + 8 * g) * LS, 1, 8 * CHZ, lc, ztab, scan_s, c);
       else if (w < 4)
         cn_line<R, Coef, CHZ, true, true, 8>(tile + (w + 8 * (g & 1) + 4 * (g >> 1)) * LS, 1, 8 * CHZ, lc, ztab, scan_s, c);
+    } else if constexpr (kWalk && BZ == 2 * (Tiles<R>::kZThreads / kWarp) && CHZ <= 12) {
+      // two lines per warp in lockstep (w and w + BZ / 2): each table value read once for
+      // both (chunks up to 12 points: at 16 the two lines' values no longer fit the registers).
+      // Lines past nl are solved too (their padding is zero), not stored.
+      const int w = threadIdx.x / kWarp;
+      cn_line2<R, Coef, CHZ>(tile + w * LS, tile + (w + BZ / 2) * LS, 1, ztab, scan_s, c);
     } else {
       for (int b = threadIdx.x / kWarp; b < nl; b += blockDim.x / kWarp) {
         if constexpr (kWalk) cn_line<R, Coef, CHZ, true, true>(tile + b * LS, 1, kWarp * CHZ, lc, ztab, scan_s, c);
