@@ -1039,6 +1039,17 @@ __device__ __forceinline__ void cn_line_any(cplx<R> *__restrict__ buf, int es, i
     default: cn_line<R, Coef, 16, SHARED_TAB, FULL>(buf, es, m, lchunk, tab, scan_s, c); break;
   }
 }
+// cn_line2 (two lines in lockstep, padded to 32 whole chunks) at the chunk 2^lchunk
+template <typename R, typename Coef>
+__device__ __forceinline__ void cn_line2_any(cplx<R> *b1, cplx<R> *b2, int es, int lchunk, const Coef *tab,
+                                             const Coef *scan_s, Coef c) {
+  switch (lchunk) {
+    case 1: cn_line2<R, Coef, 2>(b1, b2, es, tab, scan_s, c); break;
+    case 2: cn_line2<R, Coef, 4>(b1, b2, es, tab, scan_s, c); break;
+    case 3: cn_line2<R, Coef, 8>(b1, b2, es, tab, scan_s, c); break;
+    default: cn_line2<R, Coef, 16>(b1, b2, es, tab, scan_s, c); break;
+  }
+}
 
 template <typename R, typename Coef>
 struct CnCoef;
@@ -2427,8 +2438,15 @@ __device__ __forceinline__ void k_cn_body(const KArgs &a, int reduce, int renorm
     int fixed, k0;
     const size_t base = tile_origin(tile, fixed, k0);
     const int nb = min(B, a.nz - k0);
-    for (int l = threadIdx.x / kWarp; l < nb; l += blockDim.x / kWarp)
-      cn_line_any<R, Coef, true, FULL>(cur + l, SB, FULL ? m_pad : a.cn[AXIS].m, lc, tab, tab + 4 * (kWarp << lc), c);
+    if constexpr (FULL && NT == 8 * kWarp && B == 16) {
+      // 8 warps, two columns each in lockstep (w, w + 8): each table value read once for both;
+      // columns past nb are solved too (their padding is zero) and not stored
+      const int w = threadIdx.x / kWarp;
+      cn_line2_any<R, Coef>(cur + w, cur + w + 8, SB, lc, tab, tab + 4 * (kWarp << lc), c);
+    } else {
+      for (int l = threadIdx.x / kWarp; l < nb; l += blockDim.x / kWarp)
+        cn_line_any<R, Coef, true, FULL>(cur + l, SB, FULL ? m_pad : a.cn[AXIS].m, lc, tab, tab + 4 * (kWarp << lc), c);
+    }
     __syncthreads();
     if (b < nb) {
       DFAcc s0;   // this thread's share of the column: sum W_x n
@@ -2467,7 +2485,7 @@ __device__ __forceinline__ void k_cn_body(const KArgs &a, int reduce, int renorm
 // a group of same-shaped condensates (G = true, the arguments from the device array ga)
 template <typename R, typename Coef, int AXIS, int B = Tiles<R>::kCnCols, int NT = Tiles<R>::kCnThreads, bool G = false,
           bool FULL = false>
-__global__ void __launch_bounds__(NT, 512 / NT) k_cn(KArgs a, const KArgs *ga, int reduce, int renorm) {
+__global__ void __launch_bounds__(NT, (FULL && NT == 256) ? 1 : 512 / NT) k_cn(KArgs a, const KArgs *ga, int reduce, int renorm) {
   if constexpr (G) k_cn_body<R, Coef, AXIS, B, NT, FULL>(ga[blockIdx.z], reduce, renorm);
   else k_cn_body<R, Coef, AXIS, B, NT, FULL>(a, reduce, renorm);
 }
@@ -3009,6 +3027,11 @@ struct Impl {
   static constexpr bool kCtSizes = !std::is_same<R, df>::value;
   // FP32 also at nz = 96 and 64 (K1, K5; the batched small grids)
   static constexpr bool kShortCt = std::is_same<R, float>::value;
+  // the padded (FULL) chunked sweeps: the y sweep on 8 warps, two columns each in lockstep
+  // (one CTA per SM); the x sweep, whose store also takes the norm sums (a longer serial chain
+  // per thread at half the threads), on 16 warps of one column each
+  template <int AXIS>
+  static constexpr int cn_full_threads() { return AXIS == 1 ? 256 : T::kCnThreads; }
   // the FP64-class sweeps run a Thomas solve per line on two threads (k_cn_twisted), the
   // FP32 ones the chunked solver in persistent tiles (k_cn)
   static constexpr bool kCnThread = Fp64Class<R>::value;
@@ -3157,10 +3180,10 @@ struct Impl {
       chk(allow_smem(k_cn<R, R, 1>));
       chk(allow_smem(k_cn<R, C, 0>));
       chk(allow_smem(k_cn<R, C, 1>));
-      chk(allow_smem(k_cn<R, R, 0, B, NT, false, true>));
-      chk(allow_smem(k_cn<R, R, 1, B, NT, false, true>));
-      chk(allow_smem(k_cn<R, C, 0, B, NT, false, true>));
-      chk(allow_smem(k_cn<R, C, 1, B, NT, false, true>));
+      chk(allow_smem(k_cn<R, R, 0, B, cn_full_threads<0>(), false, true>));
+      chk(allow_smem(k_cn<R, R, 1, B, cn_full_threads<1>(), false, true>));
+      chk(allow_smem(k_cn<R, C, 0, B, cn_full_threads<0>(), false, true>));
+      chk(allow_smem(k_cn<R, C, 1, B, cn_full_threads<1>(), false, true>));
     }
     if constexpr (kRegFft) chk(init_reg());
     if constexpr (kAdjoint) chk(allow_smem(k5_adj_phase<R>));
@@ -3422,8 +3445,9 @@ struct Impl {
       const size_t sm = smem_cn(cn_len(a, AXIS), a.cn[AXIS].lchunk);
       const dim3 g = grid_cn(a, AXIS);
       if (cn_full(a, AXIS)) {
-        if (a.imag) k_cn<R, R, AXIS, B, NT, false, true><<<g, NT, sm, st>>>(a, nullptr, reduce, renorm);
-        else k_cn<R, C, AXIS, B, NT, false, true><<<g, NT, sm, st>>>(a, nullptr, reduce, renorm);
+        constexpr int NF = cn_full_threads<AXIS>();
+        if (a.imag) k_cn<R, R, AXIS, B, NF, false, true><<<g, NF, sm, st>>>(a, nullptr, reduce, renorm);
+        else k_cn<R, C, AXIS, B, NF, false, true><<<g, NF, sm, st>>>(a, nullptr, reduce, renorm);
       } else {
         if (a.imag) k_cn<R, R, AXIS><<<g, NT, sm, st>>>(a, nullptr, reduce, renorm);
         else k_cn<R, C, AXIS><<<g, NT, sm, st>>>(a, nullptr, reduce, renorm);
@@ -3560,10 +3584,10 @@ struct GroupLaunch {
     attr(k_cn<R, R, 1, T::kCnCols, T::kCnThreads, true>, e);
     attr(k_cn<R, C, 0, T::kCnCols, T::kCnThreads, true>, e);
     attr(k_cn<R, C, 1, T::kCnCols, T::kCnThreads, true>, e);
-    attr(k_cn<R, R, 0, T::kCnCols, T::kCnThreads, true, true>, e);
-    attr(k_cn<R, R, 1, T::kCnCols, T::kCnThreads, true, true>, e);
-    attr(k_cn<R, C, 0, T::kCnCols, T::kCnThreads, true, true>, e);
-    attr(k_cn<R, C, 1, T::kCnCols, T::kCnThreads, true, true>, e);
+    attr(k_cn<R, R, 0, T::kCnCols, I::template cn_full_threads<0>(), true, true>, e);
+    attr(k_cn<R, R, 1, T::kCnCols, I::template cn_full_threads<1>(), true, true>, e);
+    attr(k_cn<R, C, 0, T::kCnCols, I::template cn_full_threads<0>(), true, true>, e);
+    attr(k_cn<R, C, 1, T::kCnCols, I::template cn_full_threads<1>(), true, true>, e);
     return e;
   }
 
@@ -3627,7 +3651,7 @@ struct GroupLaunch {
     g.z = n;
     const size_t sm = I::smem_cn(I::cn_len(a, AXIS), a.cn[AXIS].lchunk);
     if (I::cn_full(a, AXIS))
-      k_cn<R, Co, AXIS, T::kCnCols, T::kCnThreads, true, true><<<g, T::kCnThreads, sm, st>>>(a, ga, reduce, renorm);
+      k_cn<R, Co, AXIS, T::kCnCols, I::template cn_full_threads<AXIS>(), true, true><<<g, I::template cn_full_threads<AXIS>(), sm, st>>>(a, ga, reduce, renorm);
     else
       k_cn<R, Co, AXIS, T::kCnCols, T::kCnThreads, true><<<g, T::kCnThreads, sm, st>>>(a, ga, reduce, renorm);
   }
