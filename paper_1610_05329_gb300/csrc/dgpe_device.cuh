@@ -2079,55 +2079,129 @@ __device__ __forceinline__ void k5_zline_body(const KArgs &a, const KArgs *ga) {
     const R ihx2 = R(1.0 / (a.hx * a.hx)), ihy2 = R(1.0 / (a.hy * a.hy)), ihz2 = R(1.0 / (a.hz * a.hz));
     const C *gpsi = reinterpret_cast<const C *>(a.psi);
     const size_t sx = (size_t)a.ny * nz;
-    LinePos pos(threadIdx.x, nz, blockDim.x);
-    for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
-      const int b = pos.b, n = pos.k;
-      const int j = j0 + b;
-      const C *row = tile + b * LS;
-      const C c = scale(row[cn_slot(n, lc)], sr);
-      const C zm = n > 0 ? scale(row[cn_slot(n - 1, lc)], sr) : czero<R>();
-      const C zp = n < nz - 1 ? scale(row[cn_slot(n + 1, lc)], sr) : czero<R>();
-      const size_t q = (line0 + b) * nz + n;
-      const C ym = j > 0 ? scale(gpsi[q - nz], sr) : czero<R>();
-      const C yp = j < a.ny - 1 ? scale(gpsi[q + nz], sr) : czero<R>();
-      const C xm = i > 0 ? scale(gpsi[q - sx], sr) : czero<R>();
-      const C xp = i < a.nx - 1 ? scale(gpsi[q + sx], sr) : czero<R>();
-      double ekin;
-      if (!a.kinetic5) {
-        const C lap = {(xm.re - R(2) * c.re + xp.re) * ihx2 + (ym.re - R(2) * c.re + yp.re) * ihy2 +
-                           (zm.re - R(2) * c.re + zp.re) * ihz2,
-                       (xm.im - R(2) * c.im + xp.im) * ihx2 + (ym.im - R(2) * c.im + yp.im) * ihy2 +
-                           (zm.im - R(2) * c.im + zp.im) * ihz2};
-        ekin = -0.5 * ((double)c.re * (double)lap.re + (double)c.im * (double)lap.im);
-      } else {
-        // 4th-order first derivatives (f(-2) - 8 f(-1) + 8 f(1) - f(2)) / (12 h), zero outside
-        const C zm2 = n > 1 ? scale(row[cn_slot(n - 2, lc)], sr) : czero<R>();
-        const C zp2 = n < nz - 2 ? scale(row[cn_slot(n + 2, lc)], sr) : czero<R>();
-        const C ym2 = j > 1 ? scale(gpsi[q - 2 * nz], sr) : czero<R>();
-        const C yp2 = j < a.ny - 2 ? scale(gpsi[q + 2 * nz], sr) : czero<R>();
-        const C xm2 = i > 1 ? scale(gpsi[q - 2 * sx], sr) : czero<R>();
-        const C xp2 = i < a.nx - 2 ? scale(gpsi[q + 2 * sx], sr) : czero<R>();
-        auto d1 = [](C m2, C m1, C p1, C p2, double h) {
-          const double f = 1.0 / (12.0 * h);
-          const double re = ((double)m2.re - 8.0 * (double)m1.re + 8.0 * (double)p1.re - (double)p2.re) * f;
-          const double im = ((double)m2.im - 8.0 * (double)m1.im + 8.0 * (double)p1.im - (double)p2.im) * f;
-          return re * re + im * im;
-        };
-        ekin = 0.5 * (d1(xm2, xm, xp, xp2, a.hx) + d1(ym2, ym, yp, yp2, a.hy) + d1(zm2, zm, zp, zp2, a.hz));
+    if constexpr (std::is_same<R, float>::value) {
+      // FP32 data: each per-point term in FP32 (the state's precision); the weights exact small
+      // integers (3 x the Simpson weights per axis) and the squared coordinates exact integers
+      // (the signed index squared), every product by them exact (FMA exact product) and every
+      // sum in double-float per thread, as the x sweep's norm; h^2, (1/3)^3 and the physical
+      // factors applied in FP64 to the thread's totals.  The trap term needs no sum of its own:
+      // sum w V n = vx sum w x^2 n + vy sum w y^2 n + vz sum w z^2 n.  (FP64 work per point
+      // would bound this pass on GB300's FP64 pipe.)
+      DFAcc t[7];   // n, the kinetic term, n^2, Phi n, i'^2 n, j'^2 n, k'^2 n
+      const int wx = quad_weight3(i, a.nx, a.simpson), ii = i - a.nx / 2;
+      LinePos pos(threadIdx.x, nz, blockDim.x);
+      for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
+        const int b = pos.b, n = pos.k;
+        const int j = j0 + b;
+        const int W = wx * quad_weight3(j, a.ny, a.simpson) * quad_weight3(n, nz, a.simpson);
+        if (W == 0) continue;
+        const C *row = tile + b * LS;
+        const C c = row[cn_slot(n, lc)];
+        const C zm = n > 0 ? row[cn_slot(n - 1, lc)] : czero<R>();
+        const C zp = n < nz - 1 ? row[cn_slot(n + 1, lc)] : czero<R>();
+        const size_t q = (line0 + b) * nz + n;
+        const C ym = j > 0 ? gpsi[q - nz] : czero<R>();
+        const C yp = j < a.ny - 1 ? gpsi[q + nz] : czero<R>();
+        const C xm = i > 0 ? gpsi[q - sx] : czero<R>();
+        const C xp = i < a.nx - 1 ? gpsi[q + sx] : czero<R>();
+        float kin;   // c . Lap c (the kinetic energy is -1/2 its sum), or |grad c|^2 (+1/2)
+        if (!a.kinetic5) {
+          const float lre = (xm.re - 2.0f * c.re + xp.re) * ihx2 + (ym.re - 2.0f * c.re + yp.re) * ihy2 +
+                            (zm.re - 2.0f * c.re + zp.re) * ihz2;
+          const float lim = (xm.im - 2.0f * c.im + xp.im) * ihx2 + (ym.im - 2.0f * c.im + yp.im) * ihy2 +
+                            (zm.im - 2.0f * c.im + zp.im) * ihz2;
+          kin = fmaf(c.re, lre, c.im * lim);
+        } else {
+          // 4th-order first derivatives (f(-2) - 8 f(-1) + 8 f(1) - f(2)) / (12 h), zero outside
+          const C zm2 = n > 1 ? row[cn_slot(n - 2, lc)] : czero<R>();
+          const C zp2 = n < nz - 2 ? row[cn_slot(n + 2, lc)] : czero<R>();
+          const C ym2 = j > 1 ? gpsi[q - 2 * nz] : czero<R>();
+          const C yp2 = j < a.ny - 2 ? gpsi[q + 2 * nz] : czero<R>();
+          const C xm2 = i > 1 ? gpsi[q - 2 * sx] : czero<R>();
+          const C xp2 = i < a.nx - 2 ? gpsi[q + 2 * sx] : czero<R>();
+          auto d1 = [](C m2, C m1, C p1, C p2, float f) {
+            const float re = (m2.re - 8.0f * m1.re + 8.0f * p1.re - p2.re) * f;
+            const float im = (m2.im - 8.0f * m1.im + 8.0f * p1.im - p2.im) * f;
+            return fmaf(re, re, im * im);
+          };
+          kin = d1(xm2, xm, xp, xp2, float(1.0 / (12.0 * a.hx))) + d1(ym2, ym, yp, yp2, float(1.0 / (12.0 * a.hy))) +
+                d1(zm2, zm, zp, zp2, float(1.0 / (12.0 * a.hz)));
+        }
+        const C z = res[n * SB + (b >> 1)];
+        const float phi = ((b & 1) ? z.im : z.re) * inv_ntot;
+        const float d = fmaf(c.re, c.re, c.im * c.im);
+        const int jj = j - a.ny / 2, kk = n - nz / 2;
+        const float wf = (float)W;
+        t[0].add_prod(wf, d);
+        t[1].add_prod(wf, kin);
+        t[2].add_prod(wf, d * d);
+        t[3].add_prod(wf, phi * d);
+        t[4].add_prod((float)(ii * ii * W), d);   // <= 256^2 x 64 = 2^22: exact
+        t[5].add_prod((float)(jj * jj * W), d);
+        t[6].add_prod((float)(kk * kk * W), d);
       }
-      const C z = res[n * SB + (b >> 1)];
-      const double phi = (double)(((b & 1) ? z.im : z.re) * inv_ntot);
-      const double dens = (double)c.re * (double)c.re + (double)c.im * (double)c.im;
-      const double y = coordinate(j, a.ny, a.hy), zc = coordinate(n, nz, a.hz);
-      const double w = wxi * quad_weight(j, a.ny, a.simpson) * quad_weight(n, nz, a.simpson);
-      v[0] += w * dens;
-      v[1] += w * ekin;
-      v[2] += w * (a.vx * x * x + a.vy * y * y + a.vz * zc * zc) * dens;
-      v[3] += w * a.g * dens * dens;
-      v[4] += w * a.gdd * phi * dens;
-      v[5] += w * x * x * dens;
-      v[6] += w * y * y * dens;
-      v[7] += w * zc * zc * dens;
+      const double ws = a.simpson ? 1.0 / 27.0 : 1.0;
+      const double X = t[4].value() * ws * a.hx * a.hx, Y = t[5].value() * ws * a.hy * a.hy,
+                   Z = t[6].value() * ws * a.hz * a.hz;
+      v[0] = t[0].value() * ws;
+      v[1] = (a.kinetic5 ? 0.5 : -0.5) * t[1].value() * ws;
+      v[2] = a.vx * X + a.vy * Y + a.vz * Z;
+      v[3] = a.g * t[2].value() * ws;
+      v[4] = a.gdd * t[3].value() * ws;
+      v[5] = X;
+      v[6] = Y;
+      v[7] = Z;
+    } else {
+      LinePos pos(threadIdx.x, nz, blockDim.x);
+      for (int e = threadIdx.x; e < nl * nz; e += blockDim.x, pos.next()) {
+        const int b = pos.b, n = pos.k;
+        const int j = j0 + b;
+        const C *row = tile + b * LS;
+        const C c = scale(row[cn_slot(n, lc)], sr);
+        const C zm = n > 0 ? scale(row[cn_slot(n - 1, lc)], sr) : czero<R>();
+        const C zp = n < nz - 1 ? scale(row[cn_slot(n + 1, lc)], sr) : czero<R>();
+        const size_t q = (line0 + b) * nz + n;
+        const C ym = j > 0 ? scale(gpsi[q - nz], sr) : czero<R>();
+        const C yp = j < a.ny - 1 ? scale(gpsi[q + nz], sr) : czero<R>();
+        const C xm = i > 0 ? scale(gpsi[q - sx], sr) : czero<R>();
+        const C xp = i < a.nx - 1 ? scale(gpsi[q + sx], sr) : czero<R>();
+        double ekin;
+        if (!a.kinetic5) {
+          const C lap = {(xm.re - R(2) * c.re + xp.re) * ihx2 + (ym.re - R(2) * c.re + yp.re) * ihy2 +
+                             (zm.re - R(2) * c.re + zp.re) * ihz2,
+                         (xm.im - R(2) * c.im + xp.im) * ihx2 + (ym.im - R(2) * c.im + yp.im) * ihy2 +
+                             (zm.im - R(2) * c.im + zp.im) * ihz2};
+          ekin = -0.5 * ((double)c.re * (double)lap.re + (double)c.im * (double)lap.im);
+        } else {
+          // 4th-order first derivatives (f(-2) - 8 f(-1) + 8 f(1) - f(2)) / (12 h), zero outside
+          const C zm2 = n > 1 ? scale(row[cn_slot(n - 2, lc)], sr) : czero<R>();
+          const C zp2 = n < nz - 2 ? scale(row[cn_slot(n + 2, lc)], sr) : czero<R>();
+          const C ym2 = j > 1 ? scale(gpsi[q - 2 * nz], sr) : czero<R>();
+          const C yp2 = j < a.ny - 2 ? scale(gpsi[q + 2 * nz], sr) : czero<R>();
+          const C xm2 = i > 1 ? scale(gpsi[q - 2 * sx], sr) : czero<R>();
+          const C xp2 = i < a.nx - 2 ? scale(gpsi[q + 2 * sx], sr) : czero<R>();
+          auto d1 = [](C m2, C m1, C p1, C p2, double h) {
+            const double f = 1.0 / (12.0 * h);
+            const double re = ((double)m2.re - 8.0 * (double)m1.re + 8.0 * (double)p1.re - (double)p2.re) * f;
+            const double im = ((double)m2.im - 8.0 * (double)m1.im + 8.0 * (double)p1.im - (double)p2.im) * f;
+            return re * re + im * im;
+          };
+          ekin = 0.5 * (d1(xm2, xm, xp, xp2, a.hx) + d1(ym2, ym, yp, yp2, a.hy) + d1(zm2, zm, zp, zp2, a.hz));
+        }
+        const C z = res[n * SB + (b >> 1)];
+        const double phi = (double)(((b & 1) ? z.im : z.re) * inv_ntot);
+        const double dens = (double)c.re * (double)c.re + (double)c.im * (double)c.im;
+        const double y = coordinate(j, a.ny, a.hy), zc = coordinate(n, nz, a.hz);
+        const double w = wxi * quad_weight(j, a.ny, a.simpson) * quad_weight(n, nz, a.simpson);
+        v[0] += w * dens;
+        v[1] += w * ekin;
+        v[2] += w * (a.vx * x * x + a.vy * y * y + a.vz * zc * zc) * dens;
+        v[3] += w * a.g * dens * dens;
+        v[4] += w * a.gdd * phi * dens;
+        v[5] += w * x * x * dens;
+        v[6] += w * y * y * dens;
+        v[7] += w * zc * zc * dens;
+      }
     }
     if (reduce_across_blocks<8>(v, a.partials, &a.state->ticket) && threadIdx.x == 0) {
       const double dv = a.hx * a.hy * a.hz;
