@@ -61,8 +61,8 @@ extern "C" {
 #define DGPE_IMAG_TIME 1
 
 #define DGPE_FP64 0   /* complex128 psi; FFT, phase and CN in FP64 */
-/* complex64 psi; FFT, phase and CN in FP32; the norm sums FP64-class (FP32 terms, exact weights,
- * double-float sums per point, FP64 across blocks), mu/E sums in FP64.  In real time every
+/* complex64 psi; FFT, phase and CN in FP32; the norm and the observables' sums FP64-class
+ * (FP32 terms, exact weights, double-float sums per point, FP64 across blocks).  In real time every
  * step restores the norm the real-time run began with (the norm of the state its first step
  * started from), undoing the drift of the FP32-rounded Crank-Nicolson factors (about 3e-7
  * of the norm per step, systematic); the exact scheme conserves the norm, so this corrects
