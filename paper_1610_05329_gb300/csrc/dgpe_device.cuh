@@ -2942,14 +2942,15 @@ __device__ __forceinline__ void store_half_spectrum_column(const KArgs &a, const
   }
 }
 
-template <typename R>
+// N > 0: the compile-time transforms of that length (FP32, the default z plan)
+template <typename R, int N = 0>
 __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_phase(KArgs a) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int BZ = Tiles<R>::kZLines;
   constexpr int PZ = BZ / 2;
   constexpr int SB = PZ + 1;
-  const int nz = a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
+  const int nz = N > 0 ? N : a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
   const int nl = min(BZ, a.ny - j0), np = nl >> 1;
   C *za = reinterpret_cast<C *>(smem_raw);
   C *zb = za + nz * SB;
@@ -2976,7 +2977,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_phase(KArgs a) {
   if (threadIdx.x < nl) txy[threadIdx.x] = dtv_x[i] + dtv_y[j0 + threadIdx.x];
   load_half_spectrum_column<R>(a, za, i, j0, np);
   __syncthreads();
-  C *res = fft_lines<R, +1>(za, zb, a.plan[2], PZ, np, SB, reinterpret_cast<const C *>(a.tw[2]));
+  C *res = fft_lines_n<R, +1, N, PZ, SB, Tiles<R>::kZThreads>(za, zb, a.plan[2], np, reinterpret_cast<const C *>(a.tw[2]));
   C *sbuf = (res == za) ? zb : za;
   cp_async_wait_all();
   __syncthreads();
@@ -3001,7 +3002,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_phase(KArgs a) {
     acc.add(sv * dens, sv * phi * inv_ntot, sv * z2[n]);
   }
   __syncthreads();
-  const C *res2 = fft_lines<R, -1>(sbuf, res, a.plan[2], PZ, np, SB, reinterpret_cast<const C *>(a.tw[2]));
+  const C *res2 = fft_lines_n<R, -1, N, PZ, SB, Tiles<R>::kZThreads>(sbuf, res, a.plan[2], np, reinterpret_cast<const C *>(a.tw[2]));
   store_half_spectrum_column<R>(a, res2, i, j0, np);
   for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) gb[e] = gt[e];
   double v3[3] = {acc.get(0), acc.get(1), acc.get(2)};
@@ -3013,14 +3014,14 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_phase(KArgs a) {
   }
 }
 
-template <typename R>
+template <typename R, int N = 0>
 __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_combine(KArgs a) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int BZ = Tiles<R>::kZLines;
   constexpr int PZ = BZ / 2;
   constexpr int SB = PZ + 1;
-  const int nz = a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
+  const int nz = N > 0 ? N : a.nz, i = blockIdx.y, j0 = blockIdx.x * BZ;
   const int nl = min(BZ, a.ny - j0), np = nl >> 1;
   C *za = reinterpret_cast<C *>(smem_raw);
   C *zb = za + nz * SB;
@@ -3035,7 +3036,7 @@ __global__ void __launch_bounds__(Tiles<R>::kZThreads) k5_adj_combine(KArgs a) {
   }
   load_half_spectrum_column<R>(a, za, i, j0, np);
   __syncthreads();
-  const C *res = fft_lines<R, +1>(za, zb, a.plan[2], PZ, np, SB, reinterpret_cast<const C *>(a.tw[2]));
+  const C *res = fft_lines_n<R, +1, N, PZ, SB, Tiles<R>::kZThreads>(za, zb, a.plan[2], np, reinterpret_cast<const C *>(a.tw[2]));
   cp_async_wait_all();
   __syncthreads();
   const R dtg = pick<R>(a.dtg, a.dtg_f, a.dtg_l), dtgdd = pick<R>(a.dtgdd_n, a.dtgdd_n_f, a.dtgdd_n_l);
@@ -3262,6 +3263,16 @@ struct Impl {
     if constexpr (kRegFft) chk(init_reg());
     if constexpr (kAdjoint) chk(allow_smem(k5_adj_phase<R>));
     if constexpr (kAdjoint) chk(allow_smem(k5_adj_combine<R>));
+    if constexpr (kAdjoint && kShortCt) {
+      chk(allow_smem(k5_adj_phase<R, 128>));
+      chk(allow_smem(k5_adj_phase<R, 256>));
+      chk(allow_smem(k5_adj_phase<R, 384>));
+      chk(allow_smem(k5_adj_phase<R, 512>));
+      chk(allow_smem(k5_adj_combine<R, 128>));
+      chk(allow_smem(k5_adj_combine<R, 256>));
+      chk(allow_smem(k5_adj_combine<R, 384>));
+      chk(allow_smem(k5_adj_combine<R, 512>));
+    }
     return e;
   }
 
@@ -3539,6 +3550,24 @@ struct Impl {
     return cudaGetLastError();
   }
   // Host-only bound (no device query): the CN grid never exceeds its tile count.
+  // the adjoint's phase (PHASE) or combining pass, at a compile-time length where the z plan
+  // is the default one (FP32)
+  template <bool PHASE>
+  static void adj_launch(const KArgs &a, cudaStream_t st) {
+    auto go = [&](auto len) {
+      constexpr int N = decltype(len)::value;
+      if constexpr (PHASE) k5_adj_phase<R, N><<<grid_z(a), T::kZThreads, smem_adj(a), st>>>(a);
+      else k5_adj_combine<R, N><<<grid_z(a), T::kZThreads, smem_adj(a), st>>>(a);
+    };
+    using std::integral_constant;
+    if constexpr (kShortCt) {
+      if (plan_ct(a.plan[2], 512)) return go(integral_constant<int, 512>{});
+      if (plan_ct(a.plan[2], 384)) return go(integral_constant<int, 384>{});
+      if (plan_ct(a.plan[2], 256)) return go(integral_constant<int, 256>{});
+      if (plan_ct(a.plan[2], 128)) return go(integral_constant<int, 128>{});
+    }
+    go(integral_constant<int, 0>{});
+  }
   static size_t smem_adj(const KArgs &a) {
     return smem_z_fft(a) + 2 * (size_t)T::kZLines * a.nz * E + (size_t)(2 * a.nz + T::kZLines) * sizeof(R);
   }
@@ -3548,7 +3577,7 @@ struct Impl {
     if constexpr (!kAdjoint) {
       return cudaErrorNotSupported;
     } else {
-      k5_adj_phase<R><<<grid_z(a), T::kZThreads, smem_adj(a), st>>>(a);
+      adj_launch<true>(a, st);
       return cudaGetLastError();
     }
   }
@@ -3556,7 +3585,7 @@ struct Impl {
     if constexpr (!kAdjoint) {
       return cudaErrorNotSupported;
     } else {
-      k5_adj_combine<R><<<grid_z(a), T::kZThreads, smem_adj(a), st>>>(a);
+      adj_launch<false>(a, st);
       return cudaGetLastError();
     }
   }

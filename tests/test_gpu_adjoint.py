@@ -86,7 +86,8 @@ def test_gpu_gradient_by_central_differences():
         assert dnu[s] == pytest.approx(fd, rel=2e-6, abs=1e-10)
 
 
-@pytest.mark.parametrize("shape", [(24, 24, 24), (32, 48, 24)])   # (the second: short-line x and y sweeps)
+# (the second: short-line x and y sweeps; the third: the adjoint's compile-time z transforms)
+@pytest.mark.parametrize("shape", [(24, 24, 24), (32, 48, 24), (16, 20, 128)])
 def test_mixed_precision_gradient_vs_fp64(shape):
     h, dt = 0.4, 0.01
     nu_z = np.array([0.9, 1.1, 1.0])
